@@ -1,0 +1,111 @@
+"""Pins for the oracle's quadrature tables against exact moments.
+
+Every rule is checked against integrals computed here in exact rational
+arithmetic (monomials on the reference simplex: i! j! / (i+j+2)!; on [0,1]:
+1/(k+1) and -1/(k+1)^2), not against the generator's own equations.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+
+def simplex_moment(i, j):
+    return Fraction(math.factorial(i) * math.factorial(j), math.factorial(i + j + 2))
+
+
+def max_moment_error(x, y, w, degree):
+    err = 0.0
+    for n in range(degree + 1):
+        for i in range(n + 1):
+            j = n - i
+            q = float(np.sum(w * x ** i * y ** j))
+            err = max(err, abs(q - float(simplex_moment(i, j))))
+    return err
+
+
+@pytest.mark.parametrize("name,n,degree", [("far16", 16, 8), ("far19", 19, 9), ("near49", 49, 12)])
+def test_triangle_rule_exact(tables, name, n, degree):
+    r = tables[name]
+    x, y, w = r["x"], r["y"], r["w"]
+    assert len(w) == n and r["degree"] == degree
+    assert max_moment_error(x, y, w, degree) < 2e-16 * 8
+    # positive weights, interior nodes (paper's X-G rules are positive-interior)
+    assert np.all(w > 0)
+    assert np.all(x > 0) and np.all(y > 0) and np.all(x + y < 1)
+    # the rule is not exact one degree higher (it is a genuine degree-d rule)
+    assert max_moment_error(x, y, w, degree + 1) > 1e-10
+
+
+@pytest.mark.parametrize("name", ["far16", "far19"])
+def test_far_rule_symmetric(tables, name):
+    r = tables[name]
+    pts = np.c_[1 - r["x"] - r["y"], r["x"], r["y"]]
+    key = lambda b, w: (tuple(np.round(np.sort(b), 12)), round(w, 14))
+    base = sorted(key(b, w) for b, w in zip(pts, r["w"]))
+    for perm in [(1, 2, 0), (0, 2, 1)]:
+        moved = sorted(key(b[list(perm)], w) for b, w in zip(pts, r["w"]))
+        assert moved == base
+
+
+@pytest.mark.parametrize("name,n", [("gl16", 16), ("gl7", 7)])
+def test_gauss_legendre(tables, name, n):
+    x, w = tables[name]["x"], tables[name]["w"]
+    for k in range(2 * n):
+        assert abs(np.sum(w * x ** k) - 1.0 / (k + 1)) < 4e-16
+
+
+def test_ggq8(tables):
+    """Eight nodes integrate r P_7 and r log r P_7 on [0,1] (Section 3.4)."""
+    r, w = tables["ggq8"]["r"], tables["ggq8"]["w"]
+    assert len(r) == 8 and np.all((r > 0) & (r < 1)) and np.all(w > 0)
+    for k in range(8):
+        assert abs(np.sum(w * r ** k) - 1.0 / (k + 2)) < 4e-16
+        assert abs(np.sum(w * r ** k * np.log(r)) + 1.0 / (k + 2) ** 2) < 4e-16
+    # a Gauss-Legendre rule of the same length cannot do the log family
+    g = np.polynomial.legendre.leggauss(8)
+    gx, gw = (g[0] + 1) / 2, g[1] / 2
+    assert abs(np.sum(gw * gx * np.log(gx)) + 0.25) > 1e-6
+
+
+def test_what(tables):
+    """w of Eq. rho0: largest weight among the ceil((N+1)/2) nodes closest to
+    an edge, max over edges (reading of the '~n/2 nodes' passage)."""
+    for name in ["far16", "far19", "near49"]:
+        r = tables[name]
+        k = (r["degree"] + 2) // 2
+        dists = [r["y"], r["x"], (1 - r["x"] - r["y"]) / np.sqrt(2)]
+        best = 0.0
+        for d in dists:
+            order = np.lexsort((np.arange(len(d)), d))[:k]
+            best = max(best, r["w"][order].max())
+        assert r["what"] == best
+        assert r["what"] <= r["w"].max() and 10 * r["what"] >= r["w"].max()
+
+
+def test_oracle_basis_orthonormal(tables):
+    """The oracle's P_4 basis is orthonormal on the reference simplex (degree
+    8 products, integrated exactly by the degree-12 rule) and spans P_4."""
+    from oracle.oracle import Oracle
+    o = Oracle("far19", tables=tables)
+    nr = tables["near49"]
+    K = o.basis(nr["x"], nr["y"])
+    Gm = (K * nr["w"][:, None]).T @ K
+    assert np.abs(Gm - np.eye(15)).max() < 1e-13
+    # spans P_4: every monomial of degree <= 4 is reproduced by its projection
+    for n in range(5):
+        for i in range(n + 1):
+            mono = nr["x"] ** i * nr["y"] ** (n - i)
+            c = K.T @ (nr["w"] * mono)
+            assert np.abs(K @ c - mono).max() < 1e-12
+
+
+def test_far_rule_projection_exact(tables):
+    """The discrete L2 projection with the far rule has an identity Gram
+    matrix (rule degree >= 8 = 2*4), so it reproduces P_4 exactly."""
+    from oracle.oracle import Oracle
+    o = Oracle("far19", tables=tables)
+    fr = tables["far19"]
+    K = o.basis(fr["x"], fr["y"])
+    assert np.abs((K * fr["w"][:, None]).T @ K - np.eye(15)).max() < 1e-13
