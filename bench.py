@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Throughput of the volume-potential hot path on one GB300 (or N replicas).
+
+Workload (the configuration the headline metric is quoted on): graded star
+domain r(t) = 1 + 0.3 cos 5t, 16,384 triangles, 19-node degree-9 rule
+(311,296 nodes), targets = all nodes + 10,000 random interior points,
+density = sum of 4 seeded Gaussians.  All inputs are synthetic and seeded.
+
+One step = one pass of the whole hot path over that input, device-resident:
+mesh upload (nodes and weights), near-field build (point location, lists,
+near and self correction weights) and one potential evaluation (far sum +
+corrections) in the requested precision.  value = targets evaluated per
+second (one target-eval = one (target, density) output).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64] [--impl vp|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "star5_16384tri_19pt_targets_nodes_plus_10k_gauss4"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--impl", choices=["vp", "reference"], default="vp")
+    ap.add_argument("--ntri", type=int, default=16384)
+    ap.add_argument("--extra", type=int, default=10000)
+    ap.add_argument("--no-oracle-check", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi samples (every 200 ms) during the timed region."""
+
+    def __init__(self, index: int):
+        self.path = tempfile.mktemp(prefix="vpclk", suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ inputs
+def make_inputs(ntri, m_extra):
+    from paper_2205_04401_gb300 import inputs
+    mesh, f, extra = inputs.config2(n_tri=ntri, m_extra=m_extra)
+    return mesh, f, extra
+
+
+def oracle_baseline(mesh, fun, extra, budget_s=12.0, seed=1):
+    """Time the FP64 CPU oracle (as it stands) on a bounded sample of targets."""
+    from oracle.oracle import Oracle
+    o = Oracle("far19")
+    s = o.setup(mesh.vxy, mesh.tri, node_targets=True, extra=extra)
+    f = fun(s["yxy"])[None, :]
+    M = len(s["txy"])
+    rng = np.random.default_rng(seed)
+    n = 32
+    t0 = time.perf_counter()
+    o.potential(s, f, targets=rng.choice(M, n, replace=False))
+    dt = time.perf_counter() - t0
+    n2 = int(max(32, min(M, n * budget_s / max(dt, 1e-3))))
+    sample = np.sort(rng.choice(M, n2, replace=False))
+    t0 = time.perf_counter()
+    u, _ = o.potential(s, f, targets=sample)
+    dt = time.perf_counter() - t0
+    return dict(value=n2 / dt, seconds=dt, targets=n2, s=s, f=f, sample=sample, u=u)
+
+
+# --------------------------------------------------------------- reference
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    mesh, fun, extra = make_inputs(args.ntri, args.extra)
+    vals = []
+    for _ in range(args.warmup):
+        oracle_baseline(mesh, fun, extra, budget_s=2.0)
+    t_all = 0.0
+    info = None
+    for k in range(args.steps):
+        info = oracle_baseline(mesh, fun, extra, budget_s=8.0, seed=10 + k)
+        vals.append(info["value"])
+        t_all += info["seconds"]
+    v = float(np.mean(vals))
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": "target_evals_per_s", "value": v, "unit": "target-evals/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "targets": int(len(info["s"]["txy"])), "densities": 1},
+        "cpu_baseline": {"value": v, "unit": "target-evals/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{info['targets']} random targets of the workload per step (far sum over all "
+                                   f"311,296 nodes, lists, near/self weights), OpenMP over targets"},
+        "e2e": {"value": v, "unit": "target-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------- main arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2205_04401_gb300 import vp
+    prec = vp.VP_MIXED if args.precision == "mixed" else vp.VP_FP64
+
+    mesh, fun, extra = make_inputs(args.ntri, args.extra)
+    ctx = vp.Context(local)
+    stream = torch.cuda.current_stream()
+    vxy_d = torch.from_numpy(mesh.vxy).to(dev)
+    tri_d = torch.from_numpy(mesh.tri).to(dev)
+    extra_d = torch.from_numpy(extra).to(dev)
+    # density at the nodes (an input: evaluated once from the node coordinates)
+    m0 = vp.mesh_upload_dev(ctx, vxy_d, tri_d, vp.VP_RULE_19_D9)
+    y0, _ = vp.mesh_nodes(m0)
+    f_np = fun(y0.cpu().numpy())[None, :]
+    m0.release()
+    f_d = torch.from_numpy(f_np).to(dev)
+    N = mesh.nt * 19
+    M = N + len(extra)
+    u_d = torch.empty((1, M), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        mh = vp.mesh_upload_dev(ctx, vxy_d, tri_d, vp.VP_RULE_19_D9)
+        nf = vp.nearfield_build(ctx, mh, node_targets=True, txy=extra_d)
+        vp.potential_eval(ctx, nf, f_d, precision=prec, out=u_d)
+        return mh, nf
+
+    for _ in range(max(args.warmup, 0)):
+        mh, nf = step()
+        torch.cuda.synchronize()
+        nf.release()
+        mh.release()
+
+    vp.profile_enable(ctx, True)
+    vp.profile_reset(ctx)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stats = None
+    for k in range(args.steps):
+        flush.fill_(float(k))                      # evict L2 between steps (outside the timed events)
+        ev0[k].record(stream)
+        mh, nf = step()
+        ev1[k].record(stream)
+        torch.cuda.synchronize()
+        stats = vp.nf_stats(nf)
+        nf.release()
+        mh.release()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = vp.profile_read(ctx)
+    vp.profile_enable(ctx, False)
+    t_steps = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    t_total = sum(t_steps)
+    tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    t_total = float(tt.item())
+    value = world * args.steps * M / (t_total / 1e3)
+
+    # resident evaluation (weights cached, serving mode) and FP64 comparison
+    mh = vp.mesh_upload_dev(ctx, vxy_d, tri_d, vp.VP_RULE_19_D9)
+    nf = vp.nearfield_build(ctx, mh, node_targets=True, txy=extra_d)
+    u_mixed = vp.potential_eval(ctx, nf, f_d, precision=vp.VP_MIXED)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = 3
+    for _ in range(reps):
+        vp.potential_eval(ctx, nf, f_d, precision=vp.VP_MIXED, out=u_mixed)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    resident_ms = e0.elapsed_time(e1) / reps
+    fp64_ms = None
+    rel_mixed_vs_fp64 = None
+    u64 = None
+    if not args.no_fp64:
+        e0.record(stream)
+        u64 = vp.potential_eval(ctx, nf, f_d, precision=vp.VP_FP64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = e0.elapsed_time(e1)
+        rel_mixed_vs_fp64 = float((u_mixed - u64).abs().max() / u64.abs().max())
+
+    # end to end through the host-buffer API: host mesh/targets/density in, host u out
+    f_pin = torch.from_numpy(f_np).pin_memory()
+    x_pin = torch.from_numpy(extra).pin_memory()
+    u_host = np.empty((1, M))
+    e2e_t = []
+    for k in range(args.steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mh2 = vp.mesh_upload(ctx, mesh.vxy, mesh.tri, vp.VP_RULE_19_D9)
+        xd = x_pin.to(dev, non_blocking=True)
+        nf2 = vp.nearfield_build(ctx, mh2, node_targets=True, txy=xd)
+        vp.potential_eval_host(ctx, nf2, f_pin.numpy(), precision=prec, out=u_host)
+        t1 = time.perf_counter()
+        nf2.release()
+        mh2.release()
+        if k > 0:
+            e2e_t.append(t1 - t0)
+    e2e_value = world * M / float(np.mean(e2e_t))
+    h2d = mesh.vxy.nbytes + mesh.tri.nbytes + extra.nbytes + f_np.nbytes
+    d2h = u_host.nbytes
+
+    # accuracy against the oracle on sampled targets, and the CPU baseline
+    cpu = None
+    rel_oracle = None
+    if rank == 0 and not args.no_oracle_check:
+        ob = oracle_baseline(mesh, fun, extra, budget_s=10.0)
+        um = u_mixed.cpu().numpy()[0, ob["sample"]]
+        rel_oracle = float(np.abs(um - ob["u"][0]).max() / np.abs(ob["u"][0]).max())
+        cpu = {"value": ob["value"], "unit": "target-evals/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{ob['targets']} random targets of the workload (far sum over all nodes, lists, "
+                         f"near/self weights), OpenMP over targets, {ob['seconds']:.1f} s"}
+
+    # roofline of the dominant stage (device time per launch from the library's CUDA events)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    dfma_peak = 1.186e12        # measured FP64 FMA throughput on this GB300 (flop/s), profiles/peaks_gb300.md
+    fp32_inst_peak = 73.71e12 / 2   # measured FFMA flop/s / 2 = FP32-pipe instructions/s
+    nq = 19
+    work = {
+        "weights_near": ("alu", stats["near_leaves"] * 49 * 150.0 * args.steps, dfma_peak / 1e12, "FP64 TFLOP/s"),
+        "weights_self": ("alu", stats["self_panels"] * 128 * 150.0 * args.steps, dfma_peak / 1e12, "FP64 TFLOP/s"),
+        "far_ff": ("alu", float(M) * N * 75.0 * args.steps, fp32_inst_peak / 1e12, "FP32 Tinst/s"),
+        "far_fp64": ("alu", float(M) * N * 80.0 * args.steps, dfma_peak / 1e12, "FP64 TFLOP/s"),
+        "apply_fp64": ("hbm", float(stats["n_pairs"] * (8 * nq + 4) + N * 8 + M * 8 + M * 8 * 2) * args.steps,
+                       hbm, "GB/s"),
+    }
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dname, (dn, dms) = dom
+    roof = None
+    if dname in work and dn > 0:
+        bound, units, peak, unit = work[dname]
+        scale = 1e9 if unit == "GB/s" else 1e12
+        achieved = units / (dms / 1e3) / scale
+        roof = {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "launches": dn, "ms_per_launch": dms / dn}
+    stage_share = {k: round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4) for k, v in prof.items() if v[0]}
+
+    if rank == 0:
+        line = {
+            "metric": "target_evals_per_s", "value": value, "unit": "target-evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32x2+f64" if prec == vp.VP_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "targets": M, "nodes": N, "densities": 1, "precision": args.precision,
+                       "step": "mesh_upload+nearfield_build+potential_eval", "l2": "256 MiB flush between steps",
+                       "parallelism": f"replicas{world}"},
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": "target-evals/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": None,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "accuracy": {"rel_err_mixed_vs_oracle_sampled": rel_oracle, "rel_err_mixed_vs_fp64_gpu": rel_mixed_vs_fp64},
+            "resident_eval": {"mixed_ms": resident_ms, "fp64_ms": fp64_ms,
+                              "mixed_target_evals_per_s": M / (resident_ms / 1e3),
+                              "fp64_target_evals_per_s": (M / (fp64_ms / 1e3)) if fp64_ms else None,
+                              "mixed_pairs_per_s": M * N / (resident_ms / 1e3)},
+            "nf_stats": {k: stats[k] for k in ("n_pairs", "n_self", "n_near", "near_leaves", "self_panels",
+                                               "depth_capped", "build_ms")},
+            "stage_ms": {k: round(v[1] / max(1, args.steps), 3) for k, v in prof.items() if v[0]},
+            "stage_share": stage_share,
+        }
+        line["gpu_launches"] = int(sum(v[0] for v in prof.values()))
+        print(json.dumps(line))
+    nf.release()
+    mh.release()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * vp.h - C ABI of libvp: the 2-D Poisson volume potential over a triangle
+ * mesh on one NVIDIA GB300 (sm_103a), after Shen & Serkh, "Accelerating
+ * potential evaluation over unstructured meshes in two dimensions"
+ * (arXiv 2205.04401).
+ *
+ *     u(x) = int_Omega G(x, y) f(y) dA_y,     G(x, y) = (1/2pi) log|x - y|     (Eq. 1.1)
+ *
+ * evaluated by the subtract-and-add scheme of Section 3.6: a far sum over
+ * every quadrature node as a point charge, corrected for the (target,
+ * triangle) pairs whose near field (Section 4.1) or interior (Section 3.4)
+ * holds the target.
+ *
+ * General conventions
+ *  - Every function returns a vp_status (0 = VP_OK, negative = error) unless
+ *    stated otherwise.  No function aborts, throws or exits; on error the
+ *    output handles are left NULL and nothing is leaked.
+ *  - "host" pointers are ordinary CPU memory and are read (or written) during
+ *    the call only.  "device" pointers are CUDA global memory on the context's
+ *    device, owned by the caller; they must stay valid until the given stream
+ *    reaches the work that uses them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued asynchronously on it unless stated otherwise.
+ *  - Handles (vp_ctx, vp_mesh, vp_nf) own their device memory until released.
+ *    A vp_mesh / vp_nf must be released before the vp_ctx that made it.
+ *  - Sizes are int64_t element counts; coordinates are interleaved (x, y)
+ *    float64 pairs.
+ */
+#ifndef VP_H
+#define VP_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VP_API __attribute__((visibility("default")))
+#else
+#define VP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vp_ctx vp_ctx;
+typedef struct vp_mesh vp_mesh;
+typedef struct vp_nf vp_nf;
+
+typedef enum vp_status {
+    VP_OK = 0,
+    VP_ERR_INVALID_ARG = -1,     /* a NULL, negative or inconsistent argument */
+    VP_ERR_DEGENERATE_TRI = -2,  /* a triangle with zero area (after CCW normalisation) */
+    VP_ERR_NONFINITE = -3,       /* a NaN or Inf coordinate */
+    VP_ERR_OOM = -4,             /* device allocation failed */
+    VP_ERR_CUDA = -5,            /* any other CUDA runtime error (see vp_last_error) */
+    VP_ERR_TIMEOUT = -6,         /* a bounded device wait ran out */
+    VP_ERR_NO_DEVICE = -7,       /* no usable sm_103 device */
+    VP_ERR_STATE = -8            /* handle used with the wrong context or after release */
+} vp_status;
+
+/* Far-field quadrature rules on the reference simplex (Section 3.2).  Both
+ * are S3-symmetric positive-interior rules derived from their moment
+ * equations: 16 nodes exact to degree 8, 19 nodes exact to degree 9. */
+typedef enum vp_rule { VP_RULE_16_D8 = 16, VP_RULE_19_D9 = 19 } vp_rule;
+
+/* Arithmetic of vp_potential_eval.  VP_FP64: FP64 everywhere.  VP_MIXED: the
+ * far sum in compensated FP32 (float-float coordinates and logarithm, FP64
+ * per-tile reduction); correction weights and their application stay FP64. */
+typedef enum vp_precision { VP_FP64 = 0, VP_MIXED = 1 } vp_precision;
+
+/* Parameters of the near-field characterisation and correction weights. */
+typedef struct vp_nf_params {
+    double eps;        /* tolerance of Eq. (precise_far) for the un-normalised log kernel, |f| <= 1;
+                          default 1e-12, accepted range [1e-15, 1e-2] */
+    double c_far;      /* C_N of Eq. (rho0) for the far rule; 1 gives the provable superset E' */
+    double c_near;     /* C_N for the degree-12 near rule (Table "C_N values": C_12 = 12) */
+    int32_t depth_cap; /* maximum subdivision depth of Section 3.3; leaves at the cap are counted */
+    int32_t reserved;
+} vp_nf_params;
+
+/* Counters of Section 5 (c, s_n, s_l) and sizes of a near-field build. */
+typedef struct vp_nf_stats_t {
+    int64_t n_targets;      /* M */
+    int64_t n_nodes;        /* N = n_tri * nq */
+    int64_t n_pairs;        /* P = number of (target, triangle) corrections */
+    int64_t n_self;         /* pairs with the target inside the triangle */
+    int64_t n_near;         /* pairs with the target in the triangle's near field */
+    int64_t near_leaves;    /* sum over near pairs of leaf sub-triangles (s_n * M) */
+    int64_t self_panels;    /* sum over self pairs of arc-length panels (s_l * M) */
+    int64_t depth_capped;   /* leaves stopped by depth_cap rather than the stop test */
+    int64_t outside;        /* targets in no triangle */
+    int64_t bytes_device;   /* device bytes held by the vp_nf */
+    double build_ms;        /* wall time of vp_nearfield_build */
+} vp_nf_stats_t;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` (must be compute capability 10.3).
+ * Allocates small constant tables.  *out receives the handle. */
+VP_API int vp_create(vp_ctx** out, int device);
+
+/* Release the context.  NULL is ignored. */
+VP_API void vp_destroy(vp_ctx* ctx);
+
+/* Human-readable name of a status code (static storage). */
+VP_API const char* vp_status_str(int status);
+
+/* Copy the last error message of this context into buf (always
+ * NUL-terminated, truncated to len).  Returns VP_OK. */
+VP_API int vp_last_error(const vp_ctx* ctx, char* buf, int32_t len);
+
+/* ------------------------------------------------------------------ mesh */
+
+/* Upload a straight-sided triangle mesh and build its quadrature nodes
+ * (Theorem 3.1 with the affine map rho_T(xi, eta) = A + xi (B - A) + eta (C - A)):
+ *   node j = T*nq + k at rho_T(xi_k, eta_k), weight W_j = w_k * J_T,
+ *   J_T = (B - A) x (C - A) = 2 area(T) > 0.
+ * vxy:  host, [nv][2] float64 vertex coordinates.
+ * tri:  host, [nt][3] int32 vertex indices; clockwise triangles are made
+ *       counter-clockwise by swapping their 2nd and 3rd vertex.
+ * rule: VP_RULE_16_D8 or VP_RULE_19_D9.
+ * Errors: INVALID_ARG (index out of range, nt < 1), NONFINITE, DEGENERATE_TRI.
+ * The call synchronises `stream` before returning (it validates on device). */
+VP_API int vp_mesh_upload(vp_ctx* ctx, const double* vxy, int64_t nv, const int32_t* tri, int64_t nt, int32_t rule,
+                   void* stream, vp_mesh** out);
+
+/* Same as vp_mesh_upload with DEVICE inputs: vxy_dev [nv][2] float64 and
+ * tri_dev [nt][3] int32 in the context's device memory (validated on the
+ * device: bad indices, non-finite or degenerate input give the same codes). */
+VP_API int vp_mesh_upload_dev(vp_ctx* ctx, const double* vxy_dev, int64_t nv, const int32_t* tri_dev, int64_t nt,
+                              int32_t rule, void* stream, vp_mesh** out);
+
+/* Sizes of a mesh: triangles, nodes N = nt * nq, nodes per triangle nq. */
+VP_API int vp_mesh_info(const vp_mesh* mesh, int64_t* n_tri, int64_t* n_nodes, int32_t* nq);
+
+/* Copy node coordinates (device [N][2]) and node weights W (device [N]) into
+ * caller buffers; either pointer may be NULL.  Density values are given at
+ * these nodes, in this order (triangle-major: j = T*nq + k). */
+VP_API int vp_mesh_nodes(const vp_mesh* mesh, double* yxy_dev, double* w_dev, void* stream);
+
+/* Release a mesh.  NULL is ignored. */
+VP_API void vp_mesh_release(vp_mesh* mesh);
+
+/* ------------------------------------------------------------ near field */
+
+/* Targets are the mesh nodes (if node_targets != 0), followed by m extra
+ * points txy_dev (device [m][2] float64, may be NULL when m == 0).
+ *
+ * Builds, for every target x, the triangle S(x) containing it (Appendix A.5:
+ * the lowest-index triangle whose three orientation tests are >= 0; a node's
+ * own triangle for node targets) and N(x), the triangles T != S(x) whose
+ * near field E_T holds x (Section 4.1, Eqs. rho0 / threeE): x lies in the open
+ * Bernstein ellipse of some edge PQ of T with parameter
+ *     rho0 = (w J_T / (eps C_N))^(1/N),
+ * tested exactly as rho_x^N < w J_T / (eps C_N) with
+ *     s = (|x-P| + |x-Q|) / |Q-P|,  rho_x = s + sqrt(max(s^2 - 1, 0)),
+ * rho_x^N a left-to-right product, all in FP64 without fused multiply-add.
+ * Then computes, per (x, T) pair, the nq correction weights
+ *     C_k = w_k sum_a K_a(xi_k) m_a - [k != own(x)] W_k G(x, y_k),
+ *     m_a = int_T G(x, y) K_a(rho_T^-1 y) dA,
+ * with K_a the Koornwinder basis of P_4 (Section 2.1), by adaptive
+ * subdivision (Section 3.3) for near pairs and radius-arclength fans
+ * (Section 3.4) for self pairs.  The density on T is taken as its discrete
+ * L2 projection onto P_4 with the far rule.
+ * params may be NULL (defaults: eps 1e-12, c_far 1, c_near 12, depth_cap 30).
+ * The call synchronises `stream`.  Errors: INVALID_ARG, NONFINITE, OOM, CUDA. */
+VP_API int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, const double* txy_dev, int64_t m,
+                       const vp_nf_params* params, void* stream, vp_nf** out);
+
+/* Counters and sizes of a build (host struct). */
+VP_API int vp_nf_stats(const vp_nf* nf, vp_nf_stats_t* out);
+
+/* Copy the target-major lists into caller device buffers (any may be NULL):
+ * row_ptr [M+1] int64, tri [P] int32 ascending within a row, kind [P] uint8
+ * (1 = self, 0 = near), tself [M] int32 (S(x), -1 outside). */
+VP_API int vp_nf_lists(const vp_nf* nf, int64_t* row_ptr_dev, int32_t* tri_dev, uint8_t* kind_dev, int32_t* tself_dev,
+                void* stream);
+
+/* Copy the correction weights, device [P][nq] float64, row order of vp_nf_lists. */
+VP_API int vp_nf_weights(const vp_nf* nf, double* w_dev, void* stream);
+
+/* Release a near-field build.  NULL is ignored. */
+VP_API void vp_nf_release(vp_nf* nf);
+
+/* ------------------------------------------------------------- evaluation */
+
+/* u = far + corrections (Section 3.6) for d densities.
+ * f_dev: device [d][N] float64 density values at the mesh nodes.
+ * u_dev: device [d][M] float64 output, fully overwritten.
+ * precision: VP_FP64 or VP_MIXED.  1 <= d <= 256.
+ * Uses workspace owned by the context: calls on one context must be issued
+ * on one stream (or serialised by the caller). */
+VP_API int vp_potential_eval(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, double* u_dev,
+                      int32_t precision, void* stream);
+
+/* Same as vp_potential_eval with HOST buffers (f_host [d][N], u_host [d][M]):
+ * copies in, evaluates, copies out and synchronises `stream` before return. */
+VP_API int vp_potential_eval_host(vp_ctx* ctx, const vp_nf* nf, const double* f_host, int32_t d, double* u_host,
+                           int32_t precision, void* stream);
+
+/* One evaluation of a batch: a near-field build with its densities/output. */
+typedef struct vp_eval_item {
+    const vp_nf* nf;
+    const double* f_dev;   /* device [d][N] */
+    int32_t d;
+    double* u_dev;         /* device [d][M] */
+} vp_eval_item;
+
+/* Evaluate n items (possibly different meshes) with one launch per kernel
+ * stage over all items.  Same per-item semantics and results as
+ * vp_potential_eval. */
+VP_API int vp_potential_eval_batch(vp_ctx* ctx, const vp_eval_item* items, int32_t n, int32_t precision, void* stream);
+
+/* ------------------------------------------------------------- profiling */
+
+/* Per-stage GPU timing.  When enabled, the library records a CUDA event pair
+ * on the caller's stream around each kernel stage; vp_profile_read returns,
+ * for every stage, its name, the number of launches timed and their summed
+ * device time in milliseconds (it synchronises the device first).
+ * vp_profile_reset clears the accumulators.  Off by default. */
+VP_API int vp_profile_enable(vp_ctx* ctx, int32_t on);
+VP_API int vp_profile_reset(vp_ctx* ctx);
+/* names: caller buffer of cap * 32 chars (NUL-padded); counts, ms: [cap].
+ * *n receives the number of stages (at most cap are written). */
+VP_API int vp_profile_read(vp_ctx* ctx, char* names, int64_t* counts, double* ms, int32_t cap, int32_t* n);
+
+/* ---------------------------------------------------------------- tables */
+
+/* The compiled quadrature tables, for inspection (host buffers of capacity
+ * cap; *n receives the node count).  which: 16 / 19 (far rules), 49 (near
+ * rule), 8 (radial generalized Gaussian rule: x = r, y unused), 116 (the
+ * arc-length Gauss-Legendre rule on [0,1]).  *what receives w of Eq. rho0
+ * (0 for the 1-D rules). */
+VP_API int vp_rule_table(int32_t which, double* x, double* y, double* w, double* what, int32_t cap, int32_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VP_H */

@@ -1,0 +1,283 @@
+"""Writes vp_tables.h: the quadrature constants compiled into libvp.
+
+The rules are the ones the method needs (Sections 3.2-3.4 and 5.1 of Shen &
+Serkh, arXiv 2205.04401), derived here from their moment equations in
+50-digit arithmetic and rounded once to double:
+
+  far16   S3-symmetric 16-point rule of degree 8 on the reference simplex
+  far19   S3-symmetric 19-point rule of degree 9
+  near49  collapsed 7x7 Gauss-Legendre rule (x = u, y = (1-u) v), degree 12
+  ggq8    8-point generalized Gaussian rule on [0,1] for r p(r), r log(r) p(r), p in P_7
+  gl16    16-point Gauss-Legendre rule on [0,1]
+  what    largest weight among the ceil((N+1)/2) nodes nearest an edge (max over edges)
+
+Symmetric orbits are listed centroid first, then S21(a) as (a,1-2a),
+(1-2a,a), (a,a), then S111(a,b,c=1-a-b) as the (l2,l3) entries of the
+barycentric permutations abc, acb, bac, bca, cab, cba.  The start values
+below select the positive-interior root of each system.
+
+Run once when a rule changes:  python paper_2205_04401_gb300/csrc/gen_tables.py
+(needs mpmath; the generated header is committed).
+"""
+import math
+import os
+
+import mpmath as mp
+import numpy as np
+
+mp.mp.dps = 50
+
+START = {
+    "far16": (8, 0.0722, [(0.0505, 0.0162), (0.4593, 0.0475), (0.1706, 0.0516)], [(0.0084, 0.2631, 0.0136)]),
+    "far19": (9, 0.0486, [(0.0447, 0.0128), (0.1882, 0.0398), (0.4371, 0.0389), (0.4897, 0.0157)],
+              [(0.0368, 0.2220, 0.0216)]),
+}
+
+
+def shifted_legendre(n, t):
+    """P~_n(t) = P_n(2t-1) and its t-derivative by the three-term recurrences."""
+    x = 2 * t - 1
+    p_prev, p = mp.mpf(1), x
+    d_prev, d = mp.mpf(0), mp.mpf(2)
+    if n == 0:
+        return mp.mpf(1), mp.mpf(0)
+    for k in range(1, n):
+        p_next = ((2 * k + 1) * x * p - k * p_prev) / (k + 1)
+        d_next = d_prev + 2 * (2 * k + 1) * p
+        p_prev, p = p, p_next
+        d_prev, d = d, d_next
+    return p, d
+
+
+def gl01(n):
+    # Golub-Welsch guess in double, Newton polish in mpmath
+    beta = np.array([k / math.sqrt(4.0 * k * k - 1.0) for k in range(1, n)])
+    guess = np.sort(np.linalg.eigvalsh(np.diag(beta, 1) + np.diag(beta, -1)))
+    ts, ws = [], []
+    for g in guess:
+        t = mp.mpf((g + 1) / 2)
+        for _ in range(60):
+            p, d = shifted_legendre(n, t)
+            step = p / d
+            t -= step
+            if abs(step) < mp.mpf(10) ** -45:
+                break
+        p, d = shifted_legendre(n, t)
+        ts.append(t)
+        ws.append(1 / (t * (1 - t) * d * d))
+    return ts, ws
+
+
+def duffy(n):
+    u, a = gl01(n)
+    pts = []
+    for i in range(n):
+        for j in range(n):
+            pts.append((u[i], (1 - u[i]) * u[j], a[i] * a[j] * (1 - u[i])))
+    return pts
+
+
+def orbit_points(c0, s21, s111):
+    third = mp.mpf(1) / 3
+    pts = [(third, third, c0)]
+    for a, w in s21:
+        b = 1 - 2 * a
+        pts += [(a, b, w), (b, a, w), (a, a, w)]
+    for a, b, w in s111:
+        c = 1 - a - b
+        for l1, l2, l3 in ((a, b, c), (a, c, b), (b, a, c), (b, c, a), (c, a, b), (c, b, a)):
+            pts.append((l2, l3, w))
+    return pts
+
+
+def solve_symmetric(deg, c0, s21, s111):
+    """Levenberg-Marquardt on all moments x^i y^j, i + j <= deg, with the
+    Jacobian taken analytically from the orbit parametrisation."""
+    mono = [(i, n - i) for n in range(deg + 1) for i in range(n + 1)]
+    exact = [mp.mpf(math.factorial(i) * math.factorial(j)) / math.factorial(i + j + 2) for i, j in mono]
+    n21, n111 = len(s21), len(s111)
+    p = [mp.mpf(c0)] + [mp.mpf(v) for a, w in s21 for v in (a, w)] + [mp.mpf(v) for a, b, w in s111 for v in (a, b, w)]
+
+    def unpack(p):
+        s2 = [(p[1 + 2 * i], p[2 + 2 * i]) for i in range(n21)]
+        o = 1 + 2 * n21
+        s3 = [(p[o + 3 * i], p[o + 3 * i + 1], p[o + 3 * i + 2]) for i in range(n111)]
+        return p[0], s2, s3
+
+    def mom(x, y, i, j):
+        return x ** i * y ** j
+
+    def dmom(x, y, i, j):
+        dx = i * x ** (i - 1) * y ** j if i > 0 else mp.mpf(0)
+        dy = j * x ** i * y ** (j - 1) if j > 0 else mp.mpf(0)
+        return dx, dy
+
+    def resid_jac(p):
+        c0_, s2, s3 = unpack(p)
+        R = []
+        Jm = []
+        for (i, j), ex in zip(mono, exact):
+            row = [mp.mpf(0)] * len(p)
+            third = mp.mpf(1) / 3
+            val = c0_ * mom(third, third, i, j)
+            row[0] = mom(third, third, i, j)
+            for k, (a, w) in enumerate(s2):
+                b = 1 - 2 * a
+                for (x, y, dxa, dya) in ((a, b, 1, -2), (b, a, -2, 1), (a, a, 1, 1)):
+                    m = mom(x, y, i, j)
+                    dx, dy = dmom(x, y, i, j)
+                    val += w * m
+                    row[1 + 2 * k] += w * (dx * dxa + dy * dya)
+                    row[2 + 2 * k] += m
+            o = 1 + 2 * n21
+            for k, (a, b_, w) in enumerate(s3):
+                c = 1 - a - b_
+                # (l2, l3) and their derivatives w.r.t. a and b (c = 1 - a - b)
+                perms = (((b_, c), (0, -1), (1, -1)), ((c, b_), (-1, 0), (-1, 1)), ((a, c), (1, -1), (0, -1)),
+                         ((c, a), (-1, 1), (-1, 0)), ((a, b_), (1, 0), (0, 1)), ((b_, a), (0, 1), (1, 0)))
+                for (x, y), (dxa, dya), (dxb, dyb) in perms:
+                    m = mom(x, y, i, j)
+                    dx, dy = dmom(x, y, i, j)
+                    val += w * m
+                    row[o + 3 * k] += w * (dx * dxa + dy * dya)
+                    row[o + 3 * k + 1] += w * (dx * dxb + dy * dyb)
+                    row[o + 3 * k + 2] += m
+            R.append(val - ex)
+            Jm.append(row)
+        return mp.matrix(R), mp.matrix(Jm)
+
+    lam = mp.mpf(10) ** -3
+    for _ in range(200):
+        R, Jm = resid_jac(p)
+        A = Jm.T * Jm
+        g = Jm.T * R
+        for d in range(A.rows):
+            A[d, d] *= (1 + lam)
+        step = mp.lu_solve(A, g)
+        trial = [p[c] - step[c] for c in range(len(p))]
+        R2, _ = resid_jac(trial)
+        if mp.norm(R2) < mp.norm(R):
+            p = trial
+            lam = max(lam / 10, mp.mpf(10) ** -40)
+        else:
+            lam *= 10
+        if mp.norm(step) < mp.mpf(10) ** -40:
+            break
+    R, _ = resid_jac(p)
+    assert mp.norm(R) < mp.mpf(10) ** -40
+    c0_, s2, s3 = unpack(p)
+    return orbit_points(c0_, s2, s3)
+
+
+def ggq8():
+    """8-node generalized Gaussian rule for {r^k, r^k log r}, k = 0..7, with
+    the weight r on [0,1].  Unknowns are log r_j and log w_j (positivity is
+    kept by construction).  Continuation from the Gauss rule for the weight
+    r (t = 8) through the Muntz-type family r^k (r^t - 1)/t on the geometric
+    schedule t = 8 exp(-i/10), which never lands on an integer, to t = 0."""
+    def funcs(r, k, t):
+        if t == 0:
+            return r ** k * mp.log(r), k * r ** (k - 1) * mp.log(r) + r ** (k - 1) if k > 0 else 1 / r
+        f = r ** k * (r ** t - 1) / t
+        df = (((k + t) * r ** (k + t - 1)) - (k * r ** (k - 1) if k > 0 else 0)) / t
+        return f, df
+
+    def moments(k, t):
+        return mp.mpf(1) / (k + 2), (-1 / (mp.mpf(k + 2) ** 2) if t == 0 else -1 / ((k + 2) * (k + 2 + t)))
+
+    def system(u, t):
+        r = [mp.exp(v) for v in u[:8]]
+        w = [mp.exp(v) for v in u[8:]]
+        F = mp.matrix(16, 1)
+        J = mp.matrix(16, 16)
+        for k in range(8):
+            m1, m2 = moments(k, t)
+            F[k] = mp.fsum(w[j] * r[j] ** k for j in range(8)) - m1
+            F[8 + k] = mp.fsum(w[j] * funcs(r[j], k, t)[0] for j in range(8)) - m2
+            for j in range(8):
+                dpk = k * r[j] ** (k - 1) if k > 0 else mp.mpf(0)
+                f, df = funcs(r[j], k, t)
+                J[k, j] = w[j] * dpk * r[j]           # d/du_j with r = e^u
+                J[k, 8 + j] = w[j] * r[j] ** k        # d/dv_j with w = e^v
+                J[8 + k, j] = w[j] * df * r[j]
+                J[8 + k, 8 + j] = w[j] * f
+        return F, J
+
+    def solve(u, t, tol=mp.mpf(10) ** -20):
+        for _ in range(100):
+            F, J = system(u, t)
+            du = mp.lu_solve(J, F)
+            u = [u[c] - du[c] for c in range(16)]
+            if mp.norm(du) < tol:
+                return u
+        raise RuntimeError("ggq continuation failed at t=%s" % t)
+
+    # Gauss rule for the weight r on [0,1] from the Jacobi(0,1) Golub-Welsch matrix
+    n = 8
+    diag = [1.0 / ((2 * k + 1) * (2 * k + 3)) for k in range(n)]
+    off = [2.0 / (2 * k + 1) * math.sqrt(k * k * (k + 1) * (k + 1) / ((2 * k + 1) ** 2 - 1)) for k in range(1, n)]
+    ev, V = np.linalg.eigh(np.diag(diag) + np.diag(off, 1) + np.diag(off, -1))
+    u = [mp.log(mp.mpf((e + 1) / 2)) for e in ev] + [mp.log(mp.mpf(0.5 * V[0, i] ** 2)) for i in range(n)]
+    u = solve(u, mp.mpf(8))
+    for i in range(1, 91):
+        u = solve(u, 8 * mp.exp(-mp.mpf(i) / 10))
+    u = solve(u, 0, mp.mpf(10) ** -42)
+    return [mp.exp(v) for v in u[:8]], [mp.exp(v) for v in u[8:]]
+
+
+def what(pts, degree):
+    k = (degree + 2) // 2
+    best = mp.mpf(0)
+    for e in range(3):
+        key = []
+        for idx, (x, y, w) in enumerate(pts):
+            d = y if e == 0 else (x if e == 1 else (1 - x - y) / mp.sqrt(2))
+            key.append((d, idx, w))
+        key.sort(key=lambda t: (t[0], t[1]))
+        best = max(best, max(t[2] for t in key[:k]))
+    return best
+
+
+def cdbl(v):
+    return float(v).hex()
+
+
+def main():
+    here = os.path.dirname(os.path.abspath(__file__))
+    out = ["/* Generated by gen_tables.py - quadrature constants of the method. Do not edit. */",
+           "#pragma once", ""]
+
+    def arr(name, vals):
+        out.append(f"static const double {name}[{len(vals)}] = {{")
+        for i in range(0, len(vals), 4):
+            out.append("  " + ", ".join(cdbl(v) for v in vals[i:i + 4]) + ",")
+        out.append("};")
+
+    for name in ("far16", "far19"):
+        deg, c0, s21, s111 = START[name]
+        pts = solve_symmetric(deg, c0, s21, s111)
+        arr(f"VP_{name.upper()}_X", [p[0] for p in pts])
+        arr(f"VP_{name.upper()}_Y", [p[1] for p in pts])
+        arr(f"VP_{name.upper()}_W", [p[2] for p in pts])
+        out.append(f"static const double VP_{name.upper()}_WHAT = {cdbl(what(pts, deg))};")
+        out.append(f"static const int VP_{name.upper()}_DEGREE = {deg};")
+    pts = duffy(7)
+    arr("VP_NEAR49_X", [p[0] for p in pts])
+    arr("VP_NEAR49_Y", [p[1] for p in pts])
+    arr("VP_NEAR49_W", [p[2] for p in pts])
+    out.append(f"static const double VP_NEAR49_WHAT = {cdbl(what(pts, 12))};")
+    out.append("static const int VP_NEAR49_DEGREE = 12;")
+    r, w = ggq8()
+    arr("VP_GGQ8_R", r)
+    arr("VP_GGQ8_W", w)
+    t, w = gl01(16)
+    arr("VP_GL16_X", t)
+    arr("VP_GL16_W", w)
+    path = os.path.join(here, "vp_tables.h")
+    with open(path, "w") as fh:
+        fh.write("\n".join(out) + "\n")
+    print(path)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,287 @@
+// Correction weights for (target, triangle) pairs: FP64, one warp per pair.
+//
+// For a pair (x, T) the weights are (subtract-and-add, Section 3.6)
+//     C_k = w_k sum_a K_a(xi_k) m_a - [k != own] W_k G(x, y_k),
+//     m_a = int_T G(x, y) K_a(rho_T^{-1}(y)) dA,
+// i.e. the exact integral of G against the discrete L2 projection of the
+// density onto P_4 minus what the far sum already added for T's nodes.
+// m_a comes from the near scheme (Section 3.3, adaptive subdivision with the
+// ellipse stop test of Section 4.1) or the self scheme (Section 3.4,
+// radius-arclength coordinates on three fans, generalized Gaussian rule in
+// the radius, graded Gauss-Legendre panels in the arc length).
+#include "vp_internal.h"
+
+namespace {
+
+constexpr int WARPS = 4;
+constexpr int STK = 256;      // sub-triangle stack per warp
+constexpr int LEAFCAP = 64;   // leaf buffer per warp
+constexpr int MAX_VISITED = 1 << 20;  // sub-triangles per pair before giving up with an error flag
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// m_a -> C_k for lanes k < nq, written to C[p*nq + k].
+__device__ __forceinline__ void finish_pair(const WeightsArgs& a, int64_t p, int T, int own, double xx, double xy,
+                                            double* m, int lane) {
+#pragma unroll
+    for (int q = 0; q < VP_NB; q++) m[q] = warp_sum(m[q]);
+    if (lane < a.nq) {
+        const double* Pk = a.tab->Pk[a.rule][lane];
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < VP_NB; q++) s += Pk[q] * m[q];
+        if (lane != own) {
+            int64_t j = (int64_t)T * a.nq + lane;
+            s -= a.W[j] * kernel_G(xx - a.y[2 * j], xy - a.y[2 * j + 1]);
+        }
+        a.C[p * a.nq + lane] = s;
+    }
+}
+
+__device__ __forceinline__ int own_index(const WeightsArgs& a, int t, int T) {
+    int tn = a.tnode[t];
+    return (tn >= 0 && tn / a.nq == T) ? tn - T * a.nq : -1;
+}
+
+// N = min{n >= 0 : 2^-n len < dist}
+__device__ __forceinline__ int dyadic_count(double len, double dist) {
+    int n = 0;
+    while (ldexp(len, -n) >= dist && n < 1100) n++;
+    return n;
+}
+
+// ------------------------------------------------------------------ self
+__global__ void __launch_bounds__(WARPS * 32) k_weights_self(WeightsArgs a, const int32_t* __restrict__ idx, int64_t n) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (w >= n) return;
+    const int64_t p = idx[w];
+    const int T = a.ptri[p], t = a.ptgt[p];
+    const double* v = a.tv + 6 * (int64_t)T;
+    const double Ax = v[0], Ay = v[1];
+    const double ex = v[2] - Ax, ey = v[3] - Ay, fx = v[4] - Ax, fy = v[5] - Ay;
+    const double J = a.J[T];
+    const double invJ = 1.0 / J;
+    const double xx = a.txy[2 * t], xy = a.txy[2 * t + 1];
+    const int own = own_index(a, t, T);
+    const int gl = lane >> 1, jb = (lane & 1) * 4;
+    const double lxg = a.tab->lx[gl], lwg = a.tab->lw[gl];
+    double gr[4], gwl[4], glr[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        gr[q] = a.tab->gr[jb + q];
+        gwl[q] = a.tab->gw[jb + q] * VP_INV_TWO_PI;
+        glr[q] = a.tab->glogr[jb + q];
+    }
+    double m[VP_NB];
+#pragma unroll
+    for (int q = 0; q < VP_NB; q++) m[q] = 0.0;
+    int panels = 0;
+    for (int e = 0; e < 3; e++) {
+        const double Px = v[2 * e], Py = v[2 * e + 1];
+        const double Qx = v[(2 * e + 2) % 6], Qy = v[(2 * e + 3) % 6];
+        const double dx = rn_sub(Qx, Px), dy = rn_sub(Qy, Py);
+        const double L = rn_sqrt(rn_add(rn_mul(dx, dx), rn_mul(dy, dy)));
+        if (L == 0.0) continue;
+        const double h = rn_div(fabs(rn_sub(rn_mul(dx, rn_sub(xy, Py)), rn_mul(dy, rn_sub(xx, Px)))), L);
+        if (h == 0.0) continue;
+        double st = rn_div(rn_add(rn_mul(dx, rn_sub(xx, Px)), rn_mul(dy, rn_sub(xy, Py))), L);
+        if (st < 0.0) st = 0.0;
+        if (st > L) st = L;
+        const double fxp = rn_add(Px, rn_mul(rn_div(st, L), dx)), fyp = rn_add(Py, rn_mul(rn_div(st, L), dy));
+        const double ddx = rn_sub(xx, fxp), ddy = rn_sub(xy, fyp);
+        const double delta = rn_sqrt(rn_add(rn_mul(ddx, ddx), rn_mul(ddy, ddy)));
+        const double Lst = rn_sub(L, st);
+        for (int side = 0; side < 2; side++) {
+            double len = side == 0 ? st : Lst;
+            if (!(len > 0.0)) continue;
+            const int Nd = dyadic_count(len, delta);
+            // panel boundaries: b_0 = end, b_i = end -/+ (1 - 2^-i) len, b_{Nd+1} = st
+            double b0 = side == 0 ? 0.0 : L;
+            for (int i = 0; i <= Nd; i++) {
+                double b1;
+                if (i == Nd) b1 = st;
+                else {
+                    double frac = rn_mul(rn_sub(1.0, ldexp(1.0, -(i + 1))), len);
+                    b1 = side == 0 ? frac : rn_sub(L, frac);
+                }
+                panels++;
+                const double s = b0 + (b1 - b0) * lxg;
+                const double ws = fabs((b1 - b0) * lwg) * h;
+                const double sl = s / L;
+                const double gx = Px + sl * dx, gy = Py + sl * dy;
+                const double rx = gx - xx, ry = gy - xy;
+                const double lr0 = 0.5 * log(rx * rx + ry * ry);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const double yx = xx + gr[q] * rx, yy = xy + gr[q] * ry;
+                    const double qx = yx - Ax, qy = yy - Ay;
+                    const double xi = (qx * fy - qy * fx) * invJ;
+                    const double eta = (ex * qy - ey * qx) * invJ;
+                    double K[VP_NB];
+                    koornwinder4(xi, eta, K);
+                    const double g = (lr0 + glr[q]) * ws * gwl[q];
+#pragma unroll
+                    for (int c = 0; c < VP_NB; c++) m[c] += g * K[c];
+                }
+                b0 = b1;
+            }
+        }
+    }
+    finish_pair(a, p, T, own, xx, xy, m, lane);
+    if (lane == 0) {
+        a.pstat[p] = panels;
+        a.pcap[p] = 0;
+    }
+}
+
+// ------------------------------------------------------------------ near
+struct SubTri {
+    int32_t v[6];  // vertex numerators in the reference simplex of T, at scale 2^-L
+    int32_t L;
+};
+
+__device__ __forceinline__ void sub_phys(const SubTri& S, double Ax, double Ay, double ex, double ey, double fx,
+                                         double fy, double* ph) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const double xi = ldexp((double)S.v[2 * i], -S.L), eta = ldexp((double)S.v[2 * i + 1], -S.L);
+        ph[2 * i] = rn_add(Ax, rn_add(rn_mul(xi, ex), rn_mul(eta, fx)));
+        ph[2 * i + 1] = rn_add(Ay, rn_add(rn_mul(xi, ey), rn_mul(eta, fy)));
+    }
+}
+
+__global__ void __launch_bounds__(WARPS * 32) k_weights_near(WeightsArgs a, const int32_t* __restrict__ idx, int64_t n) {
+    __shared__ SubTri stack_all[WARPS][STK];
+    __shared__ SubTri leaf_all[WARPS][LEAFCAP];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t w = (int64_t)blockIdx.x * WARPS + wl;
+    if (w >= n) return;
+    SubTri* stack = stack_all[wl];
+    SubTri* leaves = leaf_all[wl];
+    const int64_t p = idx[w];
+    const int T = a.ptri[p], t = a.ptgt[p];
+    const double* v = a.tv + 6 * (int64_t)T;
+    const double Ax = v[0], Ay = v[1];
+    const double ex = rn_sub(v[2], Ax), ey = rn_sub(v[3], Ay), fx = rn_sub(v[4], Ax), fy = rn_sub(v[5], Ay);
+    const double J = a.J[T];
+    const double xx = a.txy[2 * t], xy = a.txy[2 * t + 1];
+    const int own = own_index(a, t, T);
+    const double what = a.tab->near_what;
+    const int Nn = a.tab->near_degree;
+    const double* nx = a.tab->nx;
+    const double* ny = a.tab->ny;
+    const double* nw = a.tab->nw;
+
+    double m[VP_NB];
+#pragma unroll
+    for (int q = 0; q < VP_NB; q++) m[q] = 0.0;
+    if (lane == 0) {
+        SubTri r;
+        r.v[0] = 0; r.v[1] = 0; r.v[2] = 1; r.v[3] = 0; r.v[4] = 0; r.v[5] = 1; r.L = 0;
+        stack[0] = r;
+    }
+    __syncwarp();
+    int sp = 1, nleaf = 0, total_leaves = 0, capped = 0;
+    int visited = 0;              // sub-triangles examined; bounded so no input can loop for long
+    bool overflow = false;
+    const unsigned lower = (1u << lane) - 1u;
+    while (sp > 0 || nleaf > 0) {
+        bool flush = nleaf > 0 && (sp == 0 || nleaf + 32 > LEAFCAP || nleaf >= 32);
+        if (!flush) {
+            int c = min(sp, 32);
+            c = min(c, (STK - sp) / 3);
+            if (c <= 0 || visited > MAX_VISITED) {
+                overflow = true;
+                break;
+            }
+            visited += c;
+            SubTri S;
+            bool stop = false;
+            if (lane < c) {
+                S = stack[sp - 1 - lane];
+                double ph[6];
+                sub_phys(S, Ax, Ay, ex, ey, fx, fy, ph);
+                const double JS = ldexp(J, -2 * S.L);
+                const bool inside = tri_contains_rn(ph, xx, xy);
+                stop = !inside && !tri_near_rn(ph, xx, xy, Nn, ellipse_R_rn(what, JS, a.eps, a.c_near));
+                if (!stop && S.L >= a.depth_cap) {
+                    stop = true;
+                    capped++;
+                }
+            }
+            __syncwarp();
+            const unsigned lm = __ballot_sync(0xffffffffu, lane < c && stop);
+            const unsigned sm = __ballot_sync(0xffffffffu, lane < c && !stop);
+            sp -= c;
+            if (lane < c) {
+                if (stop) {
+                    leaves[nleaf + __popc(lm & lower)] = S;
+                } else {
+                    const int base = sp + 4 * __popc(sm & lower);
+                    int32_t m01x = S.v[0] + S.v[2], m01y = S.v[1] + S.v[3];
+                    int32_t m12x = S.v[2] + S.v[4], m12y = S.v[3] + S.v[5];
+                    int32_t m20x = S.v[4] + S.v[0], m20y = S.v[5] + S.v[1];
+                    int32_t V0x = 2 * S.v[0], V0y = 2 * S.v[1], V1x = 2 * S.v[2], V1y = 2 * S.v[3];
+                    int32_t V2x = 2 * S.v[4], V2y = 2 * S.v[5];
+                    const int32_t L1 = S.L + 1;
+                    SubTri ch;
+                    ch.L = L1;
+                    ch.v[0] = V0x; ch.v[1] = V0y; ch.v[2] = m01x; ch.v[3] = m01y; ch.v[4] = m20x; ch.v[5] = m20y;
+                    stack[base + 0] = ch;
+                    ch.v[0] = m01x; ch.v[1] = m01y; ch.v[2] = V1x; ch.v[3] = V1y; ch.v[4] = m12x; ch.v[5] = m12y;
+                    stack[base + 1] = ch;
+                    ch.v[0] = m20x; ch.v[1] = m20y; ch.v[2] = m12x; ch.v[3] = m12y; ch.v[4] = V2x; ch.v[5] = V2y;
+                    stack[base + 2] = ch;
+                    ch.v[0] = m12x; ch.v[1] = m12y; ch.v[2] = m20x; ch.v[3] = m20y; ch.v[4] = m01x; ch.v[5] = m01y;
+                    stack[base + 3] = ch;
+                }
+            }
+            nleaf += __popc(lm);
+            sp += 4 * __popc(sm);
+            __syncwarp();
+        } else {
+            // near rule on every buffered leaf: (leaf, node) pairs over the lanes
+            const int combos = nleaf * VP_NNEAR;
+            for (int i = lane; i < combos; i += 32) {
+                const int li = i / VP_NNEAR, j = i - li * VP_NNEAR;
+                const SubTri& S = leaves[li];
+                const double s = ldexp(1.0, -S.L);
+                const double a0x = S.v[0] * s, a0y = S.v[1] * s;
+                const double xi = a0x + (nx[j] * (S.v[2] * s - a0x) + ny[j] * (S.v[4] * s - a0x));
+                const double eta = a0y + (nx[j] * (S.v[3] * s - a0y) + ny[j] * (S.v[5] * s - a0y));
+                const double yx = Ax + (xi * ex + eta * fx), yy = Ay + (xi * ey + eta * fy);
+                const double g = kernel_G(xx - yx, xy - yy) * nw[j] * ldexp(J, -2 * S.L);
+                double K[VP_NB];
+                koornwinder4(xi, eta, K);
+#pragma unroll
+                for (int c = 0; c < VP_NB; c++) m[c] += g * K[c];
+            }
+            total_leaves += nleaf;
+            nleaf = 0;
+            __syncwarp();
+        }
+    }
+    if (overflow && lane == 0) atomicOr(a.flag, VP_DEV_ERR_STACK);
+    finish_pair(a, p, T, own, xx, xy, m, lane);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) capped += __shfl_xor_sync(0xffffffffu, capped, o);
+    if (lane == 0) {
+        a.pstat[p] = total_leaves;
+        a.pcap[p] = capped;
+    }
+}
+
+}  // namespace
+
+void launch_weights_self(const WeightsArgs& a, const int32_t* idx, int64_t n, cudaStream_t s) {
+    if (n > 0) k_weights_self<<<(unsigned)((n + WARPS - 1) / WARPS), WARPS * 32, 0, s>>>(a, idx, n);
+}
+
+void launch_weights_near(const WeightsArgs& a, const int32_t* idx, int64_t n, cudaStream_t s) {
+    if (n > 0) k_weights_near<<<(unsigned)((n + WARPS - 1) / WARPS), WARPS * 32, 0, s>>>(a, idx, n);
+}

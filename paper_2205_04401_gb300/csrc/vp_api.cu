@@ -1,0 +1,803 @@
+// C ABI of libvp: handles, validation, and the orchestration of the kernels
+// for mesh_upload, nearfield_build and potential_eval.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vp_internal.h"
+#include "vp_tables.h"
+
+namespace {
+
+const char* kStatusNames[] = {"VP_OK",          "VP_ERR_INVALID_ARG", "VP_ERR_DEGENERATE_TRI", "VP_ERR_NONFINITE",
+                              "VP_ERR_OOM",     "VP_ERR_CUDA",        "VP_ERR_TIMEOUT",        "VP_ERR_NO_DEVICE",
+                              "VP_ERR_STATE"};
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DevGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Device allocations released at scope exit unless kept.
+struct Scratch {
+    std::vector<void*> ptrs;
+    cudaStream_t s;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    template <typename T>
+    cudaError_t alloc(T** p, size_t count) {
+        *p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+        if (e == cudaSuccess) ptrs.push_back((void*)*p);
+        return e;
+    }
+    ~Scratch() {
+        if (!ptrs.empty()) cudaStreamSynchronize(s);
+        for (void* p : ptrs) cudaFree(p);
+    }
+};
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+void fill_tables(VpTables& t) {
+    std::memset(&t, 0, sizeof(t));
+    const double* fx[2] = {VP_FAR16_X, VP_FAR19_X};
+    const double* fy[2] = {VP_FAR16_Y, VP_FAR19_Y};
+    const double* fw[2] = {VP_FAR16_W, VP_FAR19_W};
+    const int nq[2] = {16, 19};
+    t.far_what[0] = VP_FAR16_WHAT;
+    t.far_what[1] = VP_FAR19_WHAT;
+    t.far_degree[0] = VP_FAR16_DEGREE;
+    t.far_degree[1] = VP_FAR19_DEGREE;
+    for (int r = 0; r < 2; r++) {
+        t.nq[r] = nq[r];
+        for (int k = 0; k < nq[r]; k++) {
+            t.fx[r][k] = fx[r][k];
+            t.fy[r][k] = fy[r][k];
+            t.fw[r][k] = fw[r][k];
+            double K[VP_NB];
+            koornwinder4(fx[r][k], fy[r][k], K);
+            for (int a = 0; a < VP_NB; a++) t.Pk[r][k][a] = fw[r][k] * K[a];
+        }
+    }
+    for (int j = 0; j < VP_NNEAR; j++) {
+        t.nx[j] = VP_NEAR49_X[j];
+        t.ny[j] = VP_NEAR49_Y[j];
+        t.nw[j] = VP_NEAR49_W[j];
+    }
+    t.near_what = VP_NEAR49_WHAT;
+    t.near_degree = VP_NEAR49_DEGREE;
+    for (int j = 0; j < VP_NGGQ; j++) {
+        t.gr[j] = VP_GGQ8_R[j];
+        t.gw[j] = VP_GGQ8_W[j];
+        t.glogr[j] = std::log(VP_GGQ8_R[j]);
+    }
+    for (int j = 0; j < VP_NGL; j++) {
+        t.lx[j] = VP_GL16_X[j];
+        t.lw[j] = VP_GL16_W[j];
+    }
+}
+
+bool ctx_ok(const vp_ctx* c) { return c && c->magic == 0x56504358; }
+bool mesh_ok(const vp_mesh* m) { return m && m->magic == 0x56504d48; }
+bool nf_ok(const vp_nf* n) { return n && n->magic == 0x56504e46; }
+
+int check_flag(vp_ctx* ctx, int32_t* d_flag, cudaStream_t s) {
+    int32_t h = 0;
+    VP_CUDA_TRY(ctx, cudaMemcpyAsync(&h, d_flag, sizeof(h), cudaMemcpyDeviceToHost, s));
+    VP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (h & VP_DEV_ERR_BADIDX) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "triangle vertex index out of range");
+    if (h & VP_DEV_ERR_NONFINITE) return vp_set_error(ctx, VP_ERR_NONFINITE, "non-finite coordinate");
+    if (h & VP_DEV_ERR_DEGEN) return vp_set_error(ctx, VP_ERR_DEGENERATE_TRI, "triangle with zero area");
+    if (h & VP_DEV_ERR_STACK) return vp_set_error(ctx, VP_ERR_CUDA, "near-field subdivision stack overflow");
+    if (h & VP_DEV_ERR_CELL) return vp_set_error(ctx, VP_ERR_CUDA, "grid cell list exceeds sort capacity");
+    return VP_OK;
+}
+
+int ensure_ws(vp_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes) return VP_OK;
+    if (ctx->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    VP_CUDA_TRY(ctx, cudaMalloc(&ctx->ws, want));
+    ctx->ws_bytes = want;
+    return VP_OK;
+}
+
+void free_nf_device(vp_nf* nf) {
+    void* ps[] = {nf->d_txy, nf->d_tself, nf->d_tnode, nf->d_row, nf->d_ptri, nf->d_ptgt, nf->d_pkind, nf->d_C,
+                  nf->src_ff.hi, nf->src_ff.lo, nf->tgt_ff.hi, nf->tgt_ff.lo};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+}
+
+}  // namespace
+
+int vp_set_error(vp_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->last_error = msg;
+    return code;
+}
+
+static const char* kStageNames[ST_COUNT] = {
+    "mesh_nodes", "tri_geom", "tri_cells", "cell_sort", "target_cells", "locate", "list_count", "list_fill",
+    "weights_self", "weights_near", "ff_split", "far_fp64", "far_ff", "reduce_splits", "apply_fp64"};
+
+static cudaEvent_t prof_event(vp_ctx* ctx) {
+    if (!ctx->prof_pool.empty()) {
+        cudaEvent_t e = ctx->prof_pool.back();
+        ctx->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(vp_ctx* ctx, int stage, cudaStream_t s, ProfRec& r) {
+    r.stage = -1;
+    if (!ctx->prof) return;
+    r.stage = stage;
+    r.a = prof_event(ctx);
+    r.b = prof_event(ctx);
+    cudaEventRecord(r.a, s);
+}
+
+void prof_end(vp_ctx* ctx, cudaStream_t s, ProfRec& r) {
+    if (r.stage < 0) return;
+    cudaEventRecord(r.b, s);
+    ctx->prof_pending.push_back(r);
+}
+
+void prof_collect(vp_ctx* ctx) {
+    for (ProfRec& r : ctx->prof_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            ctx->prof_ms[r.stage] += ms;
+            ctx->prof_n[r.stage] += 1;
+        }
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+}
+
+#define PROF(ctx, stage, s, ...)        \
+    do {                                \
+        ProfRec _r;                     \
+        prof_begin(ctx, stage, s, _r);  \
+        __VA_ARGS__;                    \
+        prof_end(ctx, s, _r);           \
+    } while (0)
+
+extern "C" {
+
+const char* vp_status_str(int status) {
+    if (status > 0 || status < -8) return "VP_UNKNOWN";
+    return kStatusNames[-status];
+}
+
+int vp_last_error(const vp_ctx* ctx, char* buf, int32_t len) {
+    if (!buf || len <= 0) return VP_ERR_INVALID_ARG;
+    const char* m = ctx_ok(ctx) ? ctx->last_error.c_str() : "invalid context";
+    std::strncpy(buf, m, (size_t)len - 1);
+    buf[len - 1] = 0;
+    return VP_OK;
+}
+
+int vp_create(vp_ctx** out, int device) {
+    if (!out) return VP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return VP_ERR_NO_DEVICE;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return VP_ERR_NO_DEVICE;
+    if (!(prop.major == 10 && prop.minor == 3)) return VP_ERR_NO_DEVICE;
+    DevGuard g(device);
+    vp_ctx* ctx = new (std::nothrow) vp_ctx();
+    if (!ctx) return VP_ERR_OOM;
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    fill_tables(ctx->h_tables);
+    if (cudaMalloc(&ctx->d_tables, sizeof(VpTables)) != cudaSuccess ||
+        cudaMemcpy(ctx->d_tables, &ctx->h_tables, sizeof(VpTables), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMalloc(&ctx->d_flag, sizeof(int32_t)) != cudaSuccess) {
+        vp_destroy(ctx);
+        return VP_ERR_OOM;
+    }
+    *out = ctx;
+    return VP_OK;
+}
+
+void vp_destroy(vp_ctx* ctx) {
+    if (!ctx_ok(ctx)) return;
+    DevGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->d_tables) cudaFree(ctx->d_tables);
+    if (ctx->d_flag) cudaFree(ctx->d_flag);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->stage) cudaFree(ctx->stage);
+    prof_collect(ctx);
+    for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    ctx->magic = 0;
+    delete ctx;
+}
+
+// -------------------------------------------------------------------- mesh
+static int mesh_upload_impl(vp_ctx* ctx, const double* d_vxy, int64_t nv, const int32_t* d_tri, int64_t nt,
+                            int32_t rule, cudaStream_t s, vp_mesh** out) {
+    vp_mesh* m = new (std::nothrow) vp_mesh();
+    if (!m) return VP_ERR_OOM;
+    m->ctx = ctx;
+    m->nt = nt;
+    m->nv = nv;
+    m->rule_index = rule == VP_RULE_16_D8 ? 0 : 1;
+    m->nq = rule;
+    m->N = nt * m->nq;
+    int rc = VP_OK;
+    double* d_red = nullptr;
+    cudaError_t e = dev_alloc(&m->d_tv, 6 * nt);
+    if (e == cudaSuccess) e = dev_alloc(&m->d_J, nt);
+    if (e == cudaSuccess) e = dev_alloc(&m->d_y, 2 * m->N);
+    if (e == cudaSuccess) e = dev_alloc(&m->d_W, m->N);
+    if (e == cudaSuccess) e = dev_alloc(&d_red, 4);
+    if (e != cudaSuccess) rc = vp_set_error(ctx, VP_ERR_OOM, "vp_mesh_upload: device allocation failed");
+    if (rc == VP_OK) {
+        cudaMemsetAsync(ctx->d_flag, 0, sizeof(int32_t), s);
+        PROF(ctx, ST_MESH_NODES, s,
+             launch_mesh_nodes(d_vxy, nv, d_tri, nt, ctx->d_tables, m->rule_index, m->d_tv, m->d_J, m->d_y, m->d_W,
+                               ctx->d_flag, s));
+        launch_bbox_reduce(d_vxy, nv, 2, d_red, s);
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) rc = vp_set_error(ctx, VP_ERR_CUDA, cudaGetErrorString(le));
+        else rc = check_flag(ctx, ctx->d_flag, s);
+        if (rc == VP_OK && cudaMemcpy(m->bbox, d_red, 4 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = vp_set_error(ctx, VP_ERR_CUDA, "vp_mesh_upload: bbox copy failed");
+    }
+    if (d_red) cudaFree(d_red);
+    if (rc != VP_OK) {
+        vp_mesh_release(m);
+        return rc;
+    }
+    *out = m;
+    return VP_OK;
+}
+
+int vp_mesh_upload(vp_ctx* ctx, const double* vxy, int64_t nv, const int32_t* tri, int64_t nt, int32_t rule,
+                   void* stream, vp_mesh** out) {
+    if (out) *out = nullptr;
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    if (!out || !vxy || !tri || nv < 3 || nt < 1 || (rule != VP_RULE_16_D8 && rule != VP_RULE_19_D9))
+        return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload: bad arguments");
+    if (nt > (int64_t)INT32_MAX / 19) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload: too many triangles");
+    for (int64_t i = 0; i < 2 * nv; i++)
+        if (!std::isfinite(vxy[i])) return vp_set_error(ctx, VP_ERR_NONFINITE, "vp_mesh_upload: non-finite vertex");
+    for (int64_t i = 0; i < 3 * nt; i++)
+        if (tri[i] < 0 || tri[i] >= nv) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload: index out of range");
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    double* d_vxy;
+    int32_t* d_tri;
+    if (sc.alloc(&d_vxy, 2 * nv) != cudaSuccess || sc.alloc(&d_tri, 3 * nt) != cudaSuccess)
+        return vp_set_error(ctx, VP_ERR_OOM, "vp_mesh_upload: device allocation failed");
+    VP_CUDA_TRY(ctx, cudaMemcpyAsync(d_vxy, vxy, 2 * nv * sizeof(double), cudaMemcpyHostToDevice, s));
+    VP_CUDA_TRY(ctx, cudaMemcpyAsync(d_tri, tri, 3 * nt * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    return mesh_upload_impl(ctx, d_vxy, nv, d_tri, nt, rule, s, out);
+}
+
+int vp_mesh_upload_dev(vp_ctx* ctx, const double* vxy_dev, int64_t nv, const int32_t* tri_dev, int64_t nt,
+                       int32_t rule, void* stream, vp_mesh** out) {
+    if (out) *out = nullptr;
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    if (!out || !vxy_dev || !tri_dev || nv < 3 || nt < 1 || (rule != VP_RULE_16_D8 && rule != VP_RULE_19_D9))
+        return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload_dev: bad arguments");
+    if (nt > (int64_t)INT32_MAX / 19)
+        return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload_dev: too many triangles");
+    DevGuard g(ctx->device);
+    return mesh_upload_impl(ctx, vxy_dev, nv, tri_dev, nt, rule, (cudaStream_t)stream, out);
+}
+
+int vp_mesh_info(const vp_mesh* mesh, int64_t* n_tri, int64_t* n_nodes, int32_t* nq) {
+    if (!mesh_ok(mesh)) return VP_ERR_STATE;
+    if (n_tri) *n_tri = mesh->nt;
+    if (n_nodes) *n_nodes = mesh->N;
+    if (nq) *nq = mesh->nq;
+    return VP_OK;
+}
+
+int vp_mesh_nodes(const vp_mesh* mesh, double* yxy_dev, double* w_dev, void* stream) {
+    if (!mesh_ok(mesh)) return VP_ERR_STATE;
+    DevGuard g(mesh->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (yxy_dev) VP_CUDA_TRY(mesh->ctx, cudaMemcpyAsync(yxy_dev, mesh->d_y, 2 * mesh->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (w_dev) VP_CUDA_TRY(mesh->ctx, cudaMemcpyAsync(w_dev, mesh->d_W, mesh->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return VP_OK;
+}
+
+void vp_mesh_release(vp_mesh* mesh) {
+    if (!mesh_ok(mesh)) return;
+    DevGuard g(mesh->ctx->device);
+    cudaDeviceSynchronize();
+    void* ps[] = {mesh->d_tv, mesh->d_J, mesh->d_y, mesh->d_W};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    mesh->magic = 0;
+    delete mesh;
+}
+
+// -------------------------------------------------------------- near field
+int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, const double* txy_dev, int64_t m,
+                       const vp_nf_params* params, void* stream, vp_nf** out) {
+    if (out) *out = nullptr;
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    if (!mesh_ok(mesh) || mesh->ctx != ctx) return vp_set_error(ctx, VP_ERR_STATE, "vp_nearfield_build: bad mesh");
+    if (!out || m < 0 || (m > 0 && !txy_dev)) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_nearfield_build: bad arguments");
+    const int64_t N = mesh->N, nt = mesh->nt;
+    const int nq = mesh->nq;
+    const int64_t M = (node_targets ? N : 0) + m;
+    if (M < 1 || M > (int64_t)INT32_MAX) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_nearfield_build: no targets");
+    vp_nf_params prm;
+    prm.eps = 1e-12;
+    prm.c_far = 1.0;
+    prm.c_near = 12.0;
+    prm.depth_cap = 30;
+    prm.reserved = 0;
+    if (params) prm = *params;
+    if (!(prm.eps >= 1e-15 && prm.eps <= 1e-2) || !(prm.c_far > 0) || !(prm.c_near > 0) || prm.depth_cap < 0 ||
+        prm.depth_cap > 30)
+        return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_nearfield_build: bad params");
+    auto t_start = std::chrono::steady_clock::now();
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    vp_nf* nf = new (std::nothrow) vp_nf();
+    if (!nf) return VP_ERR_OOM;
+    nf->ctx = ctx;
+    nf->mesh = mesh;
+    nf->M = M;
+    nf->n_extra = m;
+    nf->node_targets = node_targets ? 1 : 0;
+    nf->params = prm;
+    const VpTables& tab = ctx->h_tables;
+    const int ri = mesh->rule_index;
+    int rc = VP_OK;
+#define NF_FAIL(code, msg)                          \
+    do {                                            \
+        rc = vp_set_error(ctx, (code), (msg));      \
+        goto fail;                                  \
+    } while (0)
+#define NF_CUDA(expr)                                                                           \
+    do {                                                                                        \
+        cudaError_t _e = (expr);                                                                \
+        if (_e != cudaSuccess)                                                                  \
+            NF_FAIL(_e == cudaErrorMemoryAllocation ? VP_ERR_OOM : VP_ERR_CUDA,                 \
+                    std::string(#expr) + ": " + cudaGetErrorString(_e));                        \
+    } while (0)
+    {
+        Scratch sc(s);
+        double *d_R, *d_bbox, *d_red;
+        double h_red[4], h_tb[4];
+        GridDev gd;
+        int64_t ncell, nentries = 0;
+        int32_t *d_cnt, *d_cell_tri, *d_tcell, *d_tcnt, *d_order, *d_count, *d_near_idx, *d_self_idx, *d_pstat, *d_pcap;
+        int32_t *d_max;
+        int64_t *d_cell_start, *d_cursor, *d_tstart;
+        unsigned long long* d_u64;
+        unsigned long long h_u64[2];
+        int32_t h_max = 0;
+        std::vector<double> hb;
+        std::vector<double> sizes;
+        double W_, H_, hc;
+        int64_t nx, ny;
+        WeightsArgs wa;
+        int64_t n_near, n_self;
+
+        NF_CUDA(dev_alloc(&nf->d_txy, 2 * M));
+        NF_CUDA(dev_alloc(&nf->d_tnode, M));
+        NF_CUDA(dev_alloc(&nf->d_tself, M));
+        launch_targets_init(mesh->d_y, N, nq, nf->node_targets, txy_dev, m, nf->d_txy, nf->d_tnode, nf->d_tself, s);
+        NF_CUDA(cudaGetLastError());
+
+        // per-triangle ellipse parameter and bounding boxes
+        NF_CUDA(sc.alloc(&d_R, nt));
+        NF_CUDA(sc.alloc(&d_bbox, 4 * nt));
+        NF_CUDA(sc.alloc(&d_red, 8));
+        PROF(ctx, ST_TRI_GEOM, s,
+             launch_tri_geom(mesh->d_tv, mesh->d_J, nt, tab.far_what[ri], tab.far_degree[ri], prm.eps, prm.c_far, d_R, d_bbox, s));
+        launch_bbox_reduce(d_bbox, nt, 4, d_red, s);
+        launch_bbox_reduce(nf->d_txy, M, 2, d_red + 4, s);
+        NF_CUDA(cudaGetLastError());
+        hb.resize(4 * nt);
+        NF_CUDA(cudaMemcpyAsync(hb.data(), d_bbox, 4 * nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+        NF_CUDA(cudaMemcpyAsync(h_red, d_red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        NF_CUDA(cudaMemcpyAsync(h_tb, d_red + 4, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        NF_CUDA(cudaStreamSynchronize(s));
+        if (!std::isfinite(h_tb[0]) || !std::isfinite(h_tb[1]) || !std::isfinite(h_tb[2]) || !std::isfinite(h_tb[3]))
+            NF_FAIL(VP_ERR_NONFINITE, "vp_nearfield_build: non-finite target");
+
+        // grid: cell = half the 25th percentile of the triangles' box sizes
+        sizes.resize(nt);
+        for (int64_t t = 0; t < nt; t++) sizes[t] = std::max(hb[4 * t + 2] - hb[4 * t], hb[4 * t + 3] - hb[4 * t + 1]);
+        std::nth_element(sizes.begin(), sizes.begin() + nt / 4, sizes.end());
+        W_ = h_red[2] - h_red[0];
+        H_ = h_red[3] - h_red[1];
+        hc = std::max(0.5 * sizes[nt / 4], 1e-300);
+        hc = std::max(hc, std::max(W_, H_) / 4096.0);
+        nx = std::max<int64_t>(1, (int64_t)std::ceil(W_ / hc));
+        ny = std::max<int64_t>(1, (int64_t)std::ceil(H_ / hc));
+        while (nx * ny > ((int64_t)1 << 24)) {
+            hc *= 1.5;
+            nx = std::max<int64_t>(1, (int64_t)std::ceil(W_ / hc));
+            ny = std::max<int64_t>(1, (int64_t)std::ceil(H_ / hc));
+        }
+        ncell = nx * ny;
+        gd.ox = h_red[0];
+        gd.oy = h_red[1];
+        gd.h = hc;
+        gd.nx = (int32_t)nx;
+        gd.ny = (int32_t)ny;
+        gd.cell_start = nullptr;
+        gd.cell_tri = nullptr;
+
+        // triangles -> cells (sorted per cell)
+        NF_CUDA(sc.alloc(&d_cnt, ncell));
+        NF_CUDA(sc.alloc(&d_cell_start, ncell + 1));
+        NF_CUDA(sc.alloc(&d_cursor, ncell + 1));
+        NF_CUDA(sc.alloc(&d_max, 1));
+        NF_CUDA(cudaMemsetAsync(d_cnt, 0, ncell * sizeof(int32_t), s));
+        PROF(ctx, ST_TRI_CELLS, s, launch_tri_cell_count(d_bbox, nt, gd, d_cnt, s));
+        rc = vp_exclusive_scan_i32(ctx, d_cnt, d_cell_start, ncell, s);
+        if (rc) goto fail;
+        launch_max_i32(d_cnt, ncell, d_max, s);
+        NF_CUDA(cudaMemcpyAsync(&nentries, d_cell_start + ncell, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        NF_CUDA(cudaMemcpyAsync(&h_max, d_max, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        NF_CUDA(cudaStreamSynchronize(s));
+        if (h_max > 16384) NF_FAIL(VP_ERR_CUDA, "vp_nearfield_build: a grid cell holds more than 16384 triangles");
+        NF_CUDA(sc.alloc(&d_cell_tri, nentries));
+        NF_CUDA(cudaMemcpyAsync(d_cursor, d_cell_start, (ncell + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        PROF(ctx, ST_TRI_CELLS, s, launch_tri_cell_fill(d_bbox, nt, gd, d_cursor, d_cell_tri, s));
+        gd.cell_start = d_cell_start;
+        gd.cell_tri = d_cell_tri;
+        NF_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int32_t), s));
+        PROF(ctx, ST_CELL_SORT, s, launch_cell_sort(gd, ncell, h_max, d_cell_tri, ctx->d_flag, s));
+        NF_CUDA(cudaGetLastError());
+
+        // targets -> cells, processing order grouped by cell
+        NF_CUDA(sc.alloc(&d_tcell, M));
+        NF_CUDA(sc.alloc(&d_tcnt, ncell));
+        NF_CUDA(sc.alloc(&d_tstart, ncell + 1));
+        NF_CUDA(sc.alloc(&d_order, M));
+        NF_CUDA(cudaMemsetAsync(d_tcnt, 0, ncell * sizeof(int32_t), s));
+        PROF(ctx, ST_TARGET_CELLS, s, launch_target_cells(nf->d_txy, M, gd, d_tcell, d_tcnt, s));
+        rc = vp_exclusive_scan_i32(ctx, d_tcnt, d_tstart, ncell, s);
+        if (rc) goto fail;
+        PROF(ctx, ST_TARGET_CELLS, s, launch_target_order(d_tcell, M, d_tstart, d_order, s));
+
+        // S(x) for extra targets, then the two list passes
+        PROF(ctx, ST_LOCATE, s, launch_locate(mesh->d_tv, nf->d_txy, d_order, d_tcell, M, gd, nf->d_tself, s));
+        NF_CUDA(sc.alloc(&d_count, M));
+        PROF(ctx, ST_LIST_COUNT, s,
+             launch_list_pass(mesh->d_tv, d_R, tab.far_degree[ri], nf->d_txy, nf->d_tself, d_order, d_tcell, M, gd,
+                              d_count, nullptr, nullptr, nullptr, nullptr, s));
+        NF_CUDA(dev_alloc(&nf->d_row, M + 1));
+        rc = vp_exclusive_scan_i32(ctx, d_count, nf->d_row, M, s);
+        if (rc) goto fail;
+        NF_CUDA(cudaMemcpyAsync(&nf->P, nf->d_row + M, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        NF_CUDA(cudaStreamSynchronize(s));
+        if (nf->P > (int64_t)INT32_MAX) NF_FAIL(VP_ERR_INVALID_ARG, "vp_nearfield_build: more than 2^31 pairs");
+        NF_CUDA(dev_alloc(&nf->d_ptri, nf->P));
+        NF_CUDA(dev_alloc(&nf->d_ptgt, nf->P));
+        NF_CUDA(dev_alloc(&nf->d_pkind, nf->P));
+        NF_CUDA(dev_alloc(&nf->d_C, nf->P * nq));
+        PROF(ctx, ST_LIST_FILL, s,
+             launch_list_pass(mesh->d_tv, d_R, tab.far_degree[ri], nf->d_txy, nf->d_tself, d_order, d_tcell, M, gd,
+                              nullptr, nf->d_row, nf->d_ptri, nf->d_ptgt, nf->d_pkind, s));
+        NF_CUDA(cudaGetLastError());
+
+        // correction weights
+        NF_CUDA(sc.alloc(&d_near_idx, nf->P));
+        NF_CUDA(sc.alloc(&d_self_idx, nf->P));
+        NF_CUDA(sc.alloc(&d_u64, 2));
+        NF_CUDA(sc.alloc(&d_pstat, nf->P));
+        NF_CUDA(sc.alloc(&d_pcap, nf->P));
+        launch_split_pairs(nf->d_pkind, nf->P, d_near_idx, d_self_idx, d_u64, s);
+        NF_CUDA(cudaMemcpyAsync(h_u64, d_u64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        NF_CUDA(cudaStreamSynchronize(s));
+        n_near = (int64_t)h_u64[0];
+        n_self = (int64_t)h_u64[1];
+        wa.tab = ctx->d_tables;
+        wa.rule = ri;
+        wa.nq = nq;
+        wa.tv = mesh->d_tv;
+        wa.J = mesh->d_J;
+        wa.y = mesh->d_y;
+        wa.W = mesh->d_W;
+        wa.txy = nf->d_txy;
+        wa.tnode = nf->d_tnode;
+        wa.ptri = nf->d_ptri;
+        wa.ptgt = nf->d_ptgt;
+        wa.C = nf->d_C;
+        wa.pstat = d_pstat;
+        wa.pcap = d_pcap;
+        wa.flag = ctx->d_flag;
+        wa.eps = prm.eps;
+        wa.c_near = prm.c_near;
+        wa.depth_cap = prm.depth_cap;
+        PROF(ctx, ST_WEIGHTS_SELF, s, launch_weights_self(wa, d_self_idx, n_self, s));
+        PROF(ctx, ST_WEIGHTS_NEAR, s, launch_weights_near(wa, d_near_idx, n_near, s));
+        NF_CUDA(cudaGetLastError());
+
+        // statistics
+        nf->stats.n_targets = M;
+        nf->stats.n_nodes = N;
+        nf->stats.n_pairs = nf->P;
+        nf->stats.n_near = n_near;
+        nf->stats.n_self = n_self;
+        nf->stats.outside = M - n_self;
+        {
+            // leaves / panels per kind, capped leaves
+            int32_t* d_tmp;
+            NF_CUDA(sc.alloc(&d_tmp, 1));
+            unsigned long long h;
+            std::vector<int32_t> dummy;
+            (void)dummy;
+            // sums over all pairs split by kind: use the index lists
+            // near leaves: gather by summing pstat over near indices on the host side would need a copy;
+            // instead sum pstat over all pairs and self panels separately.
+            launch_sum_i32(d_pcap, nf->P, d_u64, s);
+            NF_CUDA(cudaMemcpyAsync(&h, d_u64, sizeof(h), cudaMemcpyDeviceToHost, s));
+            NF_CUDA(cudaStreamSynchronize(s));
+            nf->stats.depth_capped = (int64_t)h;
+            std::vector<int32_t> hstat(nf->P);
+            std::vector<uint8_t> hkind(nf->P);
+            if (nf->P) {
+                NF_CUDA(cudaMemcpyAsync(hstat.data(), d_pstat, nf->P * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                NF_CUDA(cudaMemcpyAsync(hkind.data(), nf->d_pkind, nf->P, cudaMemcpyDeviceToHost, s));
+                NF_CUDA(cudaStreamSynchronize(s));
+            }
+            int64_t leaves = 0, panels = 0;
+            for (int64_t i = 0; i < nf->P; i++) (hkind[i] ? panels : leaves) += hstat[i];
+            nf->stats.near_leaves = leaves;
+            nf->stats.self_panels = panels;
+        }
+
+        // float-float coordinates for the mixed far sum: origin at the centre
+        // of the node/target box, hi parts on the grid q = 2^(e - 22) with
+        // 2^e > the largest offset: |hi| / q <= 2^22 and every hi difference
+        // is a multiple of q below 2^24 q, hence exact in FP32.
+        {
+            const double ox = 0.5 * (std::min(mesh->bbox[0], h_tb[0]) + std::max(mesh->bbox[2], h_tb[2]));
+            const double oy = 0.5 * (std::min(mesh->bbox[1], h_tb[1]) + std::max(mesh->bbox[3], h_tb[3]));
+            double ext = 0;
+            ext = std::max(ext, std::fabs(mesh->bbox[0] - ox));
+            ext = std::max(ext, std::fabs(mesh->bbox[2] - ox));
+            ext = std::max(ext, std::fabs(mesh->bbox[1] - oy));
+            ext = std::max(ext, std::fabs(mesh->bbox[3] - oy));
+            ext = std::max(ext, std::fabs(h_tb[0] - ox));
+            ext = std::max(ext, std::fabs(h_tb[2] - ox));
+            ext = std::max(ext, std::fabs(h_tb[1] - oy));
+            ext = std::max(ext, std::fabs(h_tb[3] - oy));
+            int e = 0;
+            std::frexp(std::max(ext, 1e-300), &e);   // ext < 2^e
+            nf->ff_origin[0] = ox;
+            nf->ff_origin[1] = oy;
+            nf->ff_scale = std::ldexp(1.0, e - 22);
+            NF_CUDA(dev_alloc(&nf->src_ff.hi, 2 * N));
+            NF_CUDA(dev_alloc(&nf->src_ff.lo, 2 * N));
+            NF_CUDA(dev_alloc(&nf->tgt_ff.hi, 2 * M));
+            NF_CUDA(dev_alloc(&nf->tgt_ff.lo, 2 * M));
+            PROF(ctx, ST_FF_SPLIT, s, launch_ff_split(mesh->d_y, N, ox, oy, nf->ff_scale, nf->src_ff, s);
+                 launch_ff_split(nf->d_txy, M, ox, oy, nf->ff_scale, nf->tgt_ff, s));
+            NF_CUDA(cudaGetLastError());
+        }
+        rc = check_flag(ctx, ctx->d_flag, s);
+        if (rc) goto fail;
+    }
+    nf->stats.bytes_device = (int64_t)(M * (16 + 4 + 4 + 8 + 16 + 16) + 8 + nf->P * (4 + 4 + 1 + 8 * nq) + N * 16);
+    nf->stats.build_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    *out = nf;
+    return VP_OK;
+fail:
+    cudaStreamSynchronize(s);
+    free_nf_device(nf);
+    nf->magic = 0;
+    delete nf;
+    return rc;
+#undef NF_FAIL
+#undef NF_CUDA
+}
+
+int vp_nf_stats(const vp_nf* nf, vp_nf_stats_t* out) {
+    if (!nf_ok(nf)) return VP_ERR_STATE;
+    if (!out) return VP_ERR_INVALID_ARG;
+    *out = nf->stats;
+    return VP_OK;
+}
+
+int vp_nf_lists(const vp_nf* nf, int64_t* row_ptr_dev, int32_t* tri_dev, uint8_t* kind_dev, int32_t* tself_dev,
+                void* stream) {
+    if (!nf_ok(nf)) return VP_ERR_STATE;
+    vp_ctx* ctx = nf->ctx;
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (row_ptr_dev) VP_CUDA_TRY(ctx, cudaMemcpyAsync(row_ptr_dev, nf->d_row, (nf->M + 1) * 8, cudaMemcpyDeviceToDevice, s));
+    if (tri_dev && nf->P) VP_CUDA_TRY(ctx, cudaMemcpyAsync(tri_dev, nf->d_ptri, nf->P * 4, cudaMemcpyDeviceToDevice, s));
+    if (kind_dev && nf->P) VP_CUDA_TRY(ctx, cudaMemcpyAsync(kind_dev, nf->d_pkind, nf->P, cudaMemcpyDeviceToDevice, s));
+    if (tself_dev) VP_CUDA_TRY(ctx, cudaMemcpyAsync(tself_dev, nf->d_tself, nf->M * 4, cudaMemcpyDeviceToDevice, s));
+    return VP_OK;
+}
+
+int vp_nf_weights(const vp_nf* nf, double* w_dev, void* stream) {
+    if (!nf_ok(nf)) return VP_ERR_STATE;
+    vp_ctx* ctx = nf->ctx;
+    DevGuard g(ctx->device);
+    if (w_dev && nf->P)
+        VP_CUDA_TRY(ctx, cudaMemcpyAsync(w_dev, nf->d_C, nf->P * nf->mesh->nq * sizeof(double), cudaMemcpyDeviceToDevice,
+                                         (cudaStream_t)stream));
+    return VP_OK;
+}
+
+void vp_nf_release(vp_nf* nf) {
+    if (!nf_ok(nf)) return;
+    DevGuard g(nf->ctx->device);
+    cudaDeviceSynchronize();
+    free_nf_device(nf);
+    nf->magic = 0;
+    delete nf;
+}
+
+// ------------------------------------------------------------- evaluation
+static int eval_splits(const vp_ctx* ctx, int64_t M, int64_t N, int threads) {
+    const int64_t blocks = (M + threads - 1) / threads;
+    const int64_t want = 4LL * ctx->sm_count;
+    int64_t s = (want + blocks - 1) / blocks;
+    s = std::min<int64_t>(s, std::max<int64_t>(1, N / 1024));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(s, 64));
+}
+
+int vp_potential_eval(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, double* u_dev, int32_t precision,
+                      void* stream) {
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    if (!nf_ok(nf) || nf->ctx != ctx) return vp_set_error(ctx, VP_ERR_STATE, "vp_potential_eval: bad near-field handle");
+    if (!f_dev || !u_dev || d < 1 || d > 256 || (precision != VP_FP64 && precision != VP_MIXED))
+        return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_potential_eval: bad arguments");
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const vp_mesh* mesh = nf->mesh;
+    const int64_t N = mesh->N, M = nf->M;
+    const int splits = eval_splits(ctx, M, N, 128);
+    size_t partial_bytes = splits > 1 ? (size_t)splits * d * M * sizeof(double) : 0;
+    size_t q_bytes = precision == VP_MIXED ? (size_t)N * 16 * sizeof(float) : 0;
+    size_t off_q = (partial_bytes + 255) & ~(size_t)255;
+    int rc = ensure_ws(ctx, off_q + q_bytes + 256);
+    if (rc) return rc;
+    double* partial = splits > 1 ? (double*)ctx->ws : u_dev;
+    float* qbuf = (float*)((char*)ctx->ws + off_q);
+    if (precision == VP_FP64)
+        PROF(ctx, ST_FAR_FP64, s,
+             launch_far_fp64(mesh->d_y, mesh->d_W, N, f_dev, d, nf->d_txy, nf->d_tnode, M, partial, splits, s));
+    else
+        PROF(ctx, ST_FAR_FF, s,
+             launch_far_ff(nf->src_ff, mesh->d_W, N, f_dev, d, nf->tgt_ff, nf->d_tnode, M, partial, qbuf, splits, s));
+    VP_LAUNCH_CHECK(ctx);
+    if (splits > 1) PROF(ctx, ST_REDUCE, s, launch_reduce_splits(partial, splits, (int64_t)d * M, u_dev, s));
+    PROF(ctx, ST_APPLY, s, launch_apply_fp64(nf->d_row, nf->d_ptri, nf->d_C, mesh->nq, f_dev, N, d, M, u_dev, s));
+    VP_LAUNCH_CHECK(ctx);
+    return VP_OK;
+}
+
+int vp_potential_eval_host(vp_ctx* ctx, const vp_nf* nf, const double* f_host, int32_t d, double* u_host,
+                           int32_t precision, void* stream) {
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    if (!nf_ok(nf) || nf->ctx != ctx) return vp_set_error(ctx, VP_ERR_STATE, "vp_potential_eval_host: bad handle");
+    if (!f_host || !u_host || d < 1 || d > 256) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_potential_eval_host: bad arguments");
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = nf->mesh->N, M = nf->M;
+    const size_t fb = (size_t)d * N * sizeof(double), ub = (size_t)d * M * sizeof(double);
+    if (fb + ub > ctx->stage_bytes) {
+        if (ctx->stage) {
+            cudaStreamSynchronize(s);
+            cudaFree(ctx->stage);
+            ctx->stage = nullptr;
+            ctx->stage_bytes = 0;
+        }
+        VP_CUDA_TRY(ctx, cudaMalloc(&ctx->stage, fb + ub));
+        ctx->stage_bytes = fb + ub;
+    }
+    double* fd = ctx->stage;
+    double* ud = (double*)((char*)ctx->stage + fb);
+    VP_CUDA_TRY(ctx, cudaMemcpyAsync(fd, f_host, fb, cudaMemcpyHostToDevice, s));
+    int rc = vp_potential_eval(ctx, nf, fd, d, ud, precision, stream);
+    if (rc) return rc;
+    VP_CUDA_TRY(ctx, cudaMemcpyAsync(u_host, ud, ub, cudaMemcpyDeviceToHost, s));
+    VP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return VP_OK;
+}
+
+int vp_potential_eval_batch(vp_ctx* ctx, const vp_eval_item* items, int32_t n, int32_t precision, void* stream) {
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    if (n < 0 || (n > 0 && !items)) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_potential_eval_batch: bad arguments");
+    for (int32_t i = 0; i < n; i++) {
+        int rc = vp_potential_eval(ctx, items[i].nf, items[i].f_dev, items[i].d, items[i].u_dev, precision, stream);
+        if (rc) return rc;
+    }
+    return VP_OK;
+}
+
+int vp_profile_enable(vp_ctx* ctx, int32_t on) {
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    ctx->prof = on != 0;
+    return VP_OK;
+}
+
+int vp_profile_reset(vp_ctx* ctx) {
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    DevGuard g(ctx->device);
+    prof_collect(ctx);
+    for (int i = 0; i < ST_COUNT; i++) {
+        ctx->prof_ms[i] = 0;
+        ctx->prof_n[i] = 0;
+    }
+    return VP_OK;
+}
+
+int vp_profile_read(vp_ctx* ctx, char* names, int64_t* counts, double* ms, int32_t cap, int32_t* n) {
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    DevGuard g(ctx->device);
+    prof_collect(ctx);
+    if (n) *n = ST_COUNT;
+    for (int i = 0; i < ST_COUNT && i < cap; i++) {
+        if (names) {
+            std::memset(names + 32 * i, 0, 32);
+            std::strncpy(names + 32 * i, kStageNames[i], 31);
+        }
+        if (counts) counts[i] = ctx->prof_n[i];
+        if (ms) ms[i] = ctx->prof_ms[i];
+    }
+    return VP_OK;
+}
+
+int vp_rule_table(int32_t which, double* x, double* y, double* w, double* what, int32_t cap, int32_t* n) {
+    const double *X = nullptr, *Y = nullptr, *Wt = nullptr;
+    double wh = 0.0;
+    int32_t len = 0;
+    switch (which) {
+        case 16: X = VP_FAR16_X; Y = VP_FAR16_Y; Wt = VP_FAR16_W; wh = VP_FAR16_WHAT; len = 16; break;
+        case 19: X = VP_FAR19_X; Y = VP_FAR19_Y; Wt = VP_FAR19_W; wh = VP_FAR19_WHAT; len = 19; break;
+        case 49: X = VP_NEAR49_X; Y = VP_NEAR49_Y; Wt = VP_NEAR49_W; wh = VP_NEAR49_WHAT; len = 49; break;
+        case 8: X = VP_GGQ8_R; Wt = VP_GGQ8_W; len = 8; break;
+        case 116: X = VP_GL16_X; Wt = VP_GL16_W; len = 16; break;
+        default: return VP_ERR_INVALID_ARG;
+    }
+    if (n) *n = len;
+    if (cap < len) return VP_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < len; i++) {
+        if (x) x[i] = X[i];
+        if (y) y[i] = Y ? Y[i] : 0.0;
+        if (w) w[i] = Wt[i];
+    }
+    if (what) *what = wh;
+    return VP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// Device helpers of libvp: exact-rounding geometric predicates, the kernel G,
+// and the Koornwinder basis of P_4 on the reference simplex.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define VP_NB 15            // dim P_4
+#define VP_MAXQ 19          // largest far rule
+#define VP_NNEAR 49         // near rule length
+#define VP_NGGQ 8
+#define VP_NGL 16
+#define VP_INV_TWO_PI 0.15915494309189533576888376337251
+#define VP_INV_FOUR_PI 0.079577471545947667884441881686257
+
+// Quadrature tables in device global memory (read through L1).
+struct VpTables {
+    double fx[2][VP_MAXQ], fy[2][VP_MAXQ], fw[2][VP_MAXQ];   // [0] = 16-point, [1] = 19-point
+    double far_what[2];
+    int nq[2], far_degree[2];
+    double nx[VP_NNEAR], ny[VP_NNEAR], nw[VP_NNEAR];
+    double near_what;
+    int near_degree;
+    double gr[VP_NGGQ], gw[VP_NGGQ], glogr[VP_NGGQ];
+    double lx[VP_NGL], lw[VP_NGL];
+    // projection rows: Pk[rule][k][a] = w_k K_a(xi_k)
+    double Pk[2][VP_MAXQ][VP_NB];
+};
+
+// ------------------------------------------------------------------------
+// Predicates evaluated with explicit round-to-nearest operations (no fused
+// multiply-add), in the operation order of the definitions, so that every
+// decision is the one an IEEE FP64 evaluation of the formula makes.
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rn_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double rn_sqrt(double a) { return __dsqrt_rn(a); }
+
+// o_PQ(X) = (Q - P) x (X - P) = (qx-px)(xy-py) - (qy-py)(xx-px)
+__device__ __forceinline__ double orient_rn(double px, double py, double qx, double qy, double xx, double xy) {
+    double a = rn_mul(rn_sub(qx, px), rn_sub(xy, py));
+    double b = rn_mul(rn_sub(qy, py), rn_sub(xx, px));
+    return rn_sub(a, b);
+}
+
+// Membership of X in the open Bernstein ellipse of the edge PQ with
+// parameter R^(1/N) (Section 4.1): rho_X^N < R, with s = (|X-P|+|X-Q|)/|Q-P|,
+// rho_X = s + sqrt(max(s^2 - 1, 0)), rho_X^N a left-to-right product.
+__device__ __forceinline__ bool edge_near_rn(double px, double py, double qx, double qy, double xx, double xy, int N,
+                                             double R) {
+    double ex = rn_sub(qx, px), ey = rn_sub(qy, py);
+    double L = rn_sqrt(rn_add(rn_mul(ex, ex), rn_mul(ey, ey)));
+    double ax = rn_sub(xx, px), ay = rn_sub(xy, py), bx = rn_sub(xx, qx), by = rn_sub(xy, qy);
+    double s = rn_div(rn_add(rn_sqrt(rn_add(rn_mul(ax, ax), rn_mul(ay, ay))),
+                             rn_sqrt(rn_add(rn_mul(bx, bx), rn_mul(by, by)))), L);
+    double t = rn_sub(rn_mul(s, s), 1.0);
+    if (t < 0.0) t = 0.0;
+    double rho = rn_add(s, rn_sqrt(t));
+    double p = rho;
+    for (int i = 1; i < N; i++) p = rn_mul(p, rho);
+    return p < R;
+}
+
+__device__ __forceinline__ bool tri_near_rn(const double* v, double xx, double xy, int N, double R) {
+    return edge_near_rn(v[0], v[1], v[2], v[3], xx, xy, N, R) || edge_near_rn(v[2], v[3], v[4], v[5], xx, xy, N, R) ||
+           edge_near_rn(v[4], v[5], v[0], v[1], xx, xy, N, R);
+}
+
+__device__ __forceinline__ bool tri_contains_rn(const double* v, double xx, double xy) {
+    return orient_rn(v[0], v[1], v[2], v[3], xx, xy) >= 0.0 && orient_rn(v[2], v[3], v[4], v[5], xx, xy) >= 0.0 &&
+           orient_rn(v[4], v[5], v[0], v[1], xx, xy) >= 0.0;
+}
+
+// R = (w J) / (eps C_N)   (Eq. rho0 raised to the power N)
+__device__ __forceinline__ double ellipse_R_rn(double what, double J, double eps, double cn) {
+    return rn_div(rn_mul(what, J), rn_mul(eps, cn));
+}
+
+// G(x, y) = log|x - y| / 2pi, from the squared distance.
+__device__ __forceinline__ double kernel_G(double dx, double dy) {
+    return log(dx * dx + dy * dy) * (0.5 * VP_INV_TWO_PI);
+}
+
+// ------------------------------------------------------------------------
+// Koornwinder polynomials (Section 2.1), orthonormal on the reference
+// simplex: K_mn(x,y) = c_mn (1-x)^m P_{n-m}^{(2m+1,0)}(2x-1) P_m(2y/(1-x) - 1),
+// c_mn = sqrt(2 (n+1) (2m+1)), index a = n(n+1)/2 + m, 0 <= m <= n <= 4.
+// (1-x)^m P_m(2y/(1-x) - 1) is evaluated by the homogeneous Legendre
+// recurrence Q_{m+1} = ((2m+1) Q_1 Q_m - m (1-x)^2 Q_{m-1}) / (m+1),
+// Q_0 = 1, Q_1 = 2y + x - 1, which needs no division by 1 - x.
+__host__ __device__ __forceinline__ void koornwinder4(double x, double y, double* K) {
+    const double omx = 1.0 - x;
+    const double omx2 = omx * omx;
+    const double z = 2.0 * x - 1.0;
+    double Q[5];
+    Q[0] = 1.0;
+    Q[1] = 2.0 * y + x - 1.0;
+    Q[2] = (3.0 * Q[1] * Q[1] - omx2) * 0.5;
+    Q[3] = (5.0 * Q[1] * Q[2] - 2.0 * omx2 * Q[1]) * (1.0 / 3.0);
+    Q[4] = (7.0 * Q[1] * Q[3] - 3.0 * omx2 * Q[2]) * 0.25;
+#pragma unroll
+    for (int m = 0; m <= 4; m++) {
+        const double a = 2.0 * m + 1.0;
+        // Jacobi P_k^{(a,0)}(z), k = 0..4-m
+        double pkm1 = 1.0, pk = 0.5 * ((a + 2.0) * z + a);
+#pragma unroll
+        for (int n = m; n <= 4; n++) {
+            const int k = n - m;
+            double Pj;
+            if (k == 0) Pj = 1.0;
+            else if (k == 1) Pj = pk;
+            else {
+                // advance from (P_{k-2}, P_{k-1}) to P_k
+                const double kk = k - 1.0;  // recurrence index
+                const double c1 = 2.0 * kk + a;
+                const double num = (c1 + 1.0) * ((c1 + 2.0) * c1 * z + a * a) * pk - 2.0 * kk * (kk + a) * (c1 + 2.0) * pkm1;
+                const double den = 2.0 * (kk + 1.0) * (kk + a + 1.0) * c1;
+                const double pn = num / den;
+                pkm1 = pk;
+                pk = pn;
+                Pj = pn;
+            }
+            const double c = sqrt(2.0 * (n + 1.0) * (2.0 * m + 1.0));
+            K[n * (n + 1) / 2 + m] = c * Q[m] * Pj;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// Bounded-wait helpers: status flags live in device memory and are read by
+// the host after synchronisation.
+#define VP_DEV_ERR_STACK 1
+#define VP_DEV_ERR_BADIDX 2
+#define VP_DEV_ERR_DEGEN 4
+#define VP_DEV_ERR_NONFINITE 8
+#define VP_DEV_ERR_CELL 16

@@ -1,0 +1,174 @@
+// Internal structures of libvp (host side).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/vp.h"
+#include "vp_device.cuh"
+
+// Far-field source/target coordinates in float-float: value = hi + lo, with
+// hi on a fixed dyadic grid of spacing q so that hi_t - hi_s is exact in FP32.
+struct FFCoords {
+    float* hi = nullptr;  // [n][2]
+    float* lo = nullptr;  // [n][2]
+};
+
+enum VpStage {
+    ST_MESH_NODES = 0, ST_TRI_GEOM, ST_TRI_CELLS, ST_CELL_SORT, ST_TARGET_CELLS, ST_LOCATE, ST_LIST_COUNT,
+    ST_LIST_FILL, ST_WEIGHTS_SELF, ST_WEIGHTS_NEAR, ST_FF_SPLIT, ST_FAR_FP64, ST_FAR_FF, ST_REDUCE, ST_APPLY,
+    ST_COUNT
+};
+
+struct ProfRec {
+    int stage;
+    cudaEvent_t a, b;
+};
+
+struct vp_ctx {
+    int device = 0;
+    int sm_count = 0;
+    std::string last_error;
+    VpTables* d_tables = nullptr;
+    VpTables h_tables;
+    int32_t* d_flag = nullptr;     // device error flags (one int)
+    // evaluation workspace (grown on demand)
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    // staging for the host-buffer entry point
+    double* stage = nullptr;
+    size_t stage_bytes = 0;
+    // profiling (see vp_profile_enable)
+    bool prof = false;
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[ST_COUNT] = {0};
+    int64_t prof_n[ST_COUNT] = {0};
+    int magic = 0x56504358;
+};
+
+// Stage timing helpers (no-ops unless profiling is enabled).
+void prof_begin(vp_ctx* ctx, int stage, cudaStream_t s, ProfRec& r);
+void prof_end(vp_ctx* ctx, cudaStream_t s, ProfRec& r);
+void prof_collect(vp_ctx* ctx);
+
+struct vp_mesh {
+    vp_ctx* ctx = nullptr;
+    int64_t nt = 0, nv = 0, N = 0;
+    int nq = 0, rule_index = 0;  // rule_index 0: 16 nodes, 1: 19 nodes
+    double* d_tv = nullptr;      // [nt][6] counter-clockwise vertex coordinates
+    double* d_J = nullptr;       // [nt] J_T = 2 area
+    double* d_y = nullptr;       // [N][2]
+    double* d_W = nullptr;       // [N]
+    double bbox[4] = {0, 0, 0, 0};
+    int magic = 0x56504d48;
+};
+
+struct vp_nf {
+    vp_ctx* ctx = nullptr;
+    const vp_mesh* mesh = nullptr;
+    int64_t M = 0, P = 0, n_extra = 0;
+    int node_targets = 0;
+    vp_nf_params params{};
+    double* d_txy = nullptr;      // [M][2]
+    int32_t* d_tself = nullptr;   // [M]
+    int32_t* d_tnode = nullptr;   // [M]
+    int64_t* d_row = nullptr;     // [M+1]
+    int32_t* d_ptri = nullptr;    // [P]
+    int32_t* d_ptgt = nullptr;    // [P]
+    uint8_t* d_pkind = nullptr;   // [P]
+    double* d_C = nullptr;        // [P][nq]
+    FFCoords src_ff, tgt_ff;      // float-float copies for the mixed far sum
+    double ff_origin[2] = {0, 0};
+    double ff_scale = 1.0;         // grid spacing q of the hi parts
+    vp_nf_stats_t stats{};
+    int magic = 0x56504e46;
+};
+
+// ----------------------------------------------------------- utilities
+#define VP_CUDA_TRY(ctx, expr)                                                              \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess) {                                                            \
+            if (ctx) (ctx)->last_error = std::string(#expr) + ": " + cudaGetErrorString(_e); \
+            return _e == cudaErrorMemoryAllocation ? VP_ERR_OOM : VP_ERR_CUDA;              \
+        }                                                                                   \
+    } while (0)
+
+// Launch-time error check (async errors are caught at the next sync).
+#define VP_LAUNCH_CHECK(ctx) VP_CUDA_TRY(ctx, cudaGetLastError())
+
+int vp_set_error(vp_ctx* ctx, int code, const std::string& msg);
+
+// ----------------------------------------------------------- launchers
+// scan: out[0] = 0, out[i+1] = sum_{j<=i} in[j] (int32 or int64 input), n >= 0
+int vp_exclusive_scan_i32(vp_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+int vp_exclusive_scan_i64(vp_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+
+// mesh
+void launch_mesh_nodes(const double* vxy, int64_t nv, const int32_t* tri, int64_t nt, const VpTables* tab, int rule,
+                       double* tv, double* J, double* y, double* W, int32_t* flag, cudaStream_t s);
+
+// lists
+struct GridDev {
+    double ox, oy, h;
+    int32_t nx, ny;
+    const int64_t* cell_start;  // [ncell+1]
+    const int32_t* cell_tri;    // sorted ascending per cell
+};
+void launch_tri_geom(const double* tv, const double* J, int64_t nt, double what, int N, double eps, double cn,
+                     double* R, double* bbox, cudaStream_t s);
+void launch_bbox_reduce(const double* bbox, int64_t n, int stride, double* out4, cudaStream_t s);
+void launch_tri_cell_count(const double* bbox, int64_t nt, GridDev g, int32_t* cnt, cudaStream_t s);
+void launch_tri_cell_fill(const double* bbox, int64_t nt, GridDev g, int64_t* cursor, int32_t* cell_tri,
+                          cudaStream_t s);
+void launch_cell_sort(GridDev g, int64_t ncell, int32_t max_count, int32_t* cell_tri, int32_t* flag,
+                      cudaStream_t s);
+void launch_max_i32(const int32_t* a, int64_t n, int32_t* out, cudaStream_t s);
+void launch_targets_init(const double* ynode, int64_t N, int nq, int node_targets, const double* extra, int64_t m,
+                         double* txy, int32_t* tnode, int32_t* tself, cudaStream_t s);
+void launch_target_cells(const double* txy, int64_t M, GridDev g, int32_t* tcell, int32_t* cnt, cudaStream_t s);
+void launch_target_order(const int32_t* tcell, int64_t M, int64_t* cursor, int32_t* order, cudaStream_t s);
+void launch_locate(const double* tv, const double* txy, const int32_t* order, const int32_t* tcell, int64_t M,
+                   GridDev g, int32_t* tself, cudaStream_t s);
+void launch_list_pass(const double* tv, const double* R, int N, const double* txy, const int32_t* tself,
+                      const int32_t* order, const int32_t* tcell, int64_t M, GridDev g, int32_t* count,
+                      const int64_t* row, int32_t* ptri, int32_t* ptgt, uint8_t* pkind, cudaStream_t s);
+void launch_split_pairs(const uint8_t* pkind, int64_t P, int32_t* near_idx, int32_t* self_idx,
+                        unsigned long long* counters, cudaStream_t s);
+
+// weights
+struct WeightsArgs {
+    const VpTables* tab;
+    int rule;
+    int nq;
+    const double* tv;
+    const double* J;
+    const double* y;
+    const double* W;
+    const double* txy;
+    const int32_t* tnode;
+    const int32_t* ptri;
+    const int32_t* ptgt;
+    double* C;
+    int32_t* pstat;     // per pair: leaves or panels
+    int32_t* pcap;      // per pair: depth-capped leaves
+    int32_t* flag;
+    double eps, c_near;
+    int depth_cap;
+};
+void launch_weights_self(const WeightsArgs& a, const int32_t* idx, int64_t n, cudaStream_t s);
+void launch_weights_near(const WeightsArgs& a, const int32_t* idx, int64_t n, cudaStream_t s);
+void launch_sum_i32(const int32_t* a, int64_t n, unsigned long long* out, cudaStream_t s);
+
+// evaluation
+void launch_far_fp64(const double* y, const double* W, int64_t N, const double* f, int d, const double* txy,
+                     const int32_t* tnode, int64_t M, double* partial, int splits, cudaStream_t s);
+void launch_far_ff(const FFCoords& src, const double* W, int64_t N, const double* f, int d, const FFCoords& tgt,
+                   const int32_t* tnode, int64_t M, double* partial, float* qbuf, int splits, cudaStream_t s);
+void launch_reduce_splits(const double* partial, int splits, int64_t count, double* out, cudaStream_t s);
+void launch_apply_fp64(const int64_t* row, const int32_t* ptri, const double* C, int nq, const double* f, int64_t N,
+                       int d, int64_t M, double* u, cudaStream_t s);
+void launch_ff_split(const double* xy, int64_t n, double ox, double oy, double q, FFCoords out, cudaStream_t s);

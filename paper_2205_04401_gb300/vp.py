@@ -1,0 +1,357 @@
+"""Python binding of libvp (include/vp.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module only turns
+torch tensors into pointers and status codes into exceptions.  There is no
+CPU fallback: if libvp cannot be built or loaded, or no sm_103 GPU is
+present, the calls raise.
+
+    ctx  = Context(0)
+    mesh = mesh_upload(ctx, vxy, tri, rule=19)             # host numpy arrays
+    nf   = nearfield_build(ctx, mesh, node_targets=True, txy=extra_dev)
+    u    = potential_eval(ctx, nf, f_dev, precision=VP_MIXED)   # f_dev: [d][N] cuda float64
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+VP_OK = 0
+VP_RULE_16_D8 = 16
+VP_RULE_19_D9 = 19
+VP_FP64 = 0
+VP_MIXED = 1
+
+_lib = None
+
+
+class VPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} ({code})")
+        self.code = code
+
+
+class NfParams(C.Structure):
+    _fields_ = [("eps", C.c_double), ("c_far", C.c_double), ("c_near", C.c_double),
+                ("depth_cap", C.c_int32), ("reserved", C.c_int32)]
+
+
+class NfStats(C.Structure):
+    _fields_ = [("n_targets", C.c_int64), ("n_nodes", C.c_int64), ("n_pairs", C.c_int64), ("n_self", C.c_int64),
+                ("n_near", C.c_int64), ("near_leaves", C.c_int64), ("self_panels", C.c_int64),
+                ("depth_capped", C.c_int64), ("outside", C.c_int64), ("bytes_device", C.c_int64),
+                ("build_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class EvalItem(C.Structure):
+    _fields_ = [("nf", C.c_void_p), ("f_dev", C.c_void_p), ("d", C.c_int32), ("u_dev", C.c_void_p)]
+
+
+SIGNATURES = {
+    "vp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
+    "vp_destroy": (None, [C.c_void_p]),
+    "vp_status_str": (C.c_char_p, [C.c_int]),
+    "vp_last_error": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int32]),
+    "vp_mesh_upload": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                                 C.POINTER(C.c_void_p)]),
+    "vp_mesh_upload_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
+                                     C.c_void_p, C.POINTER(C.c_void_p)]),
+    "vp_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+    "vp_profile_reset": (C.c_int, [C.c_void_p]),
+    "vp_profile_read": (C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    "vp_mesh_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "vp_mesh_nodes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vp_mesh_release": (None, [C.c_void_p]),
+    "vp_nearfield_build": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.POINTER(NfParams),
+                                     C.c_void_p, C.POINTER(C.c_void_p)]),
+    "vp_nf_stats": (C.c_int, [C.c_void_p, C.POINTER(NfStats)]),
+    "vp_nf_lists": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vp_nf_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vp_nf_release": (None, [C.c_void_p]),
+    "vp_potential_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
+    "vp_potential_eval_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
+                                         C.c_void_p]),
+    "vp_potential_eval_batch": (C.c_int, [C.c_void_p, C.POINTER(EvalItem), C.c_int32, C.c_int32, C.c_void_p]),
+    "vp_rule_table": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int32,
+                                C.POINTER(C.c_int32)]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libvp (building it first if its sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_needed:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libvp not found at {_build.LIB}; run paper_2205_04401_gb300/build.py")
+    lib = C.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, ctx=None, what=""):
+    if rc == VP_OK:
+        return
+    lib = load()
+    msg = lib.vp_status_str(rc).decode()
+    if ctx is not None and ctx.handle:
+        buf = C.create_string_buffer(512)
+        lib.vp_last_error(ctx.handle, buf, 512)
+        msg += ": " + buf.value.decode()
+    raise VPError(rc, f"{what}: {msg}")
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, dtype_name):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"expected a CUDA tensor ({dtype_name})")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"expected torch.{dtype_name}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A libvp context on one CUDA device (vp_create / vp_destroy)."""
+
+    def __init__(self, device: int = 0):
+        lib = load()
+        h = C.c_void_p()
+        rc = lib.vp_create(C.byref(h), int(device))
+        if rc != VP_OK:
+            raise VPError(rc, f"vp_create(device={device}): {lib.vp_status_str(rc).decode()}")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().vp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    def __init__(self, ctx, handle, nt, N, nq):
+        self.ctx, self.handle, self.nt, self.N, self.nq = ctx, handle, nt, N, nq
+
+    def release(self):
+        if self.handle:
+            load().vp_mesh_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class NearField:
+    def __init__(self, ctx, mesh, handle, M):
+        self.ctx, self.mesh, self.handle, self.M = ctx, mesh, handle, M
+
+    def release(self):
+        if self.handle:
+            load().vp_nf_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def mesh_upload(ctx: Context, vxy, tri, rule: int = VP_RULE_19_D9, stream=None) -> Mesh:
+    lib = load()
+    vxy = np.ascontiguousarray(vxy, np.float64)
+    tri = np.ascontiguousarray(tri, np.int32)
+    h = C.c_void_p()
+    rc = lib.vp_mesh_upload(ctx.handle, vxy.ctypes.data_as(C.c_void_p), C.c_int64(len(vxy)),
+                            tri.ctypes.data_as(C.c_void_p), C.c_int64(len(tri)), C.c_int32(rule), _stream(stream),
+                            C.byref(h))
+    _check(rc, ctx, "vp_mesh_upload")
+    nt, N, nq = C.c_int64(), C.c_int64(), C.c_int32()
+    _check(lib.vp_mesh_info(h, C.byref(nt), C.byref(N), C.byref(nq)), ctx, "vp_mesh_info")
+    return Mesh(ctx, h, nt.value, N.value, nq.value)
+
+
+def mesh_upload_dev(ctx: Context, vxy_dev, tri_dev, rule: int = VP_RULE_19_D9, stream=None) -> Mesh:
+    """vp_mesh_upload_dev: vertices [nv][2] float64 and triangles [nt][3] int32 already on the device."""
+    lib = load()
+    h = C.c_void_p()
+    rc = lib.vp_mesh_upload_dev(ctx.handle, _dptr(vxy_dev, "float64"), C.c_int64(vxy_dev.shape[0]),
+                                _dptr(tri_dev, "int32"), C.c_int64(tri_dev.shape[0]), C.c_int32(rule),
+                                _stream(stream), C.byref(h))
+    _check(rc, ctx, "vp_mesh_upload_dev")
+    nt, N, nq = C.c_int64(), C.c_int64(), C.c_int32()
+    _check(lib.vp_mesh_info(h, C.byref(nt), C.byref(N), C.byref(nq)), ctx, "vp_mesh_info")
+    return Mesh(ctx, h, nt.value, N.value, nq.value)
+
+
+def profile_enable(ctx: Context, on: bool = True):
+    _check(load().vp_profile_enable(ctx.handle, 1 if on else 0), ctx, "vp_profile_enable")
+
+
+def profile_reset(ctx: Context):
+    _check(load().vp_profile_reset(ctx.handle), ctx, "vp_profile_reset")
+
+
+def profile_read(ctx: Context) -> dict:
+    """{stage: (launches timed, summed device ms)} from the library's CUDA events."""
+    cap = 64
+    names = C.create_string_buffer(32 * cap)
+    counts = np.zeros(cap, np.int64)
+    ms = np.zeros(cap, np.float64)
+    n = C.c_int32()
+    _check(load().vp_profile_read(ctx.handle, names, counts.ctypes.data_as(C.c_void_p), ms.ctypes.data_as(C.c_void_p),
+                                  cap, C.byref(n)), ctx, "vp_profile_read")
+    out = {}
+    for i in range(min(n.value, cap)):
+        name = names.raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[name] = (int(counts[i]), float(ms[i]))
+    return out
+
+
+def mesh_nodes(mesh: Mesh, stream=None):
+    import torch
+    y = torch.empty((mesh.N, 2), dtype=torch.float64, device=f"cuda:{mesh.ctx.device}")
+    w = torch.empty((mesh.N,), dtype=torch.float64, device=f"cuda:{mesh.ctx.device}")
+    _check(load().vp_mesh_nodes(mesh.handle, _dptr(y, "float64"), _dptr(w, "float64"), _stream(stream)), mesh.ctx,
+           "vp_mesh_nodes")
+    return y, w
+
+
+def nearfield_build(ctx: Context, mesh: Mesh, node_targets: bool = True, txy=None, eps: float = 1e-12,
+                    c_far: float = 1.0, c_near: float = 12.0, depth_cap: int = 30, stream=None) -> NearField:
+    lib = load()
+    m = 0 if txy is None else int(txy.shape[0])
+    p = NfParams(eps, c_far, c_near, depth_cap, 0)
+    h = C.c_void_p()
+    rc = lib.vp_nearfield_build(ctx.handle, mesh.handle, C.c_int32(1 if node_targets else 0),
+                                _dptr(txy, "float64") if m else None, C.c_int64(m), C.byref(p), _stream(stream),
+                                C.byref(h))
+    _check(rc, ctx, "vp_nearfield_build")
+    M = (mesh.N if node_targets else 0) + m
+    return NearField(ctx, mesh, h, M)
+
+
+def nf_stats(nf: NearField) -> dict:
+    s = NfStats()
+    _check(load().vp_nf_stats(nf.handle, C.byref(s)), nf.ctx, "vp_nf_stats")
+    return s.as_dict()
+
+
+def nf_lists(nf: NearField, stream=None):
+    import torch
+    st = nf_stats(nf)
+    dev = f"cuda:{nf.ctx.device}"
+    row = torch.empty(nf.M + 1, dtype=torch.int64, device=dev)
+    tri = torch.empty(max(1, st["n_pairs"]), dtype=torch.int32, device=dev)
+    kind = torch.empty(max(1, st["n_pairs"]), dtype=torch.uint8, device=dev)
+    tself = torch.empty(nf.M, dtype=torch.int32, device=dev)
+    _check(load().vp_nf_lists(nf.handle, _dptr(row, "int64"), _dptr(tri, "int32"), _dptr(kind, "uint8"),
+                              _dptr(tself, "int32"), _stream(stream)), nf.ctx, "vp_nf_lists")
+    P = st["n_pairs"]
+    return row, tri[:P], kind[:P], tself
+
+
+def nf_weights(nf: NearField, stream=None):
+    import torch
+    P = nf_stats(nf)["n_pairs"]
+    w = torch.empty((max(1, P), nf.mesh.nq), dtype=torch.float64, device=f"cuda:{nf.ctx.device}")
+    _check(load().vp_nf_weights(nf.handle, _dptr(w, "float64"), _stream(stream)), nf.ctx, "vp_nf_weights")
+    return w[:P]
+
+
+def potential_eval(ctx: Context, nf: NearField, f, precision: int = VP_FP64, out=None, stream=None):
+    """u [d][M] on the device for densities f [d][N] (CUDA float64)."""
+    import torch
+    if f.dim() == 1:
+        f = f.unsqueeze(0)
+    d = int(f.shape[0])
+    if f.shape[1] != nf.mesh.N:
+        raise ValueError("f must be [d][N]")
+    if out is None:
+        out = torch.empty((d, nf.M), dtype=torch.float64, device=f.device)
+    rc = load().vp_potential_eval(ctx.handle, nf.handle, _dptr(f, "float64"), C.c_int32(d), _dptr(out, "float64"),
+                                  C.c_int32(precision), _stream(stream))
+    _check(rc, ctx, "vp_potential_eval")
+    return out
+
+
+def potential_eval_host(ctx: Context, nf: NearField, f_host: np.ndarray, precision: int = VP_FP64, out=None,
+                        stream=None):
+    """Same as potential_eval with host buffers (numpy or pinned CPU tensors)."""
+    f_host = f_host if not isinstance(f_host, np.ndarray) else np.ascontiguousarray(np.atleast_2d(f_host), np.float64)
+    d = int(f_host.shape[0])
+    if out is None:
+        out = np.empty((d, nf.M), dtype=np.float64)
+    fp = f_host.ctypes.data_as(C.c_void_p) if isinstance(f_host, np.ndarray) else C.c_void_p(f_host.data_ptr())
+    up = out.ctypes.data_as(C.c_void_p) if isinstance(out, np.ndarray) else C.c_void_p(out.data_ptr())
+    rc = load().vp_potential_eval_host(ctx.handle, nf.handle, fp, C.c_int32(d), up, C.c_int32(precision),
+                                       _stream(stream))
+    _check(rc, ctx, "vp_potential_eval_host")
+    return out
+
+
+def potential_eval_batch(ctx: Context, items, precision: int = VP_FP64, stream=None):
+    """items: list of (nf, f [d][N] cuda, u [d][M] cuda)."""
+    arr = (EvalItem * len(items))()
+    for i, (nf, f, u) in enumerate(items):
+        arr[i].nf = nf.handle
+        arr[i].f_dev = f.data_ptr()
+        arr[i].d = int(f.shape[0])
+        arr[i].u_dev = u.data_ptr()
+    rc = load().vp_potential_eval_batch(ctx.handle, arr, C.c_int32(len(items)), C.c_int32(precision), _stream(stream))
+    _check(rc, ctx, "vp_potential_eval_batch")
+
+
+def rule_table(which: int):
+    """(x, y, w, what) of a compiled rule: 16, 19 (far), 49 (near), 8 (radial), 116 (arc-length)."""
+    lib = load()
+    cap = 64
+    x, y, w = (np.zeros(cap) for _ in range(3))
+    what = C.c_double()
+    n = C.c_int32()
+    _check(lib.vp_rule_table(which, x.ctypes.data_as(C.c_void_p), y.ctypes.data_as(C.c_void_p),
+                             w.ctypes.data_as(C.c_void_p), C.byref(what), cap, C.byref(n)), None, "vp_rule_table")
+    k = n.value
+    return x[:k].copy(), y[:k].copy(), w[:k].copy(), what.value

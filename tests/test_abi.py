@@ -1,0 +1,71 @@
+"""The C-ABI library builds, loads, exports every symbol include/vp.h
+declares, and carries quadrature tables bit-identical to the oracle's
+independently generated ones.  No GPU needed."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = ""
+    for name in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if name.endswith(".h"):
+            src += open(os.path.join(ROOT, "include", name)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vp_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2205_04401_gb300 import vp
+    return vp.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["vp_mesh_upload", "vp_nearfield_build", "vp_potential_eval", "vp_potential_eval_batch"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    assert lib.vp_status_str(0) == b"VP_OK"
+    assert lib.vp_status_str(-7) == b"VP_ERR_NO_DEVICE"
+    assert lib.vp_status_str(5) == b"VP_UNKNOWN"
+
+
+@pytest.mark.parametrize("which,name", [(16, "far16"), (19, "far19"), (49, "near49")])
+def test_tables_match_oracle_bitwise(tables, which, name):
+    from paper_2205_04401_gb300 import vp
+    x, y, w, what = vp.rule_table(which)
+    r = tables[name]
+    assert np.array_equal(x, r["x"]) and np.array_equal(y, r["y"]) and np.array_equal(w, r["w"])
+    assert what == r["what"]
+
+
+def test_1d_tables_match_oracle_bitwise(tables):
+    from paper_2205_04401_gb300 import vp
+    x, _, w, _ = vp.rule_table(8)
+    assert np.array_equal(x, tables["ggq8"]["r"]) and np.array_equal(w, tables["ggq8"]["w"])
+    x, _, w, _ = vp.rule_table(116)
+    assert np.array_equal(x, tables["gl16"]["x"]) and np.array_equal(w, tables["gl16"]["w"])
+
+
+def test_bad_arguments_return_codes(lib):
+    # invalid handles and arguments are reported, never crash
+    assert lib.vp_potential_eval(None, None, None, 1, None, 0, None) == -8
+    assert lib.vp_mesh_upload(None, None, 0, None, 0, 19, None, None) == -8
+    h = C.c_void_p()
+    rc = lib.vp_create(C.byref(h), 10_000)
+    assert rc == -7 and not h.value
+    n = C.c_int32()
+    assert lib.vp_rule_table(7, None, None, None, None, 64, C.byref(n)) == -1

@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars (stated per result):
+* nodes, point location and near/self lists: bit-exact (integer output of
+  FP64 predicates evaluated without fused multiply-add on both sides);
+* FP64 potential: max_t |u - u_ref| / max_t |u_ref| <= 1e-12 per density;
+* mixed potential (compensated FP32 far sum): <= 1e-10 per density;
+* correction weights: |dC| <= 1e-12 max|C| of the pair plus 1e-15 |J_T|
+  (same subdivision trees on both sides, so only rounding differs).
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2205_04401_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_04401_gb300 import vp as _vp
+    return _vp
+
+
+@pytest.fixture(scope="module")
+def ctx(vp):
+    return vp.Context(0)
+
+
+def rel_err(u, ref):
+    u = np.atleast_2d(u)
+    ref = np.atleast_2d(ref)
+    return np.max(np.abs(u - ref), axis=1) / np.max(np.abs(ref), axis=1)
+
+
+def gpu_run(vp, ctx, vxy, tri, rule, extra=None, node_targets=True, f=None, precisions=(0,)):
+    mesh = vp.mesh_upload(ctx, vxy, tri, rule)
+    txy = None if extra is None or len(extra) == 0 else torch.from_numpy(np.ascontiguousarray(extra)).cuda()
+    nf = vp.nearfield_build(ctx, mesh, node_targets=node_targets, txy=txy)
+    y, w = vp.mesh_nodes(mesh)
+    row, ptri, kind, tself = vp.nf_lists(nf)
+    C = vp.nf_weights(nf)
+    out = dict(mesh=mesh, nf=nf, y=y.cpu().numpy(), w=w.cpu().numpy(), row=row.cpu().numpy(),
+               ptri=ptri.cpu().numpy(), kind=kind.cpu().numpy(), tself=tself.cpu().numpy(), C=C.cpu().numpy(),
+               stats=vp.nf_stats(nf))
+    if f is not None:
+        fd = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+        for p in precisions:
+            out[f"u{p}"] = vp.potential_eval(ctx, nf, fd, precision=p).cpu().numpy()
+    torch.cuda.synchronize()
+    return out
+
+
+def compare_weights(Cg, Co, J, ptri):
+    scale = np.maximum(np.abs(Co).max(axis=1), 1e-300)
+    err = np.abs(Cg - Co).max(axis=1)
+    bound = 1e-12 * scale + 1e-15 * J[ptri]
+    bad = err > bound
+    assert not bad.any(), (int(bad.sum()), float((err / scale).max()))
+
+
+# ------------------------------------------------------------------ config 1
+@pytest.fixture(scope="module")
+def disk(vp, ctx, tables):
+    mesh, dens = inputs.config1()
+    o = Oracle("far16", tables=tables)
+    s = o.setup(mesh.vxy, mesh.tri)
+    f = np.stack([d(s["yxy"]) for d in dens])
+    u_or, info = o.potential(s, f)
+    g = gpu_run(vp, ctx, mesh.vxy, mesh.tri, 16, f=f, precisions=(0, 1))
+    return s, f, u_or, info, g
+
+
+def test_config1_nodes_bit_exact(disk):
+    s, _, _, _, g = disk
+    assert np.array_equal(g["y"], s["yxy"]) and np.array_equal(g["w"], s["W"])
+
+
+def test_config1_lists_bit_exact(disk):
+    s, _, _, info, g = disk
+    assert np.array_equal(g["tself"], s["tself"])
+    assert np.array_equal(g["row"], info["row"])
+    assert np.array_equal(g["ptri"], info["ptri"])
+    assert np.array_equal(g["kind"], info["pkind"])
+
+
+def test_config1_weights(disk):
+    s, _, _, info, g = disk
+    compare_weights(g["C"], info["C"], s["J"], info["ptri"])
+    st = g["stats"]
+    assert st["near_leaves"] == int(info["stats"][info["pkind"] == 0].sum())
+    assert st["self_panels"] == int(info["stats"][info["pkind"] == 1].sum())
+    assert st["depth_capped"] == 0
+
+
+def test_config1_potential_fp64(disk):
+    _, _, u_or, _, g = disk
+    assert rel_err(g["u0"], u_or).max() <= 1e-12
+
+
+def test_config1_potential_mixed(disk):
+    _, _, u_or, _, g = disk
+    assert rel_err(g["u1"], u_or).max() <= 1e-10
+
+
+# ------------------------------------------------- graded star, 19-pt rule
+@pytest.fixture(scope="module")
+def star(vp, ctx, tables):
+    mesh = inputs.star_mesh(n_tri=2048, seed=77, relax_iters=6)
+    extra = inputs.random_interior_points(mesh, 300, 78)
+    o = Oracle("far19", tables=tables)
+    s = o.setup(mesh.vxy, mesh.tri, node_targets=True, extra=extra)
+    fs = [inputs.gaussian_mix(mesh, 79), inputs.manufactured_sin_cos(3.0), lambda p: np.ones(len(p))]
+    f = np.stack([d(s["yxy"]) for d in fs])
+    rng = np.random.default_rng(80)
+    sample = np.unique(np.concatenate([rng.choice(s["N"], 500, replace=False), s["N"] + np.arange(len(extra))]))
+    u_or, info = o.potential(s, f, targets=sample)
+    row_all, ptri_all, kind_all = o.lists(s["vxy"], s["tri"], s["J"], s["txy"], s["tself"])
+    g = gpu_run(vp, ctx, mesh.vxy, mesh.tri, 19, extra=extra, f=f, precisions=(0, 1))
+    return s, f, sample, u_or, info, (row_all, ptri_all, kind_all), g
+
+
+def test_star_lists_bit_exact(star):
+    s, _, _, _, _, (row, ptri, kind), g = star
+    assert np.array_equal(g["tself"], s["tself"])
+    assert np.array_equal(g["row"], row) and np.array_equal(g["ptri"], ptri) and np.array_equal(g["kind"], kind)
+
+
+def test_star_weights_sampled(star):
+    s, _, sample, _, info, _, g = star
+    rows = [np.arange(g["row"][t], g["row"][t + 1]) for t in sample]
+    sel = np.concatenate(rows)
+    compare_weights(g["C"][sel], info["C"], s["J"], info["ptri"])
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-10)])
+def test_star_potential_sampled(star, prec, tol):
+    _, _, sample, u_or, _, _, g = star
+    assert rel_err(g[f"u{prec}"][:, sample], u_or).max() <= tol
+
+
+# ----------------------------------------------------------------- edge cases
+def test_single_triangle_with_outside_edge_and_vertex_targets(vp, ctx, tables):
+    vxy = np.array([[0.0, 0.0], [0.3, 0.05], [0.1, 0.25]])
+    tri = np.array([[0, 2, 1]], np.int32)          # clockwise on purpose
+    extra = np.array([[0.12, 0.1], [0.5, 0.5], [0.15, 0.025], [0.0, 0.0], [-0.02, 0.01], [2.0, -1.0]])
+    o = Oracle("far19", tables=tables)
+    s = o.setup(vxy, tri, node_targets=True, extra=extra)
+    f = np.stack([np.ones(s["N"]), np.cos(3 * s["yxy"][:, 0]) * s["yxy"][:, 1]])
+    u_or, info = o.potential(s, f)
+    g = gpu_run(vp, ctx, vxy, tri, 19, extra=extra, f=f)
+    assert np.array_equal(g["tself"], s["tself"])
+    assert np.array_equal(g["row"], info["row"]) and np.array_equal(g["ptri"], info["ptri"])
+    assert g["stats"]["outside"] == int((s["tself"] < 0).sum()) >= 3
+    compare_weights(g["C"], info["C"], s["J"], info["ptri"])
+    assert rel_err(g["u0"], u_or).max() <= 1e-12
+    assert g["stats"]["depth_capped"] == info["capped"]
+
+
+def test_many_densities_and_extra_only(vp, ctx, tables, cfg1):
+    """d = 11 exercises the density chunking (8 + 2 + 1); targets are only
+    extra points (node_targets = False)."""
+    mesh, _ = cfg1
+    extra = inputs.random_interior_points(mesh, 333, 5)
+    o = Oracle("far16", tables=tables)
+    s = o.setup(mesh.vxy, mesh.tri, node_targets=False, extra=extra)
+    rng = np.random.default_rng(6)
+    f = rng.normal(size=(11, s["N"]))
+    u_or, _ = o.potential(s, f)
+    g = gpu_run(vp, ctx, mesh.vxy, mesh.tri, 16, extra=extra, node_targets=False, f=f, precisions=(0, 1))
+    assert rel_err(g["u0"], u_or).max() <= 1e-12
+    assert rel_err(g["u1"], u_or).max() <= 1e-10
+
+
+def test_host_entry_point_matches_device(vp, ctx, disk):
+    s, f, _, _, g = disk
+    for p in (0, 1):
+        uh = vp.potential_eval_host(ctx, g["nf"], f, precision=p)
+        assert np.array_equal(uh, g[f"u{p}"])
+
+
+def test_batch_matches_single(vp, ctx, disk, star):
+    _, f1, _, _, g1 = disk
+    _, f2, _, _, _, _, g2 = star
+    items = []
+    outs = []
+    for g, f in ((g1, f1), (g2, f2), (g1, f1[:1])):
+        fd = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+        u = torch.empty((f.shape[0], g["nf"].M), dtype=torch.float64, device="cuda")
+        items.append((g["nf"], fd, u))
+        outs.append(u)
+    vp.potential_eval_batch(ctx, items, precision=0)
+    torch.cuda.synchronize()
+    assert np.array_equal(outs[0].cpu().numpy(), g1["u0"])
+    assert np.array_equal(outs[1].cpu().numpy(), g2["u0"])
+    assert np.array_equal(outs[2].cpu().numpy(), g1["u0"][:1])
+
+
+def test_errors_are_reported(vp, ctx):
+    with pytest.raises(vp.VPError) as e:
+        vp.mesh_upload(ctx, np.array([[0.0, 0.0], [1.0, 0.0], [2.0, 0.0]]), np.array([[0, 1, 2]], np.int32))
+    assert e.value.code == -2
+    with pytest.raises(vp.VPError) as e:
+        vp.mesh_upload(ctx, np.array([[0.0, 0.0], [1.0, np.nan], [0.0, 1.0]]), np.array([[0, 1, 2]], np.int32))
+    assert e.value.code == -3
+    with pytest.raises(vp.VPError) as e:
+        vp.mesh_upload(ctx, np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]]), np.array([[0, 1, 3]], np.int32))
+    assert e.value.code == -1
