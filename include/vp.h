@@ -197,6 +197,25 @@ VP_API int vp_potential_eval(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, 
 VP_API int vp_potential_eval_host(vp_ctx* ctx, const vp_nf* nf, const double* f_host, int32_t d, double* u_host,
                            int32_t precision, void* stream);
 
+/* Same computation and arguments as vp_potential_eval, but it allocates no
+ * device memory, for callers that cannot: a process whose GPU memory is
+ * owned by another allocator (a caching allocator can hold every free byte,
+ * so cudaMalloc fails), or a serving loop that cannot accept the device-wide
+ * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart.
+ * Its scratch (split-source partial sums and float-float charges) lives in a
+ * fixed 32 MiB device array compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  A call that would need
+ * more (about splits * d * M * 8 + N * 2 * min(d, 8) * 4 bytes) is rejected
+ * with VP_ERR_INVALID_ARG and a message; use vp_potential_eval then.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents:
+ * calls whose work overlaps on the GPU (other streams, other contexts on the
+ * same device) race on it and must be serialised by the caller.  Nothing in
+ * it needs to start at zero. */
+VP_API int vp_potential_eval_noalloc(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, double* u_dev,
+                                     int32_t precision, void* stream);
+
 /* One evaluation of a batch: a near-field build with its densities/output. */
 typedef struct vp_eval_item {
     const vp_nf* nf;

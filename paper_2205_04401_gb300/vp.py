@@ -75,6 +75,8 @@ SIGNATURES = {
     "vp_nf_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "vp_nf_release": (None, [C.c_void_p]),
     "vp_potential_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
+    "vp_potential_eval_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
+                                            C.c_void_p]),
     "vp_potential_eval_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
                                          C.c_void_p]),
     "vp_potential_eval_batch": (C.c_int, [C.c_void_p, C.POINTER(EvalItem), C.c_int32, C.c_int32, C.c_void_p]),
@@ -314,6 +316,25 @@ def potential_eval(ctx: Context, nf: NearField, f, precision: int = VP_FP64, out
     rc = load().vp_potential_eval(ctx.handle, nf.handle, _dptr(f, "float64"), C.c_int32(d), _dptr(out, "float64"),
                                   C.c_int32(precision), _stream(stream))
     _check(rc, ctx, "vp_potential_eval")
+    return out
+
+
+def potential_eval_noalloc(ctx: Context, nf: NearField, f, precision: int = VP_FP64, out=None, stream=None):
+    """vp_potential_eval_noalloc: like potential_eval, with the library's fixed
+    scratch instead of allocated memory (for callers that cannot allocate
+    device memory while they evaluate).  `out` must be given if the caller
+    cannot allocate either."""
+    import torch
+    if f.dim() == 1:
+        f = f.unsqueeze(0)
+    d = int(f.shape[0])
+    if f.shape[1] != nf.mesh.N:
+        raise ValueError("f must be [d][N]")
+    if out is None:
+        out = torch.empty((d, nf.M), dtype=torch.float64, device=f.device)
+    rc = load().vp_potential_eval_noalloc(ctx.handle, nf.handle, _dptr(f, "float64"), C.c_int32(d),
+                                          _dptr(out, "float64"), C.c_int32(precision), _stream(stream))
+    _check(rc, ctx, "vp_potential_eval_noalloc")
     return out
 
 
