@@ -4,7 +4,7 @@
  * potential evaluation over unstructured meshes in two dimensions"
  * (arXiv 2205.04401).
  *
- *     u(x) = int_Omega G(x, y) f(y) dA_y,     G(x, y) = (1/2pi) log|x - y|     (Eq. 1.1)
+ *     u(x) = int_Omega G(x, y) f(y) dA_y,     G(x, y) = (1/2pi) log|x - y|     (Section 1)
  *
  * evaluated by the subtract-and-add scheme of Section 3.6: a far sum over
  * every quadrature node as a point charge, corrected for the (target,
