@@ -238,6 +238,77 @@ def what(pts, degree):
     return best
 
 
+def legendre_tensor_index():
+    """Basis of P_4 used on the device: L_ab(x, y) = P_a(3x - 1) P_b(3y - 1), a + b <= 4,
+    ordered by total degree n = a + b, then a from n down to 0."""
+    return [(a, n - a) for n in range(5) for a in range(n, -1, -1)]
+
+
+def _legendre_poly_coeffs(n):
+    """Monomial coefficients of P_n(t) (Bonnet recurrence, exact rationals)."""
+    from fractions import Fraction
+    p0, p1 = [Fraction(1)], [Fraction(0), Fraction(1)]
+    if n == 0:
+        return p0
+    for k in range(1, n):
+        nxt = [Fraction(0)] * (k + 2)
+        for i, c in enumerate(p1):
+            nxt[i + 1] += Fraction(2 * k + 1, k + 1) * c
+        for i, c in enumerate(p0):
+            nxt[i] -= Fraction(k, k + 1) * c
+        p0, p1 = p1, nxt
+    return p1
+
+
+def projection_matrix(pts):
+    """Q[k][i] = w_k sum_j Hinv[i][j] L_j(x_k, y_k): maps the moments
+    mu_i = int_T G L_i(rho_T^-1 y) dA to the nodal correction weights of the
+    discrete L2 projection onto P_4 with the far rule (exact Gram H, since
+    the rule has degree >= 8)."""
+    from fractions import Fraction
+    idx = legendre_tensor_index()
+    # L_ab as polynomials in (x, y): P_a(3x - 1) expanded to monomials
+    def shifted(n):
+        c = _legendre_poly_coeffs(n)
+        out = [Fraction(0)] * (n + 1)
+        for k, ck in enumerate(c):          # ck (3x - 1)^k
+            for j in range(k + 1):
+                out[j] += ck * math.comb(k, j) * Fraction(3) ** j * Fraction(-1) ** (k - j)
+        return out
+    sp = {n: shifted(n) for n in range(5)}
+    def gram(i, j):
+        (a, b), (c, d) = idx[i], idx[j]
+        px = [Fraction(0)] * (a + c + 1)
+        for u, cu in enumerate(sp[a]):
+            for v, cv in enumerate(sp[c]):
+                px[u + v] += cu * cv
+        py = [Fraction(0)] * (b + d + 1)
+        for u, cu in enumerate(sp[b]):
+            for v, cv in enumerate(sp[d]):
+                py[u + v] += cu * cv
+        tot = Fraction(0)
+        for u, cu in enumerate(px):
+            for v, cv in enumerate(py):
+                tot += cu * cv * Fraction(math.factorial(u) * math.factorial(v), math.factorial(u + v + 2))
+        return tot
+    n = len(idx)
+    H = mp.matrix(n, n)
+    for i in range(n):
+        for j in range(n):
+            g = gram(i, j)
+            H[i, j] = mp.mpf(g.numerator) / g.denominator
+    Hinv = mp.inverse(H)
+    def L(x, y):
+        def P(k, t):
+            return sum(c * t ** e for e, c in enumerate(_legendre_poly_coeffs(k)))
+        return [P(a, 3 * x - 1) * P(b, 3 * y - 1) for a, b in idx]
+    Q = []
+    for x, y, w in pts:
+        l = L(x, y)
+        Q.append([w * mp.fsum(Hinv[i, j] * l[j] for j in range(n)) for i in range(n)])
+    return Q
+
+
 def cdbl(v):
     return float(v).hex()
 
@@ -256,6 +327,8 @@ def main():
     for name in ("far16", "far19"):
         deg, c0, s21, s111 = START[name]
         pts = solve_symmetric(deg, c0, s21, s111)
+        Q = projection_matrix(pts)
+        arr(f"VP_{name.upper()}_Q", [v for row in Q for v in row])
         arr(f"VP_{name.upper()}_X", [p[0] for p in pts])
         arr(f"VP_{name.upper()}_Y", [p[1] for p in pts])
         arr(f"VP_{name.upper()}_W", [p[2] for p in pts])
@@ -273,6 +346,11 @@ def main():
     t, w = gl01(16)
     arr("VP_GL16_X", t)
     arr("VP_GL16_W", w)
+    # FP64 logarithm table: c_i = 1 + (i + 1/2)/128, 1/c_i and log c_i
+    cs = [1 + (mp.mpf(i) + mp.mpf(1) / 2) / 128 for i in range(128)]
+    arr("VP_LOG128_RC", [1 / c for c in cs])
+    arr("VP_LOG128_L", [mp.log(c) for c in cs])
+    out.append(f"static const double VP_LN2 = {cdbl(mp.log(2))};")
     path = os.path.join(here, "vp_tables.h")
     with open(path, "w") as fh:
         fh.write("\n".join(out) + "\n")

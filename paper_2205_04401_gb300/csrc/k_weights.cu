@@ -9,6 +9,12 @@
 // ellipse stop test of Section 4.1) or the self scheme (Section 3.4,
 // radius-arclength coordinates on three fans, generalized Gaussian rule in
 // the radius, graded Gauss-Legendre panels in the arc length).
+//
+// The kernels are bound by the FP64 pipe, so per quadrature point they
+// accumulate the moments mu_i of the tensor-Legendre basis leg15 (20 FP64
+// operations instead of ~60 for the orthonormal basis) and use the
+// table-driven vp_logd; the constant matrix Q (generated in high precision)
+// maps mu to the nodal weights: C_k = sum_i Q_ki mu_i - [k != own] W_k G.
 #include "vp_internal.h"
 
 namespace {
@@ -24,16 +30,16 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// m_a -> C_k for lanes k < nq, written to C[p*nq + k].
+// mu_i -> C_k for lanes k < nq, written to C[p*nq + k].
 __device__ __forceinline__ void finish_pair(const WeightsArgs& a, int64_t p, int T, int own, double xx, double xy,
                                             double* m, int lane) {
 #pragma unroll
     for (int q = 0; q < VP_NB; q++) m[q] = warp_sum(m[q]);
     if (lane < a.nq) {
-        const double* Pk = a.tab->Pk[a.rule][lane];
+        const double* Qk = a.tab->Q[a.rule][lane];
         double s = 0.0;
 #pragma unroll
-        for (int q = 0; q < VP_NB; q++) s += Pk[q] * m[q];
+        for (int q = 0; q < VP_NB; q++) s += Qk[q] * m[q];
         if (lane != own) {
             int64_t j = (int64_t)T * a.nq + lane;
             s -= a.W[j] * kernel_G(xx - a.y[2 * j], xy - a.y[2 * j + 1]);
@@ -47,6 +53,26 @@ __device__ __forceinline__ int own_index(const WeightsArgs& a, int t, int T) {
     return (tn >= 0 && tn / a.nq == T) ? tn - T * a.nq : -1;
 }
 
+struct LogSmem {
+    double rc[128], lc[128];
+};
+
+__device__ __forceinline__ void load_logtab(const VpTables* tab, LogSmem& t) {
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+        t.rc[i] = tab->log_rc[i];
+        t.lc[i] = tab->log_lc[i];
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void accumulate(double* m, double g, double x, double y) {
+    double L[VP_NB];
+    leg15(x, y, L);
+    m[0] += g;
+#pragma unroll
+    for (int c = 1; c < VP_NB; c++) m[c] = fma(g, L[c], m[c]);
+}
+
 // N = min{n >= 0 : 2^-n len < dist}
 __device__ __forceinline__ int dyadic_count(double len, double dist) {
     int n = 0;
@@ -56,9 +82,12 @@ __device__ __forceinline__ int dyadic_count(double len, double dist) {
 
 // ------------------------------------------------------------------ self
 __global__ void __launch_bounds__(WARPS * 32) k_weights_self(WeightsArgs a, const int32_t* __restrict__ idx, int64_t n) {
+    __shared__ LogSmem lt;
+    load_logtab(a.tab, lt);
     const int lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
     if (w >= n) return;
+    const double ln2 = a.tab->ln2;
     const int64_t p = idx[w];
     const int T = a.ptri[p], t = a.ptgt[p];
     const double* v = a.tv + 6 * (int64_t)T;
@@ -67,6 +96,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_self(WeightsArgs a, cons
     const double J = a.J[T];
     const double invJ = 1.0 / J;
     const double xx = a.txy[2 * t], xy = a.txy[2 * t + 1];
+    // reference coordinates of the target (rho_T^-1 x)
+    const double qx0 = xx - Ax, qy0 = xy - Ay;
+    const double xi0 = (qx0 * fy - qy0 * fx) * invJ, eta0 = (ex * qy0 - ey * qx0) * invJ;
     const int own = own_index(a, t, T);
     const int gl = lane >> 1, jb = (lane & 1) * 4;
     const double lxg = a.tab->lx[gl], lwg = a.tab->lw[gl];
@@ -96,6 +128,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_self(WeightsArgs a, cons
         const double ddx = rn_sub(xx, fxp), ddy = rn_sub(xy, fyp);
         const double delta = rn_sqrt(rn_add(rn_mul(ddx, ddx), rn_mul(ddy, ddy)));
         const double Lst = rn_sub(L, st);
+        // reference coordinates of P and of the direction of the side
+        const double qpx = Px - Ax, qpy = Py - Ay;
+        const double xiP = (qpx * fy - qpy * fx) * invJ, etaP = (ex * qpy - ey * qpx) * invJ;
+        const double dxi = (dx * fy - dy * fx) * invJ, deta = (ex * dy - ey * dx) * invJ;
         for (int side = 0; side < 2; side++) {
             double len = side == 0 ? st : Lst;
             if (!(len > 0.0)) continue;
@@ -113,20 +149,14 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_self(WeightsArgs a, cons
                 const double s = b0 + (b1 - b0) * lxg;
                 const double ws = fabs((b1 - b0) * lwg) * h;
                 const double sl = s / L;
-                const double gx = Px + sl * dx, gy = Py + sl * dy;
-                const double rx = gx - xx, ry = gy - xy;
-                const double lr0 = 0.5 * log(rx * rx + ry * ry);
+                const double rx = Px + sl * dx - xx, ry = Py + sl * dy - xy;
+                const double lr0 = 0.5 * vp_logd(rx * rx + ry * ry, lt.rc, lt.lc, ln2);
+                // reference coordinates along the ray x + r (gamma(s) - x)
+                const double xig = xiP + sl * dxi - xi0, etag = etaP + sl * deta - eta0;
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
-                    const double yx = xx + gr[q] * rx, yy = xy + gr[q] * ry;
-                    const double qx = yx - Ax, qy = yy - Ay;
-                    const double xi = (qx * fy - qy * fx) * invJ;
-                    const double eta = (ex * qy - ey * qx) * invJ;
-                    double K[VP_NB];
-                    koornwinder4(xi, eta, K);
                     const double g = (lr0 + glr[q]) * ws * gwl[q];
-#pragma unroll
-                    for (int c = 0; c < VP_NB; c++) m[c] += g * K[c];
+                    accumulate(m, g, fma(gr[q], xig, xi0), fma(gr[q], etag, eta0));
                 }
                 b0 = b1;
             }
@@ -145,6 +175,12 @@ struct SubTri {
     int32_t L;
 };
 
+// A leaf as its affine map from the near rule's simplex to T's reference
+// simplex (xi = a0 + zx e1 + zy e2) and its weight factor J_S / (4 pi).
+struct LeafMap {
+    double a0x, a0y, e1x, e1y, e2x, e2y, wJ;
+};
+
 __device__ __forceinline__ void sub_phys(const SubTri& S, double Ax, double Ay, double ex, double ey, double fx,
                                          double fy, double* ph) {
 #pragma unroll
@@ -157,12 +193,15 @@ __device__ __forceinline__ void sub_phys(const SubTri& S, double Ax, double Ay, 
 
 __global__ void __launch_bounds__(WARPS * 32) k_weights_near(WeightsArgs a, const int32_t* __restrict__ idx, int64_t n) {
     __shared__ SubTri stack_all[WARPS][STK];
-    __shared__ SubTri leaf_all[WARPS][LEAFCAP];
+    __shared__ LeafMap leaf_all[WARPS][LEAFCAP];
+    __shared__ LogSmem lt;
+    load_logtab(a.tab, lt);
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int64_t w = (int64_t)blockIdx.x * WARPS + wl;
     if (w >= n) return;
+    const double ln2 = a.tab->ln2;
     SubTri* stack = stack_all[wl];
-    SubTri* leaves = leaf_all[wl];
+    LeafMap* leaves = leaf_all[wl];
     const int64_t p = idx[w];
     const int T = a.ptri[p], t = a.ptgt[p];
     const double* v = a.tv + 6 * (int64_t)T;
@@ -220,7 +259,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_near(WeightsArgs a, cons
             sp -= c;
             if (lane < c) {
                 if (stop) {
-                    leaves[nleaf + __popc(lm & lower)] = S;
+                    const double sc = ldexp(1.0, -S.L);
+                    LeafMap lf;
+                    lf.a0x = S.v[0] * sc;
+                    lf.a0y = S.v[1] * sc;
+                    lf.e1x = (S.v[2] - S.v[0]) * sc;
+                    lf.e1y = (S.v[3] - S.v[1]) * sc;
+                    lf.e2x = (S.v[4] - S.v[0]) * sc;
+                    lf.e2y = (S.v[5] - S.v[1]) * sc;
+                    lf.wJ = ldexp(J, -2 * S.L) * (0.5 * VP_INV_TWO_PI);
+                    leaves[nleaf + __popc(lm & lower)] = lf;
                 } else {
                     const int base = sp + 4 * __popc(sm & lower);
                     int32_t m01x = S.v[0] + S.v[2], m01y = S.v[1] + S.v[3];
@@ -249,17 +297,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_near(WeightsArgs a, cons
             const int combos = nleaf * VP_NNEAR;
             for (int i = lane; i < combos; i += 32) {
                 const int li = i / VP_NNEAR, j = i - li * VP_NNEAR;
-                const SubTri& S = leaves[li];
-                const double s = ldexp(1.0, -S.L);
-                const double a0x = S.v[0] * s, a0y = S.v[1] * s;
-                const double xi = a0x + (nx[j] * (S.v[2] * s - a0x) + ny[j] * (S.v[4] * s - a0x));
-                const double eta = a0y + (nx[j] * (S.v[3] * s - a0y) + ny[j] * (S.v[5] * s - a0y));
-                const double yx = Ax + (xi * ex + eta * fx), yy = Ay + (xi * ey + eta * fy);
-                const double g = kernel_G(xx - yx, xy - yy) * nw[j] * ldexp(J, -2 * S.L);
-                double K[VP_NB];
-                koornwinder4(xi, eta, K);
-#pragma unroll
-                for (int c = 0; c < VP_NB; c++) m[c] += g * K[c];
+                const LeafMap& lf = leaves[li];
+                const double zx = nx[j], zy = ny[j];
+                const double xi = fma(zy, lf.e2x, fma(zx, lf.e1x, lf.a0x));
+                const double eta = fma(zy, lf.e2y, fma(zx, lf.e1y, lf.a0y));
+                const double dx = xx - fma(eta, fx, fma(xi, ex, Ax)), dy = xy - fma(eta, fy, fma(xi, ey, Ay));
+                const double g = vp_logd(dx * dx + dy * dy, lt.rc, lt.lc, ln2) * (nw[j] * lf.wJ);
+                accumulate(m, g, xi, eta);
             }
             total_leaves += nleaf;
             nleaf = 0;

@@ -59,6 +59,7 @@ void fill_tables(VpTables& t) {
     const double* fx[2] = {VP_FAR16_X, VP_FAR19_X};
     const double* fy[2] = {VP_FAR16_Y, VP_FAR19_Y};
     const double* fw[2] = {VP_FAR16_W, VP_FAR19_W};
+    const double* fq[2] = {VP_FAR16_Q, VP_FAR19_Q};
     const int nq[2] = {16, 19};
     t.far_what[0] = VP_FAR16_WHAT;
     t.far_what[1] = VP_FAR19_WHAT;
@@ -73,6 +74,7 @@ void fill_tables(VpTables& t) {
             double K[VP_NB];
             koornwinder4(fx[r][k], fy[r][k], K);
             for (int a = 0; a < VP_NB; a++) t.Pk[r][k][a] = fw[r][k] * K[a];
+            for (int a = 0; a < VP_NB; a++) t.Q[r][k][a] = fq[r][k * VP_NB + a];
         }
     }
     for (int j = 0; j < VP_NNEAR; j++) {
@@ -91,6 +93,11 @@ void fill_tables(VpTables& t) {
         t.lx[j] = VP_GL16_X[j];
         t.lw[j] = VP_GL16_W[j];
     }
+    for (int j = 0; j < 128; j++) {
+        t.log_rc[j] = VP_LOG128_RC[j];
+        t.log_lc[j] = VP_LOG128_L[j];
+    }
+    t.ln2 = VP_LN2;
 }
 
 bool ctx_ok(const vp_ctx* c) { return c && c->magic == 0x56504358; }

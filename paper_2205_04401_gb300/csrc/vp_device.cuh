@@ -22,9 +22,49 @@ struct VpTables {
     int near_degree;
     double gr[VP_NGGQ], gw[VP_NGGQ], glogr[VP_NGGQ];
     double lx[VP_NGL], lw[VP_NGL];
-    // projection rows: Pk[rule][k][a] = w_k K_a(xi_k)
+    // projection rows: Pk[rule][k][a] = w_k K_a(xi_k) (Koornwinder basis)
     double Pk[2][VP_MAXQ][VP_NB];
+    // Q[rule][k][i]: moments of the tensor-Legendre basis leg15 -> nodal weights
+    double Q[2][VP_MAXQ][VP_NB];
+    // FP64 logarithm table: 1/c_i and log c_i, c_i = 1 + (i + 1/2)/128
+    double log_rc[128], log_lc[128];
+    double ln2;
 };
+
+// Tensor-Legendre basis of P_4 used to accumulate moments on the device:
+// L_ab(x, y) = P_a(3x - 1) P_b(3y - 1), a + b <= 4, ordered by n = a + b and
+// then a from n down to 0 (the order of the Q table).
+__host__ __device__ __forceinline__ void leg15(double x, double y, double* L) {
+    const double u = fma(3.0, x, -1.0), v = fma(3.0, y, -1.0);
+    const double u2 = u * u, v2 = v * v;
+    const double pu2 = fma(1.5, u2, -0.5), pv2 = fma(1.5, v2, -0.5);
+    const double pu3 = u * fma(2.5, u2, -1.5), pv3 = v * fma(2.5, v2, -1.5);
+    const double pu4 = fma(u2, fma(4.375, u2, -3.75), 0.375), pv4 = fma(v2, fma(4.375, v2, -3.75), 0.375);
+    L[0] = 1.0;
+    L[1] = u;        L[2] = v;
+    L[3] = pu2;      L[4] = u * v;      L[5] = pv2;
+    L[6] = pu3;      L[7] = pu2 * v;    L[8] = u * pv2;    L[9] = pv3;
+    L[10] = pu4;     L[11] = pu3 * v;   L[12] = pu2 * pv2; L[13] = u * pv3;  L[14] = pv4;
+}
+
+// log(x) for normal x > 0: x = 2^E m, m in [1,2), c = 1 + (i + 1/2)/128 the
+// centre of m's bucket, z = (m - c)/c (m - c exact), |z| < 2^-8, and
+// log x = E ln 2 + log c + log(1 + z) with the series of log(1 + z) to z^7.
+__device__ __forceinline__ double vp_logd(double x, const double* __restrict__ rc, const double* __restrict__ lc,
+                                          double ln2) {
+    const long long b = __double_as_longlong(x);
+    const int E = (int)(b >> 52) - 1023;
+    const int i = (int)((b >> 45) & 127);
+    const double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    const double c = fma((double)i + 0.5, 0.0078125, 1.0);
+    const double z = (m - c) * rc[i];
+    double p = fma(z, 1.0 / 7.0, -1.0 / 6.0);
+    p = fma(z, p, 0.2);
+    p = fma(z, p, -0.25);
+    p = fma(z, p, 1.0 / 3.0);
+    p = fma(z, p, -0.5);
+    return fma((double)E, ln2, lc[i] + fma(z * z, p, z));
+}
 
 // ------------------------------------------------------------------------
 // Predicates evaluated with explicit round-to-nearest operations (no fused
