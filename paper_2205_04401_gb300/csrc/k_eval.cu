@@ -137,7 +137,7 @@ __global__ void k_prep_q_ff(const double* __restrict__ W, const double* __restri
 constexpr int LOG_BITS = 9;
 constexpr int LOG_N = 1 << LOG_BITS;
 struct LogTab {
-    float4 e[LOG_N];   // rc, lh, ll, unused
+    float4 e[LOG_N];   // 1/c, log c (hi), log c (lo), c
 };
 __device__ LogTab g_logtab;
 
@@ -150,29 +150,32 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// log of the unevaluated pair (s, corr), s > 0 normal, |corr| <= 2^-20 s, as
-// b + tail with |tail| <~ 2^-19 |b| + 2^-21 and an error of about 1e-13.
+// log of the unevaluated pair (s, corr), s > 0 normal, |corr| <= 2^-24 s, as
+// hi + lo with an error of about 1e-13.
 __device__ __forceinline__ void ff_log(const float4* __restrict__ tab, float s, float corr, float& hi, float& lo) {
     const int bits = __float_as_int(s);
-    const int E = ((bits >> 23) & 0xff) - 127;
+    // exponent as a float: 2^23 + biased exponent, minus (2^23 + 127)
+    const float fe = __fsub_rn(__int_as_float((bits >> 23) | 0x4b000000), 8388735.0f);
     const int i = (bits >> (23 - LOG_BITS)) & (LOG_N - 1);
     const float m = __int_as_float((bits & 0x007fffff) | 0x3f800000);    // [1, 2)
-    const float c = __fadd_rn(1.0f, __fmul_rn(__fadd_rn((float)i, 0.5f), 1.0f / LOG_N));
-    const float4 t = tab[i];
-    const float u = __fsub_rn(m, c);                                     // exact (Sterbenz)
+    const float4 t = tab[i];                                             // 1/c, log c (hi, lo), c
+    const float u = __fsub_rn(m, t.w);                                   // exact (Sterbenz)
     const float wh = __fmul_rn(u, t.x);
-    const float wl = __fmul_rn(__fmaf_rn(-wh, c, u), t.x);              // residual u - wh c is exact
+    const float wl = __fmul_rn(__fmaf_rn(-wh, t.w, u), t.x);            // residual u - wh c is exact
     // log(1 + w) - w = -w^2/2 + w^3/3 - w^4/4  (|w| < 2^-10)
     float p = __fmaf_rn(wh, -0.25f, 0.33333334f);
     p = __fmaf_rn(wh, p, -0.5f);
     p = __fmul_rn(__fmul_rn(p, wh), wh);
-    const float fe = (float)E;
     const float P = __fmul_rn(fe, LN2_H);
     const float eP = __fmaf_rn(fe, LN2_H, -P);                          // exact product error
-    float a, ea, b, eb;
-    two_sum(P, t.y, a, ea);
+    // |P| >= ln 2 > log c whenever E != 0, and P = 0 otherwise: fast two-sum
+    const float a = __fadd_rn(P, t.y);
+    const float ea = __fsub_rn(t.y, __fsub_rn(a, P));
+    float b, eb;
     two_sum(a, wh, b, eb);
-    float tail = __fadd_rn(__fmaf_rn(-wh, wl, wl), __fmul_rn(corr, __frcp_rn(s)));
+    float rs;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(s));             // corr/s is ~2^-24: an approximate 1/s suffices
+    float tail = __fadd_rn(__fmaf_rn(-wh, wl, wl), __fmul_rn(corr, rs));
     tail = __fadd_rn(tail, __fmaf_rn(fe, LN2_L, t.z));
     tail = __fadd_rn(tail, p);
     tail = __fadd_rn(tail, __fadd_rn(__fadd_rn(ea, eb), eP));
@@ -180,8 +183,72 @@ __device__ __forceinline__ void ff_log(const float4* __restrict__ tab, float s, 
     lo = tail;
 }
 
+// |x_t - y_s|^2 as a renormalised float-float pair from the split coordinates
+// (hi parts on a common dyadic grid, so hi_t - hi_s is exact).
+__device__ __forceinline__ void ff_dist2(float thx, float thy, float tlx, float tly, float4 sv, float& s, float& corr) {
+    const float a = __fsub_rn(thx, sv.x), b = __fsub_rn(thy, sv.y);
+    const float al = __fsub_rn(tlx, sv.z), bl = __fsub_rn(tly, sv.w);
+    const float dxh = __fadd_rn(a, al), dyh = __fadd_rn(b, bl);      // |a| >= |al| or a = 0
+    const float dxl = __fadd_rn(__fsub_rn(a, dxh), al), dyl = __fadd_rn(__fsub_rn(b, dyh), bl);
+    const float p1 = __fmul_rn(dxh, dxh), p2 = __fmul_rn(dyh, dyh);
+    const float e1 = __fmaf_rn(dxh, dxh, -p1), e2 = __fmaf_rn(dyh, dyh, -p2);
+    const float big = fmaxf(p1, p2), small = fminf(p1, p2);
+    const float s0 = __fadd_rn(big, small);
+    const float e3 = __fsub_rn(small, __fsub_rn(s0, big));            // fast two-sum (big >= small >= 0)
+    float c0 = __fadd_rn(__fadd_rn(e1, e2), e3);
+    c0 = __fmaf_rn(2.0f, __fmaf_rn(dxh, dxl, __fmul_rn(dyh, dyl)), c0);
+    s = __fadd_rn(s0, c0);                                           // renormalise: |corr| <= 2^-24 s
+    corr = __fadd_rn(__fsub_rn(s0, s), c0);
+    if (!(s > 1e-30f)) {                                             // coincident points (guarded by callers)
+        s = 1e-30f;
+        corr = 0.0f;
+    }
+}
+
+// acc += q * log r^2 in float-float: exact product error and two-sum.
+__device__ __forceinline__ void ff_madd(float qh, float ql, float lh, float ll, float& sh, float& sl) {
+    const float pr = __fmul_rn(qh, lh);
+    const float pe = __fmaf_rn(qh, lh, -pr);
+    const float lo_t = __fmaf_rn(qh, ll, __fmaf_rn(ql, lh, pe));
+    float ns, ne;
+    two_sum(sh, pr, ns, ne);
+    sh = ns;
+    sl = __fadd_rn(sl, __fadd_rn(ne, lo_t));
+}
+
 constexpr int FF_THREADS = 128;
 constexpr int FF_TILE = 128;
+constexpr int FF_TPT = 2;   // targets per thread: target t and t + FF_THREADS of the block
+
+template <int D, bool CHECK_OWN>
+__device__ __forceinline__ void ff_tile(const float4* __restrict__ sxy, const float (*sq)[2 * D],
+                                        const float4* __restrict__ stab, int nt, const float* thx, const float* thy,
+                                        const float* tlx, const float* tly, const int* own_local,
+                                        float (*sh)[D], float (*sl)[D]) {
+#pragma unroll 2
+    for (int i = 0; i < nt; i++) {
+        const float4 sv = sxy[i];
+        float qh[D], ql[D];
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+            qh[k] = sq[i][k];
+            ql[k] = sq[i][D + k];
+        }
+#pragma unroll
+        for (int r = 0; r < FF_TPT; r++) {
+            float s, corr;
+            ff_dist2(thx[r], thy[r], tlx[r], tly[r], sv, s, corr);
+            if (CHECK_OWN && i == own_local[r]) {                    // own node: log 1 = 0
+                s = 1.0f;
+                corr = 0.0f;
+            }
+            float lh, ll;
+            ff_log(stab, s, corr, lh, ll);                           // log |x-y|^2 = lh + ll
+#pragma unroll
+            for (int k = 0; k < D; k++) ff_madd(qh[k], ql[k], lh, ll, sh[r][k], sl[r][k]);
+        }
+    }
+}
 
 template <int D>
 __global__ void __launch_bounds__(FF_THREADS) k_far_ff(const float* __restrict__ shi, const float* __restrict__ slo,
@@ -192,18 +259,41 @@ __global__ void __launch_bounds__(FF_THREADS) k_far_ff(const float* __restrict__
     __shared__ float4 sxy[FF_TILE];           // hi x, hi y, lo x, lo y
     __shared__ float sq[FF_TILE][2 * D];
     __shared__ float4 stab[LOG_N];
+    __shared__ int own_range[2];
     for (int i = threadIdx.x; i < LOG_N; i += FF_THREADS) stab[i] = g_logtab.e[i];
-    const int64_t t = (int64_t)blockIdx.x * FF_THREADS + threadIdx.x;
+    if (threadIdx.x == 0) {
+        own_range[0] = INT32_MAX;
+        own_range[1] = -1;
+    }
+    __syncthreads();
     const int split = blockIdx.y;
     const int64_t per = (N + splits - 1) / splits;
     const int64_t j0 = split * per, j1 = min(N, j0 + per);
-    const bool active = t < M;
-    const float thx = active ? thi[2 * t] : 0.f, thy = active ? thi[2 * t + 1] : 0.f;
-    const float tlx = active ? tlo[2 * t] : 0.f, tly = active ? tlo[2 * t + 1] : 0.f;
-    const int64_t own = active ? (int64_t)tnode[t] : -1;
-    double acc[D];
+    const int64_t tbase = (int64_t)blockIdx.x * (FF_THREADS * FF_TPT) + threadIdx.x;
+    float thx[FF_TPT], thy[FF_TPT], tlx[FF_TPT], tly[FF_TPT];
+    int64_t own[FF_TPT];
+    bool active[FF_TPT];
 #pragma unroll
-    for (int k = 0; k < D; k++) acc[k] = 0.0;
+    for (int r = 0; r < FF_TPT; r++) {
+        const int64_t t = tbase + r * FF_THREADS;
+        active[r] = t < M;
+        thx[r] = active[r] ? thi[2 * t] : 0.f;
+        thy[r] = active[r] ? thi[2 * t + 1] : 0.f;
+        tlx[r] = active[r] ? tlo[2 * t] : 0.f;
+        tly[r] = active[r] ? tlo[2 * t + 1] : 0.f;
+        own[r] = active[r] ? (int64_t)tnode[t] : -1;
+        if (own[r] >= 0) {
+            atomicMin(&own_range[0], (int)own[r]);
+            atomicMax(&own_range[1], (int)own[r]);
+        }
+    }
+    __syncthreads();
+    const int64_t own_lo = own_range[0], own_hi = own_range[1];
+    double acc[FF_TPT][D];
+#pragma unroll
+    for (int r = 0; r < FF_TPT; r++)
+#pragma unroll
+        for (int k = 0; k < D; k++) acc[r][k] = 0.0;
     for (int64_t base = j0; base < j1; base += FF_TILE) {
         const int nt = (int)min((int64_t)FF_TILE, j1 - base);
         __syncthreads();
@@ -214,54 +304,35 @@ __global__ void __launch_bounds__(FF_THREADS) k_far_ff(const float* __restrict__
             for (int k = 0; k < 2 * D; k++) sq[i][k] = q[j * 2 * D + k];
         }
         __syncthreads();
-        if (active) {
-            float sh[D], sl[D];
+        float sh[FF_TPT][D], sl[FF_TPT][D];
 #pragma unroll
-            for (int k = 0; k < D; k++) { sh[k] = 0.f; sl[k] = 0.f; }
-            const int64_t own_local = own - base;
-            for (int i = 0; i < nt; i++) {
-                const float4 sv = sxy[i];
-                // dx = (hi_t - hi_s) + (lo_t - lo_s): the hi difference is exact
-                // (same dyadic grid); renormalise to a float-float pair
-                const float a = __fsub_rn(thx, sv.x), b = __fsub_rn(thy, sv.y);
-                const float al = __fsub_rn(tlx, sv.z), bl = __fsub_rn(tly, sv.w);
-                const float dxh = __fadd_rn(a, al), dyh = __fadd_rn(b, bl);    // |a| >= |al| or a = 0
-                const float dxl = __fadd_rn(__fsub_rn(a, dxh), al), dyl = __fadd_rn(__fsub_rn(b, dyh), bl);
-                // r^2 = dxh^2 + dyh^2 + 2 (dxh dxl + dyh dyl) with exact product errors
-                const float p1 = __fmul_rn(dxh, dxh), p2 = __fmul_rn(dyh, dyh);
-                const float e1 = __fmaf_rn(dxh, dxh, -p1), e2 = __fmaf_rn(dyh, dyh, -p2);
-                const float big = fmaxf(p1, p2), small = fminf(p1, p2);
-                float s0 = __fadd_rn(big, small);
-                const float e3 = __fsub_rn(small, __fsub_rn(s0, big));  // fast two-sum (big >= small >= 0)
-                float c0 = __fadd_rn(__fadd_rn(e1, e2), e3);
-                c0 = __fmaf_rn(2.0f, __fmaf_rn(dxh, dxl, __fmul_rn(dyh, dyl)), c0);
-                // renormalise (s0, c0) so that |corr| <= 2^-24 s before the logarithm
-                float s = __fadd_rn(s0, c0);
-                float corr = __fadd_rn(__fsub_rn(s0, s), c0);
-                if (!(s > 1e-30f)) { s = 1e-30f; corr = 0.0f; }        // coincident points (guarded by callers)
-                if (i == own_local) { s = 1.0f; corr = 0.0f; }         // own node: log 1 = 0
-                float lh, ll;
-                ff_log(stab, s, corr, lh, ll);                         // log |x-y|^2 = lh + ll
+        for (int r = 0; r < FF_TPT; r++)
 #pragma unroll
-                for (int k = 0; k < D; k++) {
-                    const float qh = sq[i][k], ql = sq[i][D + k];
-                    const float pr = __fmul_rn(qh, lh);
-                    const float pe = __fmaf_rn(qh, lh, -pr);
-                    const float lo_t = __fmaf_rn(qh, ll, __fmaf_rn(ql, lh, pe));
-                    float ns, ne;
-                    two_sum(sh[k], pr, ns, ne);
-                    sh[k] = ns;
-                    sl[k] = __fadd_rn(sl[k], __fadd_rn(ne, lo_t));
-                }
+            for (int k = 0; k < D; k++) {
+                sh[r][k] = 0.f;
+                sl[r][k] = 0.f;
             }
+        // only a tile that can hold one of this block's own nodes checks indices
+        if (own_hi >= base && own_lo < base + nt) {
+            int own_local[FF_TPT];
 #pragma unroll
-            for (int k = 0; k < D; k++) acc[k] += (double)sh[k] + (double)sl[k];
+            for (int r = 0; r < FF_TPT; r++) own_local[r] = (own[r] >= base && own[r] < base + nt) ? (int)(own[r] - base) : -1;
+            ff_tile<D, true>(sxy, sq, stab, nt, thx, thy, tlx, tly, own_local, sh, sl);
+        } else {
+            ff_tile<D, false>(sxy, sq, stab, nt, thx, thy, tlx, tly, nullptr, sh, sl);
         }
+#pragma unroll
+        for (int r = 0; r < FF_TPT; r++)
+#pragma unroll
+            for (int k = 0; k < D; k++) acc[r][k] += (double)sh[r][k] + (double)sl[r][k];
     }
-    if (active) {
+#pragma unroll
+    for (int r = 0; r < FF_TPT; r++) {
+        const int64_t t = tbase + r * FF_THREADS;
+        if (!active[r]) continue;
 #pragma unroll
         for (int k = 0; k < D; k++)
-            if (d0 + k < d) partial[((int64_t)split * d + d0 + k) * M + t] = acc[k] * (0.5 * VP_INV_TWO_PI);
+            if (d0 + k < d) partial[((int64_t)split * d + d0 + k) * M + t] = acc[r][k] * (0.5 * VP_INV_TWO_PI);
     }
 }
 
@@ -278,7 +349,7 @@ void ensure_logtab() {
         // of ~1e-16, far below the 2^-48 the pair can carry
         const double L = std::log(c);
         const float lh = (float)L;
-        h.e[i] = make_float4((float)(1.0 / c), lh, (float)(L - (double)lh), 0.0f);
+        h.e[i] = make_float4((float)(1.0 / c), lh, (float)(L - (double)lh), (float)c);   // c is exact in float
     }
     cudaMemcpyToSymbol(g_logtab, &h, sizeof(h));
     g_logtab_device = dev;
@@ -306,7 +377,7 @@ void launch_far_fp64(const double* y, const double* W, int64_t N, const double* 
 void launch_far_ff(const FFCoords& src, const double* W, int64_t N, const double* f, int d, const FFCoords& tgt,
                    const int32_t* tnode, int64_t M, double* partial, float* qbuf, int splits, cudaStream_t s) {
     ensure_logtab();
-    dim3 grid((unsigned)((M + FF_THREADS - 1) / FF_THREADS), (unsigned)splits);
+    dim3 grid((unsigned)((M + FF_THREADS * FF_TPT - 1) / (FF_THREADS * FF_TPT)), (unsigned)splits);
     const unsigned pb = (unsigned)((N + 255) / 256);
     for (int d0 = 0; d0 < d;) {
         const int D = pick_chunk(d - d0);

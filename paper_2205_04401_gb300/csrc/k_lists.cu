@@ -210,7 +210,7 @@ __global__ void k_list_pass(const double* __restrict__ tv, const double* __restr
             double v[6];
 #pragma unroll
             for (int q = 0; q < 6; q++) v[q] = tv[6 * (int64_t)T + q];
-            kind = tri_near_rn(v, xx, xy, N, R[T]) ? 0 : -1;
+            kind = tri_near_fast(v, xx, xy, N, R[T]) ? 0 : -1;
         }
         if (kind >= 0) {
             if (row) {

@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_near(WeightsArgs a, cons
     const int own = own_index(a, t, T);
     const double what = a.tab->near_what;
     const int Nn = a.tab->near_degree;
+    const double R_root = ellipse_R_rn(what, J, a.eps, a.c_near);
     const double* nx = a.tab->nx;
     const double* ny = a.tab->ny;
     const double* nw = a.tab->nw;
@@ -245,9 +246,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_near(WeightsArgs a, cons
                 S = stack[sp - 1 - lane];
                 double ph[6];
                 sub_phys(S, Ax, Ay, ex, ey, fx, fy, ph);
-                const double JS = ldexp(J, -2 * S.L);
-                const bool inside = tri_contains_rn(ph, xx, xy);
-                stop = !inside && !tri_near_rn(ph, xx, xy, Nn, ellipse_R_rn(what, JS, a.eps, a.c_near));
+                // R_S = w J_S / (eps C) = R_T 4^-depth exactly (power-of-two scaling)
+                stop = !tri_near_fast(ph, xx, xy, Nn, ldexp(R_root, -2 * S.L)) && !tri_contains_rn(ph, xx, xy);
                 if (!stop && S.L >= a.depth_cap) {
                     stop = true;
                     capped++;

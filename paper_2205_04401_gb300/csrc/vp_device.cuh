@@ -111,6 +111,47 @@ __device__ __forceinline__ bool tri_contains_rn(const double* v, double xx, doub
            orient_rn(v[4], v[5], v[0], v[1], xx, xy) >= 0.0;
 }
 
+// Fast pre-test of edge_near_rn in FP32, with P and Q given relative to X
+// (px = P - X, ...).  Returns 1 (near) or 0 (far) when the FP32 value of
+// rho^N is more than 10% away from R, and 2 when the exact FP64 test must
+// decide.  For every case that does not overflow, the FP32 evaluation of
+// rho^N is within 1% of the FP64 one (s, the chord L and rho carry relative
+// errors of order 2^-24 s and sqrt(10 * 2^-24); times N <= 50), and an
+// overflow to +inf means rho^N far above any admissible R: both give the
+// exact decision.
+__device__ __forceinline__ int edge_near_f32(float px, float py, float qx, float qy, int N, float R) {
+    const float ex = qx - px, ey = qy - py;
+    const float L = sqrtf(ex * ex + ey * ey);
+    const float s = (sqrtf(px * px + py * py) + sqrtf(qx * qx + qy * qy)) / L;
+    const float t = fmaxf(s * s - 1.0f, 0.0f);
+    const float rho = s + sqrtf(t);
+    float p = rho;
+    for (int i = 1; i < N; i++) p *= rho;
+    if (p < 0.9f * R) return 1;
+    if (p > 1.1f * R) return 0;
+    return 2;
+}
+
+// Ellipse membership of X for the triangle with vertices v (FP64): the FP32
+// pre-test per edge, the exact FP64 test only for undecided edges.
+__device__ __forceinline__ bool tri_near_fast(const double* v, double xx, double xy, int N, double R) {
+    const float Rf = (float)R;
+    float d[6];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        d[2 * i] = (float)(v[2 * i] - xx);
+        d[2 * i + 1] = (float)(v[2 * i + 1] - xy);
+    }
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+        const int a = e, b = (e + 1) % 3;
+        const int r = edge_near_f32(d[2 * a], d[2 * a + 1], d[2 * b], d[2 * b + 1], N, Rf);
+        if (r == 1) return true;
+        if (r == 2 && edge_near_rn(v[2 * a], v[2 * a + 1], v[2 * b], v[2 * b + 1], xx, xy, N, R)) return true;
+    }
+    return false;
+}
+
 // R = (w J) / (eps C_N)   (Eq. rho0 raised to the power N)
 __device__ __forceinline__ double ellipse_R_rn(double what, double J, double eps, double cn) {
     return rn_div(rn_mul(what, J), rn_mul(eps, cn));
