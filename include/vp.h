@@ -224,9 +224,28 @@ typedef struct vp_eval_item {
     double* u_dev;         /* device [d][M] */
 } vp_eval_item;
 
-/* Evaluate n items (possibly different meshes) with one launch per kernel
- * stage over all items.  Same per-item semantics and results as
- * vp_potential_eval. */
+/* A prepared batch of evaluations over many near-field builds (possibly
+ * different meshes and density counts).  vp_batch_create validates the items,
+ * builds the work list of a persistent far-sum kernel (work units: an item's
+ * block of target rows, taken from an atomic counter so uneven meshes
+ * balance; one launch per density-chunk width 1/2/4/8) and of one correction
+ * launch over all items' targets, picks the targets-per-thread tile of the
+ * far sum by timing the variants once per context (autotuning, on the
+ * first batch), and captures the whole launch sequence in a CUDA graph.
+ * The item pointers (f_dev, u_dev) are read at every launch, so new
+ * densities can be written in place and the batch relaunched.
+ * vp_batch_launch replays the graph on `stream` (asynchronous).  Results
+ * agree with vp_potential_eval item by item up to the order of the far-sum
+ * partial sums.  The batch holds device descriptors and charge buffers
+ * (about N * 2 * min(d, 8) floats per item) until released. */
+typedef struct vp_batch vp_batch;
+VP_API int vp_batch_create(vp_ctx* ctx, const vp_eval_item* items, int32_t n, int32_t precision, void* stream,
+                           vp_batch** out);
+VP_API int vp_batch_launch(vp_batch* batch, void* stream);
+VP_API void vp_batch_release(vp_batch* batch);
+
+/* Evaluate n items at once: vp_batch_create + vp_batch_launch + release
+ * (synchronises `stream`). */
 VP_API int vp_potential_eval_batch(vp_ctx* ctx, const vp_eval_item* items, int32_t n, int32_t precision, void* stream);
 
 /* ------------------------------------------------------------- profiling */

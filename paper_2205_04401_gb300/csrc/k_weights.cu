@@ -24,25 +24,60 @@ constexpr int STK = 256;      // sub-triangle stack per warp
 constexpr int LEAFCAP = 64;   // leaf buffer per warp
 constexpr int MAX_VISITED = 1 << 20;  // sub-triangles per pair before giving up with an error flag
 
-__device__ __forceinline__ double warp_sum(double v) {
+
+// Reduce-scatter of 16 per-lane values over the warp: after the five steps
+// lane l holds the warp total of value (l >> 1) (16 + 8 + 4 + 2 + 1 adds
+// instead of 5 x 15 for a butterfly of every value).
+__device__ __forceinline__ double reduce_scatter16(double* v, int lane) {
+    // step with offset 16: keep the half selected by bit 4 of the lane
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int i = 0; i < 8; i++) {
+        const bool hi = lane & 16;
+        const double send = hi ? v[i] : v[i + 8];
+        const double keep = hi ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const bool hi = lane & 8;
+        const double send = hi ? v[i] : v[i + 4];
+        const double keep = hi ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const bool hi = lane & 4;
+        const double send = hi ? v[i] : v[i + 2];
+        const double keep = hi ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool hi = lane & 2;
+        const double send = hi ? v[0] : v[1];
+        const double keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 // mu_i -> C_k for lanes k < nq, written to C[p*nq + k].
 __device__ __forceinline__ void finish_pair(const WeightsArgs& a, int64_t p, int T, int own, double xx, double xy,
-                                            double* m, int lane) {
+                                            double* m, int lane, const double* rc, const double* lc, double ln2) {
+    double v[16];
 #pragma unroll
-    for (int q = 0; q < VP_NB; q++) m[q] = warp_sum(m[q]);
+    for (int q = 0; q < VP_NB; q++) v[q] = m[q];
+    v[15] = 0.0;
+    // index held by this lane after the reduce-scatter: bits 4..1 of the lane
+    const double mine = reduce_scatter16(v, lane);
+    double s = 0.0;
+    const double* Qk = a.tab->Q[a.rule][lane < a.nq ? lane : 0];
+#pragma unroll
+    for (int q = 0; q < VP_NB; q++) s = fma(Qk[q], __shfl_sync(0xffffffffu, mine, 2 * q), s);
     if (lane < a.nq) {
-        const double* Qk = a.tab->Q[a.rule][lane];
-        double s = 0.0;
-#pragma unroll
-        for (int q = 0; q < VP_NB; q++) s += Qk[q] * m[q];
         if (lane != own) {
-            int64_t j = (int64_t)T * a.nq + lane;
-            s -= a.W[j] * kernel_G(xx - a.y[2 * j], xy - a.y[2 * j + 1]);
+            const int64_t j = (int64_t)T * a.nq + lane;
+            const double dx = xx - a.y[2 * j], dy = xy - a.y[2 * j + 1];
+            s -= a.W[j] * (vp_logd(dx * dx + dy * dy, rc, lc, ln2) * (0.5 * VP_INV_TWO_PI));
         }
         a.C[p * a.nq + lane] = s;
     }
@@ -162,7 +197,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_self(WeightsArgs a, cons
             }
         }
     }
-    finish_pair(a, p, T, own, xx, xy, m, lane);
+    finish_pair(a, p, T, own, xx, xy, m, lane, lt.rc, lt.lc, ln2);
     if (lane == 0) {
         a.pstat[p] = panels;
         a.pcap[p] = 0;
@@ -311,7 +346,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_near(WeightsArgs a, cons
         }
     }
     if (overflow && lane == 0) atomicOr(a.flag, VP_DEV_ERR_STACK);
-    finish_pair(a, p, T, own, xx, xy, m, lane);
+    finish_pair(a, p, T, own, xx, xy, m, lane, lt.rc, lt.lc, ln2);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) capped += __shfl_xor_sync(0xffffffffu, capped, o);
     if (lane == 0) {

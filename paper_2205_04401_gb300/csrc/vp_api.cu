@@ -741,16 +741,6 @@ int vp_potential_eval_host(vp_ctx* ctx, const vp_nf* nf, const double* f_host, i
     return VP_OK;
 }
 
-int vp_potential_eval_batch(vp_ctx* ctx, const vp_eval_item* items, int32_t n, int32_t precision, void* stream) {
-    if (!ctx_ok(ctx)) return VP_ERR_STATE;
-    if (n < 0 || (n > 0 && !items)) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_potential_eval_batch: bad arguments");
-    for (int32_t i = 0; i < n; i++) {
-        int rc = vp_potential_eval(ctx, items[i].nf, items[i].f_dev, items[i].d, items[i].u_dev, precision, stream);
-        if (rc) return rc;
-    }
-    return VP_OK;
-}
-
 int vp_profile_enable(vp_ctx* ctx, int32_t on) {
     if (!ctx_ok(ctx)) return VP_ERR_STATE;
     ctx->prof = on != 0;

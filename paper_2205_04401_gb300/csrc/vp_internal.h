@@ -45,6 +45,7 @@ struct vp_ctx {
     std::vector<ProfRec> prof_pending;
     std::vector<cudaEvent_t> prof_pool;
     double prof_ms[ST_COUNT] = {0};
+    int ff_tpt[4] = {0, 0, 0, 0};   // autotuned targets per thread of the batched far sum, per chunk width
     int64_t prof_n[ST_COUNT] = {0};
     int magic = 0x56504358;
 };

@@ -80,6 +80,10 @@ SIGNATURES = {
     "vp_potential_eval_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
                                          C.c_void_p]),
     "vp_potential_eval_batch": (C.c_int, [C.c_void_p, C.POINTER(EvalItem), C.c_int32, C.c_int32, C.c_void_p]),
+    "vp_batch_create": (C.c_int, [C.c_void_p, C.POINTER(EvalItem), C.c_int32, C.c_int32, C.c_void_p,
+                                  C.POINTER(C.c_void_p)]),
+    "vp_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "vp_batch_release": (None, [C.c_void_p]),
     "vp_rule_table": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int32,
                                 C.POINTER(C.c_int32)]),
 }
@@ -363,6 +367,38 @@ def potential_eval_batch(ctx: Context, items, precision: int = VP_FP64, stream=N
         arr[i].u_dev = u.data_ptr()
     rc = load().vp_potential_eval_batch(ctx.handle, arr, C.c_int32(len(items)), C.c_int32(precision), _stream(stream))
     _check(rc, ctx, "vp_potential_eval_batch")
+
+
+class Batch:
+    """A prepared, graph-captured batch (vp_batch_create / vp_batch_launch)."""
+
+    def __init__(self, ctx: Context, items, precision: int = VP_MIXED, stream=None):
+        self.ctx = ctx
+        self.items = list(items)         # keep the tensors alive
+        arr = (EvalItem * len(self.items))()
+        for i, (nf, f, u) in enumerate(self.items):
+            arr[i].nf = nf.handle
+            arr[i].f_dev = f.data_ptr()
+            arr[i].d = int(f.shape[0])
+            arr[i].u_dev = u.data_ptr()
+        h = C.c_void_p()
+        _check(load().vp_batch_create(ctx.handle, arr, C.c_int32(len(self.items)), C.c_int32(precision),
+                                      _stream(stream), C.byref(h)), ctx, "vp_batch_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(load().vp_batch_launch(self.handle, _stream(stream)), self.ctx, "vp_batch_launch")
+
+    def release(self):
+        if getattr(self, "handle", None):
+            load().vp_batch_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
 
 
 def rule_table(which: int):
