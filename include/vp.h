@@ -248,6 +248,60 @@ VP_API void vp_batch_release(vp_batch* batch);
  * (synchronises `stream`). */
 VP_API int vp_potential_eval_batch(vp_ctx* ctx, const vp_eval_item* items, int32_t n, int32_t precision, void* stream);
 
+/* --------------------------------------------------------------- serving */
+
+/* A serving loop with continuous batching (no counterpart in the paper; it
+ * serves the evaluation of Section 3.6 to a stream of requests).  A worker
+ * thread owns `slots` CUDA streams.  Requests wait in a FIFO queue and are
+ * admitted as soon as a slot is free and their device footprint (densities
+ * d*N*8 B, output d*M*8 B, evaluation workspace) fits in hbm_budget_bytes
+ * next to the requests already running; each runs H2D copy, the evaluation
+ * of vp_potential_eval and the D2H copy on its slot's stream, so requests
+ * that arrive while others run overlap with them on the device.  A result
+ * does not depend on what else is in flight.  Registered near-field builds
+ * stay resident; "cold" meshes (host arrays) are uploaded and built (targets
+ * = nodes, default parameters) on their first request, whose latency
+ * includes the build.  Requests larger than the budget fail with
+ * VP_ERR_OOM.  While a server runs, the context must not be used from other
+ * threads except through the server (it shares the context's tables). */
+typedef struct vp_server vp_server;
+
+typedef struct vp_server_stats_t {
+    int64_t completed, failed, queued, cold_builds;
+    int64_t evals;            /* sum over completed requests of d * M */
+    int64_t peak_bytes;       /* largest admitted device footprint */
+    int32_t max_concurrent;   /* most requests running at once */
+    int32_t reserved;
+    double p50_ms, p99_ms;    /* latency from submission to result */
+    double p50_wait_ms;       /* time from submission to admission */
+    double evals_per_s;       /* evals / (last completion - first submission) */
+} vp_server_stats_t;
+
+VP_API int vp_server_create(vp_ctx* ctx, int32_t slots, int64_t hbm_budget_bytes, int32_t precision,
+                            vp_server** out);
+/* Serve requests against an existing near-field build (the caller keeps it
+ * alive until vp_server_destroy). */
+VP_API int vp_server_register(vp_server* server, int64_t key, const vp_nf* nf);
+/* Register host mesh arrays (copied) to be built on the first request. */
+VP_API int vp_server_register_cold(vp_server* server, int64_t key, const double* vxy, int64_t nv, const int32_t* tri,
+                                   int64_t nt, int32_t rule);
+/* N (nodes) and M (targets) of a registered mesh (cold: M = N). */
+VP_API int vp_server_mesh_size(vp_server* server, int64_t key, int64_t* n_nodes, int64_t* n_targets);
+/* Queue one request: f_host [d][N] densities, u_host [d][M] result, both host
+ * memory that must stay valid until the request completes (page-locked
+ * memory lets the copies overlap; pageable memory works but serialises the
+ * scheduler on each copy).  *ticket identifies the request. */
+VP_API int vp_server_submit(vp_server* server, int64_t key, const double* f_host, int32_t d, double* u_host,
+                            int64_t* ticket);
+/* Block until the request completes (VP_ERR_TIMEOUT after timeout_s);
+ * *status is the request's own status, *latency_ms its submission-to-result
+ * time. */
+VP_API int vp_server_wait(vp_server* server, int64_t ticket, double timeout_s, int32_t* status, double* latency_ms);
+VP_API int vp_server_stats(vp_server* server, vp_server_stats_t* out);
+/* Drain the queue, stop the worker and release the server's streams and
+ * cold builds. */
+VP_API void vp_server_destroy(vp_server* server);
+
 /* ------------------------------------------------------------- profiling */
 
 /* Per-stage GPU timing.  When enabled, the library records a CUDA event pair

@@ -673,6 +673,8 @@ void vp_nf_release(vp_nf* nf) {
 }
 
 // ------------------------------------------------------------- evaluation
+}  // extern "C"
+
 static int eval_splits(const vp_ctx* ctx, int64_t M, int64_t N, int threads) {
     const int64_t blocks = (M + threads - 1) / threads;
     const int64_t want = 4LL * ctx->sm_count;
@@ -681,6 +683,42 @@ static int eval_splits(const vp_ctx* ctx, int64_t M, int64_t N, int threads) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(s, 64));
 }
 
+size_t eval_ws_bytes(const vp_ctx* ctx, const vp_nf* nf, int d, int precision) {
+    const int64_t N = nf->mesh->N, M = nf->M;
+    const int splits = eval_splits(ctx, M, N, 128);
+    const size_t partial_bytes = splits > 1 ? (size_t)splits * d * M * sizeof(double) : 0;
+    const size_t off_q = (partial_bytes + 255) & ~(size_t)255;
+    const size_t q_bytes = precision == VP_MIXED ? (size_t)N * 16 * sizeof(float) : 0;
+    return off_q + q_bytes + 256;
+}
+
+// The evaluation with caller-provided workspace (at least eval_ws_bytes).
+int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, double* u_dev, int32_t precision,
+              cudaStream_t s, void* ws, bool profile) {
+    const vp_mesh* mesh = nf->mesh;
+    const int64_t N = mesh->N, M = nf->M;
+    const int splits = eval_splits(ctx, M, N, 128);
+    const size_t partial_bytes = splits > 1 ? (size_t)splits * d * M * sizeof(double) : 0;
+    const size_t off_q = (partial_bytes + 255) & ~(size_t)255;
+    double* partial = splits > 1 ? (double*)ws : u_dev;
+    float* qbuf = (float*)((char*)ws + off_q);
+    const bool prof_saved = ctx->prof;
+    if (!profile) ctx->prof = false;
+    if (precision == VP_FP64)
+        PROF(ctx, ST_FAR_FP64, s,
+             launch_far_fp64(mesh->d_y, mesh->d_W, N, f_dev, d, nf->d_txy, nf->d_tnode, M, partial, splits, s));
+    else
+        PROF(ctx, ST_FAR_FF, s,
+             launch_far_ff(nf->src_ff, mesh->d_W, N, f_dev, d, nf->tgt_ff, nf->d_tnode, M, partial, qbuf, splits, s));
+    if (splits > 1) PROF(ctx, ST_REDUCE, s, launch_reduce_splits(partial, splits, (int64_t)d * M, u_dev, s));
+    PROF(ctx, ST_APPLY, s, launch_apply_fp64(nf->d_row, nf->d_ptri, nf->d_C, mesh->nq, f_dev, N, d, M, u_dev, s));
+    if (!profile) ctx->prof = prof_saved;
+    VP_LAUNCH_CHECK(ctx);
+    return VP_OK;
+}
+
+extern "C" {
+
 int vp_potential_eval(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, double* u_dev, int32_t precision,
                       void* stream) {
     if (!ctx_ok(ctx)) return VP_ERR_STATE;
@@ -688,28 +726,9 @@ int vp_potential_eval(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t
     if (!f_dev || !u_dev || d < 1 || d > 256 || (precision != VP_FP64 && precision != VP_MIXED))
         return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_potential_eval: bad arguments");
     DevGuard g(ctx->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    const vp_mesh* mesh = nf->mesh;
-    const int64_t N = mesh->N, M = nf->M;
-    const int splits = eval_splits(ctx, M, N, 128);
-    size_t partial_bytes = splits > 1 ? (size_t)splits * d * M * sizeof(double) : 0;
-    size_t q_bytes = precision == VP_MIXED ? (size_t)N * 16 * sizeof(float) : 0;
-    size_t off_q = (partial_bytes + 255) & ~(size_t)255;
-    int rc = ensure_ws(ctx, off_q + q_bytes + 256);
+    int rc = ensure_ws(ctx, eval_ws_bytes(ctx, nf, d, precision));
     if (rc) return rc;
-    double* partial = splits > 1 ? (double*)ctx->ws : u_dev;
-    float* qbuf = (float*)((char*)ctx->ws + off_q);
-    if (precision == VP_FP64)
-        PROF(ctx, ST_FAR_FP64, s,
-             launch_far_fp64(mesh->d_y, mesh->d_W, N, f_dev, d, nf->d_txy, nf->d_tnode, M, partial, splits, s));
-    else
-        PROF(ctx, ST_FAR_FF, s,
-             launch_far_ff(nf->src_ff, mesh->d_W, N, f_dev, d, nf->tgt_ff, nf->d_tnode, M, partial, qbuf, splits, s));
-    VP_LAUNCH_CHECK(ctx);
-    if (splits > 1) PROF(ctx, ST_REDUCE, s, launch_reduce_splits(partial, splits, (int64_t)d * M, u_dev, s));
-    PROF(ctx, ST_APPLY, s, launch_apply_fp64(nf->d_row, nf->d_ptri, nf->d_C, mesh->nq, f_dev, N, d, M, u_dev, s));
-    VP_LAUNCH_CHECK(ctx);
-    return VP_OK;
+    return eval_impl(ctx, nf, f_dev, d, u_dev, precision, (cudaStream_t)stream, ctx->ws, true);
 }
 
 int vp_potential_eval_host(vp_ctx* ctx, const vp_nf* nf, const double* f_host, int32_t d, double* u_host,

@@ -103,6 +103,11 @@ struct vp_nf {
 
 int vp_set_error(vp_ctx* ctx, int code, const std::string& msg);
 
+// Evaluation with explicit workspace (vp_potential_eval's body).
+size_t eval_ws_bytes(const vp_ctx* ctx, const vp_nf* nf, int d, int precision);
+int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, double* u_dev, int32_t precision,
+              cudaStream_t s, void* ws, bool profile);
+
 // ----------------------------------------------------------- launchers
 // scan: out[0] = 0, out[i+1] = sum_{j<=i} in[j] (int32 or int64 input), n >= 0
 int vp_exclusive_scan_i32(vp_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);

@@ -49,6 +49,16 @@ class NfStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("queued", C.c_int64), ("cold_builds", C.c_int64),
+                ("evals", C.c_int64), ("peak_bytes", C.c_int64), ("max_concurrent", C.c_int32),
+                ("reserved", C.c_int32), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("p50_wait_ms", C.c_double), ("evals_per_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class EvalItem(C.Structure):
     _fields_ = [("nf", C.c_void_p), ("f_dev", C.c_void_p), ("d", C.c_int32), ("u_dev", C.c_void_p)]
 
@@ -84,6 +94,15 @@ SIGNATURES = {
                                   C.POINTER(C.c_void_p)]),
     "vp_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "vp_batch_release": (None, [C.c_void_p]),
+    "vp_server_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_void_p)]),
+    "vp_server_register": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    "vp_server_register_cold": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                          C.c_int32]),
+    "vp_server_mesh_size": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "vp_server_submit": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int64)]),
+    "vp_server_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "vp_server_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "vp_server_destroy": (None, [C.c_void_p]),
     "vp_rule_table": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int32,
                                 C.POINTER(C.c_int32)]),
 }
@@ -399,6 +418,76 @@ class Batch:
             self.release()
         except Exception:
             pass
+
+
+class Server:
+    """vp_server_*: continuous-batching serving loop over resident meshes."""
+
+    def __init__(self, ctx: Context, slots: int = 4, hbm_budget_bytes: int = 8 << 30, precision: int = VP_MIXED):
+        self.ctx = ctx
+        h = C.c_void_p()
+        _check(load().vp_server_create(ctx.handle, C.c_int32(slots), C.c_int64(hbm_budget_bytes),
+                                       C.c_int32(precision), C.byref(h)), ctx, "vp_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def register(self, key: int, nf: NearField):
+        _check(load().vp_server_register(self.handle, C.c_int64(key), nf.handle), self.ctx, "vp_server_register")
+        self._keep[("nf", key)] = nf
+
+    def register_cold(self, key: int, vxy, tri, rule: int = VP_RULE_19_D9):
+        vxy = np.ascontiguousarray(vxy, np.float64)
+        tri = np.ascontiguousarray(tri, np.int32)
+        _check(load().vp_server_register_cold(self.handle, C.c_int64(key), vxy.ctypes.data_as(C.c_void_p),
+                                              C.c_int64(len(vxy)), tri.ctypes.data_as(C.c_void_p),
+                                              C.c_int64(len(tri)), C.c_int32(rule)), self.ctx,
+               "vp_server_register_cold")
+
+    def mesh_size(self, key: int):
+        n, m = C.c_int64(), C.c_int64()
+        _check(load().vp_server_mesh_size(self.handle, C.c_int64(key), C.byref(n), C.byref(m)), self.ctx,
+               "vp_server_mesh_size")
+        return n.value, m.value
+
+    def submit(self, key: int, f_host: np.ndarray, u_host: np.ndarray) -> int:
+        """f_host [d][N], u_host [d][M]: contiguous float64 host arrays kept
+        alive by the caller until the request completes."""
+        if f_host.dtype != np.float64 or u_host.dtype != np.float64 or not f_host.flags.c_contiguous \
+                or not u_host.flags.c_contiguous:
+            raise TypeError("f_host and u_host must be contiguous float64 arrays")
+        t = C.c_int64()
+        _check(load().vp_server_submit(self.handle, C.c_int64(key), f_host.ctypes.data_as(C.c_void_p),
+                                       C.c_int32(f_host.shape[0]), u_host.ctypes.data_as(C.c_void_p), C.byref(t)),
+               self.ctx, "vp_server_submit")
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        st, lat = C.c_int32(), C.c_double()
+        _check(load().vp_server_wait(self.handle, C.c_int64(ticket), C.c_double(timeout_s), C.byref(st),
+                                     C.byref(lat)), self.ctx, "vp_server_wait")
+        return st.value, lat.value
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().vp_server_stats(self.handle, C.byref(s)), self.ctx, "vp_server_stats")
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().vp_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pinned_empty(shape):
+    """A page-locked host float64 array (numpy view of a pinned torch tensor)."""
+    import torch
+    return torch.empty(shape, dtype=torch.float64).pin_memory().numpy()
 
 
 def rule_table(which: int):
