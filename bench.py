@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--extra", type=int, default=10000)
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 4, 5],
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
                     help="2: the 16,384-triangle star (default); 4: 200 uneven meshes in one batched launch; "
                          "5: serving loop with Poisson arrivals")
     ap.add_argument("--nmesh", type=int, default=200)
@@ -150,6 +150,116 @@ def run_reference(args):
                          "sample": f"{info['targets']} random targets of the workload per step (far sum over all "
                                    f"311,296 nodes, lists, near/self weights), OpenMP over targets"},
         "e2e": {"value": v, "unit": "target-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------ many densities
+def run_many(args):
+    """The star workload with 64 densities at once: 56 seeded Gaussian
+    mixtures and the manufactured f = -2 k^2 sin(kx) cos(ky), k = 1..8.
+    A step is one resident evaluation (far sum + corrections) of all 64;
+    the error is stated per density against the GPU FP64 path and, on
+    sampled targets, against the oracle."""
+    import torch
+    from paper_2205_04401_gb300 import inputs, vp
+    mesh, _, extra = make_inputs(args.ntri, args.extra)
+    fs = inputs.config3_densities(mesh)
+    ctx = vp.Context(0)
+    dev = torch.device("cuda", 0)
+    mh = vp.mesh_upload(ctx, mesh.vxy, mesh.tri, vp.VP_RULE_19_D9)
+    nf = vp.nearfield_build(ctx, mh, node_targets=True, txy=torch.from_numpy(extra).to(dev))
+    y, _ = vp.mesh_nodes(mh)
+    yn = y.cpu().numpy()
+    f_np = np.ascontiguousarray(np.stack([fn(yn) for fn in fs]))
+    f = torch.from_numpy(f_np).to(dev)
+    d = f.shape[0]
+    M = nf.M
+    stream = torch.cuda.current_stream()
+    u = torch.empty((d, M), dtype=torch.float64, device=dev)
+    for _ in range(max(args.warmup, 1)):
+        vp.potential_eval(ctx, nf, f, precision=vp.VP_MIXED, out=u)
+    vp.profile_enable(ctx, True)
+    vp.profile_reset(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        vp.potential_eval(ctx, nf, f, precision=vp.VP_MIXED, out=u)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = vp.profile_read(ctx)
+    vp.profile_enable(ctx, False)
+    ms = e0.elapsed_time(e1) / args.steps
+    per_density = None
+    ms64 = None
+    if not args.no_fp64:
+        # the FP64 path on 5 of the densities (all 64 take minutes)
+        sub = [0, 20, 40, 56, 63]
+        fsub = f[sub].contiguous()
+        e0.record(stream)
+        u64 = vp.potential_eval(ctx, nf, fsub, precision=vp.VP_FP64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) * d / len(sub)
+        per_density = {str(k): float(v) for k, v in
+                       zip(sub, ((u[sub] - u64).abs().amax(1) / u64.abs().amax(1)).cpu().numpy())}
+    # the tensor-core correction apply (digit split of C and f), 5, 4 and 3 digits
+    tc = {}
+    for levels in (5, 4, 3):
+        t0 = time.perf_counter()
+        vp.nf_prepare_tc(nf, levels)
+        prep_s = time.perf_counter() - t0
+        ut = torch.empty_like(u)
+        vp.potential_eval(ctx, nf, f, precision=vp.VP_MIXED_TC, out=ut)
+        vp.profile_enable(ctx, True)
+        vp.profile_reset(ctx)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            vp.potential_eval(ctx, nf, f, precision=vp.VP_MIXED_TC, out=ut)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        status = vp.device_status(ctx)
+        p2 = vp.profile_read(ctx)
+        vp.profile_enable(ctx, False)
+        rec = {"levels": levels, "ms_per_step": e0.elapsed_time(e1) / args.steps, "device_status": status,
+               "apply_tc_ms": round(p2["apply_tc"][1] / args.steps, 3) if p2.get("apply_tc", (0,))[0] else None,
+               "prepare_s": prep_s, "plan": vp.nf_tc_info(nf)}
+        if per_density is not None:
+            rec["rel_err_per_density_vs_gpu_fp64"] = {
+                str(k): float(v) for k, v in
+                zip(sub, ((ut[sub] - u64).abs().amax(1) / u64.abs().amax(1)).cpu().numpy())}
+        rec["rel_err_vs_mixed_fp64_apply_max"] = float(((ut - u).abs().amax(1) / u.abs().amax(1)).max())
+        tc[str(levels)] = rec
+        if levels == 5:
+            u_tc5 = ut
+    rel_or = None
+    rel_or_tc = None
+    if not args.no_oracle_check:
+        from oracle.oracle import Oracle
+        o = Oracle("far19")
+        s = o.setup(mesh.vxy, mesh.tri, node_targets=True, extra=extra)
+        fo = np.stack([fn(s["yxy"]) for fn in fs])
+        smp = np.sort(np.random.default_rng(3).choice(M, 48, replace=False))
+        uo, _ = o.potential(s, fo, targets=smp)
+        ug = u.cpu().numpy()[:, smp]
+        rel_or = (np.abs(ug - uo).max(1) / np.abs(uo).max(1)).tolist()
+        ug = u_tc5.cpu().numpy()[:, smp]
+        rel_or_tc = (np.abs(ug - uo).max(1) / np.abs(uo).max(1)).tolist()
+    line = {
+        "metric": "target_evals_per_s", "value": d * M / (ms / 1e3), "unit": "target-evals/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32x2+f64", "data": "synthetic",
+        "config": {"workload": "star5_16384tri_19pt_64densities", "targets": M, "nodes": nf.mesh.N, "densities": d,
+                   "step": "resident potential_eval of 64 densities"},
+        "pair_densities_per_s": d * M * nf.mesh.N / (ms / 1e3), "clocks": clk,
+        "fp64_ms_extrapolated_to_64": ms64, "mixed_over_fp64": (ms64 / ms) if ms64 else None,
+        "rel_err_per_density_vs_gpu_fp64": per_density, "rel_err_per_density_vs_oracle_sampled": rel_or,
+        "tensor_core_apply": tc, "tc5_rel_err_per_density_vs_oracle_sampled": rel_or_tc,
+        "stage_ms": {k: round(v[1] / args.steps, 3) for k, v in prof.items() if v[0]},
     }
     print(json.dumps(line))
 
@@ -343,6 +453,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == 3:
+        return run_many(args)
     if args.config == 4:
         return run_batch(args)
     if args.config == 5:

@@ -64,8 +64,15 @@ typedef enum vp_rule { VP_RULE_16_D8 = 16, VP_RULE_19_D9 = 19 } vp_rule;
 
 /* Arithmetic of vp_potential_eval.  VP_FP64: FP64 everywhere.  VP_MIXED: the
  * far sum in compensated FP32 (float-float coordinates and logarithm, FP64
- * per-tile reduction); correction weights and their application stay FP64. */
-typedef enum vp_precision { VP_FP64 = 0, VP_MIXED = 1 } vp_precision;
+ * per-tile reduction); correction weights and their application stay FP64.
+ * VP_MIXED_TC: the far sum of VP_MIXED; the corrections applied on the tensor
+ * cores from an exact split of C and f into L balanced base-128 digits held
+ * as bf16 (vp_nf_prepare_tc), accumulated exactly in FP32 and combined in
+ * FP64.  Its only error beyond VP_MIXED is the rounding of every weight to
+ * 7L - 1 bits below the largest weight of its kind (near or self) for its
+ * target, and of every density value to 7L - 1 bits below the largest value
+ * of its density. */
+typedef enum vp_precision { VP_FP64 = 0, VP_MIXED = 1, VP_MIXED_TC = 2 } vp_precision;
 
 /* Parameters of the near-field characterisation and correction weights. */
 typedef struct vp_nf_params {
@@ -181,12 +188,39 @@ VP_API int vp_nf_weights(const vp_nf* nf, double* w_dev, void* stream);
 /* Release a near-field build.  NULL is ignored. */
 VP_API void vp_nf_release(vp_nf* nf);
 
+/* Plan of the tensor-core correction apply (VP_MIXED_TC; the last sum of the
+ * subtract-and-add evaluation, Section 3.6, as a block-sparse times dense
+ * product).  Targets are ordered along a Morton curve and cut into tiles of
+ * 128; each tile's near-field rows become one dense block row over the union
+ * of its triangles (24 columns per triangle; near and self pairs in separate
+ * runs with their own row exponents), its weights split into `levels`
+ * (3, 4 or 5) bf16 digit planes and stored on the device, levels x 2 bytes
+ * per entry of the dense rows (see vp_nf_tc_info).  The weights and densities
+ * are rounded to 7 levels - 1 bits below their run/density maximum: 5 levels
+ * hold the synthetic star workloads within 1e-10 of the FP64 result, 4 and
+ * 3 levels within about 3e-9 and 5e-7.
+ * Replaces an earlier plan of nf; synchronises `stream`.
+ * Errors: VP_ERR_INVALID_ARG for other levels or when a tile holds more than
+ * 16384 near pairs (then use VP_MIXED); VP_ERR_OOM; VP_ERR_CUDA. */
+VP_API int vp_nf_prepare_tc(vp_ctx* ctx, vp_nf* nf, int32_t levels, void* stream);
+
+/* Synchronise `stream`, then report and clear the device-side error flags of
+ * the context's asynchronous kernels (VP_ERR_TIMEOUT when a bounded wait of
+ * the tensor-core apply gave up; its output is then not valid). */
+VP_API int vp_device_status(vp_ctx* ctx, void* stream);
+
+/* The tensor-core plan of nf: digits, tiles, chunks of 48 columns and
+ * device bytes (all 0 without a plan).  Any pointer may be NULL. */
+VP_API int vp_nf_tc_info(const vp_nf* nf, int32_t* levels, int64_t* n_tiles, int64_t* n_chunks, int64_t* bytes);
+
 /* ------------------------------------------------------------- evaluation */
 
 /* u = far + corrections (Section 3.6) for d densities.
  * f_dev: device [d][N] float64 density values at the mesh nodes.
  * u_dev: device [d][M] float64 output, fully overwritten.
- * precision: VP_FP64 or VP_MIXED.  1 <= d <= 256.
+ * precision: VP_FP64, VP_MIXED or VP_MIXED_TC.  1 <= d <= 256.  VP_MIXED_TC
+ * builds the tensor-core plan with 5 digits on first use if
+ * vp_nf_prepare_tc was not called (that first call synchronises `stream`).
  * Uses workspace owned by the context: calls on one context must be issued
  * on one stream (or serialised by the caller). */
 VP_API int vp_potential_eval(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, double* u_dev,

@@ -20,6 +20,8 @@
 
 namespace {
 
+int pick_chunk(int d) { return d >= 8 ? 8 : (d >= 4 ? 4 : (d >= 2 ? 2 : 1)); }
+
 // ------------------------------------------------------------- FP64 far
 constexpr int F64_THREADS = 128;
 constexpr int F64_TILE = 128;
@@ -79,27 +81,140 @@ __global__ void k_reduce_splits(const double* __restrict__ partial, int splits, 
 }
 
 // ------------------------------------------------------- corrections
-// Warp per target: lanes run over the flattened (pair, node) entries of the
-// target's row; u[k][t] += sum C[e] f[k][T_p nq + node].
-__global__ void k_apply_fp64(const int64_t* __restrict__ row, const int32_t* __restrict__ ptri,
-                             const double* __restrict__ C, int nq, const double* __restrict__ f, int64_t N, int d,
-                             int64_t M, double* __restrict__ u) {
+// Few densities: warp per target; lanes run over the flattened (pair, node)
+// entries of the target's row, each entry's weight read once for D densities;
+// u[d0 + k][t] += sum C[e] f[d0 + k][T_p nq + node].
+template <int NQ, int D>
+__global__ void __launch_bounds__(256) k_apply_rows(const int64_t* __restrict__ row, const int32_t* __restrict__ ptri,
+                                                    const double* __restrict__ C, const double* __restrict__ f,
+                                                    int64_t N, int d, int d0, int64_t M, double* __restrict__ u) {
     const int lane = threadIdx.x & 31;
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= M) return;
-    const int64_t e0 = row[t] * nq, e1 = row[t + 1] * nq;
-    for (int k = 0; k < d; k++) {
-        const double* fk = f + (int64_t)k * N;
-        double s = 0.0;
-        for (int64_t e = e0 + lane; e < e1; e += 32) {
-            const int64_t p = e / nq;
-            const int node = (int)(e - p * nq);
-            s += C[e] * fk[(int64_t)ptri[p] * nq + node];
+    const int64_t e0 = row[t] * NQ, e1 = row[t + 1] * NQ;
+    double s[D];
+#pragma unroll
+    for (int k = 0; k < D; k++) s[k] = 0.0;
+    int64_t e = e0 + lane;
+    // four entries in flight per lane
+    for (; e + 96 < e1; e += 128) {
+        double c[4];
+        int64_t src[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int64_t ei = e + 32 * i;
+            const int64_t p = ei / NQ;
+            c[i] = C[ei];
+            src[i] = (int64_t)ptri[p] * NQ + (ei - p * NQ);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) u[(int64_t)k * M + t] += s;
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int k = 0; k < D; k++) s[k] += c[i] * f[(int64_t)(d0 + k) * N + src[i]];
     }
+    for (; e < e1; e += 32) {
+        const int64_t p = e / NQ;
+        const double c = C[e];
+        const int64_t src = (int64_t)ptri[p] * NQ + (e - p * NQ);
+#pragma unroll
+        for (int k = 0; k < D; k++) s[k] += c * f[(int64_t)(d0 + k) * N + src];
+    }
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < D; k++)
+            if (d0 + k < d) u[(int64_t)(d0 + k) * M + t] += s[k];
+    }
+}
+
+// fT[j][k] = f[k][j] (node-major copy of the densities), 32 x 32 tiles.
+__global__ void k_transpose_f(const double* __restrict__ f, int d, int64_t N, double* __restrict__ fT) {
+    __shared__ double tile[32][33];
+    const int64_t j0 = (int64_t)blockIdx.x * 32;
+    const int k0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int k = k0 + r;
+        const int64_t j = j0 + threadIdx.x;
+        tile[r][threadIdx.x] = (k < d && j < N) ? f[(int64_t)k * N + j] : 0.0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t j = j0 + r;
+        const int k = k0 + threadIdx.x;
+        if (j < N && k < d) fT[j * d + k] = tile[threadIdx.x][r];
+    }
+}
+
+// Many densities: warp per target, densities across lanes (lane + 32 i); the
+// warp loads 32 entries (weight, source node) at a time and broadcasts each,
+// so every load of the node-major densities is one coalesced row.
+template <int NQ, int DB>
+__global__ void __launch_bounds__(256) k_apply_many(const int64_t* __restrict__ row, const int32_t* __restrict__ ptri,
+                                                    const double* __restrict__ C, const double* __restrict__ fT,
+                                                    int d, int64_t M, double* __restrict__ u) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= M) return;
+    const int64_t e0 = row[t] * NQ, e1 = row[t + 1] * NQ;
+    double s[DB];
+#pragma unroll
+    for (int i = 0; i < DB; i++) s[i] = 0.0;
+    for (int64_t base = e0; base < e1; base += 32) {
+        const int n = (int)min((int64_t)32, e1 - base);
+        double myc = 0.0;
+        int64_t mysrc = 0;
+        if (lane < n) {
+            const int64_t e = base + lane;
+            const int64_t p = e / NQ;
+            myc = C[e];
+            mysrc = ((int64_t)ptri[p] * NQ + (e - p * NQ)) * d;
+        }
+        for (int j = 0; j < n; j++) {
+            const double c = __shfl_sync(0xffffffffu, myc, j);
+            const int64_t src = __shfl_sync(0xffffffffu, mysrc, j);
+#pragma unroll
+            for (int i = 0; i < DB; i++) {
+                const int k = lane + 32 * i;
+                if (k < d) s[i] += c * fT[src + k];
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < DB; i++) {
+        const int k = lane + 32 * i;
+        if (k < d) u[(int64_t)k * M + t] += s[i];
+    }
+}
+
+template <int NQ>
+void apply_rows(const int64_t* row, const int32_t* ptri, const double* C, const double* f, int64_t N, int d,
+                int64_t M, double* u, cudaStream_t s) {
+    const unsigned grid = (unsigned)((M * 32 + 255) / 256);
+    for (int d0 = 0; d0 < d;) {
+        const int D = pick_chunk(d - d0);
+        switch (D) {
+            case 8: k_apply_rows<NQ, 8><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u); break;
+            case 4: k_apply_rows<NQ, 4><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u); break;
+            case 2: k_apply_rows<NQ, 2><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u); break;
+            default: k_apply_rows<NQ, 1><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u); break;
+        }
+        d0 += D;
+    }
+}
+
+template <int NQ>
+void apply_many(const int64_t* row, const int32_t* ptri, const double* C, const double* fT, int d, int64_t M,
+                double* u, cudaStream_t s) {
+    const unsigned grid = (unsigned)((M * 32 + 255) / 256);
+    const int db = (d + 31) / 32;
+    if (db <= 1) k_apply_many<NQ, 1><<<grid, 256, 0, s>>>(row, ptri, C, fT, d, M, u);
+    else if (db <= 2) k_apply_many<NQ, 2><<<grid, 256, 0, s>>>(row, ptri, C, fT, d, M, u);
+    else if (db <= 4) k_apply_many<NQ, 4><<<grid, 256, 0, s>>>(row, ptri, C, fT, d, M, u);
+    else k_apply_many<NQ, 8><<<grid, 256, 0, s>>>(row, ptri, C, fT, d, M, u);
 }
 
 // ------------------------------------------------------ float-float far
@@ -134,8 +249,6 @@ __global__ void __launch_bounds__(FF_THREADS) k_far_ff(const float* __restrict__
     const int64_t tbase = (int64_t)blockIdx.x * (FF_THREADS * FF_TPT) + threadIdx.x;
     ff_far_block<D, FF_TPT>(sm, shi, slo, q, j0, j1, thi, tlo, tnode, M, tbase, d, d0, partial + (int64_t)split * d * M);
 }
-
-int pick_chunk(int d) { return d >= 8 ? 8 : (d >= 4 ? 4 : (d >= 2 ? 2 : 1)); }
 
 }  // namespace
 
@@ -187,9 +300,20 @@ void launch_reduce_splits(const double* partial, int splits, int64_t count, doub
     if (count > 0) k_reduce_splits<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(partial, splits, count, out);
 }
 
+size_t apply_ws_bytes(int64_t N, int d) { return d >= APPLY_MANY_MIN_D ? (size_t)N * d * sizeof(double) : 0; }
+
 void launch_apply_fp64(const int64_t* row, const int32_t* ptri, const double* C, int nq, const double* f, int64_t N,
-                       int d, int64_t M, double* u, cudaStream_t s) {
-    if (M > 0) k_apply_fp64<<<(unsigned)((M * 32 + 255) / 256), 256, 0, s>>>(row, ptri, C, nq, f, N, d, M, u);
+                       int d, int64_t M, double* u, double* fT, cudaStream_t s) {
+    if (M <= 0) return;
+    if (d >= APPLY_MANY_MIN_D && fT) {
+        dim3 tg((unsigned)((N + 31) / 32), (unsigned)((d + 31) / 32)), tb(32, 8);
+        k_transpose_f<<<tg, tb, 0, s>>>(f, d, N, fT);
+        if (nq == 19) apply_many<19>(row, ptri, C, fT, d, M, u, s);
+        else apply_many<16>(row, ptri, C, fT, d, M, u, s);
+    } else {
+        if (nq == 19) apply_rows<19>(row, ptri, C, f, N, d, M, u, s);
+        else apply_rows<16>(row, ptri, C, f, N, d, M, u, s);
+    }
 }
 
 void launch_ff_split(const double* xy, int64_t n, double ox, double oy, double q, FFCoords out, cudaStream_t s) {

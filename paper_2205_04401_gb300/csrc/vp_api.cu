@@ -113,6 +113,7 @@ int check_flag(vp_ctx* ctx, int32_t* d_flag, cudaStream_t s) {
     if (h & VP_DEV_ERR_DEGEN) return vp_set_error(ctx, VP_ERR_DEGENERATE_TRI, "triangle with zero area");
     if (h & VP_DEV_ERR_STACK) return vp_set_error(ctx, VP_ERR_CUDA, "near-field subdivision stack overflow");
     if (h & VP_DEV_ERR_CELL) return vp_set_error(ctx, VP_ERR_CUDA, "grid cell list exceeds sort capacity");
+    if (h & VP_DEV_ERR_TIMEOUT) return vp_set_error(ctx, VP_ERR_TIMEOUT, "a pipelined kernel timed out waiting for its copies");
     return VP_OK;
 }
 
@@ -135,6 +136,8 @@ void free_nf_device(vp_nf* nf) {
                   nf->src_ff.hi, nf->src_ff.lo, nf->tgt_ff.hi, nf->tgt_ff.lo};
     for (void* p : ps)
         if (p) cudaFree(p);
+    tc_plan_free(nf->tc);
+    nf->tc = nullptr;
 }
 
 }  // namespace
@@ -146,7 +149,7 @@ int vp_set_error(vp_ctx* ctx, int code, const std::string& msg) {
 
 static const char* kStageNames[ST_COUNT] = {
     "mesh_nodes", "tri_geom", "tri_cells", "cell_sort", "target_cells", "locate", "list_count", "list_fill",
-    "weights_self", "weights_near", "ff_split", "far_fp64", "far_ff", "reduce_splits", "apply_fp64"};
+    "weights_self", "weights_near", "ff_split", "far_fp64", "far_ff", "reduce_splits", "apply_fp64", "apply_tc"};
 
 static cudaEvent_t prof_event(vp_ctx* ctx) {
     if (!ctx->prof_pool.empty()) {
@@ -688,8 +691,9 @@ size_t eval_ws_bytes(const vp_ctx* ctx, const vp_nf* nf, int d, int precision) {
     const int splits = eval_splits(ctx, M, N, 128);
     const size_t partial_bytes = splits > 1 ? (size_t)splits * d * M * sizeof(double) : 0;
     const size_t off_q = (partial_bytes + 255) & ~(size_t)255;
-    const size_t q_bytes = precision == VP_MIXED ? (size_t)N * 16 * sizeof(float) : 0;
-    return off_q + q_bytes + 256;
+    const size_t q_bytes = precision != VP_FP64 ? (size_t)N * 16 * sizeof(float) : 0;
+    const size_t off_t = (off_q + q_bytes + 255) & ~(size_t)255;
+    return off_t + (precision == VP_MIXED_TC ? tc_ws_bytes(nf) : apply_ws_bytes(N, d)) + 256;
 }
 
 // The evaluation with caller-provided workspace (at least eval_ws_bytes).
@@ -702,6 +706,9 @@ int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, doub
     const size_t off_q = (partial_bytes + 255) & ~(size_t)255;
     double* partial = splits > 1 ? (double*)ws : u_dev;
     float* qbuf = (float*)((char*)ws + off_q);
+    const size_t q_bytes = precision != VP_FP64 ? (size_t)N * 16 * sizeof(float) : 0;
+    void* apply_ws = (char*)ws + ((off_q + q_bytes + 255) & ~(size_t)255);
+    double* fT = apply_ws_bytes(N, d) ? (double*)apply_ws : nullptr;
     const bool prof_saved = ctx->prof;
     if (!profile) ctx->prof = false;
     if (precision == VP_FP64)
@@ -711,7 +718,16 @@ int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, doub
         PROF(ctx, ST_FAR_FF, s,
              launch_far_ff(nf->src_ff, mesh->d_W, N, f_dev, d, nf->tgt_ff, nf->d_tnode, M, partial, qbuf, splits, s));
     if (splits > 1) PROF(ctx, ST_REDUCE, s, launch_reduce_splits(partial, splits, (int64_t)d * M, u_dev, s));
-    PROF(ctx, ST_APPLY, s, launch_apply_fp64(nf->d_row, nf->d_ptri, nf->d_C, mesh->nq, f_dev, N, d, M, u_dev, s));
+    if (precision == VP_MIXED_TC) {
+        int rc = VP_OK;
+        PROF(ctx, ST_APPLY_TC, s, rc = tc_apply(ctx, nf, f_dev, d, u_dev, apply_ws, s));
+        if (rc) {
+            if (!profile) ctx->prof = prof_saved;
+            return rc;
+        }
+    } else {
+        PROF(ctx, ST_APPLY, s, launch_apply_fp64(nf->d_row, nf->d_ptri, nf->d_C, mesh->nq, f_dev, N, d, M, u_dev, fT, s));
+    }
     if (!profile) ctx->prof = prof_saved;
     VP_LAUNCH_CHECK(ctx);
     return VP_OK;
@@ -723,9 +739,13 @@ int vp_potential_eval(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t
                       void* stream) {
     if (!ctx_ok(ctx)) return VP_ERR_STATE;
     if (!nf_ok(nf) || nf->ctx != ctx) return vp_set_error(ctx, VP_ERR_STATE, "vp_potential_eval: bad near-field handle");
-    if (!f_dev || !u_dev || d < 1 || d > 256 || (precision != VP_FP64 && precision != VP_MIXED))
+    if (!f_dev || !u_dev || d < 1 || d > 256 || precision < VP_FP64 || precision > VP_MIXED_TC)
         return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_potential_eval: bad arguments");
     DevGuard g(ctx->device);
+    if (precision == VP_MIXED_TC && !nf->tc) {
+        int rc = tc_plan_build(ctx, const_cast<vp_nf*>(nf), 5, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
     int rc = ensure_ws(ctx, eval_ws_bytes(ctx, nf, d, precision));
     if (rc) return rc;
     return eval_impl(ctx, nf, f_dev, d, u_dev, precision, (cudaStream_t)stream, ctx->ws, true);
@@ -757,6 +777,33 @@ int vp_potential_eval_host(vp_ctx* ctx, const vp_nf* nf, const double* f_host, i
     if (rc) return rc;
     VP_CUDA_TRY(ctx, cudaMemcpyAsync(u_host, ud, ub, cudaMemcpyDeviceToHost, s));
     VP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return VP_OK;
+}
+
+int vp_nf_prepare_tc(vp_ctx* ctx, vp_nf* nf, int32_t levels, void* stream) {
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    if (!nf_ok(nf) || nf->ctx != ctx) return vp_set_error(ctx, VP_ERR_STATE, "vp_nf_prepare_tc: bad near-field handle");
+    DevGuard g(ctx->device);
+    return tc_plan_build(ctx, nf, levels, (cudaStream_t)stream);
+}
+
+int vp_device_status(vp_ctx* ctx, void* stream) {
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = check_flag(ctx, ctx->d_flag, s);
+    VP_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int32_t), s));
+    VP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return rc;
+}
+
+int vp_nf_tc_info(const vp_nf* nf, int32_t* levels, int64_t* n_tiles, int64_t* n_chunks, int64_t* bytes) {
+    if (!nf_ok(nf)) return VP_ERR_STATE;
+    const TcPlan* p = nf->tc;
+    if (levels) *levels = p ? p->levels : 0;
+    if (n_tiles) *n_tiles = p ? p->n_tiles : 0;
+    if (n_chunks) *n_chunks = p ? p->n_chunks : 0;
+    if (bytes) *bytes = p ? (int64_t)p->bytes : 0;
     return VP_OK;
 }
 

@@ -19,7 +19,7 @@ struct FFCoords {
 enum VpStage {
     ST_MESH_NODES = 0, ST_TRI_GEOM, ST_TRI_CELLS, ST_CELL_SORT, ST_TARGET_CELLS, ST_LOCATE, ST_LIST_COUNT,
     ST_LIST_FILL, ST_WEIGHTS_SELF, ST_WEIGHTS_NEAR, ST_FF_SPLIT, ST_FAR_FP64, ST_FAR_FF, ST_REDUCE, ST_APPLY,
-    ST_COUNT
+    ST_APPLY_TC, ST_COUNT
 };
 
 struct ProfRec {
@@ -67,6 +67,22 @@ struct vp_mesh {
     int magic = 0x56504d48;
 };
 
+// Tensor-core correction apply: the correction matrix re-laid per tile of 128
+// targets (Morton order) as dense bf16 digit images over the union of the
+// tile's triangles (k_tc.cu).
+struct TcPlan {
+    int levels = 0;                 // digits per value
+    int64_t n_tiles = 0, n_chunks = 0;
+    int32_t* d_perm = nullptr;      // [n_tiles 128] targets of each tile (-1 pads)
+    int32_t* d_pos = nullptr;       // [M] position of each target in d_perm
+    int64_t* d_chunk_ptr = nullptr; // [n_tiles + 1] first chunk of each tile
+    int32_t* d_chunk_near = nullptr;// [n_tiles] near-pair chunks of each tile (its self chunks follow)
+    int32_t* d_chunk_tri = nullptr; // [n_chunks][2] triangles of each chunk
+    int32_t* d_rexp = nullptr;      // [2][M] row exponents of the near and the self weights
+    uint16_t* d_A = nullptr;        // [n_chunks] digit images (bf16 bits)
+    size_t a_bytes = 0, bytes = 0;
+};
+
 struct vp_nf {
     vp_ctx* ctx = nullptr;
     const vp_mesh* mesh = nullptr;
@@ -85,6 +101,7 @@ struct vp_nf {
     double ff_origin[2] = {0, 0};
     double ff_scale = 1.0;         // grid spacing q of the hi parts
     vp_nf_stats_t stats{};
+    TcPlan* tc = nullptr;          // tensor-core apply plan (vp_nf_prepare_tc)
     int magic = 0x56504e46;
 };
 
@@ -175,6 +192,16 @@ void launch_far_fp64(const double* y, const double* W, int64_t N, const double* 
 void launch_far_ff(const FFCoords& src, const double* W, int64_t N, const double* f, int d, const FFCoords& tgt,
                    const int32_t* tnode, int64_t M, double* partial, float* qbuf, int splits, cudaStream_t s);
 void launch_reduce_splits(const double* partial, int splits, int64_t count, double* out, cudaStream_t s);
+// Densities from which the correction is applied with densities across lanes
+// (needs a node-major copy of f: apply_ws_bytes); fewer, or fT == nullptr,
+// take the entry-parallel kernel that needs no workspace.
+constexpr int APPLY_MANY_MIN_D = 16;
+size_t apply_ws_bytes(int64_t N, int d);
 void launch_apply_fp64(const int64_t* row, const int32_t* ptri, const double* C, int nq, const double* f, int64_t N,
-                       int d, int64_t M, double* u, cudaStream_t s);
+                       int d, int64_t M, double* u, double* fT, cudaStream_t s);
+// tensor-core apply (k_tc.cu)
+int tc_plan_build(vp_ctx* ctx, vp_nf* nf, int levels, cudaStream_t s);
+void tc_plan_free(TcPlan* p);
+size_t tc_ws_bytes(const vp_nf* nf);
+int tc_apply(vp_ctx* ctx, const vp_nf* nf, const double* f, int d, double* u, void* ws, cudaStream_t s);
 void launch_ff_split(const double* xy, int64_t n, double ox, double oy, double q, FFCoords out, cudaStream_t s);

@@ -102,7 +102,7 @@ extern "C" int vp_potential_eval_noalloc(vp_ctx* ctx, const vp_nf* nf, const dou
         launch_far_ff(nf->src_ff, mesh->d_W, N, f_dev, d, nf->tgt_ff, nf->d_tnode, M, partial, qbuf, splits, s);
     VP_LAUNCH_CHECK(ctx);
     if (splits > 1) launch_reduce_splits(partial, splits, (int64_t)d * M, u_dev, s);
-    launch_apply_fp64(nf->d_row, nf->d_ptri, nf->d_C, mesh->nq, f_dev, N, d, M, u_dev, s);
+    launch_apply_fp64(nf->d_row, nf->d_ptri, nf->d_C, mesh->nq, f_dev, N, d, M, u_dev, nullptr, s);
     VP_LAUNCH_CHECK(ctx);
     return VP_OK;
 }

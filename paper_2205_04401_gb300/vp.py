@@ -24,6 +24,7 @@ VP_RULE_16_D8 = 16
 VP_RULE_19_D9 = 19
 VP_FP64 = 0
 VP_MIXED = 1
+VP_MIXED_TC = 2
 
 _lib = None
 
@@ -84,6 +85,10 @@ SIGNATURES = {
     "vp_nf_lists": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vp_nf_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "vp_nf_release": (None, [C.c_void_p]),
+    "vp_nf_prepare_tc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "vp_nf_tc_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_int64)]),
+    "vp_device_status": (C.c_int, [C.c_void_p, C.c_void_p]),
     "vp_potential_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
     "vp_potential_eval_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
                                             C.c_void_p]),
@@ -302,6 +307,25 @@ def nf_stats(nf: NearField) -> dict:
     s = NfStats()
     _check(load().vp_nf_stats(nf.handle, C.byref(s)), nf.ctx, "vp_nf_stats")
     return s.as_dict()
+
+
+def nf_prepare_tc(nf: NearField, levels: int = 5, stream=None):
+    """vp_nf_prepare_tc: build the tensor-core apply plan (levels 3, 4 or 5)."""
+    _check(load().vp_nf_prepare_tc(nf.ctx.handle, nf.handle, C.c_int32(levels), _stream(stream)), nf.ctx,
+           "vp_nf_prepare_tc")
+
+
+def nf_tc_info(nf: NearField) -> dict:
+    lv = C.c_int32()
+    nt, nc, nb = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load().vp_nf_tc_info(nf.handle, C.byref(lv), C.byref(nt), C.byref(nc), C.byref(nb)), nf.ctx,
+           "vp_nf_tc_info")
+    return {"levels": lv.value, "n_tiles": nt.value, "n_chunks": nc.value, "bytes": nb.value}
+
+
+def device_status(ctx: Context, stream=None) -> int:
+    """vp_device_status: synchronise and return (and clear) the device error status."""
+    return int(load().vp_device_status(ctx.handle, _stream(stream)))
 
 
 def nf_lists(nf: NearField, stream=None):

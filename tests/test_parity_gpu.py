@@ -177,6 +177,27 @@ def test_many_densities_and_extra_only(vp, ctx, tables, cfg1):
     assert rel_err(g["u1"], u_or).max() <= 1e-10
 
 
+def test_forty_densities_on_the_star_mesh(vp, ctx, tables, star):
+    """d = 40 takes the densities-across-lanes correction kernel (d >= 16):
+    the oracle on sampled targets, and each density evaluated alone (which
+    takes the entry-parallel kernel) to the FP64 bar."""
+    s, _, sample, _, _, _, g = star
+    mesh = inputs.star_mesh(n_tri=2048, seed=77, relax_iters=6)
+    fs = [inputs.gaussian_mix(mesh, 900 + i) for i in range(32)]
+    fs += [inputs.manufactured_sin_cos(float(k)) for k in range(1, 9)]
+    f = np.ascontiguousarray(np.stack([fn(s["yxy"]) for fn in fs]))
+    o = Oracle("far19", tables=tables)
+    sub = sample[::4]
+    u_or, _ = o.potential(s, f, targets=sub)
+    fd = torch.from_numpy(f).cuda()
+    for prec, tol in ((0, 1e-12), (1, 1e-10)):
+        u = vp.potential_eval(ctx, g["nf"], fd, precision=prec).cpu().numpy()
+        assert rel_err(u[:, sub], u_or).max() <= tol
+        for k in (0, 17, 39):
+            alone = vp.potential_eval(ctx, g["nf"], fd[k:k + 1].contiguous(), precision=prec).cpu().numpy()
+            assert rel_err(u[k:k + 1], alone).max() <= 1e-13
+
+
 def test_host_entry_point_matches_device(vp, ctx, disk):
     s, f, _, _, g = disk
     for p in (0, 1):
