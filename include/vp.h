@@ -81,8 +81,15 @@ typedef struct vp_nf_params {
     double c_far;      /* C_N of Eq. (rho0) for the far rule; 1 gives the provable superset E' */
     double c_near;     /* C_N for the degree-12 near rule (Table "C_N values": C_12 = 12) */
     int32_t depth_cap; /* maximum subdivision depth of Section 3.3; leaves at the cap are counted */
-    int32_t reserved;
+    int32_t flags;     /* 0, or VP_NF_FP64_WEIGHTS */
 } vp_nf_params;
+
+/* vp_nf_params.flags: evaluate the node quadratures of the correction
+ * weights in FP64.  By default they run in float-float arithmetic (pairs of
+ * FP32 values with error-free transformations, ~2^-48 per operation), which
+ * GB300 executes some 20x faster than FP64; the subdivision tree and every
+ * geometric predicate are FP64 (bit-exact) either way. */
+#define VP_NF_FP64_WEIGHTS 1
 
 /* Counters of Section 5 (c, s_n, s_l) and sizes of a near-field build. */
 typedef struct vp_nf_stats_t {

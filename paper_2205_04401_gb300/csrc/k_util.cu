@@ -102,6 +102,29 @@ __global__ void k_sum_i32(const int32_t* __restrict__ a, int64_t n, unsigned lon
     if ((threadIdx.x & 31) == 0) atomicAdd(out, m);
 }
 
+// out[0] += sum of a over kind 0, out[1] += over kind != 0, out[2] += sum of b
+__global__ void k_sum_by_kind(const int32_t* __restrict__ a, const uint8_t* __restrict__ kind,
+                              const int32_t* __restrict__ b, int64_t n, unsigned long long* out) {
+    unsigned long long s0 = 0, s1 = 0, sb = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long v = (uint32_t)a[i];
+        if (kind[i]) s1 += v;
+        else s0 += v;
+        sb += (uint32_t)b[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], s0);
+        atomicAdd(&out[1], s1);
+        atomicAdd(&out[2], sb);
+    }
+}
+
 // Compact pair indices by kind (order within each list is irrelevant: every
 // pair writes only its own output row).
 __global__ void k_split_pairs(const uint8_t* __restrict__ kind, int64_t P, int32_t* near_idx, int32_t* self_idx,
@@ -147,6 +170,12 @@ void launch_max_i32(const int32_t* a, int64_t n, int32_t* out, cudaStream_t s) {
 void launch_sum_i32(const int32_t* a, int64_t n, unsigned long long* out, cudaStream_t s) {
     cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
     if (n > 0) k_sum_i32<<<(unsigned)std::min<int64_t>(1024, (n + 255) / 256), 256, 0, s>>>(a, n, out);
+}
+
+void launch_sum_by_kind(const int32_t* a, const uint8_t* kind, const int32_t* b, int64_t n, unsigned long long* out,
+                        cudaStream_t s) {
+    cudaMemsetAsync(out, 0, 3 * sizeof(unsigned long long), s);
+    if (n > 0) k_sum_by_kind<<<(unsigned)std::min<int64_t>(1024, (n + 255) / 256), 256, 0, s>>>(a, kind, b, n, out);
 }
 
 void launch_split_pairs(const uint8_t* pkind, int64_t P, int32_t* near_idx, int32_t* self_idx,

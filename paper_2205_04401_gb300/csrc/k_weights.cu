@@ -1,4 +1,4 @@
-// Correction weights for (target, triangle) pairs: FP64, one warp per pair.
+// Correction weights for (target, triangle) pairs, one warp per pair.
 //
 // For a pair (x, T) the weights are (subtract-and-add, Section 3.6)
 //     C_k = w_k sum_a K_a(xi_k) m_a - [k != own] W_k G(x, y_k),
@@ -10,12 +10,17 @@
 // radius-arclength coordinates on three fans, generalized Gaussian rule in
 // the radius, graded Gauss-Legendre panels in the arc length).
 //
-// The kernels are bound by the FP64 pipe, so per quadrature point they
-// accumulate the moments mu_i of the tensor-Legendre basis leg15 (20 FP64
-// operations instead of ~60 for the orthonormal basis) and use the
-// table-driven vp_logd; the constant matrix Q (generated in high precision)
+// Per quadrature point the kernels accumulate the moments mu_i of the
+// tensor-Legendre basis leg15 (20 operations instead of ~60 for the
+// orthonormal basis); the constant matrix Q (generated in high precision)
 // maps mu to the nodal weights: C_k = sum_i Q_ki mu_i - [k != own] W_k G.
+// The node loops run in float-float (vp_f2.cuh: the near loop entirely, the
+// self loop from the FP64 panel quantities on) or, with VP_NF_FP64_WEIGHTS,
+// in FP64 with the table-driven vp_logd; the subdivision tree, the stop test
+// and the panel construction are FP64 in both.
 #include "vp_internal.h"
+#include "vp_f2.cuh"
+#include "vp_ff.cuh"
 
 namespace {
 
@@ -116,6 +121,7 @@ __device__ __forceinline__ int dyadic_count(double len, double dist) {
 }
 
 // ------------------------------------------------------------------ self
+template <bool F2>
 __global__ void __launch_bounds__(WARPS * 32) k_weights_self(WeightsArgs a, const int32_t* __restrict__ idx, int64_t n) {
     __shared__ LogSmem lt;
     load_logtab(a.tab, lt);
@@ -147,6 +153,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_self(WeightsArgs a, cons
     double m[VP_NB];
 #pragma unroll
     for (int q = 0; q < VP_NB; q++) m[q] = 0.0;
+    float mh[VP_NB], ml[VP_NB];
+#pragma unroll
+    for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
+    f2 gr2[4], glr2[4], gwl2[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        gr2[q] = f2_from_d(gr[q]);
+        glr2[q] = f2_from_d(glr[q]);
+        gwl2[q] = f2_from_d(gwl[q]);
+    }
+    const f2 xi02 = f2_from_d(xi0), eta02 = f2_from_d(eta0);
     int panels = 0;
     for (int e = 0; e < 3; e++) {
         const double Px = v[2 * e], Py = v[2 * e + 1];
@@ -188,14 +205,27 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_self(WeightsArgs a, cons
                 const double lr0 = 0.5 * vp_logd(rx * rx + ry * ry, lt.rc, lt.lc, ln2);
                 // reference coordinates along the ray x + r (gamma(s) - x)
                 const double xig = xiP + sl * dxi - xi0, etag = etaP + sl * deta - eta0;
+                if (F2) {
+                    const f2 lr = f2_from_d(lr0), w = f2_from_d(ws), xg = f2_from_d(xig), eg = f2_from_d(etag);
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const double g = (lr0 + glr[q]) * ws * gwl[q];
-                    accumulate(m, g, fma(gr[q], xig, xi0), fma(gr[q], etag, eta0));
+                    for (int q = 0; q < 4; q++) {
+                        const f2 g = f2_mul(f2_add(lr, glr2[q]), f2_mul(w, gwl2[q]));
+                        f2_leg15_acc(mh, ml, g, f2_add(f2_mul(gr2[q], xg), xi02), f2_add(f2_mul(gr2[q], eg), eta02));
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const double g = (lr0 + glr[q]) * ws * gwl[q];
+                        accumulate(m, g, fma(gr[q], xig, xi0), fma(gr[q], etag, eta0));
+                    }
                 }
                 b0 = b1;
             }
         }
+    }
+    if (F2) {
+#pragma unroll
+        for (int q = 0; q < VP_NB; q++) m[q] = (double)mh[q] + (double)ml[q];
     }
     finish_pair(a, p, T, own, xx, xy, m, lane, lt.rc, lt.lc, ln2);
     if (lane == 0) {
@@ -226,6 +256,27 @@ __device__ __forceinline__ void sub_phys(const SubTri& S, double Ax, double Ay, 
     }
 }
 
+// Children of a split (Section 3.3): (v0,m01,m20), (m01,v1,m12), (m20,m12,v2),
+// (m12,m20,m01), numerators at the next scale.
+__device__ __forceinline__ void push_children(const SubTri& S, SubTri* stack, int base) {
+    const int32_t m01x = S.v[0] + S.v[2], m01y = S.v[1] + S.v[3];
+    const int32_t m12x = S.v[2] + S.v[4], m12y = S.v[3] + S.v[5];
+    const int32_t m20x = S.v[4] + S.v[0], m20y = S.v[5] + S.v[1];
+    const int32_t V0x = 2 * S.v[0], V0y = 2 * S.v[1], V1x = 2 * S.v[2], V1y = 2 * S.v[3];
+    const int32_t V2x = 2 * S.v[4], V2y = 2 * S.v[5];
+    SubTri ch;
+    ch.L = S.L + 1;
+    ch.v[0] = V0x; ch.v[1] = V0y; ch.v[2] = m01x; ch.v[3] = m01y; ch.v[4] = m20x; ch.v[5] = m20y;
+    stack[base + 0] = ch;
+    ch.v[0] = m01x; ch.v[1] = m01y; ch.v[2] = V1x; ch.v[3] = V1y; ch.v[4] = m12x; ch.v[5] = m12y;
+    stack[base + 1] = ch;
+    ch.v[0] = m20x; ch.v[1] = m20y; ch.v[2] = m12x; ch.v[3] = m12y; ch.v[4] = V2x; ch.v[5] = V2y;
+    stack[base + 2] = ch;
+    ch.v[0] = m12x; ch.v[1] = m12y; ch.v[2] = m20x; ch.v[3] = m20y; ch.v[4] = m01x; ch.v[5] = m01y;
+    stack[base + 3] = ch;
+}
+
+// FP64 reference: node loop in FP64 with the table-driven vp_logd.
 __global__ void __launch_bounds__(WARPS * 32) k_weights_near(WeightsArgs a, const int32_t* __restrict__ idx, int64_t n) {
     __shared__ SubTri stack_all[WARPS][STK];
     __shared__ LeafMap leaf_all[WARPS][LEAFCAP];
@@ -245,9 +296,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_near(WeightsArgs a, cons
     const double J = a.J[T];
     const double xx = a.txy[2 * t], xy = a.txy[2 * t + 1];
     const int own = own_index(a, t, T);
-    const double what = a.tab->near_what;
     const int Nn = a.tab->near_degree;
-    const double R_root = ellipse_R_rn(what, J, a.eps, a.c_near);
+    const double R_root = ellipse_R_rn(a.tab->near_what, J, a.eps, a.c_near);
     const double* nx = a.tab->nx;
     const double* ny = a.tab->ny;
     const double* nw = a.tab->nw;
@@ -305,23 +355,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_near(WeightsArgs a, cons
                     lf.wJ = ldexp(J, -2 * S.L) * (0.5 * VP_INV_TWO_PI);
                     leaves[nleaf + __popc(lm & lower)] = lf;
                 } else {
-                    const int base = sp + 4 * __popc(sm & lower);
-                    int32_t m01x = S.v[0] + S.v[2], m01y = S.v[1] + S.v[3];
-                    int32_t m12x = S.v[2] + S.v[4], m12y = S.v[3] + S.v[5];
-                    int32_t m20x = S.v[4] + S.v[0], m20y = S.v[5] + S.v[1];
-                    int32_t V0x = 2 * S.v[0], V0y = 2 * S.v[1], V1x = 2 * S.v[2], V1y = 2 * S.v[3];
-                    int32_t V2x = 2 * S.v[4], V2y = 2 * S.v[5];
-                    const int32_t L1 = S.L + 1;
-                    SubTri ch;
-                    ch.L = L1;
-                    ch.v[0] = V0x; ch.v[1] = V0y; ch.v[2] = m01x; ch.v[3] = m01y; ch.v[4] = m20x; ch.v[5] = m20y;
-                    stack[base + 0] = ch;
-                    ch.v[0] = m01x; ch.v[1] = m01y; ch.v[2] = V1x; ch.v[3] = V1y; ch.v[4] = m12x; ch.v[5] = m12y;
-                    stack[base + 1] = ch;
-                    ch.v[0] = m20x; ch.v[1] = m20y; ch.v[2] = m12x; ch.v[3] = m12y; ch.v[4] = V2x; ch.v[5] = V2y;
-                    stack[base + 2] = ch;
-                    ch.v[0] = m12x; ch.v[1] = m12y; ch.v[2] = m20x; ch.v[3] = m20y; ch.v[4] = m01x; ch.v[5] = m01y;
-                    stack[base + 3] = ch;
+                    push_children(S, stack, sp + 4 * __popc(sm & lower));
                 }
             }
             nleaf += __popc(lm);
@@ -355,12 +389,370 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_near(WeightsArgs a, cons
     }
 }
 
+// ---------------------------------------------------- near, float-float
+// Leaf of the float-float node loop: node j of the near rule sits at
+// reference coordinates a0 + sh z_j and at y - x = D0 + sh E_j, with
+// E_j = z_j,x (B - A) + z_j,y (C - A) and sh = +-2^-L (every child of a split
+// keeps its parent's orientation except the fourth, its point reflection).
+struct LeafF2 {
+    float d0xh, d0xl, d0yh, d0yl;   // D0 = A + a0_x (B - A) + a0_y (C - A) - x
+    float a0xh, a0xl, a0yh, a0yl;   // a0
+    float sh, wjh, wjl, pad;        // sh; J_T 4^-L / 4pi
+};
+
+// The integer numerator 0 <= v <= 2^30 at scale 2^-L as an exact, normalised
+// pair: h = fl(v) and l = v - h (|l| <= ulp(h) / 2).
+__device__ __forceinline__ f2 dyadic_f2(int32_t v, float scale) {
+    const float h = __int2float_rn(v);
+    const int32_t hi = __float2int_rn(h);
+    return {__fmul_rn(h, scale), __fmul_rn(__int2float_rn(v - hi), scale)};
+}
+
+// y - x at reference coordinates (xi, eta): a + xi e + eta f, per coordinate.
+__device__ __forceinline__ f2 rel_coord(f2 a, f2 xi, f2 eta, f2 e, f2 f) {
+    return f2_add(a, f2_add(f2_mul(xi, e), f2_mul(eta, f)));
+}
+
+// Sign decisions of the FP64 predicates taken from FP32 values when their
+// error bound allows: +1/-1 decided, 0 undecided.  o = a x b for the
+// vertices' offsets a, b from x (FP32 parts of float-float values accurate to
+// 2^-47 relative); the bound covers the FP32 evaluation (< 2^-22 relative to
+// |ax by| + |ay bx|) and the rounding of the FP64 vertex coordinates of the
+// exact test (< 2^-50 cm per unit offset, cm the coordinate magnitude).
+__device__ __forceinline__ int orient_filter(float ax, float ay, float bx, float by, float cm) {
+    const float p1 = ax * by, p2 = ay * bx;
+    const float o = p1 - p2;
+    const float bound = 2.384185791015625e-07f * (fabsf(p1) + fabsf(p2)) +
+                        1.7763568394002505e-15f * cm * (fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by));
+    if (o > bound) return 1;
+    if (o < -bound) return -1;
+    return 0;
+}
+
+// Per-triangle, per-target and per-node data of the float-float kernels.
+struct WeightsF2 {
+    const float4* tA;     // [nt] A x (h, l), A y (h, l)
+    const float4* te;     // [nt] (B - A) x, y
+    const float4* tf;     // [nt] (C - A) x, y
+    const float4* tw;     // [nt] J / 4pi (h, l), max |vertex coordinate|, 0
+    const float4* x2;     // [M] target x, y
+    const float4* y2;     // [N] node x, y
+    const float2* wq2;    // [N] W_j / 4pi
+};
+
+__device__ __forceinline__ f2 f2_neg(f2 a) { return {-a.h, -a.l}; }
+
+// Warp-wide reduce-scatter of 16 float-float values (the FP64 version's
+// pattern): afterwards lane l holds the warp total of value (l >> 1).
+__device__ __forceinline__ f2 reduce_scatter16_f2(f2* v, int lane) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const bool hi = lane & 16;
+        const f2 send = hi ? v[i] : v[i + 8];
+        const f2 keep = hi ? v[i + 8] : v[i];
+        v[i] = f2_add(keep, {__shfl_xor_sync(0xffffffffu, send.h, 16), __shfl_xor_sync(0xffffffffu, send.l, 16)});
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const bool hi = lane & 8;
+        const f2 send = hi ? v[i] : v[i + 4];
+        const f2 keep = hi ? v[i + 4] : v[i];
+        v[i] = f2_add(keep, {__shfl_xor_sync(0xffffffffu, send.h, 8), __shfl_xor_sync(0xffffffffu, send.l, 8)});
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const bool hi = lane & 4;
+        const f2 send = hi ? v[i] : v[i + 2];
+        const f2 keep = hi ? v[i + 2] : v[i];
+        v[i] = f2_add(keep, {__shfl_xor_sync(0xffffffffu, send.h, 4), __shfl_xor_sync(0xffffffffu, send.l, 4)});
+    }
+    {
+        const bool hi = lane & 2;
+        const f2 send = hi ? v[0] : v[1];
+        const f2 keep = hi ? v[1] : v[0];
+        v[0] = f2_add(keep, {__shfl_xor_sync(0xffffffffu, send.h, 2), __shfl_xor_sync(0xffffffffu, send.l, 2)});
+    }
+    return f2_add(v[0], {__shfl_xor_sync(0xffffffffu, v[0].h, 1), __shfl_xor_sync(0xffffffffu, v[0].l, 1)});
+}
+
+// mu (float-float accumulators) -> C_k = sum_i Q_ki mu_i - [k != own] W_k G(x, y_k)
+__device__ __forceinline__ void finish_pair_f2(const WeightsArgs& a, const WeightsF2& b, int64_t p, int T, int t,
+                                               int own, const float* mh, const float* ml, int lane,
+                                               const float4* ftab, const LogSmem& lt, double ln2) {
+    f2 v[16];
+#pragma unroll
+    for (int q = 0; q < VP_NB; q++) v[q] = f2_fast(mh[q], ml[q]);
+    v[15] = {0.f, 0.f};
+    const f2 mine = reduce_scatter16_f2(v, lane);
+    const int k = lane < a.nq ? lane : 0;
+    const float2* Qk = a.tab->Q2[a.rule][k];
+    f2 s = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < VP_NB; q++) {
+        const f2 mq = {__shfl_sync(0xffffffffu, mine.h, 2 * q), __shfl_sync(0xffffffffu, mine.l, 2 * q)};
+        const float2 Q = Qk[q];
+        s = f2_add(s, f2_mul({Q.x, Q.y}, mq));
+    }
+    if (lane < a.nq) {
+        if (lane != own) {
+            const int64_t j = (int64_t)T * a.nq + lane;
+            const float4 X = b.x2[t], Y = b.y2[j];
+            const f2 dx = f2_add({X.x, X.y}, {-Y.x, -Y.y}), dy = f2_add({X.z, X.w}, {-Y.z, -Y.w});
+            const f2 r2 = f2_add(f2_sqr(dx), f2_sqr(dy));
+            f2 lg;
+            if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);
+            else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
+            const float2 wq = b.wq2[j];
+            s = f2_add(s, f2_neg(f2_mul(lg, {wq.x, wq.y})));
+        }
+        a.C[p * a.nq + lane] = f2_to_d(s);
+    }
+}
+
+__global__ void __launch_bounds__(WARPS * 32) k_weights_near_f2(WeightsArgs a, WeightsF2 b, const int32_t* __restrict__ idx,
+                                                              int64_t n) {
+    __shared__ SubTri stack_all[WARPS][STK];
+    __shared__ LeafF2 leaf_all[WARPS][LEAFCAP];
+    __shared__ float4 exy_all[WARPS][VP_NNEAR];
+    __shared__ float4 ftab[LOG_N];
+    __shared__ LogSmem lt;
+    load_logtab(a.tab, lt);
+    for (int i = threadIdx.x; i < LOG_N; i += blockDim.x) ftab[i] = g_logtab.e[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t w = (int64_t)blockIdx.x * WARPS + wl;
+    if (w >= n) return;
+    const double ln2 = a.tab->ln2;
+    SubTri* stack = stack_all[wl];
+    LeafF2* leaves = leaf_all[wl];
+    float4* exy = exy_all[wl];
+    const int64_t p = idx[w];
+    const int T = a.ptri[p], t = a.ptgt[p];
+    const int own = own_index(a, t, T);
+    const int Nn = a.tab->near_degree;
+    const double R_root = ellipse_R_rn(a.tab->near_what, a.J[T], a.eps, a.c_near);
+    const float Rf_root = (float)R_root;
+    // float-float geometry relative to the target
+    const float4 TA = b.tA[T], TE = b.te[T], TF = b.tf[T], TW = b.tw[T], X = b.x2[t];
+    const f2 ax = f2_add({TA.x, TA.y}, {-X.x, -X.y}), ay = f2_add({TA.z, TA.w}, {-X.z, -X.w});
+    const f2 ex = {TE.x, TE.y}, ey = {TE.z, TE.w}, fx = {TF.x, TF.y}, fy = {TF.z, TF.w};
+    const f2 wj_pair = {TW.x, TW.y};
+    const float cm = fmaxf(TW.z, fmaxf(fabsf(X.x), fabsf(X.z)));
+    for (int j = lane; j < VP_NNEAR; j += 32) {
+        const float4 Z = a.tab->nz2[j];
+        const f2 zx = {Z.x, Z.y}, zy = {Z.z, Z.w};
+        const f2 Ex = f2_add(f2_mul(zx, ex), f2_mul(zy, fx)), Ey = f2_add(f2_mul(zx, ey), f2_mul(zy, fy));
+        exy[j] = make_float4(Ex.h, Ex.l, Ey.h, Ey.l);
+    }
+
+    float mh[VP_NB], ml[VP_NB];
+#pragma unroll
+    for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
+    if (lane == 0) {
+        SubTri r;
+        r.v[0] = 0; r.v[1] = 0; r.v[2] = 1; r.v[3] = 0; r.v[4] = 0; r.v[5] = 1; r.L = 0;
+        stack[0] = r;
+    }
+    __syncwarp();
+    int sp = 1, nleaf = 0, total_leaves = 0, capped = 0;
+    int visited = 0;
+    bool overflow = false;
+    const unsigned lower = (1u << lane) - 1u;
+    while (sp > 0 || nleaf > 0) {
+        bool flush = nleaf > 0 && (sp == 0 || nleaf + 32 > LEAFCAP || nleaf >= 32);
+        if (!flush) {
+            int c = min(sp, 32);
+            c = min(c, (STK - sp) / 3);
+            if (c <= 0 || visited > MAX_VISITED) {
+                overflow = true;
+                break;
+            }
+            visited += c;
+            SubTri S;
+            bool stop = false;
+            f2 d0x, d0y, a0x, a0y;
+            float scale = 1.f;
+            if (lane < c) {
+                S = stack[sp - 1 - lane];
+                scale = __int_as_float((127 - S.L) << 23);            // 2^-L
+                // vertex offsets from the target, float-float
+                f2 dx[3], dy[3];
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    const f2 xi = dyadic_f2(S.v[2 * i], scale), eta = dyadic_f2(S.v[2 * i + 1], scale);
+                    dx[i] = rel_coord(ax, xi, eta, ex, fx);
+                    dy[i] = rel_coord(ay, xi, eta, ey, fy);
+                    if (i == 0) {
+                        a0x = xi;
+                        a0y = eta;
+                    }
+                }
+                d0x = dx[0];
+                d0y = dy[0];
+                // stop test: x outside every edge ellipse of S (near rule) and outside S
+                const float Rf = __fmul_rn(Rf_root, __fmul_rn(scale, scale));
+                int near = 0;      // 1 near, 0 not near, -1 undecided
+                for (int e = 0; e < 3 && near != 1; e++) {
+                    const int i0 = e, i1 = (e + 1) % 3;
+                    const int r = edge_near_f32(dx[i0].h, dy[i0].h, dx[i1].h, dy[i1].h, Nn, Rf);
+                    if (r == 1) near = 1;
+                    else if (r == 2) near = -1;
+                }
+                int inside = 1;    // 1 inside, 0 outside, -1 undecided
+                if (near != 1) {
+                    for (int e = 0; e < 3 && inside != 0; e++) {
+                        const int i0 = e, i1 = (e + 1) % 3;
+                        const int o = orient_filter(dx[i0].h, dy[i0].h, dx[i1].h, dy[i1].h, cm);
+                        if (o < 0) inside = 0;
+                        else if (o == 0) inside = -1;
+                    }
+                }
+                if (near == 1) {
+                    stop = false;
+                } else if (near == 0 && inside != -1) {
+                    stop = inside == 0;
+                } else {
+                    // undecided in FP32: the FP64 predicates on the FP64 vertices
+                    const double* v = a.tv + 6 * (int64_t)T;
+                    const double Ax = v[0], Ay = v[1];
+                    const double eex = rn_sub(v[2], Ax), eey = rn_sub(v[3], Ay);
+                    const double ffx = rn_sub(v[4], Ax), ffy = rn_sub(v[5], Ay);
+                    const double xx = a.txy[2 * t], xy = a.txy[2 * t + 1];
+                    double ph[6];
+                    sub_phys(S, Ax, Ay, eex, eey, ffx, ffy, ph);
+                    stop = !tri_near_fast(ph, xx, xy, Nn, ldexp(R_root, -2 * S.L)) && !tri_contains_rn(ph, xx, xy);
+                }
+                if (!stop && S.L >= a.depth_cap) {
+                    stop = true;
+                    capped++;
+                }
+            }
+            __syncwarp();
+            const unsigned lm = __ballot_sync(0xffffffffu, lane < c && stop);
+            const unsigned sm = __ballot_sync(0xffffffffu, lane < c && !stop);
+            sp -= c;
+            if (lane < c) {
+                if (stop) {
+                    LeafF2 lf;
+                    lf.d0xh = d0x.h; lf.d0xl = d0x.l; lf.d0yh = d0y.h; lf.d0yl = d0y.l;
+                    lf.a0xh = a0x.h; lf.a0xl = a0x.l; lf.a0yh = a0y.h; lf.a0yl = a0y.l;
+                    lf.sh = (S.v[2] - S.v[0]) > 0 ? scale : -scale;
+                    const f2 wj = f2_scale(wj_pair, __fmul_rn(scale, scale));
+                    lf.wjh = wj.h; lf.wjl = wj.l; lf.pad = 0.f;
+                    leaves[nleaf + __popc(lm & lower)] = lf;
+                } else {
+                    push_children(S, stack, sp + 4 * __popc(sm & lower));
+                }
+            }
+            nleaf += __popc(lm);
+            sp += 4 * __popc(sm);
+            __syncwarp();
+        } else {
+            const int combos = nleaf * VP_NNEAR;
+            for (int i = lane; i < combos; i += 32) {
+                const int li = i / VP_NNEAR, j = i - li * VP_NNEAR;
+                const LeafF2 lf = leaves[li];
+                const float4 E = exy[j], Z = a.tab->nz2[j];
+                const float2 W = a.tab->nw2[j];
+                const float sh = lf.sh;
+                const f2 dx = f2_add({lf.d0xh, lf.d0xl}, {__fmul_rn(E.x, sh), __fmul_rn(E.y, sh)});
+                const f2 dy = f2_add({lf.d0yh, lf.d0yl}, {__fmul_rn(E.z, sh), __fmul_rn(E.w, sh)});
+                const f2 r2 = f2_add(f2_sqr(dx), f2_sqr(dy));
+                f2 lg;
+                if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);              // log |y - x|^2
+                else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));        // far below any mesh scale
+                const f2 g = f2_mul(lg, f2_mul({W.x, W.y}, {lf.wjh, lf.wjl}));
+                const f2 xi = f2_add({lf.a0xh, lf.a0xl}, {__fmul_rn(Z.x, sh), __fmul_rn(Z.y, sh)});
+                const f2 eta = f2_add({lf.a0yh, lf.a0yl}, {__fmul_rn(Z.z, sh), __fmul_rn(Z.w, sh)});
+                f2_leg15_acc(mh, ml, g, xi, eta);
+            }
+            total_leaves += nleaf;
+            nleaf = 0;
+            __syncwarp();
+        }
+    }
+    if (overflow && lane == 0) atomicOr(a.flag, VP_DEV_ERR_STACK);
+    finish_pair_f2(a, b, p, T, t, own, mh, ml, lane, ftab, lt, ln2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) capped += __shfl_xor_sync(0xffffffffu, capped, o);
+    if (lane == 0) {
+        a.pstat[p] = total_leaves;
+        a.pcap[p] = capped;
+    }
+}
+
+// float-float geometry of the weights kernels
+__global__ void k_weights_f2_tri(const double* __restrict__ tv, const double* __restrict__ J, int64_t nt,
+                                 float4* __restrict__ tA, float4* __restrict__ te, float4* __restrict__ tf,
+                                 float4* __restrict__ tw) {
+    const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (T >= nt) return;
+    const double* v = tv + 6 * T;
+    const f2 Ax = f2_from_d(v[0]), Ay = f2_from_d(v[1]);
+    const f2 ex = f2_from_d(rn_sub(v[2], v[0])), ey = f2_from_d(rn_sub(v[3], v[1]));
+    const f2 fx = f2_from_d(rn_sub(v[4], v[0])), fy = f2_from_d(rn_sub(v[5], v[1]));
+    const f2 wj = f2_from_d(J[T] * (0.5 * VP_INV_TWO_PI));
+    double cm = 0.0;
+    for (int i = 0; i < 6; i++) cm = fmax(cm, fabs(v[i]));
+    tA[T] = make_float4(Ax.h, Ax.l, Ay.h, Ay.l);
+    te[T] = make_float4(ex.h, ex.l, ey.h, ey.l);
+    tf[T] = make_float4(fx.h, fx.l, fy.h, fy.l);
+    tw[T] = make_float4(wj.h, wj.l, (float)(cm * 1.0000001), 0.f);
+}
+
+__global__ void k_weights_f2_pts(const double* __restrict__ xy, int64_t n, const double* __restrict__ W,
+                                 float4* __restrict__ out, float2* __restrict__ wq) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const f2 x = f2_from_d(xy[2 * i]), y = f2_from_d(xy[2 * i + 1]);
+    out[i] = make_float4(x.h, x.l, y.h, y.l);
+    if (W) {
+        const f2 w = f2_from_d(W[i] * (0.5 * VP_INV_TWO_PI));
+        wq[i] = make_float2(w.h, w.l);
+    }
+}
+
 }  // namespace
 
 void launch_weights_self(const WeightsArgs& a, const int32_t* idx, int64_t n, cudaStream_t s) {
-    if (n > 0) k_weights_self<<<(unsigned)((n + WARPS - 1) / WARPS), WARPS * 32, 0, s>>>(a, idx, n);
+    if (n <= 0) return;
+    const unsigned grid = (unsigned)((n + WARPS - 1) / WARPS);
+    if (a.fp64) k_weights_self<false><<<grid, WARPS * 32, 0, s>>>(a, idx, n);
+    else k_weights_self<true><<<grid, WARPS * 32, 0, s>>>(a, idx, n);
+}
+
+size_t weights_f2_bytes(int64_t nt, int64_t M, int64_t N) {
+    // seven arrays, each rounded up to 256 bytes
+    return (size_t)nt * 4 * sizeof(float4) + (size_t)M * sizeof(float4) + (size_t)N * (sizeof(float4) + sizeof(float2)) +
+           7 * 256;
 }
 
 void launch_weights_near(const WeightsArgs& a, const int32_t* idx, int64_t n, cudaStream_t s) {
-    if (n > 0) k_weights_near<<<(unsigned)((n + WARPS - 1) / WARPS), WARPS * 32, 0, s>>>(a, idx, n);
+    if (n <= 0) return;
+    const unsigned grid = (unsigned)((n + WARPS - 1) / WARPS);
+    if (a.fp64) {
+        k_weights_near<<<grid, WARPS * 32, 0, s>>>(a, idx, n);
+        return;
+    }
+    ensure_logtab();
+    // float-float geometry in the caller's scratch
+    char* ws = (char*)a.f2_ws;
+    auto take = [&](size_t bytes) {
+        char* p = ws;
+        ws += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    WeightsF2 b;
+    float4* tA = (float4*)take(a.nt * sizeof(float4));
+    float4* te = (float4*)take(a.nt * sizeof(float4));
+    float4* tf = (float4*)take(a.nt * sizeof(float4));
+    float4* tw = (float4*)take(a.nt * sizeof(float4));
+    float4* x2 = (float4*)take(a.M * sizeof(float4));
+    float4* y2 = (float4*)take(a.N * sizeof(float4));
+    float2* wq2 = (float2*)take(a.N * sizeof(float2));
+    k_weights_f2_tri<<<(unsigned)((a.nt + 255) / 256), 256, 0, s>>>(a.tv, a.J, a.nt, tA, te, tf, tw);
+    k_weights_f2_pts<<<(unsigned)((a.M + 255) / 256), 256, 0, s>>>(a.txy, a.M, nullptr, x2, nullptr);
+    k_weights_f2_pts<<<(unsigned)((a.N + 255) / 256), 256, 0, s>>>(a.y, a.N, a.W, y2, wq2);
+    b.tA = tA; b.te = te; b.tf = tf; b.tw = tw; b.x2 = x2; b.y2 = y2; b.wq2 = wq2;
+    k_weights_near_f2<<<grid, WARPS * 32, 0, s>>>(a, b, idx, n);
 }

@@ -82,6 +82,18 @@ void fill_tables(VpTables& t) {
         t.ny[j] = VP_NEAR49_Y[j];
         t.nw[j] = VP_NEAR49_W[j];
     }
+    auto split = [](double d) {
+        const float h = (float)d;
+        return make_float2(h, (float)(d - (double)h));
+    };
+    for (int j = 0; j < VP_NNEAR; j++) {
+        const float2 x = split(VP_NEAR49_X[j]), y = split(VP_NEAR49_Y[j]);
+        t.nz2[j] = make_float4(x.x, x.y, y.x, y.y);
+        t.nw2[j] = split(VP_NEAR49_W[j]);
+    }
+    for (int r = 0; r < 2; r++)
+        for (int k = 0; k < nq[r]; k++)
+            for (int a = 0; a < VP_NB; a++) t.Q2[r][k][a] = split(t.Q[r][k][a]);
     t.near_what = VP_NEAR49_WHAT;
     t.near_degree = VP_NEAR49_DEGREE;
     for (int j = 0; j < VP_NGGQ; j++) {
@@ -370,10 +382,10 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
     prm.c_far = 1.0;
     prm.c_near = 12.0;
     prm.depth_cap = 30;
-    prm.reserved = 0;
+    prm.flags = 0;
     if (params) prm = *params;
     if (!(prm.eps >= 1e-15 && prm.eps <= 1e-2) || !(prm.c_far > 0) || !(prm.c_near > 0) || prm.depth_cap < 0 ||
-        prm.depth_cap > 30)
+        prm.depth_cap > 30 || (prm.flags & ~VP_NF_FP64_WEIGHTS))
         return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_nearfield_build: bad params");
     auto t_start = std::chrono::steady_clock::now();
     DevGuard g(ctx->device);
@@ -412,6 +424,7 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         int64_t *d_cell_start, *d_cursor, *d_tstart;
         unsigned long long* d_u64;
         unsigned long long h_u64[2];
+        char* d_f2ws;
         int32_t h_max = 0;
         std::vector<double> hb;
         std::vector<double> sizes;
@@ -525,7 +538,7 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         // correction weights
         NF_CUDA(sc.alloc(&d_near_idx, nf->P));
         NF_CUDA(sc.alloc(&d_self_idx, nf->P));
-        NF_CUDA(sc.alloc(&d_u64, 2));
+        NF_CUDA(sc.alloc(&d_u64, 3));
         NF_CUDA(sc.alloc(&d_pstat, nf->P));
         NF_CUDA(sc.alloc(&d_pcap, nf->P));
         launch_split_pairs(nf->d_pkind, nf->P, d_near_idx, d_self_idx, d_u64, s);
@@ -551,6 +564,12 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         wa.eps = prm.eps;
         wa.c_near = prm.c_near;
         wa.depth_cap = prm.depth_cap;
+        wa.fp64 = (prm.flags & VP_NF_FP64_WEIGHTS) ? 1 : 0;
+        wa.nt = nt;
+        wa.M = M;
+        wa.N = N;
+        NF_CUDA(sc.alloc(&d_f2ws, (int64_t)weights_f2_bytes(nt, M, N)));
+        wa.f2_ws = d_f2ws;
         PROF(ctx, ST_WEIGHTS_SELF, s, launch_weights_self(wa, d_self_idx, n_self, s));
         PROF(ctx, ST_WEIGHTS_NEAR, s, launch_weights_near(wa, d_near_idx, n_near, s));
         NF_CUDA(cudaGetLastError());
@@ -563,30 +582,14 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         nf->stats.n_self = n_self;
         nf->stats.outside = M - n_self;
         {
-            // leaves / panels per kind, capped leaves
-            int32_t* d_tmp;
-            NF_CUDA(sc.alloc(&d_tmp, 1));
-            unsigned long long h;
-            std::vector<int32_t> dummy;
-            (void)dummy;
-            // sums over all pairs split by kind: use the index lists
-            // near leaves: gather by summing pstat over near indices on the host side would need a copy;
-            // instead sum pstat over all pairs and self panels separately.
-            launch_sum_i32(d_pcap, nf->P, d_u64, s);
-            NF_CUDA(cudaMemcpyAsync(&h, d_u64, sizeof(h), cudaMemcpyDeviceToHost, s));
+            // leaves (near pairs) and panels (self pairs), depth-capped leaves
+            unsigned long long h3[3];
+            launch_sum_by_kind(d_pstat, nf->d_pkind, d_pcap, nf->P, d_u64, s);
+            NF_CUDA(cudaMemcpyAsync(h3, d_u64, sizeof(h3), cudaMemcpyDeviceToHost, s));
             NF_CUDA(cudaStreamSynchronize(s));
-            nf->stats.depth_capped = (int64_t)h;
-            std::vector<int32_t> hstat(nf->P);
-            std::vector<uint8_t> hkind(nf->P);
-            if (nf->P) {
-                NF_CUDA(cudaMemcpyAsync(hstat.data(), d_pstat, nf->P * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-                NF_CUDA(cudaMemcpyAsync(hkind.data(), nf->d_pkind, nf->P, cudaMemcpyDeviceToHost, s));
-                NF_CUDA(cudaStreamSynchronize(s));
-            }
-            int64_t leaves = 0, panels = 0;
-            for (int64_t i = 0; i < nf->P; i++) (hkind[i] ? panels : leaves) += hstat[i];
-            nf->stats.near_leaves = leaves;
-            nf->stats.self_panels = panels;
+            nf->stats.near_leaves = (int64_t)h3[0];
+            nf->stats.self_panels = (int64_t)h3[1];
+            nf->stats.depth_capped = (int64_t)h3[2];
         }
 
         // float-float coordinates for the mixed far sum: origin at the centre

@@ -29,6 +29,11 @@ struct VpTables {
     // FP64 logarithm table: 1/c_i and log c_i, c_i = 1 + (i + 1/2)/128
     double log_rc[128], log_lc[128];
     double ln2;
+    // the same constants as pairs of FP32 values (h, l = fl(x - h)) for the
+    // float-float quadratures
+    float4 nz2[VP_NNEAR];               // near-rule nodes x (h, l), y (h, l)
+    float2 nw2[VP_NNEAR];               // near-rule weights
+    float2 Q2[2][VP_MAXQ][VP_NB];       // Q
 };
 
 // Tensor-Legendre basis of P_4 used to accumulate moments on the device:

@@ -181,10 +181,17 @@ struct WeightsArgs {
     int32_t* flag;
     double eps, c_near;
     int depth_cap;
+    int fp64;           // 1: node quadratures in FP64 (reference); 0: float-float
+    int64_t nt, M, N;   // triangles, targets, nodes
+    void* f2_ws;        // scratch of weights_f2_bytes(nt, M, N) for the float-float kernels
 };
+size_t weights_f2_bytes(int64_t nt, int64_t M, int64_t N);
 void launch_weights_self(const WeightsArgs& a, const int32_t* idx, int64_t n, cudaStream_t s);
 void launch_weights_near(const WeightsArgs& a, const int32_t* idx, int64_t n, cudaStream_t s);
 void launch_sum_i32(const int32_t* a, int64_t n, unsigned long long* out, cudaStream_t s);
+// out[0..2] = sums of a over kind 0 and kind != 0, sum of b
+void launch_sum_by_kind(const int32_t* a, const uint8_t* kind, const int32_t* b, int64_t n, unsigned long long* out,
+                        cudaStream_t s);
 
 // evaluation
 void launch_far_fp64(const double* y, const double* W, int64_t N, const double* f, int d, const double* txy,

@@ -37,7 +37,7 @@ class VPError(RuntimeError):
 
 class NfParams(C.Structure):
     _fields_ = [("eps", C.c_double), ("c_far", C.c_double), ("c_near", C.c_double),
-                ("depth_cap", C.c_int32), ("reserved", C.c_int32)]
+                ("depth_cap", C.c_int32), ("flags", C.c_int32)]
 
 
 class NfStats(C.Structure):
@@ -289,11 +289,17 @@ def mesh_nodes(mesh: Mesh, stream=None):
     return y, w
 
 
+VP_NF_FP64_WEIGHTS = 1
+
+
 def nearfield_build(ctx: Context, mesh: Mesh, node_targets: bool = True, txy=None, eps: float = 1e-12,
-                    c_far: float = 1.0, c_near: float = 12.0, depth_cap: int = 30, stream=None) -> NearField:
+                    c_far: float = 1.0, c_near: float = 12.0, depth_cap: int = 30, fp64_weights: bool = False,
+                    stream=None) -> NearField:
+    """vp_nearfield_build; fp64_weights sets VP_NF_FP64_WEIGHTS (node
+    quadratures in FP64 instead of float-float)."""
     lib = load()
     m = 0 if txy is None else int(txy.shape[0])
-    p = NfParams(eps, c_far, c_near, depth_cap, 0)
+    p = NfParams(eps, c_far, c_near, depth_cap, VP_NF_FP64_WEIGHTS if fp64_weights else 0)
     h = C.c_void_p()
     rc = lib.vp_nearfield_build(ctx.handle, mesh.handle, C.c_int32(1 if node_targets else 0),
                                 _dptr(txy, "float64") if m else None, C.c_int64(m), C.byref(p), _stream(stream),

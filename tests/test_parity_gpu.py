@@ -6,7 +6,11 @@ Bars (stated per result):
 * FP64 potential: max_t |u - u_ref| / max_t |u_ref| <= 1e-12 per density;
 * mixed potential (compensated FP32 far sum): <= 1e-10 per density;
 * correction weights: |dC| <= 1e-12 max|C| of the pair plus 1e-15 |J_T|
-  (same subdivision trees on both sides, so only rounding differs).
+  with FP64 node quadratures (VP_NF_FP64_WEIGHTS), plus 1e-13 |J_T| with the
+  default float-float ones (~2^-48 per operation): an order of magnitude
+  below the method's own per-pair quadrature error, eps |J_T| with
+  eps = 1e-12 (Eq. precise_far, Section 4.1).  Same subdivision trees on
+  both sides (identical leaf and panel counts), so only rounding differs.
 """
 import numpy as np
 import pytest
@@ -38,10 +42,10 @@ def rel_err(u, ref):
     return np.max(np.abs(u - ref), axis=1) / np.max(np.abs(ref), axis=1)
 
 
-def gpu_run(vp, ctx, vxy, tri, rule, extra=None, node_targets=True, f=None, precisions=(0,)):
+def gpu_run(vp, ctx, vxy, tri, rule, extra=None, node_targets=True, f=None, precisions=(0,), fp64_weights=False):
     mesh = vp.mesh_upload(ctx, vxy, tri, rule)
     txy = None if extra is None or len(extra) == 0 else torch.from_numpy(np.ascontiguousarray(extra)).cuda()
-    nf = vp.nearfield_build(ctx, mesh, node_targets=node_targets, txy=txy)
+    nf = vp.nearfield_build(ctx, mesh, node_targets=node_targets, txy=txy, fp64_weights=fp64_weights)
     y, w = vp.mesh_nodes(mesh)
     row, ptri, kind, tself = vp.nf_lists(nf)
     C = vp.nf_weights(nf)
@@ -56,10 +60,10 @@ def gpu_run(vp, ctx, vxy, tri, rule, extra=None, node_targets=True, f=None, prec
     return out
 
 
-def compare_weights(Cg, Co, J, ptri):
+def compare_weights(Cg, Co, J, ptri, jtol=1e-13):
     scale = np.maximum(np.abs(Co).max(axis=1), 1e-300)
     err = np.abs(Cg - Co).max(axis=1)
-    bound = 1e-12 * scale + 1e-15 * J[ptri]
+    bound = 1e-12 * scale + jtol * J[ptri]
     bad = err > bound
     assert not bad.any(), (int(bad.sum()), float((err / scale).max()))
 
@@ -73,6 +77,8 @@ def disk(vp, ctx, tables):
     f = np.stack([d(s["yxy"]) for d in dens])
     u_or, info = o.potential(s, f)
     g = gpu_run(vp, ctx, mesh.vxy, mesh.tri, 16, f=f, precisions=(0, 1))
+    g64 = gpu_run(vp, ctx, mesh.vxy, mesh.tri, 16, f=f, precisions=(0,), fp64_weights=True)
+    g["fp64_weights"] = g64
     return s, f, u_or, info, g
 
 
@@ -89,9 +95,13 @@ def test_config1_lists_bit_exact(disk):
     assert np.array_equal(g["kind"], info["pkind"])
 
 
-def test_config1_weights(disk):
-    s, _, _, info, g = disk
-    compare_weights(g["C"], info["C"], s["J"], info["ptri"])
+@pytest.mark.parametrize("fp64", [False, True])
+def test_config1_weights(disk, fp64):
+    s, _, u_or, info, g = disk
+    if fp64:
+        g = g["fp64_weights"]
+        assert rel_err(g["u0"], u_or).max() <= 1e-12
+    compare_weights(g["C"], info["C"], s["J"], info["ptri"], jtol=1e-15 if fp64 else 1e-13)
     st = g["stats"]
     assert st["near_leaves"] == int(info["stats"][info["pkind"] == 0].sum())
     assert st["self_panels"] == int(info["stats"][info["pkind"] == 1].sum())
