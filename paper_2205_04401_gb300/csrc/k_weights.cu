@@ -121,7 +121,6 @@ __device__ __forceinline__ int dyadic_count(double len, double dist) {
 }
 
 // ------------------------------------------------------------------ self
-template <bool F2>
 __global__ void __launch_bounds__(WARPS * 32) k_weights_self(WeightsArgs a, const int32_t* __restrict__ idx, int64_t n) {
     __shared__ LogSmem lt;
     load_logtab(a.tab, lt);
@@ -153,17 +152,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_self(WeightsArgs a, cons
     double m[VP_NB];
 #pragma unroll
     for (int q = 0; q < VP_NB; q++) m[q] = 0.0;
-    float mh[VP_NB], ml[VP_NB];
-#pragma unroll
-    for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
-    f2 gr2[4], glr2[4], gwl2[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        gr2[q] = f2_from_d(gr[q]);
-        glr2[q] = f2_from_d(glr[q]);
-        gwl2[q] = f2_from_d(gwl[q]);
-    }
-    const f2 xi02 = f2_from_d(xi0), eta02 = f2_from_d(eta0);
     int panels = 0;
     for (int e = 0; e < 3; e++) {
         const double Px = v[2 * e], Py = v[2 * e + 1];
@@ -205,27 +193,14 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_self(WeightsArgs a, cons
                 const double lr0 = 0.5 * vp_logd(rx * rx + ry * ry, lt.rc, lt.lc, ln2);
                 // reference coordinates along the ray x + r (gamma(s) - x)
                 const double xig = xiP + sl * dxi - xi0, etag = etaP + sl * deta - eta0;
-                if (F2) {
-                    const f2 lr = f2_from_d(lr0), w = f2_from_d(ws), xg = f2_from_d(xig), eg = f2_from_d(etag);
 #pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const f2 g = f2_mul(f2_add(lr, glr2[q]), f2_mul(w, gwl2[q]));
-                        f2_leg15_acc(mh, ml, g, f2_add(f2_mul(gr2[q], xg), xi02), f2_add(f2_mul(gr2[q], eg), eta02));
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const double g = (lr0 + glr[q]) * ws * gwl[q];
-                        accumulate(m, g, fma(gr[q], xig, xi0), fma(gr[q], etag, eta0));
-                    }
+                for (int q = 0; q < 4; q++) {
+                    const double g = (lr0 + glr[q]) * ws * gwl[q];
+                    accumulate(m, g, fma(gr[q], xig, xi0), fma(gr[q], etag, eta0));
                 }
                 b0 = b1;
             }
         }
-    }
-    if (F2) {
-#pragma unroll
-        for (int q = 0; q < VP_NB; q++) m[q] = (double)mh[q] + (double)ml[q];
     }
     finish_pair(a, p, T, own, xx, xy, m, lane, lt.rc, lt.lc, ln2);
     if (lane == 0) {
@@ -681,6 +656,125 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_near_f2(WeightsArgs a, W
     }
 }
 
+// ---------------------------------------------------- self, float-float
+// Section 3.4 with the per-edge geometry that fixes the panels (side
+// lengths, the foot of the perpendicular, the distance to the side, the
+// dyadic panel counts) in FP64 exactly as in the FP64 kernel, and everything
+// per panel and per point in float-float.  Lanes: Gauss-Legendre node
+// lane >> 1 of every panel, GGQ nodes 4 (lane & 1) .. +3.
+__global__ void __launch_bounds__(WARPS * 32) k_weights_self_f2(WeightsArgs a, WeightsF2 b, const int32_t* __restrict__ idx,
+                                                              int64_t n) {
+    __shared__ float4 ftab[LOG_N];
+    __shared__ LogSmem lt;
+    load_logtab(a.tab, lt);
+    for (int i = threadIdx.x; i < LOG_N; i += blockDim.x) ftab[i] = g_logtab.e[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (w >= n) return;
+    const double ln2 = a.tab->ln2;
+    const int64_t p = idx[w];
+    const int T = a.ptri[p], t = a.ptgt[p];
+    const double* v = a.tv + 6 * (int64_t)T;
+    const double Ax = v[0], Ay = v[1];
+    const double ex = v[2] - Ax, ey = v[3] - Ay, fx = v[4] - Ax, fy = v[5] - Ay;
+    const double invJ = 1.0 / a.J[T];
+    const double xx = a.txy[2 * t], xy = a.txy[2 * t + 1];
+    const double qx0 = xx - Ax, qy0 = xy - Ay;
+    const f2 xi0 = f2_from_d((qx0 * fy - qy0 * fx) * invJ), eta0 = f2_from_d((ex * qy0 - ey * qx0) * invJ);
+    const int own = own_index(a, t, T);
+    // float-float triangle relative to the target
+    const float4 TA = b.tA[T], TE = b.te[T], TF = b.tf[T], X = b.x2[t];
+    const f2 ax = f2_add({TA.x, TA.y}, {-X.x, -X.y}), ay = f2_add({TA.z, TA.w}, {-X.z, -X.w});
+    const f2 e2x = {TE.x, TE.y}, e2y = {TE.z, TE.w}, f2x = {TF.x, TF.y}, f2y = {TF.z, TF.w};
+    const int gl = lane >> 1, jb = (lane & 1) * 4;
+    const float2 LX = a.tab->lx2[gl], LW = a.tab->lw2[gl];
+    const f2 lx = {LX.x, LX.y}, lw = {LW.x, LW.y};
+    f2 gr[4], glr[4], gwl[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const float2 r = a.tab->gr2[jb + q], lr = a.tab->glr2[jb + q], gw = a.tab->gwl2[jb + q];
+        gr[q] = {r.x, r.y};
+        glr[q] = {lr.x, lr.y};
+        gwl[q] = {gw.x, gw.y};
+    }
+    float mh[VP_NB], ml[VP_NB];
+#pragma unroll
+    for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
+    int panels = 0;
+    for (int e = 0; e < 3; e++) {
+        const double Px = v[2 * e], Py = v[2 * e + 1];
+        const double Qx = v[(2 * e + 2) % 6], Qy = v[(2 * e + 3) % 6];
+        const double dx = rn_sub(Qx, Px), dy = rn_sub(Qy, Py);
+        const double L = rn_sqrt(rn_add(rn_mul(dx, dx), rn_mul(dy, dy)));
+        if (L == 0.0) continue;
+        const double h = rn_div(fabs(rn_sub(rn_mul(dx, rn_sub(xy, Py)), rn_mul(dy, rn_sub(xx, Px)))), L);
+        if (h == 0.0) continue;
+        double st = rn_div(rn_add(rn_mul(dx, rn_sub(xx, Px)), rn_mul(dy, rn_sub(xy, Py))), L);
+        if (st < 0.0) st = 0.0;
+        if (st > L) st = L;
+        const double fxp = rn_add(Px, rn_mul(rn_div(st, L), dx)), fyp = rn_add(Py, rn_mul(rn_div(st, L), dy));
+        const double ddx = rn_sub(xx, fxp), ddy = rn_sub(xy, fyp);
+        const double delta = rn_sqrt(rn_add(rn_mul(ddx, ddx), rn_mul(ddy, ddy)));
+        const double Lst = rn_sub(L, st);
+        // the side in float-float: P - x, Q - P, and in reference coordinates
+        const f2 pxr = e == 0 ? ax : f2_add(ax, e == 1 ? e2x : f2x);
+        const f2 pyr = e == 0 ? ay : f2_add(ay, e == 1 ? e2y : f2y);
+        const f2 sdx = e == 0 ? e2x : (e == 1 ? f2_add(f2x, f2_neg(e2x)) : f2_neg(f2x));
+        const f2 sdy = e == 0 ? e2y : (e == 1 ? f2_add(f2y, f2_neg(e2y)) : f2_neg(f2y));
+        const float pref_x = e == 1 ? 1.f : 0.f, pref_y = e == 2 ? 1.f : 0.f;        // P in T's simplex
+        const float dref_x = e == 0 ? 1.f : (e == 1 ? -1.f : 0.f);                   // Q - P there
+        const float dref_y = e == 0 ? 0.f : (e == 1 ? 1.f : -1.f);
+        const f2 xiP = f2_add_f(f2_neg(xi0), pref_x), etaP = f2_add_f(f2_neg(eta0), pref_y);   // P - x, reference
+        const f2 invL = f2_from_d(1.0 / L), h2 = f2_from_d(h), L2 = f2_from_d(L), st2 = f2_from_d(st);
+        for (int side = 0; side < 2; side++) {
+            const double len = side == 0 ? st : Lst;
+            if (!(len > 0.0)) continue;
+            const int Nd = dyadic_count(len, delta);
+            const f2 len2 = side == 0 ? st2 : f2_add(L2, f2_neg(st2));
+            // panel boundaries: b_0 = end, b_i = end -/+ (1 - 2^-i) len, b_{Nd+1} = st
+            f2 b0 = side == 0 ? f2{0.f, 0.f} : L2;
+            for (int i = 0; i <= Nd; i++) {
+                f2 b1;
+                if (i == Nd) {
+                    b1 = st2;
+                } else {
+                    const int k = i + 1;                                      // 1 - 2^-k, exact as a pair
+                    const f2 om = k <= 24 ? f2{__fsub_rn(1.f, __int_as_float((127 - k) << 23)), 0.f}
+                                          : f2{1.f, -__int_as_float((127 - min(k, 126)) << 23)};
+                    const f2 frac = f2_mul(len2, om);
+                    b1 = side == 0 ? frac : f2_add(L2, f2_neg(frac));
+                }
+                panels++;
+                const f2 D = f2_add(b1, f2_neg(b0));
+                const f2 s = f2_add(b0, f2_mul(D, lx));
+                f2 wd = f2_mul(D, lw);
+                if (wd.h < 0.f) wd = f2_neg(wd);
+                const f2 ws = f2_mul(wd, h2);
+                const f2 sl = f2_mul(s, invL);
+                const f2 rx = f2_add(pxr, f2_mul(sl, sdx)), ry = f2_add(pyr, f2_mul(sl, sdy));
+                const f2 r2 = f2_add(f2_sqr(rx), f2_sqr(ry));
+                f2 lg;
+                if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);
+                else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
+                const f2 lr0 = f2_scale(lg, 0.5f);                            // log r0
+                const f2 xig = f2_add(xiP, f2_scale(sl, dref_x)), etag = f2_add(etaP, f2_scale(sl, dref_y));
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const f2 g = f2_mul(f2_add(lr0, glr[q]), f2_mul(ws, gwl[q]));
+                    f2_leg15_acc(mh, ml, g, f2_add(f2_mul(gr[q], xig), xi0), f2_add(f2_mul(gr[q], etag), eta0));
+                }
+                b0 = b1;
+            }
+        }
+    }
+    finish_pair_f2(a, b, p, T, t, own, mh, ml, lane, ftab, lt, ln2);
+    if (lane == 0) {
+        a.pstat[p] = panels;
+        a.pcap[p] = 0;
+    }
+}
+
 // float-float geometry of the weights kernels
 __global__ void k_weights_f2_tri(const double* __restrict__ tv, const double* __restrict__ J, int64_t nt,
                                  float4* __restrict__ tA, float4* __restrict__ te, float4* __restrict__ tf,
@@ -714,28 +808,14 @@ __global__ void k_weights_f2_pts(const double* __restrict__ xy, int64_t n, const
 
 }  // namespace
 
-void launch_weights_self(const WeightsArgs& a, const int32_t* idx, int64_t n, cudaStream_t s) {
-    if (n <= 0) return;
-    const unsigned grid = (unsigned)((n + WARPS - 1) / WARPS);
-    if (a.fp64) k_weights_self<false><<<grid, WARPS * 32, 0, s>>>(a, idx, n);
-    else k_weights_self<true><<<grid, WARPS * 32, 0, s>>>(a, idx, n);
-}
-
 size_t weights_f2_bytes(int64_t nt, int64_t M, int64_t N) {
     // seven arrays, each rounded up to 256 bytes
     return (size_t)nt * 4 * sizeof(float4) + (size_t)M * sizeof(float4) + (size_t)N * (sizeof(float4) + sizeof(float2)) +
            7 * 256;
 }
 
-void launch_weights_near(const WeightsArgs& a, const int32_t* idx, int64_t n, cudaStream_t s) {
-    if (n <= 0) return;
-    const unsigned grid = (unsigned)((n + WARPS - 1) / WARPS);
-    if (a.fp64) {
-        k_weights_near<<<grid, WARPS * 32, 0, s>>>(a, idx, n);
-        return;
-    }
-    ensure_logtab();
-    // float-float geometry in the caller's scratch
+// float-float triangles, targets and nodes in the caller's scratch
+static WeightsF2 weights_f2_prepare(const WeightsArgs& a, cudaStream_t s) {
     char* ws = (char*)a.f2_ws;
     auto take = [&](size_t bytes) {
         char* p = ws;
@@ -750,9 +830,23 @@ void launch_weights_near(const WeightsArgs& a, const int32_t* idx, int64_t n, cu
     float4* x2 = (float4*)take(a.M * sizeof(float4));
     float4* y2 = (float4*)take(a.N * sizeof(float4));
     float2* wq2 = (float2*)take(a.N * sizeof(float2));
-    k_weights_f2_tri<<<(unsigned)((a.nt + 255) / 256), 256, 0, s>>>(a.tv, a.J, a.nt, tA, te, tf, tw);
-    k_weights_f2_pts<<<(unsigned)((a.M + 255) / 256), 256, 0, s>>>(a.txy, a.M, nullptr, x2, nullptr);
-    k_weights_f2_pts<<<(unsigned)((a.N + 255) / 256), 256, 0, s>>>(a.y, a.N, a.W, y2, wq2);
+    if (a.nt > 0) k_weights_f2_tri<<<(unsigned)((a.nt + 255) / 256), 256, 0, s>>>(a.tv, a.J, a.nt, tA, te, tf, tw);
+    if (a.M > 0) k_weights_f2_pts<<<(unsigned)((a.M + 255) / 256), 256, 0, s>>>(a.txy, a.M, nullptr, x2, nullptr);
+    if (a.N > 0) k_weights_f2_pts<<<(unsigned)((a.N + 255) / 256), 256, 0, s>>>(a.y, a.N, a.W, y2, wq2);
     b.tA = tA; b.te = te; b.tf = tf; b.tw = tw; b.x2 = x2; b.y2 = y2; b.wq2 = wq2;
-    k_weights_near_f2<<<grid, WARPS * 32, 0, s>>>(a, b, idx, n);
+    return b;
+}
+
+void launch_weights(const WeightsArgs& a, const int32_t* self_idx, int64_t n_self, const int32_t* near_idx,
+                    int64_t n_near, cudaStream_t s, vp_ctx* ctx) {
+    const unsigned gs = (unsigned)((n_self + WARPS - 1) / WARPS), gn = (unsigned)((n_near + WARPS - 1) / WARPS);
+    if (a.fp64) {
+        PROF(ctx, ST_WEIGHTS_SELF, s, if (n_self > 0) k_weights_self<<<gs, WARPS * 32, 0, s>>>(a, self_idx, n_self));
+        PROF(ctx, ST_WEIGHTS_NEAR, s, if (n_near > 0) k_weights_near<<<gn, WARPS * 32, 0, s>>>(a, near_idx, n_near));
+        return;
+    }
+    ensure_logtab();
+    const WeightsF2 b = weights_f2_prepare(a, s);
+    PROF(ctx, ST_WEIGHTS_SELF, s, if (n_self > 0) k_weights_self_f2<<<gs, WARPS * 32, 0, s>>>(a, b, self_idx, n_self));
+    PROF(ctx, ST_WEIGHTS_NEAR, s, if (n_near > 0) k_weights_near_f2<<<gn, WARPS * 32, 0, s>>>(a, b, near_idx, n_near));
 }

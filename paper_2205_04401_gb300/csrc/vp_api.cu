@@ -94,6 +94,15 @@ void fill_tables(VpTables& t) {
     for (int r = 0; r < 2; r++)
         for (int k = 0; k < nq[r]; k++)
             for (int a = 0; a < VP_NB; a++) t.Q2[r][k][a] = split(t.Q[r][k][a]);
+    for (int j = 0; j < VP_NGL; j++) {
+        t.lx2[j] = split(VP_GL16_X[j]);
+        t.lw2[j] = split(VP_GL16_W[j]);
+    }
+    for (int j = 0; j < VP_NGGQ; j++) {
+        t.gr2[j] = split(VP_GGQ8_R[j]);
+        t.glr2[j] = split(std::log(VP_GGQ8_R[j]));
+        t.gwl2[j] = split(VP_GGQ8_W[j] * VP_INV_TWO_PI);
+    }
     t.near_what = VP_NEAR49_WHAT;
     t.near_degree = VP_NEAR49_DEGREE;
     for (int j = 0; j < VP_NGGQ; j++) {
@@ -201,14 +210,6 @@ void prof_collect(vp_ctx* ctx) {
     }
     ctx->prof_pending.clear();
 }
-
-#define PROF(ctx, stage, s, ...)        \
-    do {                                \
-        ProfRec _r;                     \
-        prof_begin(ctx, stage, s, _r);  \
-        __VA_ARGS__;                    \
-        prof_end(ctx, s, _r);           \
-    } while (0)
 
 extern "C" {
 
@@ -570,8 +571,7 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         wa.N = N;
         NF_CUDA(sc.alloc(&d_f2ws, (int64_t)weights_f2_bytes(nt, M, N)));
         wa.f2_ws = d_f2ws;
-        PROF(ctx, ST_WEIGHTS_SELF, s, launch_weights_self(wa, d_self_idx, n_self, s));
-        PROF(ctx, ST_WEIGHTS_NEAR, s, launch_weights_near(wa, d_near_idx, n_near, s));
+        launch_weights(wa, d_self_idx, n_self, d_near_idx, n_near, s, ctx);
         NF_CUDA(cudaGetLastError());
 
         // statistics

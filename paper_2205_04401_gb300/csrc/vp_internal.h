@@ -55,6 +55,15 @@ void prof_begin(vp_ctx* ctx, int stage, cudaStream_t s, ProfRec& r);
 void prof_end(vp_ctx* ctx, cudaStream_t s, ProfRec& r);
 void prof_collect(vp_ctx* ctx);
 
+// Run the statements between the events of a profiled stage.
+#define PROF(ctx, stage, s, ...)        \
+    do {                                \
+        ProfRec _r;                     \
+        prof_begin(ctx, stage, s, _r);  \
+        __VA_ARGS__;                    \
+        prof_end(ctx, s, _r);           \
+    } while (0)
+
 struct vp_mesh {
     vp_ctx* ctx = nullptr;
     int64_t nt = 0, nv = 0, N = 0;
@@ -186,8 +195,9 @@ struct WeightsArgs {
     void* f2_ws;        // scratch of weights_f2_bytes(nt, M, N) for the float-float kernels
 };
 size_t weights_f2_bytes(int64_t nt, int64_t M, int64_t N);
-void launch_weights_self(const WeightsArgs& a, const int32_t* idx, int64_t n, cudaStream_t s);
-void launch_weights_near(const WeightsArgs& a, const int32_t* idx, int64_t n, cudaStream_t s);
+// self and near weights (stages ST_WEIGHTS_SELF, ST_WEIGHTS_NEAR)
+void launch_weights(const WeightsArgs& a, const int32_t* self_idx, int64_t n_self, const int32_t* near_idx,
+                    int64_t n_near, cudaStream_t s, vp_ctx* ctx);
 void launch_sum_i32(const int32_t* a, int64_t n, unsigned long long* out, cudaStream_t s);
 // out[0..2] = sums of a over kind 0 and kind != 0, sum of b
 void launch_sum_by_kind(const int32_t* a, const uint8_t* kind, const int32_t* b, int64_t n, unsigned long long* out,
