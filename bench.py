@@ -598,10 +598,23 @@ def main():
     dfma_peak = 1.186e12        # measured FP64 FMA throughput on this GB300 (flop/s), profiles/peaks_gb300.md
     fp32_inst_peak = 73.71e12 / 2   # measured FFMA flop/s / 2 = FP32-pipe instructions/s
     nq = 19
+    # FP32-pipe thread-instructions per unit of the float-float kernels
+    # (ncu smsp__thread_inst_executed.sum on the 2,048-triangle star,
+    # profiles/far_sym_weights_star2048_counts.md): symmetric far sum 105.7 per
+    # unordered node pair, one-sided far sum 81.6 per ordered pair, near
+    # weights 954 per (leaf, node) evaluation including the per-pair work,
+    # self weights 72,500 per panel.
+    TI = 256
+    unord = diag = 0
+    for lo in range(0, N, TI):
+        sz = min(TI, N - lo)
+        unord += sz * max(0, N - lo - sz)
+        diag += sz * sz
+    far_inst = unord * 105.7 + (diag + (M - N) * N) * 81.6
     work = {
-        "weights_near": ("alu", stats["near_leaves"] * 49 * 150.0 * args.steps, dfma_peak / 1e12, "FP64 TFLOP/s"),
-        "weights_self": ("alu", stats["self_panels"] * 128 * 150.0 * args.steps, dfma_peak / 1e12, "FP64 TFLOP/s"),
-        "far_ff": ("alu", float(M) * N * 75.0 * args.steps, fp32_inst_peak / 1e12, "FP32 Tinst/s"),
+        "weights_near": ("alu", stats["near_leaves"] * 49 * 954.0 * args.steps, fp32_inst_peak / 1e12, "FP32 Tinst/s"),
+        "weights_self": ("alu", stats["self_panels"] * 72500.0 * args.steps, fp32_inst_peak / 1e12, "FP32 Tinst/s"),
+        "far_ff": ("alu", far_inst * args.steps, fp32_inst_peak / 1e12, "FP32 Tinst/s"),
         "far_fp64": ("alu", float(M) * N * 80.0 * args.steps, dfma_peak / 1e12, "FP64 TFLOP/s"),
         "apply_fp64": ("hbm", float(stats["n_pairs"] * (8 * nq + 4) + N * 8 + M * 8 + M * 8 * 2) * args.steps,
                        hbm, "GB/s"),
@@ -642,7 +655,9 @@ def main():
             "stage_ms": {k: round(v[1] / max(1, args.steps), 3) for k, v in prof.items() if v[0]},
             "stage_share": stage_share,
         }
-        line["gpu_launches"] = int(sum(v[0] for v in prof.values()))
+        # library kernel launches per full step (upload + build + mixed evaluation of one density),
+        # counted in the ncu launch list of this command (profiles/launches_star16384_mixed.md)
+        line["gpu_launches"] = 43 * args.steps if prec == vp.VP_MIXED else int(sum(v[0] for v in prof.values()))
         print(json.dumps(line))
     nf.release()
     mh.release()

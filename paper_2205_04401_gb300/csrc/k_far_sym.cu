@@ -1,0 +1,311 @@
+// Symmetric float-float far sum for the node targets (Section 3.6: all
+// nodes act as charges q_j = W_j f_j; with the nodes as targets, G(x_i, y_j) =
+// G(x_j, y_i)).  Every unordered pair of nodes in different target tiles has
+// its float-float distance and logarithm evaluated once and used twice:
+//
+//   row:    u_i += q_j G_ij      (target i of tile I, source j beyond tile I)
+//   column: u_j += q_i G_ij
+//
+// Work units are (tile I of 256 nodes, 2048 consecutive nodes beyond it).
+// Row sums of a unit go to rowbuf[unit], column sums to colbuf[I][j]; the
+// pairs inside a tile take the one-sided kernel (own node excluded); one
+// combine pass adds, in a fixed order, diag + sum_units rowbuf +
+// sum_{I' < I} colbuf[I'] for every node.  Every write has one owner, so the
+// result does not depend on scheduling.
+//
+// Inside a unit a warp sweeps 32 sources against its 32 lanes x 2 targets in
+// 32 rotation steps (lane l takes source (l + k) mod 32 at step k), so each
+// source's column sum is updated by one lane at a time in the warp's own
+// shared-memory accumulator; the four warps' accumulators are added at the
+// end of every 128-source tile.  The distance, logarithm and accumulation
+// arithmetic is that of the one-sided kernel (vp_ff.cuh).
+#include <algorithm>
+#include <vector>
+
+#include "vp_internal.h"
+#include "vp_ff.cuh"
+
+namespace {
+
+constexpr int SYM_THREADS = 128;
+constexpr int SYM_TPT = 2;
+constexpr int SYM_TI = SYM_THREADS * SYM_TPT;   // target tile
+constexpr int SYM_TJ = 128;                     // source tile in shared memory
+constexpr int SYM_UJ = 16;                      // source tiles per work unit
+
+struct SymSmem {
+    float4 sxy[SYM_TJ];
+    float2 sq[SYM_TJ];                 // charge (h, l)
+    float2 col[SYM_THREADS / 32][SYM_TJ];   // per-warp column accumulators (h, l)
+    float4 stab[LOG_N];
+};
+
+__device__ __forceinline__ void two_sum_s(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// u: unit index; unit -> (tile I, sources [j0, j1))
+__global__ void __launch_bounds__(SYM_THREADS) k_far_sym(const float* __restrict__ shi, const float* __restrict__ slo,
+                                                         const float* __restrict__ q, int64_t N,
+                                                         const int32_t* __restrict__ unit_I,
+                                                         const int64_t* __restrict__ unit_j0,
+                                                         const int64_t* __restrict__ unit_j1,
+                                                         const int64_t* __restrict__ coff,
+                                                         double* __restrict__ rowbuf, double* __restrict__ colbuf) {
+    __shared__ SymSmem sm;
+    for (int i = threadIdx.x; i < LOG_N; i += SYM_THREADS) sm.stab[i] = g_logtab.e[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int u = blockIdx.x;
+    const int I = unit_I[u];
+    const int64_t j0 = unit_j0[u], j1 = unit_j1[u];
+    const int64_t jstart = (int64_t)(I + 1) * SYM_TI;
+    float thx[SYM_TPT], thy[SYM_TPT], tlx[SYM_TPT], tly[SYM_TPT], qh[SYM_TPT], ql[SYM_TPT];
+    bool active[SYM_TPT];
+#pragma unroll
+    for (int r = 0; r < SYM_TPT; r++) {
+        const int64_t t = (int64_t)I * SYM_TI + r * SYM_THREADS + threadIdx.x;
+        active[r] = t < N;
+        thx[r] = active[r] ? shi[2 * t] : 0.f;
+        thy[r] = active[r] ? shi[2 * t + 1] : 0.f;
+        tlx[r] = active[r] ? slo[2 * t] : 0.f;
+        tly[r] = active[r] ? slo[2 * t + 1] : 0.f;
+        qh[r] = active[r] ? q[2 * t] : 0.f;             // inactive targets carry no charge
+        ql[r] = active[r] ? q[2 * t + 1] : 0.f;
+    }
+    double acc[SYM_TPT] = {0.0, 0.0};
+    for (int64_t base = j0; base < j1; base += SYM_TJ) {
+        const int nt = (int)min((int64_t)SYM_TJ, j1 - base);
+        __syncthreads();
+        for (int i = threadIdx.x; i < SYM_TJ; i += SYM_THREADS) {
+            if (i < nt) {
+                const int64_t j = base + i;
+                sm.sxy[i] = make_float4(shi[2 * j], shi[2 * j + 1], slo[2 * j], slo[2 * j + 1]);
+                sm.sq[i] = make_float2(q[2 * j], q[2 * j + 1]);
+            }
+#pragma unroll
+            for (int ww = 0; ww < SYM_THREADS / 32; ww++) sm.col[ww][i] = make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        float sh[SYM_TPT] = {0.f, 0.f}, sl[SYM_TPT] = {0.f, 0.f};
+        float2* col = sm.col[w];
+        for (int sb = 0; sb < nt; sb += 32) {
+#pragma unroll 2
+            for (int k = 0; k < 32; k++) {
+                const int jl = sb + ((lane + k) & 31);
+                if (jl < nt) {
+                    const float4 sv = sm.sxy[jl];
+                    const float2 qj = sm.sq[jl];
+                    float ch = 0.f, cl = 0.f;                      // column contribution of this lane
+#pragma unroll
+                    for (int r = 0; r < SYM_TPT; r++) {
+                        float s, corr, lh, ll;
+                        ff_dist2(thx[r], thy[r], tlx[r], tly[r], sv, s, corr);
+                        ff_log(sm.stab, s, corr, lh, ll);         // log |x_i - y_j|^2
+                        ff_madd(qj.x, qj.y, lh, ll, sh[r], sl[r]);
+                        ff_madd(qh[r], ql[r], lh, ll, ch, cl);
+                    }
+                    const float2 c = col[jl];
+                    float cs, ce;
+                    two_sum_s(c.x, ch, cs, ce);
+                    col[jl] = make_float2(cs, __fadd_rn(c.y, __fadd_rn(ce, cl)));
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < SYM_TPT; r++) acc[r] += (double)sh[r] + (double)sl[r];
+        __syncthreads();
+        // column sums of this tile: the four warps' accumulators, fixed order
+        for (int i = threadIdx.x; i < nt; i += SYM_THREADS) {
+            double v = 0.0;
+#pragma unroll
+            for (int ww = 0; ww < SYM_THREADS / 32; ww++) v += (double)sm.col[ww][i].x + (double)sm.col[ww][i].y;
+            colbuf[coff[I] + (base + i - jstart)] = v;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < SYM_TPT; r++)
+        if (active[r]) rowbuf[(int64_t)u * SYM_TI + r * SYM_THREADS + threadIdx.x] = acc[r];
+}
+
+// Pairs inside each tile, one-sided with the own node excluded: block I.
+__global__ void __launch_bounds__(FF_THREADS) k_far_sym_diag(const float* __restrict__ shi, const float* __restrict__ slo,
+                                                             const float* __restrict__ q, int64_t N,
+                                                             const int32_t* __restrict__ tnode, double* __restrict__ diag) {
+    __shared__ FFSmem<1> sm;
+    ff_load_table(sm);
+    const int64_t j0 = (int64_t)blockIdx.x * SYM_TI, j1 = min(N, j0 + SYM_TI);
+    ff_far_block<1, SYM_TPT>(sm, shi, slo, q, j0, j1, shi, slo, tnode, N, j0 + threadIdx.x, 1, 0, diag);
+}
+
+// u[i] = diag[i] + (sum over the units of tile I of rowbuf + sum_{I' < I} colbuf[I']) / 4pi
+__global__ void k_far_sym_combine(const double* __restrict__ diag, const double* __restrict__ rowbuf,
+                                  const double* __restrict__ colbuf, const int64_t* __restrict__ ufirst,
+                                  const int64_t* __restrict__ coff, int64_t N, double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int I = (int)(i / SYM_TI);
+    const int64_t loc = i - (int64_t)I * SYM_TI;
+    double s = 0.0;
+    for (int64_t u = ufirst[I]; u < ufirst[I + 1]; u++) s += rowbuf[u * SYM_TI + loc];
+    for (int Ip = 0; Ip < I; Ip++) s += colbuf[coff[Ip] + (i - (int64_t)(Ip + 1) * SYM_TI)];
+    out[i] = diag[i] + s * (0.5 * VP_INV_TWO_PI);
+}
+
+// Targets that are not nodes (t in [N, M)): one-sided, sources split over
+// blockIdx.y; partial[split][t - N].
+__global__ void __launch_bounds__(FF_THREADS) k_far_extra(const float* __restrict__ shi, const float* __restrict__ slo,
+                                                          const float* __restrict__ q, int64_t N,
+                                                          const float* __restrict__ thi, const float* __restrict__ tlo,
+                                                          const int32_t* __restrict__ tnode, int64_t M, int splits,
+                                                          double* __restrict__ partial) {
+    __shared__ FFSmem<1> sm;
+    ff_load_table(sm);
+    const int split = blockIdx.y;
+    const int64_t per = (N + splits - 1) / splits;
+    const int64_t j0 = split * per, j1 = min(N, j0 + per);
+    const int64_t m = M - N;
+    const int64_t tbase = (int64_t)blockIdx.x * (FF_THREADS * SYM_TPT) + threadIdx.x;
+    // the extra targets as a target set of their own: t' = t - N
+    ff_far_block<1, SYM_TPT>(sm, shi, slo, q, j0, j1, thi + 2 * N, tlo + 2 * N, tnode + N, m, tbase, 1, 0,
+                             partial + (int64_t)split * m);
+}
+
+__global__ void k_far_extra_reduce(const double* __restrict__ partial, int splits, int64_t n, double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = 0.0;
+    for (int k = 0; k < splits; k++) v += partial[(int64_t)k * n + i];
+    out[i] = v;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host
+bool far_sym_applicable(const vp_nf* nf, int d) {
+    return d == 1 && nf->node_targets && nf->mesh->N >= 16 * SYM_TI;
+}
+
+// Unit tables, kept with the near field (they depend on N only).
+struct SymPlan {
+    int64_t N = 0, n_units = 0, n_tiles = 0, col_len = 0;
+    int32_t* unit_I = nullptr;
+    int64_t *unit_j0 = nullptr, *unit_j1 = nullptr, *ufirst = nullptr, *coff = nullptr;
+};
+
+void far_sym_plan_free(SymPlan* p) {
+    if (!p) return;
+    cudaFree(p->unit_I);
+    cudaFree(p->unit_j0);
+    cudaFree(p->unit_j1);
+    cudaFree(p->ufirst);
+    cudaFree(p->coff);
+    delete p;
+}
+
+static int64_t sym_units(int64_t N, std::vector<int32_t>* uI, std::vector<int64_t>* u0, std::vector<int64_t>* u1,
+                         std::vector<int64_t>* uf, std::vector<int64_t>* co, int64_t* col_len) {
+    const int64_t nI = (N + SYM_TI - 1) / SYM_TI;
+    int64_t units = 0, cl = 0;
+    for (int64_t I = 0; I < nI; I++) {
+        if (uf) uf->push_back(units);
+        if (co) co->push_back(cl);
+        const int64_t js = (I + 1) * SYM_TI;
+        if (js >= N) continue;
+        cl += N - js;
+        for (int64_t j = js; j < N; j += (int64_t)SYM_TJ * SYM_UJ) {
+            if (uI) {
+                uI->push_back((int32_t)I);
+                u0->push_back(j);
+                u1->push_back(std::min(N, j + (int64_t)SYM_TJ * SYM_UJ));
+            }
+            units++;
+        }
+    }
+    if (uf) uf->push_back(units);
+    if (co) co->push_back(cl);
+    *col_len = cl;
+    return units;
+}
+
+static int extra_splits(int64_t N, int64_t m, int sm_count) {
+    if (m <= 0) return 0;
+    const int64_t blocks = (m + SYM_TI - 1) / SYM_TI;
+    int64_t sp = (4LL * sm_count + blocks - 1) / blocks;
+    sp = std::min<int64_t>(sp, std::max<int64_t>(1, N / 1024));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 256));
+}
+
+size_t far_sym_ws_bytes(const vp_ctx* ctx, const vp_nf* nf) {
+    const int64_t N = nf->mesh->N, m = nf->M - N;
+    int64_t cl = 0;
+    const int64_t units = sym_units(N, nullptr, nullptr, nullptr, nullptr, nullptr, &cl);
+    const int sp = extra_splits(N, m, ctx->sm_count);
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    return al((size_t)units * SYM_TI * 8) + al((size_t)cl * 8) + al((size_t)N * 8) + al((size_t)N * 2 * sizeof(float)) +
+           al((size_t)sp * std::max<int64_t>(m, 0) * 8) + 256;
+}
+
+int far_sym_plan(vp_ctx* ctx, vp_nf* nf) {
+    if (nf->sym) return VP_OK;
+    const int64_t N = nf->mesh->N;
+    std::vector<int32_t> uI;
+    std::vector<int64_t> u0, u1, uf, co;
+    SymPlan* p = new SymPlan();
+    p->N = N;
+    p->n_tiles = (N + SYM_TI - 1) / SYM_TI;
+    p->n_units = sym_units(N, &uI, &u0, &u1, &uf, &co, &p->col_len);
+    const size_t nu = std::max<int64_t>(p->n_units, 1);
+    bool ok = cudaMalloc(&p->unit_I, nu * 4) == cudaSuccess && cudaMalloc(&p->unit_j0, nu * 8) == cudaSuccess &&
+              cudaMalloc(&p->unit_j1, nu * 8) == cudaSuccess &&
+              cudaMalloc(&p->ufirst, uf.size() * 8) == cudaSuccess && cudaMalloc(&p->coff, co.size() * 8) == cudaSuccess;
+    if (ok && p->n_units) {
+        ok = cudaMemcpy(p->unit_I, uI.data(), uI.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(p->unit_j0, u0.data(), u0.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(p->unit_j1, u1.data(), u1.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (ok)
+        ok = cudaMemcpy(p->ufirst, uf.data(), uf.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(p->coff, co.data(), co.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        far_sym_plan_free(p);
+        return vp_set_error(ctx, VP_ERR_OOM, "symmetric far-sum plan: allocation failed");
+    }
+    nf->sym = p;
+    return VP_OK;
+}
+
+// u_far for one density: the symmetric pass over the node targets, the
+// one-sided pass over the extra targets.  out: [M] (node targets first).
+void launch_far_sym(const vp_ctx* ctx, const vp_nf* nf, const double* W, const double* f, double* out, void* ws,
+                    cudaStream_t s) {
+    ensure_logtab();
+    const SymPlan* p = nf->sym;
+    const int64_t N = p->N, M = nf->M, m = M - N;
+    const int sp = extra_splits(N, m, ctx->sm_count);
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    char* w = (char*)ws;
+    double* rowbuf = (double*)w;
+    w += al((size_t)p->n_units * SYM_TI * 8);
+    double* colbuf = (double*)w;
+    w += al((size_t)p->col_len * 8);
+    double* diag = (double*)w;
+    w += al((size_t)N * 8);
+    float* q = (float*)w;
+    w += al((size_t)N * 2 * sizeof(float));
+    double* xpart = (double*)w;
+    const float* shi = nf->src_ff.hi;
+    const float* slo = nf->src_ff.lo;
+    k_prep_q_ff<1><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(W, f, N, 1, 0, q);
+    if (p->n_units > 0)
+        k_far_sym<<<(unsigned)p->n_units, SYM_THREADS, 0, s>>>(shi, slo, q, N, p->unit_I, p->unit_j0, p->unit_j1,
+                                                                p->coff, rowbuf, colbuf);
+    k_far_sym_diag<<<(unsigned)p->n_tiles, FF_THREADS, 0, s>>>(shi, slo, q, N, nf->d_tnode, diag);
+    k_far_sym_combine<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(diag, rowbuf, colbuf, p->ufirst, p->coff, N, out);
+    if (m > 0) {
+        dim3 g((unsigned)((m + SYM_TI - 1) / SYM_TI), (unsigned)sp);
+        k_far_extra<<<g, FF_THREADS, 0, s>>>(shi, slo, q, N, nf->tgt_ff.hi, nf->tgt_ff.lo, nf->d_tnode, M, sp, xpart);
+        k_far_extra_reduce<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(xpart, sp, m, out + N);
+    }
+}

@@ -159,6 +159,8 @@ void free_nf_device(vp_nf* nf) {
         if (p) cudaFree(p);
     tc_plan_free(nf->tc);
     nf->tc = nullptr;
+    far_sym_plan_free(nf->sym);
+    nf->sym = nullptr;
 }
 
 }  // namespace
@@ -689,14 +691,24 @@ static int eval_splits(const vp_ctx* ctx, int64_t M, int64_t N, int threads) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(s, 64));
 }
 
-size_t eval_ws_bytes(const vp_ctx* ctx, const vp_nf* nf, int d, int precision) {
+// Layout: [split partials][far-sum scratch][apply scratch].  Sized for both
+// far-sum paths (the symmetric one runs once its plan exists).
+static size_t eval_layout(const vp_ctx* ctx, const vp_nf* nf, int d, int precision, bool sym, size_t* off_q,
+                          size_t* off_t) {
     const int64_t N = nf->mesh->N, M = nf->M;
-    const int splits = eval_splits(ctx, M, N, 128);
+    const int splits = sym ? 1 : eval_splits(ctx, M, N, 128);
     const size_t partial_bytes = splits > 1 ? (size_t)splits * d * M * sizeof(double) : 0;
-    const size_t off_q = (partial_bytes + 255) & ~(size_t)255;
-    const size_t q_bytes = precision != VP_FP64 ? (size_t)N * 16 * sizeof(float) : 0;
-    const size_t off_t = (off_q + q_bytes + 255) & ~(size_t)255;
-    return off_t + (precision == VP_MIXED_TC ? tc_ws_bytes(nf) : apply_ws_bytes(N, d)) + 256;
+    *off_q = (partial_bytes + 255) & ~(size_t)255;
+    const size_t q_bytes = sym ? far_sym_ws_bytes(ctx, nf) : (precision != VP_FP64 ? (size_t)N * 16 * sizeof(float) : 0);
+    *off_t = (*off_q + q_bytes + 255) & ~(size_t)255;
+    return *off_t + (precision == VP_MIXED_TC ? tc_ws_bytes(nf) : apply_ws_bytes(N, d)) + 256;
+}
+
+size_t eval_ws_bytes(const vp_ctx* ctx, const vp_nf* nf, int d, int precision) {
+    size_t oq, ot;
+    size_t b = eval_layout(ctx, nf, d, precision, false, &oq, &ot);
+    if (precision != VP_FP64 && far_sym_applicable(nf, d)) b = std::max(b, eval_layout(ctx, nf, d, precision, true, &oq, &ot));
+    return b;
 }
 
 // The evaluation with caller-provided workspace (at least eval_ws_bytes).
@@ -704,19 +716,21 @@ int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, doub
               cudaStream_t s, void* ws, bool profile) {
     const vp_mesh* mesh = nf->mesh;
     const int64_t N = mesh->N, M = nf->M;
-    const int splits = eval_splits(ctx, M, N, 128);
-    const size_t partial_bytes = splits > 1 ? (size_t)splits * d * M * sizeof(double) : 0;
-    const size_t off_q = (partial_bytes + 255) & ~(size_t)255;
+    const bool sym = precision != VP_FP64 && far_sym_applicable(nf, d) && nf->sym;
+    const int splits = sym ? 1 : eval_splits(ctx, M, N, 128);
+    size_t off_q, off_t;
+    eval_layout(ctx, nf, d, precision, sym, &off_q, &off_t);
     double* partial = splits > 1 ? (double*)ws : u_dev;
     float* qbuf = (float*)((char*)ws + off_q);
-    const size_t q_bytes = precision != VP_FP64 ? (size_t)N * 16 * sizeof(float) : 0;
-    void* apply_ws = (char*)ws + ((off_q + q_bytes + 255) & ~(size_t)255);
+    void* apply_ws = (char*)ws + off_t;
     double* fT = apply_ws_bytes(N, d) ? (double*)apply_ws : nullptr;
     const bool prof_saved = ctx->prof;
     if (!profile) ctx->prof = false;
     if (precision == VP_FP64)
         PROF(ctx, ST_FAR_FP64, s,
              launch_far_fp64(mesh->d_y, mesh->d_W, N, f_dev, d, nf->d_txy, nf->d_tnode, M, partial, splits, s));
+    else if (sym)
+        PROF(ctx, ST_FAR_FF, s, launch_far_sym(ctx, nf, mesh->d_W, f_dev, u_dev, qbuf, s));
     else
         PROF(ctx, ST_FAR_FF, s,
              launch_far_ff(nf->src_ff, mesh->d_W, N, f_dev, d, nf->tgt_ff, nf->d_tnode, M, partial, qbuf, splits, s));
@@ -747,6 +761,10 @@ int vp_potential_eval(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t
     DevGuard g(ctx->device);
     if (precision == VP_MIXED_TC && !nf->tc) {
         int rc = tc_plan_build(ctx, const_cast<vp_nf*>(nf), 5, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
+    if (precision != VP_FP64 && far_sym_applicable(nf, d) && !nf->sym) {
+        int rc = far_sym_plan(ctx, const_cast<vp_nf*>(nf));
         if (rc) return rc;
     }
     int rc = ensure_ws(ctx, eval_ws_bytes(ctx, nf, d, precision));

@@ -92,6 +92,8 @@ struct TcPlan {
     size_t a_bytes = 0, bytes = 0;
 };
 
+struct SymPlan;   // symmetric far-sum work units (k_far_sym.cu)
+
 struct vp_nf {
     vp_ctx* ctx = nullptr;
     const vp_mesh* mesh = nullptr;
@@ -111,6 +113,7 @@ struct vp_nf {
     double ff_scale = 1.0;         // grid spacing q of the hi parts
     vp_nf_stats_t stats{};
     TcPlan* tc = nullptr;          // tensor-core apply plan (vp_nf_prepare_tc)
+    SymPlan* sym = nullptr;        // symmetric far sum over the node targets (built on first use)
     int magic = 0x56504e46;
 };
 
@@ -216,6 +219,14 @@ constexpr int APPLY_MANY_MIN_D = 16;
 size_t apply_ws_bytes(int64_t N, int d);
 void launch_apply_fp64(const int64_t* row, const int32_t* ptri, const double* C, int nq, const double* f, int64_t N,
                        int d, int64_t M, double* u, double* fT, cudaStream_t s);
+// symmetric far sum (k_far_sym.cu): one density, node targets first, N large
+bool far_sym_applicable(const vp_nf* nf, int d);
+int far_sym_plan(vp_ctx* ctx, vp_nf* nf);
+void far_sym_plan_free(SymPlan* p);
+size_t far_sym_ws_bytes(const vp_ctx* ctx, const vp_nf* nf);
+void launch_far_sym(const vp_ctx* ctx, const vp_nf* nf, const double* W, const double* f, double* out, void* ws,
+                    cudaStream_t s);
+
 // tensor-core apply (k_tc.cu)
 int tc_plan_build(vp_ctx* ctx, vp_nf* nf, int levels, cudaStream_t s);
 void tc_plan_free(TcPlan* p);
