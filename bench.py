@@ -600,17 +600,17 @@ def main():
     nq = 19
     # FP32-pipe thread-instructions per unit of the float-float kernels
     # (ncu smsp__thread_inst_executed.sum on the 2,048-triangle star,
-    # profiles/far_sym_weights_star2048_counts.md): symmetric far sum 105.7 per
+    # profiles/far_sym_weights_star2048_counts.md): symmetric far sum 96.4 per
     # unordered node pair, one-sided far sum 81.6 per ordered pair, near
     # weights 954 per (leaf, node) evaluation including the per-pair work,
     # self weights 72,500 per panel.
-    TI = 256
+    TI = 512
     unord = diag = 0
     for lo in range(0, N, TI):
         sz = min(TI, N - lo)
         unord += sz * max(0, N - lo - sz)
         diag += sz * sz
-    far_inst = unord * 105.7 + (diag + (M - N) * N) * 81.6
+    far_inst = unord * 96.4 + (diag + (M - N) * N) * 81.6
     work = {
         "weights_near": ("alu", stats["near_leaves"] * 49 * 954.0 * args.steps, fp32_inst_peak / 1e12, "FP32 Tinst/s"),
         "weights_self": ("alu", stats["self_panels"] * 72500.0 * args.steps, fp32_inst_peak / 1e12, "FP32 Tinst/s"),

@@ -6,14 +6,14 @@
 //   row:    u_i += q_j G_ij      (target i of tile I, source j beyond tile I)
 //   column: u_j += q_i G_ij
 //
-// Work units are (tile I of 256 nodes, 2048 consecutive nodes beyond it).
+// Work units are (tile I of 512 nodes, 2048 consecutive nodes beyond it).
 // Row sums of a unit go to rowbuf[unit], column sums to colbuf[I][j]; the
 // pairs inside a tile take the one-sided kernel (own node excluded); one
 // combine pass adds, in a fixed order, diag + sum_units rowbuf +
 // sum_{I' < I} colbuf[I'] for every node.  Every write has one owner, so the
 // result does not depend on scheduling.
 //
-// Inside a unit a warp sweeps 32 sources against its 32 lanes x 2 targets in
+// Inside a unit a warp sweeps 32 sources against its 32 lanes x 4 targets in
 // 32 rotation steps (lane l takes source (l + k) mod 32 at step k), so each
 // source's column sum is updated by one lane at a time in the warp's own
 // shared-memory accumulator; the four warps' accumulators are added at the
@@ -28,7 +28,7 @@
 namespace {
 
 constexpr int SYM_THREADS = 128;
-constexpr int SYM_TPT = 2;
+constexpr int SYM_TPT = 4;
 constexpr int SYM_TI = SYM_THREADS * SYM_TPT;   // target tile
 constexpr int SYM_TJ = 128;                     // source tile in shared memory
 constexpr int SYM_UJ = 16;                      // source tiles per work unit
@@ -74,7 +74,9 @@ __global__ void __launch_bounds__(SYM_THREADS) k_far_sym(const float* __restrict
         qh[r] = active[r] ? q[2 * t] : 0.f;             // inactive targets carry no charge
         ql[r] = active[r] ? q[2 * t + 1] : 0.f;
     }
-    double acc[SYM_TPT] = {0.0, 0.0};
+    double acc[SYM_TPT];
+#pragma unroll
+    for (int r = 0; r < SYM_TPT; r++) acc[r] = 0.0;
     for (int64_t base = j0; base < j1; base += SYM_TJ) {
         const int nt = (int)min((int64_t)SYM_TJ, j1 - base);
         __syncthreads();
@@ -88,7 +90,9 @@ __global__ void __launch_bounds__(SYM_THREADS) k_far_sym(const float* __restrict
             for (int ww = 0; ww < SYM_THREADS / 32; ww++) sm.col[ww][i] = make_float2(0.f, 0.f);
         }
         __syncthreads();
-        float sh[SYM_TPT] = {0.f, 0.f}, sl[SYM_TPT] = {0.f, 0.f};
+        float sh[SYM_TPT], sl[SYM_TPT];
+#pragma unroll
+        for (int r = 0; r < SYM_TPT; r++) sh[r] = sl[r] = 0.f;
         float2* col = sm.col[w];
         for (int sb = 0; sb < nt; sb += 32) {
 #pragma unroll 2
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(SYM_THREADS) k_far_sym(const float* __restrict
 #pragma unroll
                     for (int r = 0; r < SYM_TPT; r++) {
                         float s, corr, lh, ll;
-                        ff_dist2(thx[r], thy[r], tlx[r], tly[r], sv, s, corr);
+                        ff_dist2<false>(thx[r], thy[r], tlx[r], tly[r], sv, s, corr);   // distinct nodes
                         ff_log(sm.stab, s, corr, lh, ll);         // log |x_i - y_j|^2
                         ff_madd(qj.x, qj.y, lh, ll, sh[r], sl[r]);
                         ff_madd(qh[r], ql[r], lh, ll, ch, cl);

@@ -61,7 +61,9 @@ __device__ __forceinline__ void ff_log(const float4* __restrict__ tab, float s, 
 }
 
 // |x_t - y_s|^2 as a renormalised float-float pair from the split coordinates
-// (hi parts on a common dyadic grid, so hi_t - hi_s is exact).
+// (hi parts on a common dyadic grid, so hi_t - hi_s is exact).  GUARD: map
+// coincident points to s = 1e-30 (callers that cannot meet them skip it).
+template <bool GUARD = true>
 __device__ __forceinline__ void ff_dist2(float thx, float thy, float tlx, float tly, float4 sv, float& s, float& corr) {
     const float a = __fsub_rn(thx, sv.x), b = __fsub_rn(thy, sv.y);
     const float al = __fsub_rn(tlx, sv.z), bl = __fsub_rn(tly, sv.w);
@@ -76,7 +78,7 @@ __device__ __forceinline__ void ff_dist2(float thx, float thy, float tlx, float 
     c0 = __fmaf_rn(2.0f, __fmaf_rn(dxh, dxl, __fmul_rn(dyh, dyl)), c0);
     s = __fadd_rn(s0, c0);                                           // renormalise: |corr| <= 2^-24 s
     corr = __fadd_rn(__fsub_rn(s0, s), c0);
-    if (!(s > 1e-30f)) {                                             // coincident points (guarded by callers)
+    if (GUARD && !(s > 1e-30f)) {                                    // coincident points (guarded by callers)
         s = 1e-30f;
         corr = 0.0f;
     }

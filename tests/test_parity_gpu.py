@@ -233,7 +233,7 @@ def test_symmetric_far_sum_single_density(vp, ctx, tables, star, which):
         u_or, _ = o.potential(s, f, targets=sample)
         m = vp.mesh_upload(ctx, mesh.vxy, mesh.tri, 19)
         nf = vp.nearfield_build(ctx, m, node_targets=True, txy=torch.from_numpy(extra).cuda())
-        assert s["N"] % 256 != 0
+        assert s["N"] % 512 != 0
     fd = torch.from_numpy(np.ascontiguousarray(f)).cuda()
     u = vp.potential_eval(ctx, nf, fd, precision=1).cpu().numpy()
     ub = torch.empty((1, nf.M), dtype=torch.float64, device="cuda")
