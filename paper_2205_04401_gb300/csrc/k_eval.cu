@@ -83,52 +83,145 @@ __global__ void k_reduce_splits(const double* __restrict__ partial, int splits, 
 // ------------------------------------------------------- corrections
 // Few densities: warp per target; lanes run over the flattened (pair, node)
 // entries of the target's row, each entry's weight read once for D densities;
-// u[d0 + k][t] += sum C[e] f[d0 + k][T_p nq + node].
+// u[d0 + k][t] += sum C[e] f[d0 + k][T_p nq + node].  Eight entries per lane
+// are in flight (predicated, no tail loop) and u[t] is fetched before the
+// row, so a warp has up to 16 independent loads outstanding.
 template <int NQ, int D>
 __global__ void __launch_bounds__(256) k_apply_rows(const int64_t* __restrict__ row, const int32_t* __restrict__ ptri,
                                                     const double* __restrict__ C, const double* __restrict__ f,
                                                     int64_t N, int d, int d0, int64_t M, double* __restrict__ u) {
+    constexpr int U = 8;
     const int lane = threadIdx.x & 31;
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= M) return;
-    const int64_t e0 = row[t] * NQ, e1 = row[t + 1] * NQ;
+    double u0[D];
+    if (lane < D) {
+#pragma unroll
+        for (int k = 0; k < D; k++)
+            if (k == lane) u0[k] = d0 + k < d ? u[(int64_t)(d0 + k) * M + t] : 0.0;
+    }
+    // row-local 32-bit indexing: entry r of the row is node r % NQ of pair r / NQ
+    const int64_t p0 = row[t];
+    const int len = (int)((row[t + 1] - p0) * NQ);
+    const double* __restrict__ Crow = C + p0 * NQ;
+    const int32_t* __restrict__ prow = ptri + p0;
     double s[D];
 #pragma unroll
     for (int k = 0; k < D; k++) s[k] = 0.0;
-    int64_t e = e0 + lane;
-    // four entries in flight per lane
-    for (; e + 96 < e1; e += 128) {
-        double c[4];
-        int64_t src[4];
+    for (int r = lane; r < len; r += 32 * U) {
+        double c[U];
+        int src[U];
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int64_t ei = e + 32 * i;
-            const int64_t p = ei / NQ;
-            c[i] = C[ei];
-            src[i] = (int64_t)ptri[p] * NQ + (ei - p * NQ);
+        for (int i = 0; i < U; i++) {
+            const int ri = r + 32 * i;
+            const bool ok = ri < len;
+            const int pl = ri / NQ;
+            c[i] = ok ? Crow[ri] : 0.0;
+            src[i] = ok ? prow[pl] * NQ + (ri - pl * NQ) : 0;
         }
 #pragma unroll
-        for (int i = 0; i < 4; i++)
+        for (int i = 0; i < U; i++)
 #pragma unroll
-            for (int k = 0; k < D; k++) s[k] += c[i] * f[(int64_t)(d0 + k) * N + src[i]];
-    }
-    for (; e < e1; e += 32) {
-        const int64_t p = e / NQ;
-        const double c = C[e];
-        const int64_t src = (int64_t)ptri[p] * NQ + (e - p * NQ);
-#pragma unroll
-        for (int k = 0; k < D; k++) s[k] += c * f[(int64_t)(d0 + k) * N + src];
+            for (int k = 0; k < D; k++) s[k] = fma(c[i], f[(int64_t)(d0 + k) * N + src[i]], s[k]);
     }
 #pragma unroll
     for (int k = 0; k < D; k++) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
     }
-    if (lane == 0) {
+    if (lane < D) {
 #pragma unroll
         for (int k = 0; k < D; k++)
-            if (d0 + k < d) u[(int64_t)(d0 + k) * M + t] += s[k];
+            if (k == lane && d0 + k < d) u[(int64_t)(d0 + k) * M + t] = u0[k] + s[k];
     }
+}
+
+// Float-float apply (mixed precision): weights and densities as pairs of FP32
+// values (h + l, ~2^-48 relative), products split exactly, sums kept as
+// (two-sum hi, FP32 error) pairs; GB300's FP64 FMA rate (2 per SM per clock)
+// would otherwise bound the apply at one DFMA per weight entry.
+// Entries in flight per lane and resident blocks per SM of the float-float
+// apply (timed on the 16,384-triangle star: 4 and 8 give 0.28 ms against
+// 0.36 ms for 8 and 4).
+#ifndef VP_APPLY_U
+#define VP_APPLY_U 4
+#endif
+#ifndef VP_APPLY_MINB
+#define VP_APPLY_MINB 8
+#endif
+template <int NQ, int D>
+__global__ void __launch_bounds__(256, D <= 2 ? VP_APPLY_MINB : 2) k_apply_rows_f2(const int64_t* __restrict__ row, const int32_t* __restrict__ ptri,
+                                                       const float2* __restrict__ C2, const float2* __restrict__ f2v,
+                                                       int64_t N, int d, int d0, int64_t M, double* __restrict__ u) {
+    constexpr int U = VP_APPLY_U;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= M) return;
+    double u0[D];
+    if (lane < D) {
+#pragma unroll
+        for (int k = 0; k < D; k++)
+            if (k == lane) u0[k] = d0 + k < d ? u[(int64_t)(d0 + k) * M + t] : 0.0;
+    }
+    const int64_t p0 = row[t];
+    const int len = (int)((row[t + 1] - p0) * NQ);
+    const float2* __restrict__ Crow = C2 + p0 * NQ;
+    const int32_t* __restrict__ prow = ptri + p0;
+    float ah[D], al[D];
+#pragma unroll
+    for (int k = 0; k < D; k++) ah[k] = al[k] = 0.f;
+    for (int r = lane; r < len; r += 32 * U) {
+        float2 c[U];
+        int src[U];
+#pragma unroll
+        for (int i = 0; i < U; i++) {
+            const int ri = r + 32 * i;
+            const bool ok = ri < len;
+            const int pl = ri / NQ;
+            c[i] = ok ? Crow[ri] : make_float2(0.f, 0.f);
+            src[i] = ok ? prow[pl] * NQ + (ri - pl * NQ) : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < U; i++)
+#pragma unroll
+            for (int k = 0; k < D; k++) {
+                const float2 fv = f2v[(int64_t)(d0 + k) * N + src[i]];
+                const float p = __fmul_rn(c[i].x, fv.x);
+                float e = __fmaf_rn(c[i].x, fv.x, -p);
+                e = __fmaf_rn(c[i].x, fv.y, __fmaf_rn(c[i].y, fv.x, e));
+                const float sm = __fadd_rn(ah[k], p);
+                const float bb = __fsub_rn(sm, ah[k]);
+                const float er = __fadd_rn(__fsub_rn(ah[k], __fsub_rn(sm, bb)), __fsub_rn(p, bb));
+                ah[k] = sm;
+                al[k] = __fadd_rn(al[k], __fadd_rn(er, e));
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, ah[k], o), ol = __shfl_xor_sync(0xffffffffu, al[k], o);
+            const float sm = __fadd_rn(ah[k], oh);
+            const float bb = __fsub_rn(sm, ah[k]);
+            const float er = __fadd_rn(__fsub_rn(ah[k], __fsub_rn(sm, bb)), __fsub_rn(oh, bb));
+            ah[k] = sm;
+            al[k] = __fadd_rn(__fadd_rn(al[k], ol), er);
+        }
+    }
+    if (lane < D) {
+#pragma unroll
+        for (int k = 0; k < D; k++)
+            if (k == lane && d0 + k < d) u[(int64_t)(d0 + k) * M + t] = u0[k] + ((double)ah[k] + (double)al[k]);
+    }
+}
+
+// out[i] = (h, l) with h = fl32(x[i]), l = fl32(x[i] - h)
+__global__ void k_to_f2(const double* __restrict__ x, int64_t n, float2* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    const float h = __double2float_rn(v);
+    out[i] = make_float2(h, __double2float_rn(v - (double)h));
 }
 
 // fT[j][k] = f[k][j] (node-major copy of the densities), 32 x 32 tiles.
@@ -201,6 +294,22 @@ void apply_rows(const int64_t* row, const int32_t* ptri, const double* C, const 
             case 4: k_apply_rows<NQ, 4><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u); break;
             case 2: k_apply_rows<NQ, 2><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u); break;
             default: k_apply_rows<NQ, 1><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u); break;
+        }
+        d0 += D;
+    }
+}
+
+template <int NQ>
+void apply_rows_f2(const int64_t* row, const int32_t* ptri, const float2* C2, const float2* f2v, int64_t N, int d,
+                   int64_t M, double* u, cudaStream_t s) {
+    const unsigned grid = (unsigned)((M * 32 + 255) / 256);
+    for (int d0 = 0; d0 < d;) {
+        const int D = pick_chunk(d - d0);
+        switch (D) {
+            case 8: k_apply_rows_f2<NQ, 8><<<grid, 256, 0, s>>>(row, ptri, C2, f2v, N, d, d0, M, u); break;
+            case 4: k_apply_rows_f2<NQ, 4><<<grid, 256, 0, s>>>(row, ptri, C2, f2v, N, d, d0, M, u); break;
+            case 2: k_apply_rows_f2<NQ, 2><<<grid, 256, 0, s>>>(row, ptri, C2, f2v, N, d, d0, M, u); break;
+            default: k_apply_rows_f2<NQ, 1><<<grid, 256, 0, s>>>(row, ptri, C2, f2v, N, d, d0, M, u); break;
         }
         d0 += D;
     }
@@ -314,6 +423,18 @@ void launch_apply_fp64(const int64_t* row, const int32_t* ptri, const double* C,
         if (nq == 19) apply_rows<19>(row, ptri, C, f, N, d, M, u, s);
         else apply_rows<16>(row, ptri, C, f, N, d, M, u, s);
     }
+}
+
+void launch_to_f2(const double* x, int64_t n, float2* out, cudaStream_t s) {
+    if (n > 0) k_to_f2<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, out);
+}
+
+void launch_apply_f2(const int64_t* row, const int32_t* ptri, const float2* C2, int nq, const double* f, int64_t N,
+                     int d, int64_t M, double* u, float2* f2v, cudaStream_t s) {
+    if (M <= 0) return;
+    launch_to_f2(f, (int64_t)d * N, f2v, s);
+    if (nq == 19) apply_rows_f2<19>(row, ptri, C2, f2v, N, d, M, u, s);
+    else apply_rows_f2<16>(row, ptri, C2, f2v, N, d, M, u, s);
 }
 
 void launch_ff_split(const double* xy, int64_t n, double ox, double oy, double q, FFCoords out, cudaStream_t s) {

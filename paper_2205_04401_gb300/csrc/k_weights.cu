@@ -494,6 +494,7 @@ __device__ __forceinline__ void finish_pair_f2(const WeightsArgs& a, const Weigh
             s = f2_add(s, f2_neg(f2_mul(lg, {wq.x, wq.y})));
         }
         a.C[p * a.nq + lane] = f2_to_d(s);
+        if (a.C2) a.C2[p * a.nq + lane] = make_float2(s.h, s.l);
     }
 }
 

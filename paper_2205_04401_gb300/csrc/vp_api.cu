@@ -153,7 +153,7 @@ int ensure_ws(vp_ctx* ctx, size_t bytes) {
 }
 
 void free_nf_device(vp_nf* nf) {
-    void* ps[] = {nf->d_txy, nf->d_tself, nf->d_tnode, nf->d_row, nf->d_ptri, nf->d_ptgt, nf->d_pkind, nf->d_C,
+    void* ps[] = {nf->d_txy, nf->d_tself, nf->d_tnode, nf->d_row, nf->d_ptri, nf->d_ptgt, nf->d_pkind, nf->d_C, nf->d_C2,
                   nf->src_ff.hi, nf->src_ff.lo, nf->tgt_ff.hi, nf->tgt_ff.lo};
     for (void* p : ps)
         if (p) cudaFree(p);
@@ -568,6 +568,8 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         wa.c_near = prm.c_near;
         wa.depth_cap = prm.depth_cap;
         wa.fp64 = (prm.flags & VP_NF_FP64_WEIGHTS) ? 1 : 0;
+        if (!wa.fp64) NF_CUDA(dev_alloc(&nf->d_C2, nf->P * nq));
+        wa.C2 = nf->d_C2;
         wa.nt = nt;
         wa.M = M;
         wa.N = N;
@@ -701,7 +703,8 @@ static size_t eval_layout(const vp_ctx* ctx, const vp_nf* nf, int d, int precisi
     *off_q = (partial_bytes + 255) & ~(size_t)255;
     const size_t q_bytes = sym ? far_sym_ws_bytes(ctx, nf) : (precision != VP_FP64 ? (size_t)N * 16 * sizeof(float) : 0);
     *off_t = (*off_q + q_bytes + 255) & ~(size_t)255;
-    return *off_t + (precision == VP_MIXED_TC ? tc_ws_bytes(nf) : apply_ws_bytes(N, d)) + 256;
+    const size_t f2_bytes = precision == VP_MIXED && d < APPLY_MANY_MIN_D ? (size_t)N * d * sizeof(float2) : 0;
+    return *off_t + std::max(precision == VP_MIXED_TC ? tc_ws_bytes(nf) : apply_ws_bytes(N, d), f2_bytes) + 256;
 }
 
 size_t eval_ws_bytes(const vp_ctx* ctx, const vp_nf* nf, int d, int precision) {
@@ -742,6 +745,9 @@ int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, doub
             if (!profile) ctx->prof = prof_saved;
             return rc;
         }
+    } else if (precision == VP_MIXED && d < APPLY_MANY_MIN_D && nf->d_C2) {
+        PROF(ctx, ST_APPLY, s,
+             launch_apply_f2(nf->d_row, nf->d_ptri, nf->d_C2, mesh->nq, f_dev, N, d, M, u_dev, (float2*)apply_ws, s));
     } else {
         PROF(ctx, ST_APPLY, s, launch_apply_fp64(nf->d_row, nf->d_ptri, nf->d_C, mesh->nq, f_dev, N, d, M, u_dev, fT, s));
     }
@@ -767,6 +773,7 @@ int vp_potential_eval(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t
         int rc = far_sym_plan(ctx, const_cast<vp_nf*>(nf));
         if (rc) return rc;
     }
+
     int rc = ensure_ws(ctx, eval_ws_bytes(ctx, nf, d, precision));
     if (rc) return rc;
     return eval_impl(ctx, nf, f_dev, d, u_dev, precision, (cudaStream_t)stream, ctx->ws, true);

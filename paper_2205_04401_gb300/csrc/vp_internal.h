@@ -108,6 +108,7 @@ struct vp_nf {
     int32_t* d_ptgt = nullptr;    // [P]
     uint8_t* d_pkind = nullptr;   // [P]
     double* d_C = nullptr;        // [P][nq]
+    float2* d_C2 = nullptr;       // [P][nq] the same weights as float-float pairs (float-float builds)
     FFCoords src_ff, tgt_ff;      // float-float copies for the mixed far sum
     double ff_origin[2] = {0, 0};
     double ff_scale = 1.0;         // grid spacing q of the hi parts
@@ -188,6 +189,7 @@ struct WeightsArgs {
     const int32_t* ptri;
     const int32_t* ptgt;
     double* C;
+    float2* C2;         // float-float copy of C (float-float kernels), or nullptr
     int32_t* pstat;     // per pair: leaves or panels
     int32_t* pcap;      // per pair: depth-capped leaves
     int32_t* flag;
@@ -233,3 +235,7 @@ void tc_plan_free(TcPlan* p);
 size_t tc_ws_bytes(const vp_nf* nf);
 int tc_apply(vp_ctx* ctx, const vp_nf* nf, const double* f, int d, double* u, void* ws, cudaStream_t s);
 void launch_ff_split(const double* xy, int64_t n, double ox, double oy, double q, FFCoords out, cudaStream_t s);
+// float-float copies and the float-float apply of the mixed path (d < APPLY_MANY_MIN_D)
+void launch_to_f2(const double* x, int64_t n, float2* out, cudaStream_t s);
+void launch_apply_f2(const int64_t* row, const int32_t* ptri, const float2* C2, int nq, const double* f, int64_t N,
+                     int d, int64_t M, double* u, float2* f2v, cudaStream_t s);
