@@ -616,8 +616,11 @@ def main():
         "weights_self": ("alu", stats["self_panels"] * 72500.0 * args.steps, fp32_inst_peak / 1e12, "FP32 Tinst/s"),
         "far_ff": ("alu", far_inst * args.steps, fp32_inst_peak / 1e12, "FP32 Tinst/s"),
         "far_fp64": ("alu", float(M) * N * 80.0 * args.steps, dfma_peak / 1e12, "FP64 TFLOP/s"),
-        "apply_fp64": ("hbm", float(stats["n_pairs"] * (8 * nq + 4) + N * 8 + M * 8 + M * 8 * 2) * args.steps,
+        "apply": ("hbm", float(stats["n_pairs"] * (8 * nq + 4) + N * 8 + M * 8 + M * 8 * 2) * args.steps,
                        hbm, "GB/s"),
+        # list passes: targets read (16 B), per pair triangle + target + kind written (9 B), row pointers
+        "list_fill": ("hbm", float(M * 16 + stats["n_pairs"] * 9 + (M + 1) * 8) * args.steps, hbm, "GB/s"),
+        "list_count": ("hbm", float(M * 16 + M * 4) * args.steps, hbm, "GB/s"),
     }
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     dname, (dn, dms) = dom
@@ -629,6 +632,15 @@ def main():
         roof = {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": None, "launches": dn, "ms_per_launch": dms / dn}
     stage_share = {k: round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4) for k, v in prof.items() if v[0]}
+    # every modelled stage against its own bound (the dominant one is "roofline")
+    rooflines = {}
+    for k, (bound, units, peak, unit) in work.items():
+        n_l, ms_l = prof.get(k, (0, 0.0))
+        if n_l and ms_l > 0:
+            sc = 1e9 if unit == "GB/s" else 1e12
+            a = units / (ms_l / 1e3) / sc
+            rooflines[k] = {"bound": bound, "achieved": round(a, 3), "peak": peak, "unit": unit,
+                            "frac": round(a / peak, 4), "ms_per_launch": round(ms_l / n_l, 4)}
 
     if rank == 0:
         line = {
@@ -644,6 +656,7 @@ def main():
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": None,
             "roofline": roof,
+            "rooflines_by_stage": rooflines,
             "cpu_baseline": cpu,
             "accuracy": {"rel_err_mixed_vs_oracle_sampled": rel_oracle, "rel_err_mixed_vs_fp64_gpu": rel_mixed_vs_fp64},
             "resident_eval": {"mixed_ms": resident_ms, "fp64_ms": fp64_ms,

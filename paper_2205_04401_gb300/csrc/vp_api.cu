@@ -172,7 +172,7 @@ int vp_set_error(vp_ctx* ctx, int code, const std::string& msg) {
 
 static const char* kStageNames[ST_COUNT] = {
     "mesh_nodes", "tri_geom", "tri_cells", "cell_sort", "target_cells", "locate", "list_count", "list_fill",
-    "weights_self", "weights_near", "ff_split", "far_fp64", "far_ff", "reduce_splits", "apply_fp64", "apply_tc"};
+    "weights_self", "weights_near", "ff_split", "far_fp64", "far_ff", "reduce_splits", "apply", "apply_tc"};
 
 static cudaEvent_t prof_event(vp_ctx* ctx) {
     if (!ctx->prof_pool.empty()) {
