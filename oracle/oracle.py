@@ -240,12 +240,96 @@ class Oracle:
         self.L.or_self_panel_counts(_ptr(A, D), _ptr(B, D), _ptr(Cv, D), D(x[0]), D(x[1]), _ptr(out, I32))
         return out
 
-    # -- composition
-    def setup(self, vxy, tri, node_targets=True, extra=None):
-        """Nodes, targets, S(x) and lists.  Targets: all nodes (if
-        node_targets), then the extra points."""
+    # -- curved elements (blending map; see oracle.c)
+    @staticmethod
+    def _curves(curves, nt):
+        cidx = np.ascontiguousarray(curves["cidx"], np.int32)
+        coef = np.ascontiguousarray(curves["coef"], np.float64)
+        assert len(cidx) == nt and coef.ndim == 3 and coef.shape[1] == 2
+        return cidx, coef, int(coef.shape[2] - 1)
+
+    def nodes_curved(self, vxy, tri, curves):
         vxy = np.ascontiguousarray(vxy, np.float64)
-        tri_ccw, yxy, W, J = self.nodes(vxy, tri)
+        tri = np.ascontiguousarray(tri, np.int32)
+        nt = len(tri)
+        cidx, coef, K = self._curves(curves, nt)
+        tri_ccw = np.empty_like(tri)
+        yxy = np.empty((nt * self.nq, 2))
+        W = np.empty(nt * self.nq)
+        J = np.empty(nt)
+        rc = self.L.or_nodes_curved(_ptr(vxy, D), I64(len(vxy)), _ptr(tri, I32), I64(nt), _ptr(cidx, I32),
+                                    _ptr(coef, D), C.c_int(K), C.byref(self.p), _ptr(tri_ccw, I32), _ptr(yxy, D),
+                                    _ptr(W, D), _ptr(J, D))
+        if rc != 0:
+            raise ValueError(f"or_nodes_curved failed: {rc}")
+        return tri_ccw, yxy, W, J
+
+    def locate_curved(self, vxy, tri_ccw, curves, pts):
+        cidx, coef, K = self._curves(curves, len(tri_ccw))
+        pts = np.ascontiguousarray(pts, np.float64)
+        out = np.empty(len(pts), np.int32)
+        self.L.or_locate_curved(_ptr(vxy, D), _ptr(tri_ccw, I32), I64(len(tri_ccw)), _ptr(cidx, I32), _ptr(coef, D),
+                                C.c_int(K), _ptr(pts, D), I64(len(pts)), _ptr(out, I32))
+        return out
+
+    def map_curved(self, vxy, tri_ccw, curves, T, xi, eta):
+        cidx, coef, K = self._curves(curves, len(tri_ccw))
+        T = np.ascontiguousarray(T, np.int64)
+        xi = np.ascontiguousarray(xi, np.float64)
+        eta = np.ascontiguousarray(eta, np.float64)
+        y = np.empty((len(T), 2))
+        det = np.empty(len(T))
+        self.L.or_map_curved(_ptr(np.ascontiguousarray(vxy, np.float64), D), _ptr(tri_ccw, I32), _ptr(cidx, I32),
+                             _ptr(coef, D), C.c_int(K), _ptr(T, I64), _ptr(xi, D), _ptr(eta, D), I64(len(T)),
+                             _ptr(y, D), _ptr(det, D))
+        return y, det
+
+    def inverse_curved(self, vxy, tri_ccw, curves, T, pts):
+        cidx, coef, K = self._curves(curves, len(tri_ccw))
+        T = np.ascontiguousarray(T, np.int64)
+        pts = np.ascontiguousarray(pts, np.float64)
+        ref = np.empty((len(T), 2))
+        it = np.empty(len(T), np.int32)
+        self.L.or_inverse_curved(_ptr(np.ascontiguousarray(vxy, np.float64), D), _ptr(tri_ccw, I32),
+                                 _ptr(cidx, I32), _ptr(coef, D), C.c_int(K), _ptr(T, I64), _ptr(pts, D),
+                                 I64(len(T)), _ptr(ref, D), _ptr(it, I32))
+        return ref, it
+
+    def weights_curved(self, s, pt, ptri, pkind, pown):
+        cidx, coef, K = self._curves(s["curves"], len(s["tri"]))
+        pt = np.ascontiguousarray(pt, np.int64)
+        ptri = np.ascontiguousarray(ptri, np.int32)
+        pkind = np.ascontiguousarray(pkind, np.uint8)
+        pown = np.ascontiguousarray(pown, np.int32)
+        n = len(pt)
+        out = np.empty((n, self.nq))
+        stats = np.empty(n, np.int64)
+        capped = I64(0)
+        self.L.or_weights_curved(_ptr(s["vxy"], D), _ptr(s["tri"], I32), _ptr(s["J"], D), _ptr(cidx, I32),
+                                 _ptr(coef, D), C.c_int(K), C.byref(self.p), _ptr(s["yxy"], D), _ptr(s["W"], D),
+                                 _ptr(s["txy"], D), _ptr(pt, I64), _ptr(ptri, I32), _ptr(pkind, U8),
+                                 _ptr(pown, I32), I64(n), _ptr(out, D), _ptr(stats, I64), C.byref(capped))
+        return out, stats, int(capped.value)
+
+    def pair_moments_curved(self, s, T, x, kind):
+        cidx, coef, K = self._curves(s["curves"], len(s["tri"]))
+        m = np.empty(NB)
+        st = I64(0)
+        self.L.or_pair_moments_curved(C.byref(self.p), _ptr(s["vxy"], D), _ptr(s["tri"], I32), _ptr(s["J"], D),
+                                      _ptr(cidx, I32), _ptr(coef, D), C.c_int(K), I64(T), D(x[0]), D(x[1]),
+                                      C.c_int(kind), _ptr(m, D), C.byref(st))
+        return m, int(st.value)
+
+    # -- composition
+    def setup(self, vxy, tri, node_targets=True, extra=None, curves=None):
+        """Nodes, targets, S(x) and lists.  Targets: all nodes (if
+        node_targets), then the extra points.  curves: optional curved
+        elements {"cidx": [nt], "coef": [ncurve][2][K+1]}."""
+        vxy = np.ascontiguousarray(vxy, np.float64)
+        if curves is not None:
+            tri_ccw, yxy, W, J = self.nodes_curved(vxy, tri, curves)
+        else:
+            tri_ccw, yxy, W, J = self.nodes(vxy, tri)
         N = len(W)
         parts, tnode, tself = [], [], []
         if node_targets:
@@ -256,10 +340,11 @@ class Oracle:
             extra = np.ascontiguousarray(extra, np.float64)
             parts.append(extra)
             tnode.append(np.full(len(extra), -1, np.int64))
-            tself.append(self.locate(vxy, tri_ccw, extra))
+            tself.append(self.locate_curved(vxy, tri_ccw, curves, extra) if curves is not None
+                         else self.locate(vxy, tri_ccw, extra))
         txy = np.ascontiguousarray(np.vstack(parts))
         return dict(vxy=vxy, tri=tri_ccw, yxy=yxy, W=W, J=J, txy=txy, tnode=np.concatenate(tnode),
-                    tself=np.concatenate(tself), N=N)
+                    tself=np.concatenate(tself), N=N, curves=curves)
 
     def own_index(self, s, t_idx, ptri):
         tn = s["tnode"][t_idx]
@@ -277,7 +362,10 @@ class Oracle:
         pt_local = np.repeat(np.arange(len(idx)), np.diff(row))
         pt = idx[pt_local]
         pown = self.own_index(s, pt, ptri)
-        Cw, stats, capped = self.weights(s["vxy"], s["tri"], s["J"], s["txy"], pt, ptri, pkind, pown)
+        if s.get("curves") is not None:
+            Cw, stats, capped = self.weights_curved(s, pt, ptri, pkind, pown)
+        else:
+            Cw, stats, capped = self.weights(s["vxy"], s["tri"], s["J"], s["txy"], pt, ptri, pkind, pown)
         fT = f.reshape(f.shape[0], -1, self.nq)           # [d][T][nq]
         corr = np.einsum("pk,dpk->dp", Cw, fT[:, ptri, :])
         u = ufar.copy()

@@ -363,6 +363,61 @@ def disk_uniform_mesh(n_tri: int, seed: int, relax_iters: int = 8) -> Mesh:
     return _build(dom, n_tri, lambda p: np.ones(len(p)), seed, relax_iters, name=f"disk_{n_tri}")
 
 
+def curved_boundary(mesh: Mesh, circles, K: int = 15):
+    """Curved boundary elements for a mesh whose boundary edges lie on circles.
+
+    circles: list of (cx, cy, R).  Every triangle with a boundary edge on one
+    of the circles is rotated (orientation kept) so that the edge is
+    v0 -> v1, and its curved side is the arc from v0 to v1 (the short way
+    round), given as the deviation from the chord,
+        c(xi) - (1 - xi) v0 - xi v1 = xi (1 - xi) D(xi),
+    with D interpolated at K+1 Chebyshev points of [0, 1]
+    (D = sum_k a_k T_k(2 xi - 1)).  Returns (tri, {"cidx", "coef"}): the
+    rotated triangles, the curve index of every triangle (-1 straight) and
+    the coefficients [ncurve][2][K+1].
+    """
+    tri = mesh.tri.copy()
+    vxy = mesh.vxy
+    edges = {}
+    for t in range(len(tri)):
+        for e in range(3):
+            a, b = int(tri[t, e]), int(tri[t, (e + 1) % 3])
+            edges.setdefault((min(a, b), max(a, b)), []).append((t, e))
+    cidx = np.full(len(tri), -1, np.int32)
+    coefs = []
+    z = np.cos(np.pi * (np.arange(K + 1) + 0.5) / (K + 1))       # Chebyshev points of the first kind
+    xs = 0.5 * (z + 1.0)
+    V = np.polynomial.chebyshev.chebvander(z, K)
+    for (a, b), owners in edges.items():
+        if len(owners) != 1:
+            continue
+        t, e = owners[0]
+        va, vb = vxy[tri[t, e]], vxy[tri[t, (e + 1) % 3]]
+        circ = None
+        for cx, cy, R in circles:
+            ra, rb = math.hypot(va[0] - cx, va[1] - cy), math.hypot(vb[0] - cx, vb[1] - cy)
+            if abs(ra - R) < 1e-9 * R and abs(rb - R) < 1e-9 * R:
+                circ = (cx, cy, R)
+                break
+        if circ is None or cidx[t] >= 0:
+            continue
+        tri[t] = np.roll(tri[t], -e)                                 # boundary edge first, orientation kept
+        v0, v1 = vxy[tri[t, 0]], vxy[tri[t, 1]]
+        cx, cy, R = circ
+        th0 = math.atan2(v0[1] - cy, v0[0] - cx)
+        dth = math.atan2(v1[1] - cy, v1[0] - cx) - th0
+        dth = (dth + math.pi) % (2 * math.pi) - math.pi
+        th = th0 + xs * dth
+        c = np.stack([cx + R * np.cos(th), cy + R * np.sin(th)], axis=1)
+        # endpoints exactly at v0, v1
+        c += (1 - xs)[:, None] * (v0 - [cx + R * math.cos(th0), cy + R * math.sin(th0)])
+        c += xs[:, None] * (v1 - [cx + R * math.cos(th0 + dth), cy + R * math.sin(th0 + dth)])
+        Dv = (c - (1 - xs)[:, None] * v0 - xs[:, None] * v1) / (xs * (1 - xs))[:, None]
+        coefs.append(np.linalg.solve(V, Dv).T)                       # [2][K+1]
+        cidx[t] = len(coefs) - 1
+    return tri, {"cidx": cidx, "coef": np.ascontiguousarray(np.array(coefs).reshape(-1, 2, K + 1))}
+
+
 def random_interior_points(mesh: Mesh, m: int, seed: int) -> np.ndarray:
     """m points uniform in the meshed polygon (rejection sampling)."""
     rng = np.random.default_rng(seed)
