@@ -548,8 +548,13 @@ int or_nodes_curved(const double* vxy, int64_t nv, const int32_t* tri, int64_t n
 
 /* Point location with curved elements: a straight triangle as in
  * or_locate_one; a curved one holds x when x is on the inner side of its two
- * straight sides and the Newton preimage has eta >= 0 (inner side of the
- * curve; App. A.5 with the polar-angle test replaced by the preimage). */
+ * straight sides and the Newton preimage lies in the reference simplex:
+ * eta >= 0 (inner side of the curve), and xi >= -1e-9, xi + eta <= 1 + 1e-9
+ * (the straight sides, already decided exactly by the orientation tests; the
+ * slack only absorbs the preimage's rounding).  App. A.5 with the polar-angle
+ * test replaced by the preimage.  Far from the element the blending map has
+ * other roots (its curve term is a polynomial in xi), which lie outside the
+ * simplex: the bounds on xi reject them. */
 int64_t or_locate_curved_one(const or_geom* g, int64_t nt, double x, double y) {
     for (int64_t t = 0; t < nt; t++) {
         const int32_t* v = g->tri + 3 * t;
@@ -562,7 +567,8 @@ int64_t or_locate_curved_one(const or_geom* g, int64_t nt, double x, double y) {
                 return t;
         } else if (orient(Bx, By, Cx, Cy, x, y) >= 0 && orient(Cx, Cy, Ax, Ay, x, y) >= 0) {
             double xi, eta;
-            if (geom_inverse(g, t, x, y, &xi, &eta) > 0 && eta >= 0.0) return t;
+            if (geom_inverse(g, t, x, y, &xi, &eta) > 0 && eta >= 0.0 && xi >= -1e-9 && xi + eta <= 1.0 + 1e-9)
+                return t;
         }
     }
     return -1;

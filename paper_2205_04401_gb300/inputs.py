@@ -418,6 +418,20 @@ def curved_boundary(mesh: Mesh, circles, K: int = 15):
     return tri, {"cidx": cidx, "coef": np.ascontiguousarray(np.array(coefs).reshape(-1, 2, K + 1))}
 
 
+def snap_to_circles(mesh: Mesh, circles, tol: float = 1e-6) -> Mesh:
+    """A copy of the mesh whose vertices within tol (relative) of one of the
+    circles (cx, cy, R) are moved radially onto it, so that boundary edges
+    sampled from a circle as a fine polyline become chords of the circle
+    (what curved_boundary expects)."""
+    vxy = mesh.vxy.copy()
+    for cx, cy, R in circles:
+        d = vxy - [cx, cy]
+        r = np.hypot(d[:, 0], d[:, 1])
+        on = np.abs(r - R) < tol * R
+        vxy[on] = np.array([cx, cy]) + d[on] * (R / r[on])[:, None]
+    return Mesh(vxy, mesh.tri.copy(), mesh.loops, mesh.name)
+
+
 def random_interior_points(mesh: Mesh, m: int, seed: int) -> np.ndarray:
     """m points uniform in the meshed polygon (rejection sampling)."""
     rng = np.random.default_rng(seed)

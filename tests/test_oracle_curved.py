@@ -156,3 +156,39 @@ def test_curved_disk_quadratic_density_converges(tables):
         ex = (np.sum(s["txy"] ** 2, 1) ** 2 - 1) / 16
         errs.append(np.abs(u[0] - ex).max() / np.abs(ex).max())
     assert errs[0] <= 1e-10 and errs[1] <= errs[0] / 3
+
+
+def test_curved_annulus_location_and_closed_form(tables):
+    """Annulus with both circles curved.  Points that lie in the wedge of a
+    hole element's two straight sides, beyond its curved side (seen through
+    the hole), belong to the straight elements that hold them: away from the
+    curved sides the curved and straight locations agree.  With f = 1 the
+    potential is the unit disk's minus the hole's,
+        u(x) = (|x|^2 - 1)/4 - (r0^2/2) log|x|,   r0 < |x| < 1,
+    (outside a disk of radius a and unit density, (a^2/2) log|x|), at the
+    nodes and at points down to 1e-6 from both circles."""
+    r0 = 0.45
+    circles = [(0.0, 0.0, 1.0), (0.0, 0.0, r0)]
+    mesh = inputs.snap_to_circles(inputs.annulus_mesh(600, 21, r0), circles)
+    tri, cur = inputs.curved_boundary(mesh, circles)
+    assert (cur["cidx"] >= 0).sum() > 60
+    o = Oracle("far19", tables=tables)
+    tri_ccw, _, W, _ = o.nodes_curved(mesh.vxy, tri, cur)
+    assert abs(W.sum() - math.pi * (1 - r0 ** 2)) <= 1e-13
+    rng = np.random.default_rng(8)
+    r = np.sqrt(rng.uniform((r0 + 0.05) ** 2, 0.95 ** 2, 3000))
+    th = rng.random(3000) * 2 * np.pi
+    p = np.stack([r * np.cos(th), r * np.sin(th)], 1)
+    lc = o.locate_curved(mesh.vxy, tri_ccw, cur, p)
+    assert (lc >= 0).all() and np.array_equal(lc, o.locate(mesh.vxy, tri_ccw, p))
+    gaps = 10.0 ** rng.uniform(-6, -1, 80)
+    th = rng.random(80) * 2 * np.pi
+    rr = np.where(np.arange(80) % 2 == 0, 1 - gaps, r0 * (1 + gaps))
+    extra = np.stack([rr * np.cos(th), rr * np.sin(th)], 1)
+    s = o.setup(mesh.vxy, tri, node_targets=True, extra=extra, curves=cur)
+    assert (s["tself"] >= 0).all()
+    u, info = o.potential(s, np.ones((1, s["N"])))
+    rt = np.hypot(s["txy"][:, 0], s["txy"][:, 1])
+    ex = (rt ** 2 - 1) / 4 - 0.5 * r0 ** 2 * np.log(rt)
+    assert np.abs(u[0] - ex).max() / np.abs(ex).max() <= 1e-11
+    assert info["capped"] == 0
