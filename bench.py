@@ -45,9 +45,10 @@ def parse():
     ap.add_argument("--extra", type=int, default=10000)
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
-                    help="2: the 16,384-triangle star (default); 4: 200 uneven meshes in one batched launch; "
-                         "5: serving loop with Poisson arrivals")
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5, 6],
+                    help="2: the 16,384-triangle star (default); 3: 64 densities; 4: 200 uneven meshes in one "
+                         "batched launch; 5: serving loop with Poisson arrivals; 6: annulus with curved boundary "
+                         "elements")
     ap.add_argument("--nmesh", type=int, default=200)
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--tmax", type=int, default=8000, help="largest pool mesh (triangles) for --config 5")
@@ -448,6 +449,127 @@ def run_serving(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------ curved elements
+def run_curved(args):
+    """Annulus 0.45 < |x| < 1 with both circles represented exactly by curved
+    boundary elements (blending map), args.ntri triangles, 19-node rule,
+    targets = nodes + args.extra uniform points, f = 1.  A step is the config-2
+    step on this mesh: curved mesh upload + near-field build + mixed
+    evaluation.  With f = 1 the exact potential is known,
+    u = (|x|^2 - 1)/4 - (r0^2/2) log|x|, and the error is stated against it;
+    the same mesh with straight (chord) boundary elements is timed beside."""
+    import torch
+    from paper_2205_04401_gb300 import inputs, vp
+    r0 = 0.45
+    circles = [(0.0, 0.0, 1.0), (0.0, 0.0, r0)]
+    mesh = inputs.snap_to_circles(inputs.annulus_mesh(args.ntri, 2205044016, r0), circles)
+    tri, cur = inputs.curved_boundary(mesh, circles)
+    rng = np.random.default_rng(2205044016)
+    rr = np.sqrt(rng.uniform(r0 ** 2, 1.0, args.extra))
+    th = rng.random(args.extra) * 2 * np.pi
+    extra = np.ascontiguousarray(np.stack([rr * np.cos(th), rr * np.sin(th)], 1))
+    ctx = vp.Context(0)
+    dev = torch.device("cuda", 0)
+    extra_d = torch.from_numpy(extra).to(dev)
+    N = mesh.nt * 19
+    M = N + len(extra)
+    f_d = torch.ones((1, N), dtype=torch.float64, device=dev)
+    u_d = torch.empty((1, M), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(curved):
+        mh = (vp.mesh_upload_curved(ctx, mesh.vxy, tri, cur, vp.VP_RULE_19_D9) if curved
+              else vp.mesh_upload(ctx, mesh.vxy, tri, vp.VP_RULE_19_D9))
+        nf = vp.nearfield_build(ctx, mh, node_targets=True, txy=extra_d)
+        vp.potential_eval(ctx, nf, f_d, precision=vp.VP_MIXED, out=u_d)
+        return mh, nf
+
+    res = {}
+    for curved in (True, False):
+        for _ in range(max(args.warmup, 1)):
+            mh, nf = step(curved)
+            torch.cuda.synchronize()
+            nf.release()
+            mh.release()
+        vp.profile_enable(ctx, True)
+        vp.profile_reset(ctx)
+        clocks = Clocks(0)
+        t_all = 0.0
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mh, nf = step(curved)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_all += e0.elapsed_time(e1)
+            st = vp.nf_stats(nf)
+            y, _ = vp.mesh_nodes(mh)
+            if k < args.steps - 1:
+                nf.release()
+                mh.release()
+        clk = clocks.stop()
+        prof = vp.profile_read(ctx)
+        vp.profile_enable(ctx, False)
+        u = u_d.cpu().numpy()[0]
+        txy = np.vstack([y.cpu().numpy(), extra])
+        r = np.hypot(txy[:, 0], txy[:, 1])
+        ex = (r ** 2 - 1) / 4 - 0.5 * r0 ** 2 * np.log(r)
+        res[curved] = dict(ms=t_all / args.steps, clocks=clk, stats=st,
+                           stage_ms={k2: round(v[1] / args.steps, 3) for k2, v in prof.items() if v[0]},
+                           err=float(np.abs(u - ex).max() / np.abs(ex).max()), mh=mh, nf=nf)
+        if not curved:
+            nf.release()
+            mh.release()
+    c, sline = res[True], res[False]
+    n_curved_pairs = None
+    cpu = None
+    if not args.no_oracle_check:
+        from oracle.oracle import Oracle
+        o = Oracle("far19")
+        s = o.setup(mesh.vxy, tri, node_targets=True, extra=extra, curves=cur)
+        smp = np.sort(np.random.default_rng(5).choice(M, 64, replace=False))
+        t0 = time.perf_counter()
+        f = np.ones((1, s["N"]))
+        uo, info = o.potential(s, f, targets=smp)
+        dt = time.perf_counter() - t0
+        n2 = int(max(64, min(M, 64 * 10.0 / max(dt, 1e-3))))
+        smp2 = np.sort(np.random.default_rng(6).choice(M, n2, replace=False))
+        t0 = time.perf_counter()
+        uo2, info2 = o.potential(s, f, targets=smp2)
+        dt = time.perf_counter() - t0
+        ug = u_d  # the last curved evaluation is overwritten by the straight run: evaluate again
+        vp.potential_eval(ctx, c["nf"], f_d, precision=vp.VP_MIXED, out=u_d)
+        ug = u_d.cpu().numpy()[0]
+        c["err_vs_oracle_sampled"] = float(np.abs(ug[smp2] - uo2[0]).max() / np.abs(uo2[0]).max())
+        n_curved_pairs = int((cur["cidx"][info2["ptri"]] >= 0).sum())
+        cpu = {"value": n2 / dt, "unit": "target-evals/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n2} random targets of the curved annulus (far sum over all nodes, lists, near/self "
+                         f"weights with curved elements), OpenMP over targets, {dt:.1f} s"}
+    c["nf"].release()
+    c["mh"].release()
+    line = {
+        "metric": "target_evals_per_s", "value": M / (c["ms"] / 1e3), "unit": "target-evals/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": c["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f64", "data": "synthetic",
+        "config": {"workload": f"annulus_curved_{mesh.nt}tri_19pt_targets_nodes_plus_{len(extra)}_f1",
+                   "targets": M, "nodes": N, "curved_triangles": int((cur["cidx"] >= 0).sum()),
+                   "step": "mesh_upload_curved+nearfield_build+potential_eval", "l2": "256 MiB flush between steps"},
+        "clocks": c["clocks"],
+        "rel_err_vs_exact": c["err"], "rel_err_vs_oracle_sampled": c.get("err_vs_oracle_sampled"),
+        "curved_pairs_in_oracle_sample": n_curved_pairs,
+        "nf_stats": {k: c["stats"][k] for k in ("n_pairs", "n_self", "n_near", "near_leaves", "self_panels",
+                                                 "depth_capped", "build_ms")},
+        "stage_ms": c["stage_ms"],
+        "straight_chords": {"ms_per_step": sline["ms"], "rel_err_vs_exact": sline["err"],
+                            "stage_ms": sline["stage_ms"]},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    ctx.close()
+
+
 # ----------------------------------------------------------------- main arm
 def main():
     args = parse()
@@ -459,6 +581,8 @@ def main():
         return run_batch(args)
     if args.config == 5:
         return run_serving(args)
+    if args.config == 6:
+        return run_curved(args)
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -596,25 +720,30 @@ def main():
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
     dfma_peak = 1.186e12        # measured FP64 FMA throughput on this GB300 (flop/s), profiles/peaks_gb300.md
-    fp32_inst_peak = 73.71e12 / 2   # measured FFMA flop/s / 2 = FP32-pipe instructions/s
+    # Issue peak of the float-float kernels (bound "alu"): every SM sub-partition
+    # issues one warp instruction per clock, so 152 SMs x 4 x 32 lanes x the
+    # maximum SM clock thread-instructions per second (FP32, integer, shared
+    # memory and shuffle instructions all take an issue slot).
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    issue_peak = 152 * 4 * 32 * sm_mhz * 1e6
     nq = 19
-    # FP32-pipe thread-instructions per unit of the float-float kernels
-    # (ncu smsp__thread_inst_executed.sum on the 2,048-triangle star,
-    # profiles/far_sym_weights_star2048_counts.md): symmetric far sum 96.4 per
-    # unordered node pair, one-sided far sum 81.6 per ordered pair, near
-    # weights 954 per (leaf, node) evaluation including the per-pair work,
-    # self weights 72,500 per panel.
-    TI = 512
+    # thread-instructions per unit of the float-float kernels (ncu
+    # smsp__thread_inst_executed.sum on the 2,048-triangle star,
+    # profiles/far_sym_weights_star2048_counts.md): symmetric far sum 105.7 per
+    # unordered node pair, its diagonal tiles 85.7 and the extra targets 83.5
+    # per ordered pair, near weights 954 per (leaf, node) evaluation including
+    # the per-pair work, self weights 72,500 per panel.
+    TI = 512                     # target tile of the symmetric far sum
     unord = diag = 0
     for lo in range(0, N, TI):
         sz = min(TI, N - lo)
         unord += sz * max(0, N - lo - sz)
         diag += sz * sz
-    far_inst = unord * 96.4 + (diag + (M - N) * N) * 81.6
+    far_inst = unord * 105.7 + diag * 85.7 + (M - N) * N * 83.5
     work = {
-        "weights_near": ("alu", stats["near_leaves"] * 49 * 954.0 * args.steps, fp32_inst_peak / 1e12, "FP32 Tinst/s"),
-        "weights_self": ("alu", stats["self_panels"] * 72500.0 * args.steps, fp32_inst_peak / 1e12, "FP32 Tinst/s"),
-        "far_ff": ("alu", far_inst * args.steps, fp32_inst_peak / 1e12, "FP32 Tinst/s"),
+        "weights_near": ("alu", stats["near_leaves"] * 49 * 954.0 * args.steps, issue_peak / 1e12, "Tinst/s"),
+        "weights_self": ("alu", stats["self_panels"] * 72500.0 * args.steps, issue_peak / 1e12, "Tinst/s"),
+        "far_ff": ("alu", far_inst * args.steps, issue_peak / 1e12, "Tinst/s"),
         "far_fp64": ("alu", float(M) * N * 80.0 * args.steps, dfma_peak / 1e12, "FP64 TFLOP/s"),
         "apply": ("hbm", float(stats["n_pairs"] * (8 * nq + 4) + N * 8 + M * 8 + M * 8 * 2) * args.steps,
                        hbm, "GB/s"),
@@ -670,7 +799,7 @@ def main():
         }
         # library kernel launches per full step (upload + build + mixed evaluation of one density),
         # counted in the ncu launch list of this command (profiles/launches_star16384_mixed.md)
-        line["gpu_launches"] = 43 * args.steps if prec == vp.VP_MIXED else int(sum(v[0] for v in prof.values()))
+        line["gpu_launches"] = 44 * args.steps if prec == vp.VP_MIXED else int(sum(v[0] for v in prof.values()))
         print(json.dumps(line))
     nf.release()
     mh.release()

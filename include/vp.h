@@ -143,6 +143,34 @@ VP_API int vp_mesh_upload(vp_ctx* ctx, const double* vxy, int64_t nv, const int3
 VP_API int vp_mesh_upload_dev(vp_ctx* ctx, const double* vxy_dev, int64_t nv, const int32_t* tri_dev, int64_t nt,
                               int32_t rule, void* stream, vp_mesh** out);
 
+/* Upload a mesh with curved elements (Section 3.1, blending map of Eq.
+ * for:blend) from HOST arrays and build its nodes and weights (Theorem 3.1
+ * with |det J_rho|).  A curved element is a counter-clockwise triangle
+ * (v0, v1, v2) whose side v0 -> v1 is the curve c(xi), xi in [0, 1], given by
+ * its deviation from the chord,
+ *     c(xi) - (1 - xi) v0 - xi v1 = xi (1 - xi) D(xi),   D(xi) = sum_{k<=K} a_k T_k(2 xi - 1),
+ * and mapped from the reference simplex by
+ *     rho(xi, eta) = v0 + xi (v1 - v0) + eta (v2 - v0) + xi (1 - xi - eta) D(xi):
+ *   node j = T*nq + k at rho_T(xi_k, eta_k), W_j = w_k det J_rho(xi_k, eta_k).
+ * vxy, tri, rule: as vp_mesh_upload (straight triangles may be clockwise;
+ *       curved ones must be counter-clockwise, else VP_ERR_INVALID_ARG).
+ * cidx: host [nt] int32, the curve of each triangle, -1 for a straight one.
+ * coef: host [ncurve][2][K+1] float64, the Chebyshev coefficients a_k of D,
+ *       x then y (may be NULL when ncurve == 0); 0 <= K <= 64.
+ * Near-field builds on such a mesh take, for a curved triangle: its chord
+ * triangle for the near-field ellipses (the last remark of Section 4.1) and
+ * J_T (the chord's 2 area) in the ellipse parameter; the curved element
+ * itself for point location (the two straight sides' orientation tests and
+ * the Newton preimage, eta >= 0) and for the correction weights (the
+ * subdivision of Section 3.3 in reference coordinates mapped through rho;
+ * the radius-arclength fans of Section 3.4 around rho^-1(x)).
+ * Errors: those of vp_mesh_upload; INVALID_ARG for a curve index outside
+ * [-1, ncurve) or K outside [0, 64]; NONFINITE for a non-finite coefficient;
+ * DEGENERATE_TRI when det J_rho <= 0 at a node.  Synchronises `stream`. */
+VP_API int vp_mesh_upload_curved(vp_ctx* ctx, const double* vxy, int64_t nv, const int32_t* tri, int64_t nt,
+                                 const int32_t* cidx, const double* coef, int64_t ncurve, int32_t K, int32_t rule,
+                                 void* stream, vp_mesh** out);
+
 /* Sizes of a mesh: triangles, nodes N = nt * nq, nodes per triangle nq. */
 VP_API int vp_mesh_info(const vp_mesh* mesh, int64_t* n_tri, int64_t* n_nodes, int32_t* nq);
 

@@ -1,0 +1,232 @@
+// Correction apply of one density in the mixed path, streamed through shared
+// memory by the bulk-copy engine: the last sum of the subtract-and-add
+// evaluation (Section 3.6),
+//     u(x_t) += sum_{(t, T) in lists} sum_k C[t,T,k] f_{T,k}.
+//
+// The weights are pair-major (pairs in target order, nq float-float weights
+// per pair), so a run of pairs is a run of bytes.  Work is cut into tiles of
+// 32 pairs (4,864 bytes of weights for nq = 19).  Each warp of a persistent
+// grid owns a ring of VP_AS_STAGES tiles in shared memory that one lane
+// refills with cp.async.bulk (three copies per tile: weights, triangles,
+// targets, all completing on the stage's mbarrier), so that the warp computes
+// one tile while the next ones stream in.  A tile is processed in two
+// passes over shared memory: entry-parallel (consecutive lanes take
+// consecutive weights, so their density gathers, float-float values of 8
+// bytes from the L2-resident density, are coalesced) forming the float-float
+// products in place, then pair-parallel (lane l sums the nq products of pair
+// p0 + l), followed by a float-float segmented sum over the lanes by target
+// (the pairs of a target are adjacent).  The FP64 pipe, slow on this part,
+// only converts the segment sums.  A target whose whole row lies in the tile is updated directly;
+// the first and last segment of a tile whose rows cross the tile boundary go
+// to two per-tile slots, and a second kernel adds those, in tile order, to
+// the targets whose rows cross tiles.  The order of every sum is fixed, so
+// the result does not depend on timing.
+#include <algorithm>
+#include <climits>
+
+#include "vp_internal.h"
+#include "vp_async.cuh"
+#include "vp_f2.cuh"
+
+#ifndef VP_AS_WARPS
+#define VP_AS_WARPS 16
+#endif
+#ifndef VP_AS_STAGES
+#define VP_AS_STAGES 2
+#endif
+
+namespace {
+
+constexpr int AS_WARPS = VP_AS_WARPS;
+constexpr int AS_STAGES = VP_AS_STAGES;
+constexpr int AS_TILE = 32;   // pairs per tile (one per lane)
+
+template <int NQ>
+struct __align__(16) AsStage {
+    float2 C[AS_TILE * NQ];   // weights of the tile's pairs, (h, l) per weight
+    int32_t tri[AS_TILE];     // triangle of each pair
+    int32_t tgt[AS_TILE];     // target of each pair
+};
+
+template <int NQ>
+constexpr size_t as_smem_bytes() {
+    return (size_t)AS_WARPS * AS_STAGES * sizeof(AsStage<NQ>) + (size_t)AS_WARPS * AS_STAGES * sizeof(uint64_t);
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(AS_WARPS * 32, 1)
+    k_apply_stream(const int64_t* __restrict__ row, const int32_t* __restrict__ ptri, const int32_t* __restrict__ ptgt,
+                   const float2* __restrict__ C2, const float2* __restrict__ fd2, int64_t P, double* __restrict__ u,
+                   double* __restrict__ slots, int32_t* flag) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    using St = AsStage<NQ>;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    St* st = reinterpret_cast<St*>(smem) + wid * AS_STAGES;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + AS_WARPS * AS_STAGES * sizeof(St)) + wid * AS_STAGES;
+    const int64_t ntiles = (P + AS_TILE - 1) / AS_TILE;
+    const int64_t stride = (int64_t)gridDim.x * AS_WARPS;
+    const int64_t first = (int64_t)blockIdx.x * AS_WARPS + wid;
+    if (lane == 0) {
+        for (int s = 0; s < AS_STAGES; s++) mbar_init(smem_u32(&bar[s]), 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    // one lane: stream tile `tile` into stage s (sizes rounded up to 16 bytes;
+    // the arrays carry 16 bytes of padding past their last element)
+    auto issue = [&](int s, int64_t tile) {
+        const int64_t p0 = tile * AS_TILE;
+        const int n = (int)min((int64_t)AS_TILE, P - p0);
+        const uint32_t cb = (uint32_t)((n * NQ * (int)sizeof(float2) + 15) & ~15);
+        const uint32_t ib = (uint32_t)((n * (int)sizeof(int32_t) + 15) & ~15);
+        const uint32_t b = smem_u32(&bar[s]);
+        mbar_expect_tx(b, cb + 2 * ib);
+        bulk_g2s(smem_u32(st[s].C), C2 + p0 * NQ, cb, b);
+        bulk_g2s(smem_u32(st[s].tri), ptri + p0, ib, b);
+        bulk_g2s(smem_u32(st[s].tgt), ptgt + p0, ib, b);
+    };
+    if (lane == 0)
+        for (int s = 0; s < AS_STAGES; s++)
+            if (first + s * stride < ntiles) issue(s, first + s * stride);
+    int64_t k = 0;
+    bool ok = true;
+    for (int64_t tile = first; tile < ntiles; tile += stride, k++) {
+        const int s = (int)(k % AS_STAGES);
+        if (!mbar_wait(smem_u32(&bar[s]), (uint32_t)((k / AS_STAGES) & 1))) {
+            ok = false;
+            break;
+        }
+        const int64_t p0 = tile * AS_TILE;
+        const int n = (int)min((int64_t)AS_TILE, P - p0);
+        // entry-parallel pass: entry e = 32 i + lane of the tile (pair e / NQ,
+        // node e % NQ), so that the density gathers of consecutive lanes are
+        // consecutive addresses; the float-float product C_e f_e replaces C_e
+        // in shared memory
+        float2* C = st[s].C;
+        // all density gathers first (independent loads in flight together),
+        // then the products
+        float2 fv[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; i++) {
+            const int e = 32 * i + lane;
+            const int j = e / NQ;
+            const int64_t src = j < n ? (int64_t)st[s].tri[j] * NQ + (e - j * NQ) : 0;
+            fv[i] = __ldg(fd2 + src);
+        }
+        // this lane's pair: target, row bounds and current value, loaded
+        // early so that their latency overlaps the products
+        int t = INT_MAX;   // padding lanes form their own segment
+        int64_t r0 = 0, r1 = 0;
+        double u0 = 0.0;
+        if (lane < n) {
+            t = st[s].tgt[lane];
+            r0 = row[t];
+            r1 = row[t + 1];
+            u0 = u[t];
+        }
+#pragma unroll
+        for (int i = 0; i < NQ; i++) {
+            const int e = 32 * i + lane;
+            if (e / NQ < n) {
+                const float2 c = C[e];
+                const float p = __fmul_rn(c.x, fv[i].x);
+                float er = __fmaf_rn(c.x, fv[i].x, -p);
+                er = __fmaf_rn(c.x, fv[i].y, __fmaf_rn(c.y, fv[i].x, er));
+                C[e] = make_float2(p, er);
+            }
+        }
+        __syncwarp();
+        // pair-parallel pass: lane l sums the NQ products of pair p0 + l in
+        // four interleaved float-float partial sums (shorter dependency
+        // chains), combined in a fixed order
+        f2 ps = {0.f, 0.f};
+        if (lane < n) {
+            const float2* c = C + lane * NQ;
+            f2 a4[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+            for (int q = 0; q < NQ; q++) {
+                const float2 v = c[q];
+                a4[q & 3] = f2_add(a4[q & 3], {v.x, v.y});
+            }
+            ps = f2_add(f2_add(a4[0], a4[1]), f2_add(a4[2], a4[3]));
+        }
+        // segmented inclusive sum over the lanes (targets are non-decreasing)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float vh = __shfl_up_sync(0xffffffffu, ps.h, o), vl = __shfl_up_sync(0xffffffffu, ps.l, o);
+            const int kt = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o && kt == t) ps = f2_add(ps, {vh, vl});
+        }
+        const int t_next = __shfl_down_sync(0xffffffffu, t, 1);
+        const int t_lane0 = __shfl_sync(0xffffffffu, t, 0);
+        if (lane < n && (lane == n - 1 || t_next != t)) {   // the last lane of a segment
+            const double sum = (double)ps.h + (double)ps.l;
+            if (r0 >= p0 && r1 <= p0 + AS_TILE) {
+                u[t] = u0 + sum;                              // the whole row is in this tile
+            } else {
+                if (t == t_lane0) slots[2 * tile] = sum;      // segment at the start of the tile
+                if (lane == n - 1) slots[2 * tile + 1] = sum; // segment at the end of the tile
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && tile + AS_STAGES * stride < ntiles) issue(s, tile + AS_STAGES * stride);
+    }
+    if (!ok) {
+        // a copy never completed: report, wait (bounded) for the copies still
+        // in flight into this warp's stages, and leave
+        if (lane == 0) {
+            atomicOr(flag, VP_DEV_ERR_TIMEOUT);
+            for (int j = 0; j < AS_STAGES; j++) {
+                const int64_t kk = k + j;
+                if (first + kk * stride < ntiles)
+                    mbar_wait(smem_u32(&bar[kk % AS_STAGES]), (uint32_t)((kk / AS_STAGES) & 1));
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Targets whose rows cross tiles: u[t] += (end segment of the first tile) +
+// (whole middle tiles) + (start segment of the last tile), in tile order.
+__global__ void k_apply_stream_fix(const int64_t* __restrict__ row, int64_t M, const double* __restrict__ slots,
+                                   double* __restrict__ u) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M) return;
+    const int64_t r0 = row[t], r1 = row[t + 1];
+    if (r1 <= r0) return;
+    const int64_t a = r0 / AS_TILE, b = (r1 - 1) / AS_TILE;
+    if (a == b) return;
+    double s = slots[2 * a + 1];
+    for (int64_t i = a + 1; i < b; i++) s += slots[2 * i];
+    s += slots[2 * b];
+    u[t] += s;
+}
+
+template <int NQ>
+void apply_stream(const int64_t* row, const int32_t* ptri, const int32_t* ptgt, const float2* C2, const float2* fd2,
+                  int64_t P, int64_t M, double* u, double* slots, int32_t* flag, int sm_count, cudaStream_t s) {
+    constexpr size_t smem = as_smem_bytes<NQ>();
+    cudaFuncSetAttribute(k_apply_stream<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t ntiles = (P + AS_TILE - 1) / AS_TILE;
+    // one CTA per SM (persistent), fewer when there are fewer tiles than warps
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(sm_count, (ntiles + AS_WARPS - 1) / AS_WARPS));
+    k_apply_stream<NQ><<<grid, AS_WARPS * 32, smem, s>>>(row, ptri, ptgt, C2, fd2, P, u, slots, flag);
+    k_apply_stream_fix<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(row, M, slots, u);
+}
+
+}  // namespace
+
+size_t apply_stream_ws_bytes(int64_t N, int64_t P) {
+    return (((size_t)N * sizeof(float2) + 255) & ~(size_t)255) + (size_t)((P + AS_TILE - 1) / AS_TILE) * 2 * sizeof(double);
+}
+
+void launch_apply_stream(const int64_t* row, const int32_t* ptri, const int32_t* ptgt, const float2* C2, int nq,
+                         const double* f, int64_t N, int64_t P, int64_t M, double* u, void* ws, int32_t* flag,
+                         int sm_count, cudaStream_t s) {
+    if (P <= 0 || M <= 0) return;
+    // the density as float-float pairs, then the slots
+    float2* fd2 = (float2*)ws;
+    double* slots = (double*)((char*)ws + (((size_t)N * sizeof(float2) + 255) & ~(size_t)255));
+    launch_to_f2(f, N, fd2, s);
+    if (nq == 19) apply_stream<19>(row, ptri, ptgt, C2, fd2, P, M, u, slots, flag, sm_count, s);
+    else apply_stream<16>(row, ptri, ptgt, C2, fd2, P, M, u, slots, flag, sm_count, s);
+}

@@ -31,6 +31,7 @@
 #include <cmath>
 
 #include "vp_internal.h"
+#include "vp_async.cuh"
 
 namespace {
 
@@ -44,7 +45,6 @@ constexpr int TC_STAGES = 3;
 constexpr int TC_THREADS = 128;
 constexpr int TC_TMEM_COLS = 512;
 constexpr int TC_PAIR_CAP = 16384;  // near pairs per tile the plan can hold
-constexpr long long TC_WAIT_CYCLES = 1LL << 32;   // about 2 s at 2 GHz
 
 __host__ __device__ constexpr uint32_t a_chunk_bytes(int L) { return (uint32_t)L * TC_KSTEPS * 4096u; }
 __host__ __device__ constexpr int dens_per_pass(int L) { return L <= 4 ? 64 : 32; }   // dn (2L - 1) <= 512 columns
@@ -410,35 +410,6 @@ __global__ void k_fdigits(const double* __restrict__ f, int64_t N, int64_t nT, i
 }
 
 // ------------------------------------------------------------ tcgen05 glue
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait on the phase of the given parity
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > TC_WAIT_CYCLES) return false;
-    return true;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
 __device__ __forceinline__ void cp16(uint32_t dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }

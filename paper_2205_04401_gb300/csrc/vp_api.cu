@@ -135,6 +135,7 @@ int check_flag(vp_ctx* ctx, int32_t* d_flag, cudaStream_t s) {
     if (h & VP_DEV_ERR_STACK) return vp_set_error(ctx, VP_ERR_CUDA, "near-field subdivision stack overflow");
     if (h & VP_DEV_ERR_CELL) return vp_set_error(ctx, VP_ERR_CUDA, "grid cell list exceeds sort capacity");
     if (h & VP_DEV_ERR_TIMEOUT) return vp_set_error(ctx, VP_ERR_TIMEOUT, "a pipelined kernel timed out waiting for its copies");
+    if (h & VP_DEV_ERR_CURVED_CW) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "a curved element is clockwise");
     return VP_OK;
 }
 
@@ -172,7 +173,8 @@ int vp_set_error(vp_ctx* ctx, int code, const std::string& msg) {
 
 static const char* kStageNames[ST_COUNT] = {
     "mesh_nodes", "tri_geom", "tri_cells", "cell_sort", "target_cells", "locate", "list_count", "list_fill",
-    "weights_self", "weights_near", "ff_split", "far_fp64", "far_ff", "reduce_splits", "apply", "apply_tc"};
+    "weights_self", "weights_near", "ff_split", "far_fp64", "far_ff", "reduce_splits", "apply", "apply_tc",
+    "weights_curved"};
 
 static cudaEvent_t prof_event(vp_ctx* ctx) {
     if (!ctx->prof_pool.empty()) {
@@ -267,11 +269,28 @@ void vp_destroy(vp_ctx* ctx) {
 }
 
 // -------------------------------------------------------------------- mesh
+// Curves of vp_mesh_upload_curved, already on the device and owned by the
+// new mesh from the call on (released with it, or on failure).
+struct CurvesIn {
+    int32_t* d_cidx = nullptr;
+    double* d_coef = nullptr;
+    int64_t ncurve = 0;
+    int K = 0;
+};
+
 static int mesh_upload_impl(vp_ctx* ctx, const double* d_vxy, int64_t nv, const int32_t* d_tri, int64_t nt,
-                            int32_t rule, cudaStream_t s, vp_mesh** out) {
+                            int32_t rule, cudaStream_t s, vp_mesh** out, CurvesIn cin = CurvesIn()) {
     vp_mesh* m = new (std::nothrow) vp_mesh();
-    if (!m) return VP_ERR_OOM;
+    if (!m) {
+        if (cin.d_cidx) cudaFree(cin.d_cidx);
+        if (cin.d_coef) cudaFree(cin.d_coef);
+        return VP_ERR_OOM;
+    }
     m->ctx = ctx;
+    m->d_cidx = cin.d_cidx;
+    m->d_coef = cin.d_coef;
+    m->ncurve = cin.ncurve;
+    m->K = cin.K;
     m->nt = nt;
     m->nv = nv;
     m->rule_index = rule == VP_RULE_16_D8 ? 0 : 1;
@@ -283,19 +302,34 @@ static int mesh_upload_impl(vp_ctx* ctx, const double* d_vxy, int64_t nv, const 
     if (e == cudaSuccess) e = dev_alloc(&m->d_J, nt);
     if (e == cudaSuccess) e = dev_alloc(&m->d_y, 2 * m->N);
     if (e == cudaSuccess) e = dev_alloc(&m->d_W, m->N);
-    if (e == cudaSuccess) e = dev_alloc(&d_red, 4);
+    if (e == cudaSuccess) e = dev_alloc(&d_red, 8);
     if (e != cudaSuccess) rc = vp_set_error(ctx, VP_ERR_OOM, "vp_mesh_upload: device allocation failed");
     if (rc == VP_OK) {
         cudaMemsetAsync(ctx->d_flag, 0, sizeof(int32_t), s);
         PROF(ctx, ST_MESH_NODES, s,
              launch_mesh_nodes(d_vxy, nv, d_tri, nt, ctx->d_tables, m->rule_index, m->d_tv, m->d_J, m->d_y, m->d_W,
                                ctx->d_flag, s));
+        if (m->d_cidx)
+            PROF(ctx, ST_MESH_NODES, s,
+                 launch_mesh_nodes_curved(d_vxy, nv, d_tri, nt, mesh_curves(m), ctx->d_tables, m->rule_index, m->d_tv,
+                                          m->d_y, m->d_W, ctx->d_flag, s));
         launch_bbox_reduce(d_vxy, nv, 2, d_red, s);
+        if (m->d_cidx) launch_bbox_reduce(m->d_y, m->N, 2, d_red + 4, s);   // nodes on the curved sides' bulges
         cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess) rc = vp_set_error(ctx, VP_ERR_CUDA, cudaGetErrorString(le));
         else rc = check_flag(ctx, ctx->d_flag, s);
-        if (rc == VP_OK && cudaMemcpy(m->bbox, d_red, 4 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        double hb[8];
+        if (rc == VP_OK && cudaMemcpy(hb, d_red, 8 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
             rc = vp_set_error(ctx, VP_ERR_CUDA, "vp_mesh_upload: bbox copy failed");
+        if (rc == VP_OK) {
+            for (int i = 0; i < 4; i++) m->bbox[i] = hb[i];
+            if (m->d_cidx) {
+                m->bbox[0] = std::min(m->bbox[0], hb[4]);
+                m->bbox[1] = std::min(m->bbox[1], hb[5]);
+                m->bbox[2] = std::max(m->bbox[2], hb[6]);
+                m->bbox[3] = std::max(m->bbox[3], hb[7]);
+            }
+        }
     }
     if (d_red) cudaFree(d_red);
     if (rc != VP_OK) {
@@ -341,6 +375,56 @@ int vp_mesh_upload_dev(vp_ctx* ctx, const double* vxy_dev, int64_t nv, const int
     return mesh_upload_impl(ctx, vxy_dev, nv, tri_dev, nt, rule, (cudaStream_t)stream, out);
 }
 
+int vp_mesh_upload_curved(vp_ctx* ctx, const double* vxy, int64_t nv, const int32_t* tri, int64_t nt,
+                          const int32_t* cidx, const double* coef, int64_t ncurve, int32_t K, int32_t rule,
+                          void* stream, vp_mesh** out) {
+    if (out) *out = nullptr;
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    if (!out || !vxy || !tri || !cidx || nv < 3 || nt < 1 || ncurve < 0 || (ncurve > 0 && !coef) || K < 0 ||
+        K > VP_MAX_CHEB || (rule != VP_RULE_16_D8 && rule != VP_RULE_19_D9))
+        return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload_curved: bad arguments");
+    if (nt > (int64_t)INT32_MAX / 19) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload_curved: too many triangles");
+    for (int64_t i = 0; i < 2 * nv; i++)
+        if (!std::isfinite(vxy[i])) return vp_set_error(ctx, VP_ERR_NONFINITE, "vp_mesh_upload_curved: non-finite vertex");
+    for (int64_t i = 0; i < 3 * nt; i++)
+        if (tri[i] < 0 || tri[i] >= nv)
+            return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload_curved: index out of range");
+    for (int64_t i = 0; i < nt; i++)
+        if (cidx[i] < -1 || cidx[i] >= ncurve)
+            return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload_curved: curve index out of range");
+    const int64_t ncoef = ncurve * 2 * (K + 1);
+    for (int64_t i = 0; i < ncoef; i++)
+        if (!std::isfinite(coef[i]))
+            return vp_set_error(ctx, VP_ERR_NONFINITE, "vp_mesh_upload_curved: non-finite curve coefficient");
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    double* d_vxy;
+    int32_t* d_tri;
+    if (sc.alloc(&d_vxy, 2 * nv) != cudaSuccess || sc.alloc(&d_tri, 3 * nt) != cudaSuccess)
+        return vp_set_error(ctx, VP_ERR_OOM, "vp_mesh_upload_curved: device allocation failed");
+    CurvesIn cin;
+    cin.ncurve = ncurve;
+    cin.K = K;
+    if (dev_alloc(&cin.d_cidx, nt) != cudaSuccess ||
+        (ncoef > 0 && dev_alloc(&cin.d_coef, ncoef) != cudaSuccess)) {
+        if (cin.d_cidx) cudaFree(cin.d_cidx);
+        return vp_set_error(ctx, VP_ERR_OOM, "vp_mesh_upload_curved: device allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(d_vxy, vxy, 2 * nv * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tri, tri, 3 * nt * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cin.d_cidx, cidx, nt * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && ncoef > 0)
+        e = cudaMemcpyAsync(cin.d_coef, coef, ncoef * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host arrays are read during the call only
+    if (e != cudaSuccess) {
+        cudaFree(cin.d_cidx);
+        if (cin.d_coef) cudaFree(cin.d_coef);
+        return vp_set_error(ctx, VP_ERR_CUDA, std::string("vp_mesh_upload_curved: copy failed: ") + cudaGetErrorString(e));
+    }
+    return mesh_upload_impl(ctx, d_vxy, nv, d_tri, nt, rule, s, out, cin);
+}
+
 int vp_mesh_info(const vp_mesh* mesh, int64_t* n_tri, int64_t* n_nodes, int32_t* nq) {
     if (!mesh_ok(mesh)) return VP_ERR_STATE;
     if (n_tri) *n_tri = mesh->nt;
@@ -362,7 +446,7 @@ void vp_mesh_release(vp_mesh* mesh) {
     if (!mesh_ok(mesh)) return;
     DevGuard g(mesh->ctx->device);
     cudaDeviceSynchronize();
-    void* ps[] = {mesh->d_tv, mesh->d_J, mesh->d_y, mesh->d_W};
+    void* ps[] = {mesh->d_tv, mesh->d_J, mesh->d_y, mesh->d_W, mesh->d_cidx, mesh->d_coef};
     for (void* p : ps)
         if (p) cudaFree(p);
     mesh->magic = 0;
@@ -426,7 +510,8 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         int32_t *d_max;
         int64_t *d_cell_start, *d_cursor, *d_tstart;
         unsigned long long* d_u64;
-        unsigned long long h_u64[2];
+        unsigned long long h_u64[4] = {0, 0, 0, 0};
+        int32_t *d_cnear_idx = nullptr, *d_cself_idx = nullptr;
         char* d_f2ws;
         int32_t h_max = 0;
         std::vector<double> hb;
@@ -448,6 +533,7 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         NF_CUDA(sc.alloc(&d_red, 8));
         PROF(ctx, ST_TRI_GEOM, s,
              launch_tri_geom(mesh->d_tv, mesh->d_J, nt, tab.far_what[ri], tab.far_degree[ri], prm.eps, prm.c_far, d_R, d_bbox, s));
+        if (mesh->d_cidx) launch_curved_bbox(nt, mesh_curves(mesh), d_bbox, s);
         launch_bbox_reduce(d_bbox, nt, 4, d_red, s);
         launch_bbox_reduce(nf->d_txy, M, 2, d_red + 4, s);
         NF_CUDA(cudaGetLastError());
@@ -518,7 +604,11 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         PROF(ctx, ST_TARGET_CELLS, s, launch_target_order(d_tcell, M, d_tstart, d_order, s));
 
         // S(x) for extra targets, then the two list passes
-        PROF(ctx, ST_LOCATE, s, launch_locate(mesh->d_tv, nf->d_txy, d_order, d_tcell, M, gd, nf->d_tself, s));
+        if (mesh->d_cidx)
+            PROF(ctx, ST_LOCATE, s,
+                 launch_locate_curved(mesh->d_tv, mesh_curves(mesh), nf->d_txy, d_order, d_tcell, M, gd, nf->d_tself, s));
+        else
+            PROF(ctx, ST_LOCATE, s, launch_locate(mesh->d_tv, nf->d_txy, d_order, d_tcell, M, gd, nf->d_tself, s));
         NF_CUDA(sc.alloc(&d_count, M));
         PROF(ctx, ST_LIST_COUNT, s,
              launch_list_pass(mesh->d_tv, d_R, tab.far_degree[ri], nf->d_txy, nf->d_tself, d_order, d_tcell, M, gd,
@@ -529,8 +619,10 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         NF_CUDA(cudaMemcpyAsync(&nf->P, nf->d_row + M, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         NF_CUDA(cudaStreamSynchronize(s));
         if (nf->P > (int64_t)INT32_MAX) NF_FAIL(VP_ERR_INVALID_ARG, "vp_nearfield_build: more than 2^31 pairs");
-        NF_CUDA(dev_alloc(&nf->d_ptri, nf->P));
-        NF_CUDA(dev_alloc(&nf->d_ptgt, nf->P));
+        // pair arrays carry 16 bytes of padding (the streamed apply copies
+        // whole 16-byte units)
+        NF_CUDA(dev_alloc(&nf->d_ptri, nf->P + 4));
+        NF_CUDA(dev_alloc(&nf->d_ptgt, nf->P + 4));
         NF_CUDA(dev_alloc(&nf->d_pkind, nf->P));
         NF_CUDA(dev_alloc(&nf->d_C, nf->P * nq));
         PROF(ctx, ST_LIST_FILL, s,
@@ -541,11 +633,20 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         // correction weights
         NF_CUDA(sc.alloc(&d_near_idx, nf->P));
         NF_CUDA(sc.alloc(&d_self_idx, nf->P));
-        NF_CUDA(sc.alloc(&d_u64, 3));
+        NF_CUDA(sc.alloc(&d_u64, 4));
         NF_CUDA(sc.alloc(&d_pstat, nf->P));
         NF_CUDA(sc.alloc(&d_pcap, nf->P));
-        launch_split_pairs(nf->d_pkind, nf->P, d_near_idx, d_self_idx, d_u64, s);
-        NF_CUDA(cudaMemcpyAsync(h_u64, d_u64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        if (mesh->d_cidx) {
+            // pairs on curved triangles get their own lists and kernels
+            NF_CUDA(sc.alloc(&d_cnear_idx, nf->P));
+            NF_CUDA(sc.alloc(&d_cself_idx, nf->P));
+            launch_split_pairs4(nf->d_pkind, nf->d_ptri, mesh_curves(mesh), nf->P, d_near_idx, d_self_idx, d_cnear_idx,
+                                d_cself_idx, d_u64, s);
+            NF_CUDA(cudaMemcpyAsync(h_u64, d_u64, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        } else {
+            launch_split_pairs(nf->d_pkind, nf->P, d_near_idx, d_self_idx, d_u64, s);
+            NF_CUDA(cudaMemcpyAsync(h_u64, d_u64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        }
         NF_CUDA(cudaStreamSynchronize(s));
         n_near = (int64_t)h_u64[0];
         n_self = (int64_t)h_u64[1];
@@ -568,7 +669,7 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         wa.c_near = prm.c_near;
         wa.depth_cap = prm.depth_cap;
         wa.fp64 = (prm.flags & VP_NF_FP64_WEIGHTS) ? 1 : 0;
-        if (!wa.fp64) NF_CUDA(dev_alloc(&nf->d_C2, nf->P * nq));
+        if (!wa.fp64) NF_CUDA(dev_alloc(&nf->d_C2, nf->P * nq + 2));
         wa.C2 = nf->d_C2;
         wa.nt = nt;
         wa.M = M;
@@ -576,15 +677,18 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         NF_CUDA(sc.alloc(&d_f2ws, (int64_t)weights_f2_bytes(nt, M, N)));
         wa.f2_ws = d_f2ws;
         launch_weights(wa, d_self_idx, n_self, d_near_idx, n_near, s, ctx);
+        if (mesh->d_cidx)
+            launch_weights_curved(wa, mesh_curves(mesh), d_cself_idx, (int64_t)h_u64[3], d_cnear_idx,
+                                  (int64_t)h_u64[2], s, ctx);
         NF_CUDA(cudaGetLastError());
 
         // statistics
         nf->stats.n_targets = M;
         nf->stats.n_nodes = N;
         nf->stats.n_pairs = nf->P;
-        nf->stats.n_near = n_near;
-        nf->stats.n_self = n_self;
-        nf->stats.outside = M - n_self;
+        nf->stats.n_near = n_near + (int64_t)h_u64[2];
+        nf->stats.n_self = n_self + (int64_t)h_u64[3];
+        nf->stats.outside = M - nf->stats.n_self;
         {
             // leaves (near pairs) and panels (self pairs), depth-capped leaves
             unsigned long long h3[3];
@@ -703,7 +807,8 @@ static size_t eval_layout(const vp_ctx* ctx, const vp_nf* nf, int d, int precisi
     *off_q = (partial_bytes + 255) & ~(size_t)255;
     const size_t q_bytes = sym ? far_sym_ws_bytes(ctx, nf) : (precision != VP_FP64 ? (size_t)N * 16 * sizeof(float) : 0);
     *off_t = (*off_q + q_bytes + 255) & ~(size_t)255;
-    const size_t f2_bytes = precision == VP_MIXED && d < APPLY_MANY_MIN_D ? (size_t)N * d * sizeof(float2) : 0;
+    size_t f2_bytes = precision == VP_MIXED && d < APPLY_MANY_MIN_D ? (size_t)N * d * sizeof(float2) : 0;
+    if (precision == VP_MIXED && d == 1) f2_bytes = std::max(f2_bytes, apply_stream_ws_bytes(N, nf->P));
     return *off_t + std::max(precision == VP_MIXED_TC ? tc_ws_bytes(nf) : apply_ws_bytes(N, d), f2_bytes) + 256;
 }
 
@@ -745,6 +850,10 @@ int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, doub
             if (!profile) ctx->prof = prof_saved;
             return rc;
         }
+    } else if (precision == VP_MIXED && d == 1 && nf->d_C2) {
+        PROF(ctx, ST_APPLY, s,
+             launch_apply_stream(nf->d_row, nf->d_ptri, nf->d_ptgt, nf->d_C2, mesh->nq, f_dev, N, nf->P, M, u_dev,
+                                 apply_ws, ctx->d_flag, ctx->sm_count, s));
     } else if (precision == VP_MIXED && d < APPLY_MANY_MIN_D && nf->d_C2) {
         PROF(ctx, ST_APPLY, s,
              launch_apply_f2(nf->d_row, nf->d_ptri, nf->d_C2, mesh->nq, f_dev, N, d, M, u_dev, (float2*)apply_ws, s));

@@ -8,6 +8,7 @@
 
 #include "../../include/vp.h"
 #include "vp_device.cuh"
+#include "vp_curved.cuh"
 
 // Far-field source/target coordinates in float-float: value = hi + lo, with
 // hi on a fixed dyadic grid of spacing q so that hi_t - hi_s is exact in FP32.
@@ -19,7 +20,7 @@ struct FFCoords {
 enum VpStage {
     ST_MESH_NODES = 0, ST_TRI_GEOM, ST_TRI_CELLS, ST_CELL_SORT, ST_TARGET_CELLS, ST_LOCATE, ST_LIST_COUNT,
     ST_LIST_FILL, ST_WEIGHTS_SELF, ST_WEIGHTS_NEAR, ST_FF_SPLIT, ST_FAR_FP64, ST_FAR_FF, ST_REDUCE, ST_APPLY,
-    ST_APPLY_TC, ST_COUNT
+    ST_APPLY_TC, ST_WEIGHTS_CURVED, ST_COUNT
 };
 
 struct ProfRec {
@@ -72,7 +73,13 @@ struct vp_mesh {
     double* d_J = nullptr;       // [nt] J_T = 2 area
     double* d_y = nullptr;       // [N][2]
     double* d_W = nullptr;       // [N]
-    double bbox[4] = {0, 0, 0, 0};
+    double bbox[4] = {0, 0, 0, 0};   // of the vertices and, with curves, of the curved sides
+    // curved elements (vp_mesh_upload_curved): curve of each triangle (-1
+    // straight) and Chebyshev coefficients [ncurve][2][K+1]; nullptr if none
+    int32_t* d_cidx = nullptr;
+    double* d_coef = nullptr;
+    int64_t ncurve = 0;
+    int K = 0;
     int magic = 0x56504d48;
 };
 
@@ -175,6 +182,19 @@ void launch_list_pass(const double* tv, const double* R, int N, const double* tx
 void launch_split_pairs(const uint8_t* pkind, int64_t P, int32_t* near_idx, int32_t* self_idx,
                         unsigned long long* counters, cudaStream_t s);
 
+// curved elements (k_curved.cu)
+inline CurveDev mesh_curves(const vp_mesh* m) { return CurveDev{m->d_cidx, m->d_coef, m->K}; }
+void launch_mesh_nodes_curved(const double* vxy, int64_t nv, const int32_t* tri, int64_t nt, CurveDev cv,
+                              const VpTables* tab, int rule, const double* tv, double* y, double* W, int32_t* flag,
+                              cudaStream_t s);
+void launch_curved_bbox(int64_t nt, CurveDev cv, double* bbox, cudaStream_t s);
+void launch_locate_curved(const double* tv, CurveDev cv, const double* txy, const int32_t* order,
+                          const int32_t* tcell, int64_t M, GridDev g, int32_t* tself, cudaStream_t s);
+// counters[0..3]: near straight, self straight, near curved, self curved
+void launch_split_pairs4(const uint8_t* pkind, const int32_t* ptri, CurveDev cv, int64_t P, int32_t* near_idx,
+                         int32_t* self_idx, int32_t* cnear_idx, int32_t* cself_idx, unsigned long long* counters,
+                         cudaStream_t s);
+
 // weights
 struct WeightsArgs {
     const VpTables* tab;
@@ -203,6 +223,9 @@ size_t weights_f2_bytes(int64_t nt, int64_t M, int64_t N);
 // self and near weights (stages ST_WEIGHTS_SELF, ST_WEIGHTS_NEAR)
 void launch_weights(const WeightsArgs& a, const int32_t* self_idx, int64_t n_self, const int32_t* near_idx,
                     int64_t n_near, cudaStream_t s, vp_ctx* ctx);
+// correction weights of the pairs on curved triangles (stage ST_WEIGHTS_CURVED)
+void launch_weights_curved(const WeightsArgs& a, CurveDev cv, const int32_t* self_idx, int64_t n_self,
+                           const int32_t* near_idx, int64_t n_near, cudaStream_t s, vp_ctx* ctx);
 void launch_sum_i32(const int32_t* a, int64_t n, unsigned long long* out, cudaStream_t s);
 // out[0..2] = sums of a over kind 0 and kind != 0, sum of b
 void launch_sum_by_kind(const int32_t* a, const uint8_t* kind, const int32_t* b, int64_t n, unsigned long long* out,
@@ -239,3 +262,9 @@ void launch_ff_split(const double* xy, int64_t n, double ox, double oy, double q
 void launch_to_f2(const double* x, int64_t n, float2* out, cudaStream_t s);
 void launch_apply_f2(const int64_t* row, const int32_t* ptri, const float2* C2, int nq, const double* f, int64_t N,
                      int d, int64_t M, double* u, float2* f2v, cudaStream_t s);
+// streamed float-float apply of one density (k_apply_stream.cu), workspace of
+// apply_stream_ws_bytes(N, P); ptri, ptgt and C2 carry 16 bytes of padding
+size_t apply_stream_ws_bytes(int64_t N, int64_t P);
+void launch_apply_stream(const int64_t* row, const int32_t* ptri, const int32_t* ptgt, const float2* C2, int nq,
+                         const double* f, int64_t N, int64_t P, int64_t M, double* u, void* ws, int32_t* flag,
+                         int sm_count, cudaStream_t s);

@@ -73,6 +73,9 @@ SIGNATURES = {
                                  C.POINTER(C.c_void_p)]),
     "vp_mesh_upload_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
                                      C.c_void_p, C.POINTER(C.c_void_p)]),
+    "vp_mesh_upload_curved": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                        C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
+                                        C.POINTER(C.c_void_p)]),
     "vp_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "vp_profile_reset": (C.c_int, [C.c_void_p]),
     "vp_profile_read": (C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
@@ -251,6 +254,28 @@ def mesh_upload_dev(ctx: Context, vxy_dev, tri_dev, rule: int = VP_RULE_19_D9, s
                                 _dptr(tri_dev, "int32"), C.c_int64(tri_dev.shape[0]), C.c_int32(rule),
                                 _stream(stream), C.byref(h))
     _check(rc, ctx, "vp_mesh_upload_dev")
+    nt, N, nq = C.c_int64(), C.c_int64(), C.c_int32()
+    _check(lib.vp_mesh_info(h, C.byref(nt), C.byref(N), C.byref(nq)), ctx, "vp_mesh_info")
+    return Mesh(ctx, h, nt.value, N.value, nq.value)
+
+
+def mesh_upload_curved(ctx: Context, vxy, tri, curves, rule: int = VP_RULE_19_D9, stream=None) -> Mesh:
+    """vp_mesh_upload_curved: host vertices, triangles and curves
+    {"cidx": [nt] int32 (-1 straight), "coef": [ncurve][2][K+1] float64}."""
+    lib = load()
+    vxy = np.ascontiguousarray(vxy, np.float64)
+    tri = np.ascontiguousarray(tri, np.int32)
+    cidx = np.ascontiguousarray(curves["cidx"], np.int32)
+    coef = np.ascontiguousarray(curves["coef"], np.float64)
+    if coef.ndim != 3 or coef.shape[1] != 2 or len(cidx) != len(tri):
+        raise ValueError("curves: cidx [nt] and coef [ncurve][2][K+1] expected")
+    h = C.c_void_p()
+    rc = lib.vp_mesh_upload_curved(ctx.handle, vxy.ctypes.data_as(C.c_void_p), C.c_int64(len(vxy)),
+                                   tri.ctypes.data_as(C.c_void_p), C.c_int64(len(tri)),
+                                   cidx.ctypes.data_as(C.c_void_p), coef.ctypes.data_as(C.c_void_p),
+                                   C.c_int64(coef.shape[0]), C.c_int32(coef.shape[2] - 1), C.c_int32(rule),
+                                   _stream(stream), C.byref(h))
+    _check(rc, ctx, "vp_mesh_upload_curved")
     nt, N, nq = C.c_int64(), C.c_int64(), C.c_int32()
     _check(lib.vp_mesh_info(h, C.byref(nt), C.byref(N), C.byref(nq)), ctx, "vp_mesh_info")
     return Mesh(ctx, h, nt.value, N.value, nq.value)

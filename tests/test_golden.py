@@ -1,0 +1,91 @@
+"""Pins against numbers the paper prints (tests/golden/paper_tables.txt,
+each block citing its table).  No GPU needed.
+
+* C_12 = 12 (Table "C_N values") is the near rule's constant: the default of
+  vp_nf_params.c_near and of the oracle.
+* The generalized Gaussian rule of Section 3.4 has order 8 and length 8
+  (Table "ord_len_quad"); the library's and the oracle's GGQ tables have 8
+  nodes and integrate r p(r) and r log(r) p(r) for deg p <= 7.
+* The Vioreanu-Rokhlin interpolation rules have length dim P_{N_s} =
+  (N_s + 1)(N_s + 2)/2 (Table "ord_len_interp").
+* Table "near_corr": near corrections and sub-triangles per target grow as
+  eps falls.  The oracle on the unit disk (its own far rule, so not the
+  paper's values) must show the same monotone growth, with each s_n step
+  larger than the matching c step in ratio, as the paper's numbers do.
+"""
+import os
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def load_golden():
+    blocks, cur = {}, None
+    for line in open(os.path.join(HERE, "golden", "paper_tables.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("["):
+            cur = line.strip("[]")
+            blocks[cur] = []
+            continue
+        blocks[cur].append(line.split())
+    return blocks
+
+
+@pytest.fixture(scope="module")
+def golden():
+    return load_golden()
+
+
+def test_cn_table_and_defaults(golden):
+    cn = {int(r[0]): float(r[1]) for r in golden["cn_values"]}
+    assert cn[12] == 12.0
+    # C_N decreases toward 1 as N grows (the caption's claim)
+    ns = sorted(cn)
+    assert all(cn[a] >= cn[b] for a, b in zip(ns, ns[1:])) and cn[max(ns)] == 1.0
+    from oracle.oracle import Oracle
+    assert Oracle("far19").p.near_cn == cn[12]
+    import re
+    hdr = open(os.path.join(os.path.dirname(HERE), "include", "vp.h")).read()
+    assert re.search(r"C_12 = 12", hdr)
+    src = open(os.path.join(os.path.dirname(HERE), "paper_2205_04401_gb300", "csrc", "vp_api.cu")).read()
+    assert "prm.c_near = 12.0;" in src
+
+
+def test_ggq_length_and_moments(golden, tables):
+    row = [r for r in golden["quad_lengths"] if r[0] == "GGQ"][0]
+    order, length = int(row[1]), int(row[2])
+    r, w = np.array(tables["ggq8"]["r"]), np.array(tables["ggq8"]["w"])
+    assert len(r) == length == order == 8
+    for k in range(order):
+        # int_0^1 r^(k+1) dr and int_0^1 r^(k+1) log r dr
+        assert abs(np.sum(w * r ** k) - 1.0 / (k + 2)) <= 1e-15
+        assert abs(np.sum(w * r ** k * np.log(r)) + 1.0 / (k + 2) ** 2) <= 1e-15
+
+
+def test_interpolation_rule_lengths_are_dim_pn(golden):
+    for ns, nf, length, _ in golden["interp_lengths"]:
+        ns = int(ns)
+        assert int(length) == (ns + 1) * (ns + 2) // 2
+
+
+def test_near_corrections_grow_like_the_paper(golden, tables, cfg1):
+    from oracle.oracle import Oracle
+    rows = [(float(e), float(c), float(s)) for e, c, s in golden["near_corr"]]
+    mesh, _ = cfg1
+    cs, ss = [], []
+    for eps, _, _ in rows:
+        o = Oracle("far16", tables=tables, eps=eps)
+        s = o.setup(mesh.vxy, mesh.tri)
+        idx = np.arange(0, s["N"], 5)
+        _, info = o.potential(s, np.ones((1, s["N"])), targets=idx)
+        near = info["pkind"] == 0
+        cs.append(near.sum() / len(idx))
+        ss.append(info["stats"][near].sum() / len(idx))
+    pc = [r[1] for r in rows]
+    ps = [r[2] for r in rows]
+    assert all(a < b for a, b in zip(pc, pc[1:])) and all(a < b for a, b in zip(ps, ps[1:]))
+    assert all(a < b for a, b in zip(cs, cs[1:])) and all(a < b for a, b in zip(ss, ss[1:]))
