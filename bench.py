@@ -45,10 +45,10 @@ def parse():
     ap.add_argument("--extra", type=int, default=10000)
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5, 6],
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5, 6, 7],
                     help="2: the 16,384-triangle star (default); 3: 64 densities; 4: 200 uneven meshes in one "
                          "batched launch; 5: serving loop with Poisson arrivals; 6: annulus with curved boundary "
-                         "elements")
+                         "elements; 7: interpolation on a staggered mesh")
     ap.add_argument("--nmesh", type=int, default=200)
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--tmax", type=int, default=8000, help="largest pool mesh (triangles) for --config 5")
@@ -570,6 +570,137 @@ def run_curved(args):
     ctx.close()
 
 
+# ------------------------------------------------ staggered interpolation
+def run_interp(args):
+    """Interpolation of the potential over a staggered mesh (Sections 3.5 and
+    4.3) on the unit disk at the paper's finest mesh size: quadrature mesh of
+    2,766 curved triangles (h0 = 0.05), 19-node rule; interpolation meshes of
+    order N_s = 20 (231 nodes per element, 638,946 targets): the quadrature
+    mesh itself, and a staggered mesh of the same size.  f = 1, so the exact
+    potential (|x|^2 - 1)/4 is known.  A step is: near-field build for the
+    interpolation nodes + mixed evaluation + expansion coefficients +
+    interpolation at 10^6 random points (staggered mesh); value = interpolated
+    point values per second.  The near corrections (c), sub-triangles (s_n)
+    and self panels (s_l) per target of both meshes are reported (Tables
+    near_corr and self_stag)."""
+    import torch
+    from paper_2205_04401_gb300 import inputs, vp
+    circ = [(0.0, 0.0, 1.0)]
+    q = inputs.disk_mesh(n_b=126, n_i=1321)
+    tq, cq = inputs.curved_boundary(q, circ)
+    st = inputs.disk_mesh(n_b=126, n_i=1321, stagger=True)
+    ts, cs = inputs.curved_boundary(st, circ)
+    Ns = 20
+    ctx = vp.Context(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    mesh = vp.mesh_upload_curved(ctx, q.vxy, tq, cq, vp.VP_RULE_19_D9)
+    f = torch.ones((1, mesh.N), dtype=torch.float64, device=dev)
+    rng = np.random.default_rng(2205044017)
+    mq = 1_000_000
+    r = np.sqrt(rng.random(mq)) * (1 - 1e-12)
+    th = rng.random(mq) * 2 * np.pi
+    pts_np = np.ascontiguousarray(np.stack([r * np.cos(th), r * np.sin(th)], 1))
+    pts = torch.from_numpy(pts_np).to(dev)
+    ex = (np.sum(pts_np ** 2, 1) - 1) / 4
+    res = {}
+    for name, (vxy, tri, cur) in (("same", (q.vxy, tq, cq)), ("staggered", (st.vxy, ts, cs))):
+        it = vp.Interp(ctx, vxy, tri, Ns, curves=cur)
+        nodes = it.nodes()
+
+        def step():
+            nf = vp.nearfield_build(ctx, mesh, node_targets=False, txy=nodes)
+            u = vp.potential_eval(ctx, nf, f, precision=vp.VP_MIXED)
+            coef = it.coeffs(u)
+            val, elem = it.eval(coef, pts)
+            return nf, val, elem
+
+        for _ in range(max(args.warmup, 1)):
+            nf, _, _ = step()
+            torch.cuda.synchronize()
+            nf.release()
+        clocks = Clocks(0)
+        vp.profile_enable(ctx, True)
+        vp.profile_reset(ctx)
+        t_all = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for k in range(args.steps):
+            e0.record(stream)
+            nf, val, elem = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_all += e0.elapsed_time(e1)
+            stt = vp.nf_stats(nf)
+            if k < args.steps - 1:
+                nf.release()
+        clk = clocks.stop()
+        prof = vp.profile_read(ctx)
+        vp.profile_enable(ctx, False)
+        # the interpolation kernels alone
+        u = vp.potential_eval(ctx, nf, f, precision=vp.VP_MIXED)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        coef = it.coeffs(u)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        coef_ms = e0.elapsed_time(e1)
+        e0.record(stream)
+        val, elem = it.eval(coef, pts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        eval_ms = e0.elapsed_time(e1)
+        v = val.cpu().numpy()[0]
+        ok = elem.cpu().numpy() >= 0
+        M = it.n_nodes
+        res[name] = dict(
+            ms_per_step=t_all / args.steps, targets=M, clocks=clk,
+            c_per_target=stt["n_near"] / M, s_n_per_target=stt["near_leaves"] / M,
+            s_l_per_target=stt["self_panels"] / M, outside=stt["outside"], build_ms=stt["build_ms"],
+            stage_ms={k2: round(v2[1] / args.steps, 3) for k2, v2 in prof.items() if v2[0]},
+            coeffs_ms=coef_ms, interp_eval_ms=eval_ms, interp_points_per_s=mq / (eval_ms / 1e3),
+            points_located=int(ok.sum()),
+            rel_err_interp_vs_exact=float(np.abs(v[ok] - ex[ok]).max() / np.abs(ex).max()),
+            rel_err_nodes_vs_exact=float(np.abs(u.cpu().numpy()[0] - (np.sum(nodes.cpu().numpy() ** 2, 1) - 1) / 4).max()
+                                         / 0.25))
+        nf.release()
+        it.release()
+    cpu = None
+    if not args.no_oracle_check:
+        from oracle.oracle import Oracle
+        o = Oracle("far19")
+        it = vp.Interp(ctx, st.vxy, ts, Ns, curves=cs)
+        nodes = it.nodes().cpu().numpy()
+        it.release()
+        s = o.setup(q.vxy, tq, node_targets=False, extra=nodes, curves=cq)
+        n2 = 2000
+        smp = np.sort(np.random.default_rng(9).choice(len(nodes), n2, replace=False))
+        t0 = time.perf_counter()
+        o.potential(s, np.ones((1, s["N"])), targets=smp)
+        dt = time.perf_counter() - t0
+        cpu = {"value": n2 / dt, "unit": "target-evals/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n2} random interpolation nodes of the staggered mesh (far sum, lists, near/self weights "
+                         f"with curved elements), OpenMP over targets, {dt:.1f} s"}
+    stg, same = res["staggered"], res["same"]
+    line = {
+        "metric": "interpolated_points_per_s", "value": 1e6 / (stg["ms_per_step"] / 1e3), "unit": "points/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": stg["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f64", "data": "synthetic",
+        "config": {"workload": "disk_curved_2766tri_19pt_interp_Ns20_staggered_f1", "quadrature_nodes": mesh.N,
+                   "interp_nodes": stg["targets"], "query_points": mq,
+                   "step": "nearfield_build(interp nodes)+potential_eval+interp_coeffs+interp_eval(1e6 points)"},
+        "target_evals_per_s_at_nodes": stg["targets"] / (stg["ms_per_step"] / 1e3),
+        "staggered": stg, "same_mesh": same,
+        "ratios_staggered_over_same": {"c": stg["c_per_target"] / same["c_per_target"],
+                                       "s_n": stg["s_n_per_target"] / same["s_n_per_target"],
+                                       "s_l": stg["s_l_per_target"] / same["s_l_per_target"],
+                                       "step_time": stg["ms_per_step"] / same["ms_per_step"]},
+        "cpu_baseline": cpu,
+    }
+    mesh.release()
+    print(json.dumps(line))
+    ctx.close()
+
+
 # ----------------------------------------------------------------- main arm
 def main():
     args = parse()
@@ -583,6 +714,8 @@ def main():
         return run_serving(args)
     if args.config == 6:
         return run_curved(args)
+    if args.config == 7:
+        return run_interp(args)
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -758,8 +891,11 @@ def main():
         bound, units, peak, unit = work[dname]
         scale = 1e9 if unit == "GB/s" else 1e12
         achieved = units / (dms / 1e3) / scale
+        # DRAM bytes per far-sum stage (k_far_sym + its combine + k_far_extra), one ncu capture of
+        # this workload (profiles/dram_star16384_far_sum.md); other stages: not captured at this size
+        traffic = 1.8719e9 if (dname == "far_ff" and args.ntri == 16384 and args.extra == 10000) else None
         roof = {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "launches": dn, "ms_per_launch": dms / dn}
+                "frac": achieved / peak, "traffic": traffic, "launches": dn, "ms_per_launch": dms / dn}
     stage_share = {k: round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4) for k, v in prof.items() if v[0]}
     # every modelled stage against its own bound (the dominant one is "roofline")
     rooflines = {}

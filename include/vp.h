@@ -384,6 +384,45 @@ VP_API int vp_profile_reset(vp_ctx* ctx);
  * *n receives the number of stages (at most cap are written). */
 VP_API int vp_profile_read(vp_ctx* ctx, char* names, int64_t* counts, double* ms, int32_t cap, int32_t* n);
 
+/* --------------------------------------------------------- interpolation */
+
+/* Interpolation of the potential over the elements of an interpolation mesh
+ * (Section 3.5), e.g. a mesh staggered with the quadrature mesh (Section
+ * 4.3), so that u can be evaluated anywhere from one evaluation at the
+ * interpolation nodes.  On each element Delta with map rho (affine, or the
+ * blending map of a curved element) the Koornwinder expansion of u o rho of
+ * degree N_s (`order`, 1..20) comes from u at dim P_{N_s} = (N_s+1)(N_s+2)/2
+ * interpolation nodes by the inverse interpolation matrix, and
+ * u(x) = I(rho^{-1}(x)) (the affine inverse, or Newton's method on curved
+ * elements).  The nodes are the Blyth-Pozrikidis construction on the N_s+1
+ * Gauss-Legendre points (all inside the element, S3-symmetric; the paper's
+ * Vioreanu-Rokhlin tables are not used), node (i, j, k), i + j + k = N_s, at
+ *     xi = (1 + 2 v_i - v_j - v_k)/3, eta = (1 + 2 v_j - v_i - v_k)/3,
+ * v the Gauss-Legendre points mapped to [0, 1], ordered by j, then i.
+ * vxy, tri: host arrays as vp_mesh_upload; cidx, coef, ncurve, K: curved
+ * elements as vp_mesh_upload_curved, or cidx = NULL for a straight mesh.
+ * Errors: those of the mesh uploads; INVALID_ARG for order outside 1..20. */
+typedef struct vp_interp vp_interp;
+VP_API int vp_interp_create(vp_ctx* ctx, const double* vxy, int64_t nv, const int32_t* tri, int64_t nt,
+                            const int32_t* cidx, const double* coef, int64_t ncurve, int32_t K, int32_t order,
+                            void* stream, vp_interp** out);
+/* Elements, nodes (n_tri * nodes_per_tri) and nodes per element. */
+VP_API int vp_interp_info(const vp_interp* interp, int64_t* n_tri, int64_t* n_nodes, int32_t* nodes_per_tri);
+/* Node coordinates, device [n_nodes][2], element-major: the targets at which
+ * the potential is evaluated (extra targets of vp_nearfield_build). */
+VP_API int vp_interp_nodes(const vp_interp* interp, double* xy_dev, void* stream);
+/* Expansion coefficients: u_dev device [d][n_nodes] values at the nodes ->
+ * coef_dev device [d][n_tri][nodes_per_tri] (Koornwinder index
+ * n (n + 1)/2 + m of K_mn, Section 2.1). */
+VP_API int vp_interp_coeffs(vp_interp* interp, const double* u_dev, int32_t d, double* coef_dev, void* stream);
+/* u at m points pts_dev (device [m][2]) -> out_dev device [d][m]; elem_dev
+ * (device [m] int32, may be NULL) receives the element of each point (the
+ * lowest-index element that holds it, Appendix A.5); points in no element
+ * give NaN and -1. */
+VP_API int vp_interp_eval(vp_interp* interp, const double* coef_dev, int32_t d, const double* pts_dev, int64_t m,
+                          double* out_dev, int32_t* elem_dev, void* stream);
+VP_API void vp_interp_release(vp_interp* interp);
+
 /* ---------------------------------------------------------------- tables */
 
 /* The compiled quadrature tables, for inspection (host buffers of capacity

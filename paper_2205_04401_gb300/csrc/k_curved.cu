@@ -19,7 +19,9 @@
 //    the dyadic counts of Section 3.4 from that distance and the physical
 //    chord lengths on either side of s~.
 // Curved pairs are a small share of all pairs (only boundary triangles are
-// curved), so these kernels keep the whole node loop in FP64.
+// curved), so these kernels keep the whole node loop in FP64; the map at the
+// quadrature nodes (no decision depends on it) uses Clenshaw sums with fused
+// multiply-adds, the decisions the exact-rounding map.
 #include "vp_internal.h"
 #include "vp_curved.cuh"
 #include "vp_weights.cuh"
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_near_curved(WeightsArgs 
 #pragma unroll
     for (int q = 0; q < 6; q++) v[q] = a.tv[6 * (int64_t)T + q];
     const double* ax = curve_coef(cv, T);
+    const double* dax = curve_dcoef(cv, T);
     const int K = cv.K;
     const double J = a.J[T];
     const double xx = a.txy[2 * t], xy = a.txy[2 * t + 1];
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_near_curved(WeightsArgs 
                 const double xi = fma(zy, lf.e2x, fma(zx, lf.e1x, lf.a0x));
                 const double eta = fma(zy, lf.e2y, fma(zx, lf.e1y, lf.a0y));
                 double y[2], det;
-                geom_map_rn(v, ax, K, xi, eta, y, nullptr, &det);
+                geom_map_fast(v, ax, dax, K, xi, eta, y, &det);
                 const double dx = xx - y[0], dy = xy - y[1];
                 const double g = vp_logd(dx * dx + dy * dy, lt.rc, lt.lc, ln2) * (nw[j] * lf.wJ * det);
                 accumulate(m, g, xi, eta);
@@ -276,6 +279,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_self_curved(WeightsArgs 
 #pragma unroll
     for (int q = 0; q < 6; q++) v[q] = a.tv[6 * (int64_t)T + q];
     const double* ax = curve_coef(cv, T);
+    const double* dax = curve_dcoef(cv, T);
     const int K = cv.K;
     const double xx = a.txy[2 * t], xy = a.txy[2 * t + 1];
     const int own = own_index(a, t, T);
@@ -360,7 +364,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_self_curved(WeightsArgs 
                     const double r = gr[q];
                     const double yxi = fma(r, gx, pxi), yeta = fma(r, gy, peta);
                     double y[2], det;
-                    geom_map_rn(v, ax, K, yxi, yeta, y, nullptr, &det);
+                    geom_map_fast(v, ax, dax, K, yxi, yeta, y, &det);
                     const double dx = y[0] - xx, dy = y[1] - xy;
                     // log r + log(|rho(y) - x| / r), the second term smooth in r
                     const double lg = glr[q] + 0.5 * vp_logd((dx * dx + dy * dy) / (r * r), lt.rc, lt.lc, ln2);

@@ -274,6 +274,7 @@ void vp_destroy(vp_ctx* ctx) {
 struct CurvesIn {
     int32_t* d_cidx = nullptr;
     double* d_coef = nullptr;
+    double* d_dcoef = nullptr;
     int64_t ncurve = 0;
     int K = 0;
 };
@@ -284,11 +285,13 @@ static int mesh_upload_impl(vp_ctx* ctx, const double* d_vxy, int64_t nv, const 
     if (!m) {
         if (cin.d_cidx) cudaFree(cin.d_cidx);
         if (cin.d_coef) cudaFree(cin.d_coef);
+        if (cin.d_dcoef) cudaFree(cin.d_dcoef);
         return VP_ERR_OOM;
     }
     m->ctx = ctx;
     m->d_cidx = cin.d_cidx;
     m->d_coef = cin.d_coef;
+    m->d_dcoef = cin.d_dcoef;
     m->ncurve = cin.ncurve;
     m->K = cin.K;
     m->nt = nt;
@@ -406,9 +409,19 @@ int vp_mesh_upload_curved(vp_ctx* ctx, const double* vxy, int64_t nv, const int3
     CurvesIn cin;
     cin.ncurve = ncurve;
     cin.K = K;
+    // Chebyshev coefficients of dD/dt (t = 2 xi - 1), per curve and coordinate:
+    // c_{K-1} = 2 K a_K, c_{k-1} = c_{k+1} + 2 k a_k, then c_0 / 2
+    std::vector<double> dcoef((size_t)ncoef, 0.0);
+    for (int64_t c = 0; c < 2 * ncurve; c++) {
+        const double* a = coef + c * (K + 1);
+        double* d = dcoef.data() + c * (K + 1);
+        for (int k = K; k >= 1; k--) d[k - 1] = (k + 1 <= K ? d[k + 1] : 0.0) + 2.0 * k * a[k];
+        d[0] *= 0.5;
+    }
     if (dev_alloc(&cin.d_cidx, nt) != cudaSuccess ||
-        (ncoef > 0 && dev_alloc(&cin.d_coef, ncoef) != cudaSuccess)) {
+        (ncoef > 0 && (dev_alloc(&cin.d_coef, ncoef) != cudaSuccess || dev_alloc(&cin.d_dcoef, ncoef) != cudaSuccess))) {
         if (cin.d_cidx) cudaFree(cin.d_cidx);
+        if (cin.d_coef) cudaFree(cin.d_coef);
         return vp_set_error(ctx, VP_ERR_OOM, "vp_mesh_upload_curved: device allocation failed");
     }
     cudaError_t e = cudaMemcpyAsync(d_vxy, vxy, 2 * nv * sizeof(double), cudaMemcpyHostToDevice, s);
@@ -416,10 +429,13 @@ int vp_mesh_upload_curved(vp_ctx* ctx, const double* vxy, int64_t nv, const int3
     if (e == cudaSuccess) e = cudaMemcpyAsync(cin.d_cidx, cidx, nt * sizeof(int32_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && ncoef > 0)
         e = cudaMemcpyAsync(cin.d_coef, coef, ncoef * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && ncoef > 0)
+        e = cudaMemcpyAsync(cin.d_dcoef, dcoef.data(), ncoef * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host arrays are read during the call only
     if (e != cudaSuccess) {
         cudaFree(cin.d_cidx);
         if (cin.d_coef) cudaFree(cin.d_coef);
+        if (cin.d_dcoef) cudaFree(cin.d_dcoef);
         return vp_set_error(ctx, VP_ERR_CUDA, std::string("vp_mesh_upload_curved: copy failed: ") + cudaGetErrorString(e));
     }
     return mesh_upload_impl(ctx, d_vxy, nv, d_tri, nt, rule, s, out, cin);
@@ -446,7 +462,7 @@ void vp_mesh_release(vp_mesh* mesh) {
     if (!mesh_ok(mesh)) return;
     DevGuard g(mesh->ctx->device);
     cudaDeviceSynchronize();
-    void* ps[] = {mesh->d_tv, mesh->d_J, mesh->d_y, mesh->d_W, mesh->d_cidx, mesh->d_coef};
+    void* ps[] = {mesh->d_tv, mesh->d_J, mesh->d_y, mesh->d_W, mesh->d_cidx, mesh->d_coef, mesh->d_dcoef};
     for (void* p : ps)
         if (p) cudaFree(p);
     mesh->magic = 0;
@@ -975,6 +991,338 @@ int vp_profile_read(vp_ctx* ctx, char* names, int64_t* counts, double* ms, int32
         if (ms) ms[i] = ctx->prof_ms[i];
     }
     return VP_OK;
+}
+
+// ---------------------------------------------------------- interpolation
+}  // extern "C"
+
+namespace {
+
+// Reference interpolation nodes of order N (the Blyth-Pozrikidis
+// construction on the N + 1 Gauss-Legendre points) and the inverse of their
+// Koornwinder interpolation matrix, in long double on the host.
+void interp_reference(int N, std::vector<double>& zx, std::vector<double>& zy, std::vector<double>& Vinv) {
+    typedef long double LD;
+    const int n1 = N + 1;
+    // Gauss-Legendre points: Newton on P_{n1} from Chebyshev-like guesses
+    std::vector<LD> g(n1);
+    const LD pi = 3.141592653589793238462643383279502884L;
+    for (int i = 0; i < n1; i++) {
+        LD x = std::cos(pi * (i + 0.75L) / (n1 + 0.5L));
+        for (int it = 0; it < 100; it++) {
+            LD p0 = 1.0L, p1 = x;
+            for (int k = 1; k < n1; k++) {
+                const LD p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+                p0 = p1;
+                p1 = p2;
+            }
+            const LD dp = n1 * (x * p1 - p0) / (x * x - 1.0L);
+            const LD dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-30L) break;
+        }
+        g[i] = x;
+    }
+    std::sort(g.begin(), g.end());
+    std::vector<LD> v(n1);
+    for (int i = 0; i < n1; i++) v[i] = 0.5L * (g[i] + 1.0L);
+    const int nn = (N + 1) * (N + 2) / 2;
+    std::vector<LD> X, Y;
+    for (int j = 0; j <= N; j++)
+        for (int i = 0; i <= N - j; i++) {
+            const int k = N - i - j;
+            X.push_back((1.0L + 2.0L * v[i] - v[j] - v[k]) / 3.0L);
+            Y.push_back((1.0L + 2.0L * v[j] - v[i] - v[k]) / 3.0L);
+        }
+    // interpolation matrix A[i][a] = K_a(node i) (Section 2.1)
+    std::vector<LD> A((size_t)nn * nn);
+    for (int r = 0; r < nn; r++) {
+        const LD x = X[r], y = Y[r], w = 1.0L - x, s = 2.0L * y - w, z = 2.0L * x - 1.0L;
+        std::vector<LD> H(N + 2);
+        H[0] = 1.0L;
+        H[1] = s;
+        for (int m = 1; m < N; m++) H[m + 1] = ((2 * m + 1) * s * H[m] - m * w * w * H[m - 1]) / (m + 1);
+        for (int m = 0; m <= N; m++) {
+            const LD a = 2.0L * m + 1.0L;
+            LD pkm1 = 0.0L, pk = 1.0L;
+            for (int k = 0; k <= N - m; k++) {
+                const int n = m + k;
+                A[(size_t)r * nn + n * (n + 1) / 2 + m] = std::sqrt(2.0L * a * (n + 1)) * H[m] * pk;
+                LD pn;
+                if (k == 0) pn = 0.5L * ((a + 2.0L) * z + a);
+                else {
+                    const LD c1 = 2.0L * k + a;
+                    pn = ((c1 + 1.0L) * ((c1 + 2.0L) * c1 * z + a * a) * pk - 2.0L * k * (k + a) * (c1 + 2.0L) * pkm1) /
+                         (2.0L * (k + 1.0L) * (k + a + 1.0L) * c1);
+                }
+                pkm1 = pk;
+                pk = pn;
+            }
+        }
+    }
+    // Gauss-Jordan with partial pivoting: [A | I] -> [I | A^-1]
+    std::vector<LD> B((size_t)nn * nn, 0.0L);
+    for (int i = 0; i < nn; i++) B[(size_t)i * nn + i] = 1.0L;
+    for (int c = 0; c < nn; c++) {
+        int piv = c;
+        for (int r = c + 1; r < nn; r++)
+            if (std::fabs(A[(size_t)r * nn + c]) > std::fabs(A[(size_t)piv * nn + c])) piv = r;
+        if (piv != c)
+            for (int k = 0; k < nn; k++) {
+                std::swap(A[(size_t)c * nn + k], A[(size_t)piv * nn + k]);
+                std::swap(B[(size_t)c * nn + k], B[(size_t)piv * nn + k]);
+            }
+        const LD d = A[(size_t)c * nn + c];
+        for (int k = 0; k < nn; k++) {
+            A[(size_t)c * nn + k] /= d;
+            B[(size_t)c * nn + k] /= d;
+        }
+        for (int r = 0; r < nn; r++) {
+            if (r == c) continue;
+            const LD f = A[(size_t)r * nn + c];
+            if (f == 0.0L) continue;
+            for (int k = 0; k < nn; k++) {
+                A[(size_t)r * nn + k] -= f * A[(size_t)c * nn + k];
+                B[(size_t)r * nn + k] -= f * B[(size_t)c * nn + k];
+            }
+        }
+    }
+    // coefficients = A^-1 u: row a of A^-1 (basis a) against node values
+    zx.resize(nn);
+    zy.resize(nn);
+    Vinv.resize((size_t)nn * nn);
+    for (int i = 0; i < nn; i++) {
+        zx[i] = (double)X[i];
+        zy[i] = (double)Y[i];
+    }
+    for (size_t i = 0; i < (size_t)nn * nn; i++) Vinv[i] = (double)B[i];
+}
+
+// Recurrence table of the device's Koornwinder sums (k_interp.cu), for
+// degree N with nn = dim P_N entries per array, index a = n (n + 1)/2 + m:
+// [c_mn][jA][jB][jC] (the Jacobi coefficients that advance P_{n-m}^{(2m+1,0)}
+// to degree n - m + 1, stored at a) then hA[m], hB[m], m = 0..N.
+void interp_recurrences(int N, std::vector<double>& rec) {
+    typedef long double LD;
+    const int nn = (N + 1) * (N + 2) / 2;
+    rec.assign(4 * nn + 2 * (N + 1), 0.0);
+    for (int m = 0; m <= N; m++) {
+        const LD al = 2.0L * m + 1.0L;
+        for (int n = m; n <= N; n++) {
+            const int a = n * (n + 1) / 2 + m, k = n - m;
+            rec[a] = (double)std::sqrt(2.0L * al * (n + 1));
+            LD A, B, Cc;
+            if (k == 0) {
+                A = 0.5L * (al + 2.0L);
+                B = 0.5L * al;
+                Cc = 0.0L;
+            } else {
+                const LD c1 = 2.0L * k + al, den = 2.0L * (k + 1) * (k + al + 1) * c1;
+                A = (c1 + 1.0L) * (c1 + 2.0L) * c1 / den;
+                B = (c1 + 1.0L) * al * al / den;
+                Cc = 2.0L * k * (k + al) * (c1 + 2.0L) / den;
+            }
+            rec[nn + a] = (double)A;
+            rec[2 * nn + a] = (double)B;
+            rec[3 * nn + a] = (double)Cc;
+        }
+        rec[4 * nn + m] = (double)((2.0L * m + 1.0L) / (m + 1.0L));
+        rec[4 * nn + (N + 1) + m] = (double)((LD)m / (m + 1.0L));
+    }
+}
+
+}  // namespace
+
+struct vp_interp {
+    vp_ctx* ctx = nullptr;
+    vp_mesh* mesh = nullptr;       // the interpolation mesh (its own quadrature nodes are unused)
+    int N = 0, nn = 0;
+    double* d_zx = nullptr;        // [nn] reference nodes
+    double* d_zy = nullptr;
+    double* d_Vinv = nullptr;      // [nn][nn] basis x node
+    double* d_rec = nullptr;       // Koornwinder recurrence table (interp_recurrences)
+    int64_t* d_cell_start = nullptr;
+    int32_t* d_cell_tri = nullptr;
+    GridDev g{};
+    int magic = 0x56504950;
+};
+
+static bool interp_ok(const vp_interp* p) { return p && p->magic == 0x56504950; }
+
+static void interp_free(vp_interp* p) {
+    void* ps[] = {p->d_zx, p->d_zy, p->d_Vinv, p->d_rec, p->d_cell_start, p->d_cell_tri};
+    for (void* q : ps)
+        if (q) cudaFree(q);
+    if (p->mesh) vp_mesh_release(p->mesh);
+    p->magic = 0;
+    delete p;
+}
+
+extern "C" {
+
+int vp_interp_create(vp_ctx* ctx, const double* vxy, int64_t nv, const int32_t* tri, int64_t nt, const int32_t* cidx,
+                     const double* coef, int64_t ncurve, int32_t K, int32_t order, void* stream, vp_interp** out) {
+    if (out) *out = nullptr;
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    if (!out || order < 1 || order > 20) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_interp_create: bad arguments");
+    vp_interp* ip = new (std::nothrow) vp_interp();
+    if (!ip) return VP_ERR_OOM;
+    ip->ctx = ctx;
+    ip->N = order;
+    ip->nn = (order + 1) * (order + 2) / 2;
+    int rc = cidx ? vp_mesh_upload_curved(ctx, vxy, nv, tri, nt, cidx, coef, ncurve, K, VP_RULE_16_D8, stream, &ip->mesh)
+                  : vp_mesh_upload(ctx, vxy, nv, tri, nt, VP_RULE_16_D8, stream, &ip->mesh);
+    if (rc) {
+        delete ip;
+        return rc;
+    }
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> zx, zy, Vinv, rec;
+    interp_reference(order, zx, zy, Vinv);
+    interp_recurrences(order, rec);
+    const int nn = ip->nn;
+#define IP_FAIL(code, msg)                     \
+    do {                                       \
+        rc = vp_set_error(ctx, (code), (msg)); \
+        interp_free(ip);                       \
+        return rc;                             \
+    } while (0)
+    if (dev_alloc(&ip->d_zx, nn) != cudaSuccess || dev_alloc(&ip->d_zy, nn) != cudaSuccess ||
+        dev_alloc(&ip->d_Vinv, (size_t)nn * nn) != cudaSuccess || dev_alloc(&ip->d_rec, rec.size()) != cudaSuccess)
+        IP_FAIL(VP_ERR_OOM, "vp_interp_create: device allocation failed");
+    if (cudaMemcpyAsync(ip->d_rec, rec.data(), rec.size() * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        IP_FAIL(VP_ERR_CUDA, "vp_interp_create: copy failed");
+    if (cudaMemcpyAsync(ip->d_zx, zx.data(), nn * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ip->d_zy, zy.data(), nn * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ip->d_Vinv, Vinv.data(), (size_t)nn * nn * sizeof(double), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+        IP_FAIL(VP_ERR_CUDA, "vp_interp_create: copy failed");
+    // grid of element boxes for point location
+    {
+        const vp_mesh* m = ip->mesh;
+        Scratch sc(s);
+        double *d_bbox, *d_red;
+        int32_t *d_cnt, *d_max;
+        int64_t* d_cursor;
+        if (sc.alloc(&d_bbox, 4 * nt) != cudaSuccess || sc.alloc(&d_red, 4) != cudaSuccess)
+            IP_FAIL(VP_ERR_OOM, "vp_interp_create: device allocation failed");
+        launch_tri_bbox(m->d_tv, nt, d_bbox, s);
+        if (m->d_cidx) launch_curved_bbox(nt, mesh_curves(m), d_bbox, s);
+        launch_bbox_reduce(d_bbox, nt, 4, d_red, s);
+        std::vector<double> hb(4 * nt);
+        double h_red[4];
+        if (cudaMemcpyAsync(hb.data(), d_bbox, 4 * nt * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(h_red, d_red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            IP_FAIL(VP_ERR_CUDA, "vp_interp_create: box copy failed");
+        // cell = the median element box size
+        std::vector<double> sizes(nt);
+        for (int64_t t = 0; t < nt; t++) sizes[t] = std::max(hb[4 * t + 2] - hb[4 * t], hb[4 * t + 3] - hb[4 * t + 1]);
+        std::nth_element(sizes.begin(), sizes.begin() + nt / 2, sizes.end());
+        const double W_ = h_red[2] - h_red[0], H_ = h_red[3] - h_red[1];
+        double hc = std::max(sizes[nt / 2], std::max(W_, H_) / 4096.0);
+        hc = std::max(hc, 1e-300);
+        int64_t nx = std::max<int64_t>(1, (int64_t)std::ceil(W_ / hc)), ny = std::max<int64_t>(1, (int64_t)std::ceil(H_ / hc));
+        while (nx * ny > ((int64_t)1 << 24)) {
+            hc *= 1.5;
+            nx = std::max<int64_t>(1, (int64_t)std::ceil(W_ / hc));
+            ny = std::max<int64_t>(1, (int64_t)std::ceil(H_ / hc));
+        }
+        const int64_t ncell = nx * ny;
+        GridDev gd;
+        gd.ox = h_red[0];
+        gd.oy = h_red[1];
+        gd.h = hc;
+        gd.nx = (int32_t)nx;
+        gd.ny = (int32_t)ny;
+        gd.cell_start = nullptr;
+        gd.cell_tri = nullptr;
+        int64_t nentries = 0;
+        int32_t h_max = 0;
+        if (sc.alloc(&d_cnt, ncell) != cudaSuccess || sc.alloc(&d_cursor, ncell + 1) != cudaSuccess ||
+            sc.alloc(&d_max, 1) != cudaSuccess || dev_alloc(&ip->d_cell_start, ncell + 1) != cudaSuccess)
+            IP_FAIL(VP_ERR_OOM, "vp_interp_create: device allocation failed");
+        cudaMemsetAsync(d_cnt, 0, ncell * sizeof(int32_t), s);
+        launch_tri_cell_count(d_bbox, nt, gd, d_cnt, s);
+        rc = vp_exclusive_scan_i32(ctx, d_cnt, ip->d_cell_start, ncell, s);
+        if (rc) {
+            interp_free(ip);
+            return rc;
+        }
+        launch_max_i32(d_cnt, ncell, d_max, s);
+        if (cudaMemcpyAsync(&nentries, ip->d_cell_start + ncell, sizeof(int64_t), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(&h_max, d_max, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            IP_FAIL(VP_ERR_CUDA, "vp_interp_create: grid count failed");
+        if (h_max > 16384) IP_FAIL(VP_ERR_CUDA, "vp_interp_create: a grid cell holds more than 16384 elements");
+        if (dev_alloc(&ip->d_cell_tri, std::max<int64_t>(1, nentries)) != cudaSuccess)
+            IP_FAIL(VP_ERR_OOM, "vp_interp_create: device allocation failed");
+        cudaMemcpyAsync(d_cursor, ip->d_cell_start, (ncell + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+        launch_tri_cell_fill(d_bbox, nt, gd, d_cursor, ip->d_cell_tri, s);
+        gd.cell_start = ip->d_cell_start;
+        gd.cell_tri = ip->d_cell_tri;
+        cudaMemsetAsync(ctx->d_flag, 0, sizeof(int32_t), s);
+        launch_cell_sort(gd, ncell, h_max, ip->d_cell_tri, ctx->d_flag, s);
+        if (cudaGetLastError() != cudaSuccess) IP_FAIL(VP_ERR_CUDA, "vp_interp_create: grid build failed");
+        rc = check_flag(ctx, ctx->d_flag, s);
+        if (rc) {
+            interp_free(ip);
+            return rc;
+        }
+        ip->g = gd;
+    }
+#undef IP_FAIL
+    *out = ip;
+    return VP_OK;
+}
+
+int vp_interp_info(const vp_interp* ip, int64_t* n_tri, int64_t* n_nodes, int32_t* nodes_per_tri) {
+    if (!interp_ok(ip)) return VP_ERR_STATE;
+    if (n_tri) *n_tri = ip->mesh->nt;
+    if (n_nodes) *n_nodes = ip->mesh->nt * ip->nn;
+    if (nodes_per_tri) *nodes_per_tri = ip->nn;
+    return VP_OK;
+}
+
+int vp_interp_nodes(const vp_interp* ip, double* xy_dev, void* stream) {
+    if (!interp_ok(ip)) return VP_ERR_STATE;
+    if (!xy_dev) return vp_set_error(ip->ctx, VP_ERR_INVALID_ARG, "vp_interp_nodes: bad arguments");
+    DevGuard g(ip->ctx->device);
+    launch_interp_nodes(ip->mesh->d_tv, mesh_curves(ip->mesh), ip->mesh->nt, ip->d_zx, ip->d_zy, ip->nn, xy_dev,
+                        (cudaStream_t)stream);
+    VP_LAUNCH_CHECK(ip->ctx);
+    return VP_OK;
+}
+
+int vp_interp_coeffs(vp_interp* ip, const double* u_dev, int32_t d, double* coef_dev, void* stream) {
+    if (!interp_ok(ip)) return VP_ERR_STATE;
+    if (!u_dev || !coef_dev || d < 1 || d > 65535)
+        return vp_set_error(ip->ctx, VP_ERR_INVALID_ARG, "vp_interp_coeffs: bad arguments");
+    DevGuard g(ip->ctx->device);
+    launch_interp_coeffs(ip->d_Vinv, ip->nn, ip->mesh->nt, d, u_dev, coef_dev, (cudaStream_t)stream);
+    VP_LAUNCH_CHECK(ip->ctx);
+    return VP_OK;
+}
+
+int vp_interp_eval(vp_interp* ip, const double* coef_dev, int32_t d, const double* pts_dev, int64_t m,
+                   double* out_dev, int32_t* elem_dev, void* stream) {
+    if (!interp_ok(ip)) return VP_ERR_STATE;
+    if (!coef_dev || d < 1 || m < 0 || (m > 0 && (!pts_dev || !out_dev)))
+        return vp_set_error(ip->ctx, VP_ERR_INVALID_ARG, "vp_interp_eval: bad arguments");
+    DevGuard g(ip->ctx->device);
+    launch_interp_eval(ip->mesh->d_tv, mesh_curves(ip->mesh), ip->g, pts_dev, m, ip->N, ip->nn, ip->mesh->nt,
+                       ip->d_rec, coef_dev, d, out_dev, elem_dev, (cudaStream_t)stream);
+    VP_LAUNCH_CHECK(ip->ctx);
+    return VP_OK;
+}
+
+void vp_interp_release(vp_interp* ip) {
+    if (!interp_ok(ip)) return;
+    DevGuard g(ip->ctx->device);
+    cudaDeviceSynchronize();
+    interp_free(ip);
 }
 
 int vp_rule_table(int32_t which, double* x, double* y, double* w, double* what, int32_t cap, int32_t* n) {

@@ -22,6 +22,7 @@
 struct CurveDev {
     const int32_t* cidx;
     const double* coef;
+    const double* dcoef;   // [c][2][K+1]: Chebyshev coefficients of dD/dt (d/dxi = 2 d/dt)
     int K;
 };
 
@@ -81,6 +82,48 @@ __device__ __forceinline__ void geom_map_rn(const double* v, const double* __res
         Jm[3] = a22;
     }
     if (det) *det = rn_sub(rn_mul(a11, a22), rn_mul(a12, a21));
+}
+
+// Sum_k a_k T_k(t) by Clenshaw's recurrence (fused multiply-adds).
+__device__ __forceinline__ double cheb_clenshaw(const double* __restrict__ a, int K, double t) {
+    const double t2 = 2.0 * t;
+    double b1 = 0.0, b2 = 0.0;
+    for (int k = K; k >= 1; k--) {
+        const double b0 = fma(t2, b1, a[k] - b2);
+        b2 = b1;
+        b1 = b0;
+    }
+    return fma(t, b1, a[0] - b2);
+}
+
+// rho_T(xi, eta) and det J_rho for quadrature nodes, where no decision
+// depends on the last bit: Clenshaw sums of D and of its derivative series
+// (dcoef) with fused multiply-adds, about a third of the operations of
+// geom_map_rn.  The results agree with geom_map_rn to rounding.
+__device__ __forceinline__ void geom_map_fast(const double* v, const double* __restrict__ ax,
+                                              const double* __restrict__ dax, int K, double xi, double eta, double* y,
+                                              double* det) {
+    const double Ax = v[0], Ay = v[1];
+    const double ex = v[2] - Ax, ey = v[3] - Ay;
+    const double fx = v[4] - Ax, fy = v[5] - Ay;
+    double yx = fma(eta, fx, fma(xi, ex, Ax)), yy = fma(eta, fy, fma(xi, ey, Ay));
+    double a11 = ex, a21 = ey, a12 = fx, a22 = fy;
+    if (ax) {
+        const double t = fma(2.0, xi, -1.0);
+        const double Dx = cheb_clenshaw(ax, K, t), Dy = cheb_clenshaw(ax + (K + 1), K, t);
+        const double dDx = 2.0 * cheb_clenshaw(dax, K, t), dDy = 2.0 * cheb_clenshaw(dax + (K + 1), K, t);
+        const double b = xi * (1.0 - xi - eta);
+        const double bx = 1.0 - 2.0 * xi - eta;
+        yx = fma(b, Dx, yx);
+        yy = fma(b, Dy, yy);
+        a11 = fma(bx, Dx, fma(b, dDx, a11));
+        a21 = fma(bx, Dy, fma(b, dDy, a21));
+        a12 = fma(-xi, Dx, a12);
+        a22 = fma(-xi, Dy, a22);
+    }
+    y[0] = yx;
+    y[1] = yy;
+    *det = a11 * a22 - a12 * a21;
 }
 
 // rho_T^{-1}(x) by Newton's method started from the chord triangle's affine
@@ -144,4 +187,9 @@ __device__ __forceinline__ const double* curve_coef(const CurveDev& c, int64_t T
     if (!c.cidx) return nullptr;
     const int k = c.cidx[T];
     return k >= 0 ? c.coef + (int64_t)k * 2 * (c.K + 1) : nullptr;
+}
+__device__ __forceinline__ const double* curve_dcoef(const CurveDev& c, int64_t T) {
+    if (!c.cidx) return nullptr;
+    const int k = c.cidx[T];
+    return k >= 0 ? c.dcoef + (int64_t)k * 2 * (c.K + 1) : nullptr;
 }

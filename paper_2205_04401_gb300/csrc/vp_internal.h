@@ -78,6 +78,7 @@ struct vp_mesh {
     // straight) and Chebyshev coefficients [ncurve][2][K+1]; nullptr if none
     int32_t* d_cidx = nullptr;
     double* d_coef = nullptr;
+    double* d_dcoef = nullptr;     // Chebyshev coefficients of dD/dt, same layout
     int64_t ncurve = 0;
     int K = 0;
     int magic = 0x56504d48;
@@ -183,7 +184,7 @@ void launch_split_pairs(const uint8_t* pkind, int64_t P, int32_t* near_idx, int3
                         unsigned long long* counters, cudaStream_t s);
 
 // curved elements (k_curved.cu)
-inline CurveDev mesh_curves(const vp_mesh* m) { return CurveDev{m->d_cidx, m->d_coef, m->K}; }
+inline CurveDev mesh_curves(const vp_mesh* m) { return CurveDev{m->d_cidx, m->d_coef, m->d_dcoef, m->K}; }
 void launch_mesh_nodes_curved(const double* vxy, int64_t nv, const int32_t* tri, int64_t nt, CurveDev cv,
                               const VpTables* tab, int rule, const double* tv, double* y, double* W, int32_t* flag,
                               cudaStream_t s);
@@ -223,6 +224,16 @@ size_t weights_f2_bytes(int64_t nt, int64_t M, int64_t N);
 // self and near weights (stages ST_WEIGHTS_SELF, ST_WEIGHTS_NEAR)
 void launch_weights(const WeightsArgs& a, const int32_t* self_idx, int64_t n_self, const int32_t* near_idx,
                     int64_t n_near, cudaStream_t s, vp_ctx* ctx);
+// interpolation over a mesh (k_interp.cu)
+void launch_interp_nodes(const double* tv, CurveDev cv, int64_t nt, const double* zx, const double* zy, int nn,
+                         double* xy, cudaStream_t s);
+void launch_interp_coeffs(const double* Vinv, int nn, int64_t nt, int d, const double* u, double* coef,
+                          cudaStream_t s);
+void launch_tri_bbox(const double* tv, int64_t nt, double* bbox, cudaStream_t s);
+// rec: the recurrence table of interp_recurrences (vp_api.cu)
+void launch_interp_eval(const double* tv, CurveDev cv, GridDev g, const double* pts, int64_t m, int N, int nn,
+                        int64_t nt, const double* rec, const double* coef, int d, double* out, int32_t* elem,
+                        cudaStream_t s);
 // correction weights of the pairs on curved triangles (stage ST_WEIGHTS_CURVED)
 void launch_weights_curved(const WeightsArgs& a, CurveDev cv, const int32_t* self_idx, int64_t n_self,
                            const int32_t* near_idx, int64_t n_near, cudaStream_t s, vp_ctx* ctx);

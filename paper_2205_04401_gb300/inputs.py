@@ -294,11 +294,15 @@ def _build(dom: _Domain, n_tri: int, hfun_rel, seed: int, relax_iters: int = 12,
 
 
 # ----------------------------------------------------------------- fixtures
-def disk_mesh(seed: int = 2205044011, n_b: int = 32, n_i: int = 113) -> Mesh:
+def disk_mesh(seed: int = 2205044011, n_b: int = 32, n_i: int = 113, stagger: bool = False) -> Mesh:
     """Unit disk: n_b vertices on the circle, n_i jittered-hex interior
-    points, Delaunay.  The default gives 2*113 + 32 - 2 = 256 triangles."""
+    points, Delaunay.  The default gives 2*113 + 32 - 2 = 256 triangles.
+    stagger=True shifts the initial tiling to the centroids of its triangles
+    (by (h/2, h sqrt(3)/6)) and the boundary vertices by half a spacing, so
+    that the mesh's edges avoid those of the unshifted mesh (the staggered
+    interpolation mesh of Section 4.3)."""
     rng = np.random.default_rng(seed)
-    th = 2 * np.pi * np.arange(n_b) / n_b
+    th = 2 * np.pi * (np.arange(n_b) + (0.5 if stagger else 0.0)) / n_b
     bpts = np.stack([np.cos(th), np.sin(th)], axis=1)
     h_b = 2 * math.sin(math.pi / n_b)
     r_keep = math.cos(math.pi / n_b) - 0.45 * h_b
@@ -306,8 +310,8 @@ def disk_mesh(seed: int = 2205044011, n_b: int = 32, n_i: int = 113) -> Mesh:
     def lattice(h, jit):
         nx = int(2.5 / h) + 2
         ii, jj = np.meshgrid(np.arange(-nx, nx + 1), np.arange(-nx, nx + 1), indexing="ij")
-        x = (ii + 0.5 * (jj % 2)) * h
-        y = jj * h * math.sqrt(3) / 2
+        x = (ii + 0.5 * (jj % 2) + (0.5 if stagger else 0.0)) * h
+        y = (jj * math.sqrt(3) / 2 + (math.sqrt(3) / 6 if stagger else 0.0)) * h
         p = np.stack([x.ravel(), y.ravel()], axis=1)
         return p + jit[: len(p)] * h
 
@@ -326,7 +330,7 @@ def disk_mesh(seed: int = 2205044011, n_b: int = 32, n_i: int = 113) -> Mesh:
     vxy, tri, ok = _triangulate(bpts, p, [bpts], 0)
     if not ok:
         raise RuntimeError("disk mesh invalid")
-    return Mesh(vxy=vxy, tri=tri, loops=[bpts], name=f"disk{len(tri)}")
+    return Mesh(vxy=vxy, tri=tri, loops=[bpts], name=f"disk{len(tri)}" + ("_staggered" if stagger else ""))
 
 
 def star_mesh(n_tri: int = 16384, seed: int = 2205044012, lobes: int = 5, amp: float = 0.3,

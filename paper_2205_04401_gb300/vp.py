@@ -76,6 +76,14 @@ SIGNATURES = {
     "vp_mesh_upload_curved": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                                         C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
                                         C.POINTER(C.c_void_p)]),
+    "vp_interp_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                   C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "vp_interp_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "vp_interp_nodes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vp_interp_coeffs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "vp_interp_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]),
+    "vp_interp_release": (None, [C.c_void_p]),
     "vp_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "vp_profile_reset": (C.c_int, [C.c_void_p]),
     "vp_profile_read": (C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
@@ -279,6 +287,79 @@ def mesh_upload_curved(ctx: Context, vxy, tri, curves, rule: int = VP_RULE_19_D9
     nt, N, nq = C.c_int64(), C.c_int64(), C.c_int32()
     _check(lib.vp_mesh_info(h, C.byref(nt), C.byref(N), C.byref(nq)), ctx, "vp_mesh_info")
     return Mesh(ctx, h, nt.value, N.value, nq.value)
+
+
+class Interp:
+    """vp_interp: interpolation of the potential over the elements of a mesh
+    (Section 3.5).  curves: None (straight) or {"cidx", "coef"} as for
+    mesh_upload_curved."""
+
+    def __init__(self, ctx: Context, vxy, tri, order: int, curves=None, stream=None):
+        lib = load()
+        self.ctx = ctx
+        vxy = np.ascontiguousarray(vxy, np.float64)
+        tri = np.ascontiguousarray(tri, np.int32)
+        h = C.c_void_p()
+        if curves is None:
+            rc = lib.vp_interp_create(ctx.handle, vxy.ctypes.data_as(C.c_void_p), C.c_int64(len(vxy)),
+                                      tri.ctypes.data_as(C.c_void_p), C.c_int64(len(tri)), None, None,
+                                      C.c_int64(0), C.c_int32(0), C.c_int32(order), _stream(stream), C.byref(h))
+        else:
+            cidx = np.ascontiguousarray(curves["cidx"], np.int32)
+            coef = np.ascontiguousarray(curves["coef"], np.float64)
+            rc = lib.vp_interp_create(ctx.handle, vxy.ctypes.data_as(C.c_void_p), C.c_int64(len(vxy)),
+                                      tri.ctypes.data_as(C.c_void_p), C.c_int64(len(tri)),
+                                      cidx.ctypes.data_as(C.c_void_p), coef.ctypes.data_as(C.c_void_p),
+                                      C.c_int64(coef.shape[0]), C.c_int32(coef.shape[2] - 1), C.c_int32(order),
+                                      _stream(stream), C.byref(h))
+        _check(rc, ctx, "vp_interp_create")
+        self.handle = h
+        nt, n, nn = C.c_int64(), C.c_int64(), C.c_int32()
+        _check(lib.vp_interp_info(h, C.byref(nt), C.byref(n), C.byref(nn)), ctx, "vp_interp_info")
+        self.nt, self.n_nodes, self.nn, self.order = nt.value, n.value, nn.value, order
+
+    def nodes(self, stream=None):
+        import torch
+        out = torch.empty((self.n_nodes, 2), dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        _check(load().vp_interp_nodes(self.handle, _dptr(out, "float64"), _stream(stream)), self.ctx,
+               "vp_interp_nodes")
+        return out
+
+    def coeffs(self, u, stream=None):
+        """u: device [d][n_nodes] -> device [d][nt][nn]."""
+        import torch
+        if u.dim() == 1:
+            u = u[None, :]
+        u = u.contiguous()
+        d = u.shape[0]
+        out = torch.empty((d, self.nt, self.nn), dtype=torch.float64, device=u.device)
+        _check(load().vp_interp_coeffs(self.handle, _dptr(u, "float64"), C.c_int32(d), _dptr(out, "float64"),
+                                       _stream(stream)), self.ctx, "vp_interp_coeffs")
+        return out
+
+    def eval(self, coef, pts, stream=None):
+        """coef [d][nt][nn], pts device [m][2] -> (device [d][m], device [m] int32)."""
+        import torch
+        coef = coef.contiguous()
+        pts = pts.contiguous()
+        d, m = coef.shape[0], pts.shape[0]
+        out = torch.empty((d, m), dtype=torch.float64, device=pts.device)
+        elem = torch.empty(m, dtype=torch.int32, device=pts.device)
+        _check(load().vp_interp_eval(self.handle, _dptr(coef, "float64"), C.c_int32(d), _dptr(pts, "float64"),
+                                     C.c_int64(m), _dptr(out, "float64"), _dptr(elem, "int32"), _stream(stream)),
+               self.ctx, "vp_interp_eval")
+        return out, elem
+
+    def release(self):
+        if getattr(self, "handle", None):
+            load().vp_interp_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
 
 
 def profile_enable(ctx: Context, on: bool = True):
