@@ -5,7 +5,7 @@
 //
 // The weights are pair-major (pairs in target order, nq float-float weights
 // per pair), so a run of pairs is a run of bytes.  Work is cut into tiles of
-// 32 pairs (4,864 bytes of weights for nq = 19).  Each warp of a persistent
+// AS_TILE pairs (32 by default: 4,864 bytes of weights for nq = 19).  Each warp of a persistent
 // grid owns a ring of VP_AS_STAGES tiles in shared memory that one lane
 // refills with cp.async.bulk (three copies per tile: weights, triangles,
 // targets, all completing on the stage's mbarrier), so that the warp computes
@@ -34,12 +34,16 @@
 #ifndef VP_AS_STAGES
 #define VP_AS_STAGES 2
 #endif
+#ifndef VP_AS_TILE
+#define VP_AS_TILE 32
+#endif
 
 namespace {
 
 constexpr int AS_WARPS = VP_AS_WARPS;
 constexpr int AS_STAGES = VP_AS_STAGES;
-constexpr int AS_TILE = 32;   // pairs per tile (one per lane)
+constexpr int AS_TILE = VP_AS_TILE;   // pairs per tile: 32 (one per lane) or 16 (two lanes per pair)
+static_assert(AS_TILE == 32 || AS_TILE == 16, "tile of 16 or 32 pairs");
 
 template <int NQ>
 struct __align__(16) AsStage {
@@ -104,27 +108,31 @@ __global__ void __launch_bounds__(AS_WARPS * 32, 1)
         float2* C = st[s].C;
         // all density gathers first (independent loads in flight together),
         // then the products
-        float2 fv[NQ];
+        constexpr int NI = (AS_TILE * NQ + 31) / 32;   // entries per lane
+        float2 fv[NI];
 #pragma unroll
-        for (int i = 0; i < NQ; i++) {
+        for (int i = 0; i < NI; i++) {
             const int e = 32 * i + lane;
             const int j = e / NQ;
             const int64_t src = j < n ? (int64_t)st[s].tri[j] * NQ + (e - j * NQ) : 0;
             fv[i] = __ldg(fd2 + src);
         }
-        // this lane's pair: target, row bounds and current value, loaded
-        // early so that their latency overlaps the products
+        // this lane's pair (lane mod AS_TILE): target, row bounds and current
+        // value, loaded early so that their latency overlaps the products
+        const int pl = lane & (AS_TILE - 1);
         int t = INT_MAX;   // padding lanes form their own segment
         int64_t r0 = 0, r1 = 0;
         double u0 = 0.0;
-        if (lane < n) {
-            t = st[s].tgt[lane];
-            r0 = row[t];
-            r1 = row[t + 1];
-            u0 = u[t];
+        if (pl < n) {
+            t = st[s].tgt[pl];
+            if (lane == pl) {
+                r0 = row[t];
+                r1 = row[t + 1];
+                u0 = u[t];
+            }
         }
 #pragma unroll
-        for (int i = 0; i < NQ; i++) {
+        for (int i = 0; i < NI; i++) {
             const int e = 32 * i + lane;
             if (e / NQ < n) {
                 const float2 c = C[e];
@@ -135,30 +143,40 @@ __global__ void __launch_bounds__(AS_WARPS * 32, 1)
             }
         }
         __syncwarp();
-        // pair-parallel pass: lane l sums the NQ products of pair p0 + l in
-        // four interleaved float-float partial sums (shorter dependency
-        // chains), combined in a fixed order
+        // pair-parallel pass: the NQ products of pair p0 + pl, in interleaved
+        // float-float partial sums combined in a fixed order (with 16-pair
+        // tiles the two half-warps take the first and second half of them)
         f2 ps = {0.f, 0.f};
-        if (lane < n) {
-            const float2* c = C + lane * NQ;
+        if (pl < n) {
+            constexpr int HQ = AS_TILE == 32 ? NQ : (NQ + 1) / 2;
+            const int q0 = AS_TILE == 32 ? 0 : (lane >> 4) * HQ;
+            const float2* c = C + pl * NQ;
             f2 a4[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
-            for (int q = 0; q < NQ; q++) {
-                const float2 v = c[q];
-                a4[q & 3] = f2_add(a4[q & 3], {v.x, v.y});
+            for (int q = 0; q < HQ; q++) {
+                if (q0 + q < NQ) {
+                    const float2 v = c[q0 + q];
+                    a4[q & 3] = f2_add(a4[q & 3], {v.x, v.y});
+                }
             }
             ps = f2_add(f2_add(a4[0], a4[1]), f2_add(a4[2], a4[3]));
         }
-        // segmented inclusive sum over the lanes (targets are non-decreasing)
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const float vh = __shfl_up_sync(0xffffffffu, ps.h, o), vl = __shfl_up_sync(0xffffffffu, ps.l, o);
-            const int kt = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o && kt == t) ps = f2_add(ps, {vh, vl});
+        if (AS_TILE == 16) {
+            // both halves: (first half) + (second half), the same on both
+            const float oh = __shfl_xor_sync(0xffffffffu, ps.h, 16), ol = __shfl_xor_sync(0xffffffffu, ps.l, 16);
+            ps = lane < 16 ? f2_add(ps, {oh, ol}) : f2_add({oh, ol}, ps);
         }
-        const int t_next = __shfl_down_sync(0xffffffffu, t, 1);
+        // segmented inclusive sum over the pairs (targets are non-decreasing)
+#pragma unroll
+        for (int o = 1; o < AS_TILE; o <<= 1) {
+            const float vh = __shfl_up_sync(0xffffffffu, ps.h, o, AS_TILE);
+            const float vl = __shfl_up_sync(0xffffffffu, ps.l, o, AS_TILE);
+            const int kt = __shfl_up_sync(0xffffffffu, t, o, AS_TILE);
+            if (pl >= o && kt == t) ps = f2_add(ps, {vh, vl});
+        }
+        const int t_next = __shfl_down_sync(0xffffffffu, t, 1, AS_TILE);
         const int t_lane0 = __shfl_sync(0xffffffffu, t, 0);
-        if (lane < n && (lane == n - 1 || t_next != t)) {   // the last lane of a segment
+        if (lane == pl && lane < n && (lane == n - 1 || t_next != t)) {   // the last pair of a segment
             const double sum = (double)ps.h + (double)ps.l;
             if (r0 >= p0 && r1 <= p0 + AS_TILE) {
                 u[t] = u0 + sum;                              // the whole row is in this tile

@@ -367,7 +367,7 @@ def disk_uniform_mesh(n_tri: int, seed: int, relax_iters: int = 8) -> Mesh:
     return _build(dom, n_tri, lambda p: np.ones(len(p)), seed, relax_iters, name=f"disk_{n_tri}")
 
 
-def curved_boundary(mesh: Mesh, circles, K: int = 15):
+def curved_boundary(mesh: Mesh, circles, K=None, tol: float = 1e-15):
     """Curved boundary elements for a mesh whose boundary edges lie on circles.
 
     circles: list of (cx, cy, R).  Every triangle with a boundary edge on one
@@ -376,10 +376,18 @@ def curved_boundary(mesh: Mesh, circles, K: int = 15):
     round), given as the deviation from the chord,
         c(xi) - (1 - xi) v0 - xi v1 = xi (1 - xi) D(xi),
     with D interpolated at K+1 Chebyshev points of [0, 1]
-    (D = sum_k a_k T_k(2 xi - 1)).  Returns (tri, {"cidx", "coef"}): the
-    rotated triangles, the curve index of every triangle (-1 straight) and
-    the coefficients [ncurve][2][K+1].
+    (D = sum_k a_k T_k(2 xi - 1)).  K=None takes the smallest K (2..15) whose
+    curves stay within tol R of their circles on 401 points of every arc
+    (higher coefficients would only carry rounding noise).  Returns
+    (tri, {"cidx", "coef"}): the rotated triangles, the curve index of every
+    triangle (-1 straight) and the coefficients [ncurve][2][K+1].
     """
+    if K is None:
+        for k in range(2, 16):
+            tri, cur = curved_boundary(mesh, circles, K=k)
+            if _curve_deviation(mesh.vxy, tri, cur, circles) <= tol:
+                return tri, cur
+        return tri, cur
     tri = mesh.tri.copy()
     vxy = mesh.vxy
     edges = {}
@@ -420,6 +428,23 @@ def curved_boundary(mesh: Mesh, circles, K: int = 15):
         coefs.append(np.linalg.solve(V, Dv).T)                       # [2][K+1]
         cidx[t] = len(coefs) - 1
     return tri, {"cidx": cidx, "coef": np.ascontiguousarray(np.array(coefs).reshape(-1, 2, K + 1))}
+
+
+def _curve_deviation(vxy, tri, cur, circles) -> float:
+    """Largest |distance to the circle - R| / R over 401 points of every curved side."""
+    xs = np.linspace(0.0, 1.0, 401)
+    t = 2.0 * xs - 1.0
+    worst = 0.0
+    for T in np.where(cur["cidx"] >= 0)[0]:
+        a = cur["coef"][cur["cidx"][T]]
+        v0, v1 = vxy[tri[T, 0]], vxy[tri[T, 1]]
+        D = np.stack([np.polynomial.chebyshev.chebval(t, a[0]), np.polynomial.chebyshev.chebval(t, a[1])], 1)
+        c = (1 - xs)[:, None] * v0 + xs[:, None] * v1 + (xs * (1 - xs))[:, None] * D
+        best = np.inf
+        for cx, cy, R in circles:
+            best = min(best, np.abs(np.hypot(c[:, 0] - cx, c[:, 1] - cy) - R).max() / R)
+        worst = max(worst, best)
+    return worst
 
 
 def snap_to_circles(mesh: Mesh, circles, tol: float = 1e-6) -> Mesh:
