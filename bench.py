@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp64", "fmm"], default="mixed",
+                    help="mixed: direct float-float far sum (default); fp64; fmm: far sum by the fast multipole method")
     ap.add_argument("--impl", choices=["vp", "reference"], default="vp")
     ap.add_argument("--ntri", type=int, default=16384)
     ap.add_argument("--extra", type=int, default=10000)
@@ -436,6 +437,8 @@ def run_serving(args):
     cap = sat["req_per_s"]
     light = serve(max(100, args.requests // 4), 1.0 / (0.7 * cap), vp.VP_MIXED, 12, check=10)
     f64 = serve(max(20, args.requests // 40), 0.002, vp.VP_FP64, 13)
+    # the same saturated trace with the far sum by the fast multipole method
+    fmm = serve(args.requests, 0.002, vp.VP_MIXED_FMM, 11, check=40)
     line = {
         "metric": "target_evals_per_s", "value": sat["evals_per_s"], "unit": "target-evals/s", "n_gpus": 1,
         "steps": 1, "warmup": 0, "ms_per_step": 1e3 * sat["wall_s"], "higher_is_better": True, "scaling": "weak",
@@ -444,6 +447,7 @@ def run_serving(args):
                    "hbm_budget_bytes": 24 << 30, "requests": args.requests},
         "saturated_mixed": sat, "seventy_percent_load_mixed": light, "saturated_fp64": f64,
         "served_mixed_over_fp64_evals_per_s": sat["evals_per_s"] / f64["evals_per_s"],
+        "same_trace_mixed_fmm": fmm, "served_fmm_over_fp64_evals_per_s": fmm["evals_per_s"] / f64["evals_per_s"],
         "setup_s": {"meshes": t_mesh, "upload_and_build": t_build},
     }
     print(json.dumps(line))
@@ -726,7 +730,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_2205_04401_gb300 import vp
-    prec = vp.VP_MIXED if args.precision == "mixed" else vp.VP_FP64
+    prec = {"mixed": vp.VP_MIXED, "fp64": vp.VP_FP64, "fmm": vp.VP_MIXED_FMM}[args.precision]
 
     mesh, fun, extra = make_inputs(args.ntri, args.extra)
     ctx = vp.Context(local)
@@ -802,6 +806,18 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     resident_ms = e0.elapsed_time(e1) / reps
+    # the same resident evaluation with the far sum by the fast multipole method
+    t0 = time.perf_counter()
+    u_fmm = vp.potential_eval(ctx, nf, f_d, precision=vp.VP_MIXED_FMM)
+    torch.cuda.synchronize()
+    fmm_first_s = time.perf_counter() - t0
+    e0.record(stream)
+    for _ in range(reps):
+        vp.potential_eval(ctx, nf, f_d, precision=vp.VP_MIXED_FMM, out=u_fmm)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fmm_ms = e0.elapsed_time(e1) / reps
+    rel_fmm_vs_mixed = float((u_fmm - u_mixed).abs().max() / u_mixed.abs().max())
     fp64_ms = None
     rel_mixed_vs_fp64 = None
     u64 = None
@@ -912,7 +928,7 @@ def main():
             "metric": "target_evals_per_s", "value": value, "unit": "target-evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32x2+f64" if prec == vp.VP_MIXED else "f64", "data": "synthetic",
+            "dtype": "f64" if prec == vp.VP_FP64 else "f32x2+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "targets": M, "nodes": N, "densities": 1, "precision": args.precision,
                        "step": "mesh_upload+nearfield_build+potential_eval", "l2": "256 MiB flush between steps",
                        "parallelism": f"replicas{world}"},
@@ -924,7 +940,9 @@ def main():
             "rooflines_by_stage": rooflines,
             "cpu_baseline": cpu,
             "accuracy": {"rel_err_mixed_vs_oracle_sampled": rel_oracle, "rel_err_mixed_vs_fp64_gpu": rel_mixed_vs_fp64},
-            "resident_eval": {"mixed_ms": resident_ms, "fp64_ms": fp64_ms,
+            "resident_eval": {"mixed_ms": resident_ms, "fp64_ms": fp64_ms, "fmm_ms": fmm_ms,
+                              "fmm_first_call_s": fmm_first_s, "fmm_target_evals_per_s": M / (fmm_ms / 1e3),
+                              "rel_err_fmm_vs_mixed": rel_fmm_vs_mixed,
                               "mixed_target_evals_per_s": M / (resident_ms / 1e3),
                               "fp64_target_evals_per_s": (M / (fp64_ms / 1e3)) if fp64_ms else None,
                               "mixed_pairs_per_s": M * N / (resident_ms / 1e3)},

@@ -71,8 +71,16 @@ typedef enum vp_rule { VP_RULE_16_D8 = 16, VP_RULE_19_D9 = 19 } vp_rule;
  * FP64.  Its only error beyond VP_MIXED is the rounding of every weight to
  * 7L - 1 bits below the largest weight of its kind (near or self) for its
  * target, and of every density value to 7L - 1 bits below the largest value
- * of its density. */
-typedef enum vp_precision { VP_FP64 = 0, VP_MIXED = 1, VP_MIXED_TC = 2 } vp_precision;
+ * of its density.  VP_MIXED_FMM: the corrections of VP_MIXED, the far sum by a
+ * fast multipole method (the coupling of Section 3.6, where the paper calls a
+ * library FMM): a uniform quadtree over the nodes and targets, complex
+ * multipole and local expansions of 40 terms in FP64 with the Greengard-
+ * Rokhlin translations, and the leaf and adjacent boxes summed directly in
+ * float-float; its translations keep a point source at the nearest corner of
+ * a well-separated box within 4e-16 of the direct value.  Its plan (tree,
+ * sorted nodes and targets) is built on the first evaluation of a vp_nf,
+ * which synchronises `stream`. */
+typedef enum vp_precision { VP_FP64 = 0, VP_MIXED = 1, VP_MIXED_TC = 2, VP_MIXED_FMM = 3 } vp_precision;
 
 /* Parameters of the near-field characterisation and correction weights. */
 typedef struct vp_nf_params {
@@ -248,6 +256,12 @@ VP_API int vp_device_status(vp_ctx* ctx, void* stream);
  * device bytes (all 0 without a plan).  Any pointer may be NULL. */
 VP_API int vp_nf_tc_info(const vp_nf* nf, int32_t* levels, int64_t* n_tiles, int64_t* n_chunks, int64_t* bytes);
 
+/* The fast-multipole plan of nf (VP_MIXED_FMM): leaf level of its quadtree
+ * (chosen per build from a cost model of direct pairs against translations)
+ * and the number of boxes over all levels; 0 before the first VP_MIXED_FMM
+ * evaluation.  Either pointer may be NULL. */
+VP_API int vp_nf_fmm_info(const vp_nf* nf, int32_t* leaf_level, int64_t* n_boxes);
+
 /* ------------------------------------------------------------- evaluation */
 
 /* u = far + corrections (Section 3.6) for d densities.
@@ -346,6 +360,8 @@ typedef struct vp_server_stats_t {
     double evals_per_s;       /* evals / (last completion - first submission) */
 } vp_server_stats_t;
 
+/* precision: VP_FP64, VP_MIXED or VP_MIXED_FMM (the multipole plan of a mesh
+ * is built when it is registered, or right after a cold mesh's build). */
 VP_API int vp_server_create(vp_ctx* ctx, int32_t slots, int64_t hbm_budget_bytes, int32_t precision,
                             vp_server** out);
 /* Serve requests against an existing near-field build (the caller keeps it

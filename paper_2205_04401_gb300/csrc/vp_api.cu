@@ -162,6 +162,8 @@ void free_nf_device(vp_nf* nf) {
     nf->tc = nullptr;
     far_sym_plan_free(nf->sym);
     nf->sym = nullptr;
+    fmm_plan_free(nf->fmm);
+    nf->fmm = nullptr;
 }
 
 }  // namespace
@@ -174,7 +176,7 @@ int vp_set_error(vp_ctx* ctx, int code, const std::string& msg) {
 static const char* kStageNames[ST_COUNT] = {
     "mesh_nodes", "tri_geom", "tri_cells", "cell_sort", "target_cells", "locate", "list_count", "list_fill",
     "weights_self", "weights_near", "ff_split", "far_fp64", "far_ff", "reduce_splits", "apply", "apply_tc",
-    "weights_curved"};
+    "weights_curved", "far_fmm"};
 
 static cudaEvent_t prof_event(vp_ctx* ctx) {
     if (!ctx->prof_pool.empty()) {
@@ -818,20 +820,24 @@ static int eval_splits(const vp_ctx* ctx, int64_t M, int64_t N, int threads) {
 static size_t eval_layout(const vp_ctx* ctx, const vp_nf* nf, int d, int precision, bool sym, size_t* off_q,
                           size_t* off_t) {
     const int64_t N = nf->mesh->N, M = nf->M;
-    const int splits = sym ? 1 : eval_splits(ctx, M, N, 128);
+    const bool fmm = precision == VP_MIXED_FMM;
+    const int splits = (sym || fmm) ? 1 : eval_splits(ctx, M, N, 128);
     const size_t partial_bytes = splits > 1 ? (size_t)splits * d * M * sizeof(double) : 0;
     *off_q = (partial_bytes + 255) & ~(size_t)255;
-    const size_t q_bytes = sym ? far_sym_ws_bytes(ctx, nf) : (precision != VP_FP64 ? (size_t)N * 16 * sizeof(float) : 0);
+    const size_t q_bytes = fmm ? fmm_ws_bytes(nf, d)
+                               : sym ? far_sym_ws_bytes(ctx, nf) : (precision != VP_FP64 ? (size_t)N * 16 * sizeof(float) : 0);
     *off_t = (*off_q + q_bytes + 255) & ~(size_t)255;
-    size_t f2_bytes = precision == VP_MIXED && d < APPLY_MANY_MIN_D ? (size_t)N * d * sizeof(float2) : 0;
-    if (precision == VP_MIXED && d == 1) f2_bytes = std::max(f2_bytes, apply_stream_ws_bytes(N, nf->P));
+    const bool mixed_apply = precision == VP_MIXED || precision == VP_MIXED_FMM;
+    size_t f2_bytes = mixed_apply && d < APPLY_MANY_MIN_D ? (size_t)N * d * sizeof(float2) : 0;
+    if (mixed_apply && d == 1) f2_bytes = std::max(f2_bytes, apply_stream_ws_bytes(N, nf->P));
     return *off_t + std::max(precision == VP_MIXED_TC ? tc_ws_bytes(nf) : apply_ws_bytes(N, d), f2_bytes) + 256;
 }
 
 size_t eval_ws_bytes(const vp_ctx* ctx, const vp_nf* nf, int d, int precision) {
     size_t oq, ot;
     size_t b = eval_layout(ctx, nf, d, precision, false, &oq, &ot);
-    if (precision != VP_FP64 && far_sym_applicable(nf, d)) b = std::max(b, eval_layout(ctx, nf, d, precision, true, &oq, &ot));
+    if ((precision == VP_MIXED || precision == VP_MIXED_TC) && far_sym_applicable(nf, d))
+        b = std::max(b, eval_layout(ctx, nf, d, precision, true, &oq, &ot));
     return b;
 }
 
@@ -840,8 +846,9 @@ int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, doub
               cudaStream_t s, void* ws, bool profile) {
     const vp_mesh* mesh = nf->mesh;
     const int64_t N = mesh->N, M = nf->M;
-    const bool sym = precision != VP_FP64 && far_sym_applicable(nf, d) && nf->sym;
-    const int splits = sym ? 1 : eval_splits(ctx, M, N, 128);
+    const bool fmm = precision == VP_MIXED_FMM;
+    const bool sym = (precision == VP_MIXED || precision == VP_MIXED_TC) && far_sym_applicable(nf, d) && nf->sym;
+    const int splits = (sym || fmm) ? 1 : eval_splits(ctx, M, N, 128);
     size_t off_q, off_t;
     eval_layout(ctx, nf, d, precision, sym, &off_q, &off_t);
     double* partial = splits > 1 ? (double*)ws : u_dev;
@@ -853,7 +860,14 @@ int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, doub
     if (precision == VP_FP64)
         PROF(ctx, ST_FAR_FP64, s,
              launch_far_fp64(mesh->d_y, mesh->d_W, N, f_dev, d, nf->d_txy, nf->d_tnode, M, partial, splits, s));
-    else if (sym)
+    else if (fmm) {
+        int rc = VP_OK;
+        PROF(ctx, ST_FAR_FMM, s, rc = fmm_far(ctx, nf, f_dev, d, u_dev, qbuf, s));
+        if (rc) {
+            if (!profile) ctx->prof = prof_saved;
+            return rc;
+        }
+    } else if (sym)
         PROF(ctx, ST_FAR_FF, s, launch_far_sym(ctx, nf, mesh->d_W, f_dev, u_dev, qbuf, s));
     else
         PROF(ctx, ST_FAR_FF, s,
@@ -866,11 +880,11 @@ int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, doub
             if (!profile) ctx->prof = prof_saved;
             return rc;
         }
-    } else if (precision == VP_MIXED && d == 1 && nf->d_C2) {
+    } else if ((precision == VP_MIXED || fmm) && d == 1 && nf->d_C2) {
         PROF(ctx, ST_APPLY, s,
              launch_apply_stream(nf->d_row, nf->d_ptri, nf->d_ptgt, nf->d_C2, mesh->nq, f_dev, N, nf->P, M, u_dev,
                                  apply_ws, ctx->d_flag, ctx->sm_count, s));
-    } else if (precision == VP_MIXED && d < APPLY_MANY_MIN_D && nf->d_C2) {
+    } else if ((precision == VP_MIXED || fmm) && d < APPLY_MANY_MIN_D && nf->d_C2) {
         PROF(ctx, ST_APPLY, s,
              launch_apply_f2(nf->d_row, nf->d_ptri, nf->d_C2, mesh->nq, f_dev, N, d, M, u_dev, (float2*)apply_ws, s));
     } else {
@@ -887,14 +901,18 @@ int vp_potential_eval(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t
                       void* stream) {
     if (!ctx_ok(ctx)) return VP_ERR_STATE;
     if (!nf_ok(nf) || nf->ctx != ctx) return vp_set_error(ctx, VP_ERR_STATE, "vp_potential_eval: bad near-field handle");
-    if (!f_dev || !u_dev || d < 1 || d > 256 || precision < VP_FP64 || precision > VP_MIXED_TC)
+    if (!f_dev || !u_dev || d < 1 || d > 256 || precision < VP_FP64 || precision > VP_MIXED_FMM)
         return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_potential_eval: bad arguments");
     DevGuard g(ctx->device);
     if (precision == VP_MIXED_TC && !nf->tc) {
         int rc = tc_plan_build(ctx, const_cast<vp_nf*>(nf), 5, (cudaStream_t)stream);
         if (rc) return rc;
     }
-    if (precision != VP_FP64 && far_sym_applicable(nf, d) && !nf->sym) {
+    if (precision == VP_MIXED_FMM && !nf->fmm) {
+        int rc = fmm_plan_build(ctx, const_cast<vp_nf*>(nf), (cudaStream_t)stream);
+        if (rc) return rc;
+    }
+    if ((precision == VP_MIXED || precision == VP_MIXED_TC) && far_sym_applicable(nf, d) && !nf->sym) {
         int rc = far_sym_plan(ctx, const_cast<vp_nf*>(nf));
         if (rc) return rc;
     }
@@ -948,6 +966,13 @@ int vp_device_status(vp_ctx* ctx, void* stream) {
     VP_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int32_t), s));
     VP_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     return rc;
+}
+
+int vp_nf_fmm_info(const vp_nf* nf, int32_t* leaf_level, int64_t* n_boxes) {
+    if (!nf_ok(nf)) return VP_ERR_STATE;
+    if (leaf_level) *leaf_level = fmm_level(nf);
+    if (n_boxes) *n_boxes = fmm_boxes(nf);
+    return VP_OK;
 }
 
 int vp_nf_tc_info(const vp_nf* nf, int32_t* levels, int64_t* n_tiles, int64_t* n_chunks, int64_t* bytes) {

@@ -20,7 +20,7 @@ struct FFCoords {
 enum VpStage {
     ST_MESH_NODES = 0, ST_TRI_GEOM, ST_TRI_CELLS, ST_CELL_SORT, ST_TARGET_CELLS, ST_LOCATE, ST_LIST_COUNT,
     ST_LIST_FILL, ST_WEIGHTS_SELF, ST_WEIGHTS_NEAR, ST_FF_SPLIT, ST_FAR_FP64, ST_FAR_FF, ST_REDUCE, ST_APPLY,
-    ST_APPLY_TC, ST_WEIGHTS_CURVED, ST_COUNT
+    ST_APPLY_TC, ST_WEIGHTS_CURVED, ST_FAR_FMM, ST_COUNT
 };
 
 struct ProfRec {
@@ -101,6 +101,7 @@ struct TcPlan {
 };
 
 struct SymPlan;   // symmetric far-sum work units (k_far_sym.cu)
+struct FmmPlan;   // quadtree, sorted sources and targets, translation tables (k_fmm.cu)
 
 struct vp_nf {
     vp_ctx* ctx = nullptr;
@@ -123,6 +124,7 @@ struct vp_nf {
     vp_nf_stats_t stats{};
     TcPlan* tc = nullptr;          // tensor-core apply plan (vp_nf_prepare_tc)
     SymPlan* sym = nullptr;        // symmetric far sum over the node targets (built on first use)
+    FmmPlan* fmm = nullptr;        // fast multipole far sum (VP_MIXED_FMM, built on first use)
     int magic = 0x56504e46;
 };
 
@@ -262,6 +264,15 @@ void far_sym_plan_free(SymPlan* p);
 size_t far_sym_ws_bytes(const vp_ctx* ctx, const vp_nf* nf);
 void launch_far_sym(const vp_ctx* ctx, const vp_nf* nf, const double* W, const double* f, double* out, void* ws,
                     cudaStream_t s);
+
+// fast multipole far sum (k_fmm.cu): plan on first use, workspace, evaluation
+// (writes u = far sum, d densities), leaf level of a plan
+int fmm_plan_build(vp_ctx* ctx, vp_nf* nf, cudaStream_t s);
+void fmm_plan_free(FmmPlan* p);
+size_t fmm_ws_bytes(const vp_nf* nf, int d);
+int fmm_far(vp_ctx* ctx, const vp_nf* nf, const double* f, int d, double* u, void* ws, cudaStream_t s);
+int fmm_level(const vp_nf* nf);
+int64_t fmm_boxes(const vp_nf* nf);
 
 // tensor-core apply (k_tc.cu)
 int tc_plan_build(vp_ctx* ctx, vp_nf* nf, int levels, cudaStream_t s);

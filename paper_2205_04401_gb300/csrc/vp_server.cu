@@ -109,6 +109,14 @@ static int build_cold(vp_server* sv, ServedMesh& m) {
         vp_mesh_release(mesh);
         return rc;
     }
+    if (sv->precision == VP_MIXED_FMM) {
+        rc = fmm_plan_build(sv->ctx, nf, sv->build_stream);   // the multipole plan before the first request
+        if (rc) {
+            vp_nf_release(nf);
+            vp_mesh_release(mesh);
+            return rc;
+        }
+    }
     m.mesh = mesh;
     m.nf = nf;
     m.owned = true;
@@ -239,7 +247,8 @@ extern "C" {
 int vp_server_create(vp_ctx* ctx, int32_t slots, int64_t hbm_budget_bytes, int32_t precision, vp_server** out) {
     if (out) *out = nullptr;
     if (!ctx || ctx->magic != 0x56504358) return VP_ERR_STATE;
-    if (!out || slots < 1 || slots > 64 || hbm_budget_bytes <= 0 || (precision != VP_FP64 && precision != VP_MIXED))
+    if (!out || slots < 1 || slots > 64 || hbm_budget_bytes <= 0 ||
+        (precision != VP_FP64 && precision != VP_MIXED && precision != VP_MIXED_FMM))
         return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_server_create: bad arguments");
     DevScope dg(ctx->device);
     vp_server* sv = new (std::nothrow) vp_server();
@@ -273,6 +282,11 @@ int vp_server_register(vp_server* sv, int64_t key, const vp_nf* nf) {
         return vp_set_error(sv->ctx, VP_ERR_STATE, "vp_server_register: bad near-field handle");
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->meshes.count(key)) return vp_set_error(sv->ctx, VP_ERR_INVALID_ARG, "vp_server_register: key in use");
+    if (sv->precision == VP_MIXED_FMM && !nf->fmm) {
+        // the multipole plan is built here, before requests reach the mesh
+        const int rc = fmm_plan_build(sv->ctx, const_cast<vp_nf*>(nf), sv->build_stream);
+        if (rc) return rc;
+    }
     ServedMesh m;
     m.nf = const_cast<vp_nf*>(nf);
     sv->meshes[key] = std::move(m);

@@ -25,6 +25,7 @@ VP_RULE_19_D9 = 19
 VP_FP64 = 0
 VP_MIXED = 1
 VP_MIXED_TC = 2
+VP_MIXED_FMM = 3
 
 _lib = None
 
@@ -100,6 +101,7 @@ SIGNATURES = {
     "vp_nf_tc_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64)]),
     "vp_device_status": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "vp_nf_fmm_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "vp_potential_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
     "vp_potential_eval_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
                                             C.c_void_p]),
@@ -433,6 +435,12 @@ def nf_tc_info(nf: NearField) -> dict:
     _check(load().vp_nf_tc_info(nf.handle, C.byref(lv), C.byref(nt), C.byref(nc), C.byref(nb)), nf.ctx,
            "vp_nf_tc_info")
     return {"levels": lv.value, "n_tiles": nt.value, "n_chunks": nc.value, "bytes": nb.value}
+
+
+def nf_fmm_info(nf: NearField) -> dict:
+    lvl, nb = C.c_int32(), C.c_int64()
+    _check(load().vp_nf_fmm_info(nf.handle, C.byref(lvl), C.byref(nb)), nf.ctx, "vp_nf_fmm_info")
+    return {"leaf_level": lvl.value, "boxes": nb.value}
 
 
 def device_status(ctx: Context, stream=None) -> int:
