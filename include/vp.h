@@ -320,7 +320,10 @@ typedef struct vp_eval_item {
  * vp_batch_launch replays the graph on `stream` (asynchronous).  Results
  * agree with vp_potential_eval item by item up to the order of the far-sum
  * partial sums.  The batch holds device descriptors and charge buffers
- * (about N * 2 * min(d, 8) floats per item) until released. */
+ * (about N * 2 * min(d, 8) floats per item) until released.
+ * precision: VP_FP64, VP_MIXED, or VP_MIXED_FMM (then the graph holds every
+ * item's multipole evaluation in turn, with one workspace for the largest
+ * item; the items' multipole plans are built by vp_batch_create). */
 typedef struct vp_batch vp_batch;
 VP_API int vp_batch_create(vp_ctx* ctx, const vp_eval_item* items, int32_t n, int32_t precision, void* stream,
                            vp_batch** out);

@@ -223,7 +223,14 @@ template <int NQ>
 void apply_stream(const int64_t* row, const int32_t* ptri, const int32_t* ptgt, const float2* C2, const float2* fd2,
                   int64_t P, int64_t M, double* u, double* slots, int32_t* flag, int sm_count, cudaStream_t s) {
     constexpr size_t smem = as_smem_bytes<NQ>();
-    cudaFuncSetAttribute(k_apply_stream<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the shared-memory attribute once per device (not again inside a graph capture)
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaFuncSetAttribute(k_apply_stream<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
     const int64_t ntiles = (P + AS_TILE - 1) / AS_TILE;
     // one CTA per SM (persistent), fewer when there are fewer tiles than warps
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(sm_count, (ntiles + AS_WARPS - 1) / AS_WARPS));

@@ -192,6 +192,7 @@ struct vp_batch {
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    void* fmm_ws = nullptr;        // VP_MIXED_FMM: one workspace, items run in turn
     int magic = 0x56504254;
 };
 
@@ -238,15 +239,55 @@ static void free_batch(vp_batch* b) {
     if (b->d_apply_begin) cudaFree(b->d_apply_begin);
     if (b->qbuf) cudaFree(b->qbuf);
     if (b->counters) cudaFree(b->counters);
+    if (b->fmm_ws) cudaFree(b->fmm_ws);
     b->magic = 0;
     delete b;
+}
+
+// VP_MIXED_FMM batches: the multipole plans of the items (built here when
+// missing), one workspace for the largest item, and every item's evaluation
+// (multipole far sum, then the corrections) captured in turn into one graph.
+static int batch_create_fmm(vp_ctx* ctx, vp_batch* b, cudaStream_t s) {
+    size_t ws = 0;
+    for (const auto& it : b->items) {
+        vp_nf* nf = const_cast<vp_nf*>(it.nf);
+        if (!nf->fmm) {
+            const int rc = fmm_plan_build(ctx, nf, s);
+            if (rc) return rc;
+        }
+        ws = std::max(ws, eval_ws_bytes(ctx, nf, it.d, VP_MIXED_FMM));
+    }
+    if (cudaMalloc(&b->fmm_ws, std::max<size_t>(ws, 256)) != cudaSuccess)
+        return vp_set_error(ctx, VP_ERR_OOM, "vp_batch_create: workspace");
+    // one evaluation outside the capture (first-use set-up of the kernels)
+    const vp_eval_item& i0 = b->items[0];
+    int rc = eval_impl(ctx, i0.nf, i0.f_dev, i0.d, i0.u_dev, VP_MIXED_FMM, s, b->fmm_ws, false);
+    if (rc) return rc;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return vp_set_error(ctx, VP_ERR_CUDA, "vp_batch_create: warm-up");
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return vp_set_error(ctx, VP_ERR_CUDA, "vp_batch_create: stream");
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return vp_set_error(ctx, VP_ERR_CUDA, "vp_batch_create: capture");
+    for (const auto& it : b->items) {
+        rc = eval_impl(ctx, it.nf, it.f_dev, it.d, it.u_dev, VP_MIXED_FMM, b->cap, b->fmm_ws, false);
+        if (rc) break;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->cap, &g);
+    b->graph = g;
+    if (rc) return rc;
+    if (ec != cudaSuccess || cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+        return vp_set_error(ctx, VP_ERR_CUDA, "vp_batch_create: graph");
+    b->total_targets = 0;
+    for (const auto& it : b->items) b->total_targets += it.nf->M;
+    return VP_OK;
 }
 
 extern "C" int vp_batch_create(vp_ctx* ctx, const vp_eval_item* items, int32_t n, int32_t precision, void* stream,
                                vp_batch** out) {
     if (out) *out = nullptr;
     if (!ctx || ctx->magic != 0x56504358) return VP_ERR_STATE;
-    if (!out || n < 1 || !items || (precision != VP_FP64 && precision != VP_MIXED))
+    if (!out || n < 1 || !items || (precision != VP_FP64 && precision != VP_MIXED && precision != VP_MIXED_FMM))
         return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_batch_create: bad arguments");
     for (int32_t i = 0; i < n; i++) {
         const vp_eval_item& it = items[i];
@@ -263,6 +304,15 @@ extern "C" int vp_batch_create(vp_ctx* ctx, const vp_eval_item* items, int32_t n
     b->precision = precision;
     b->items.assign(items, items + n);
     int rc = VP_OK;
+    if (precision == VP_MIXED_FMM) {
+        rc = batch_create_fmm(ctx, b, s);
+        if (rc) {
+            free_batch(b);
+            return rc;
+        }
+        *out = b;
+        return VP_OK;
+    }
     // far-sum entries per chunk width, charge buffers, apply descriptors
     std::vector<BatchFar> far[4];
     std::vector<int64_t> far_begin[4];
