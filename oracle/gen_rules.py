@@ -233,6 +233,36 @@ def what_for(X, Y, W, degree):
     return best
 
 
+def conical_rule(degree):
+    """Conical-product Gauss far rule of total degree `degree` (Section 4.2's
+    higher far orders): m = (degree + 3) // 2 Gauss-Legendre points u_i with
+    weights a_i on [0, 1]; node k = i m + j at (u_i, (1 - u_i) u_j) with weight
+    a_i a_j (1 - u_i), the collapse (u, v) -> (u, (1 - u) v) of the square onto
+    the simplex, exact for total degree 2m - 2.
+
+    w-hat (Eq. rho0): over the three edges, the largest weight among the
+    (degree + 2) // 2 nodes nearest the edge, nodes whose distance equals that
+    of the last of them to 1e-9 relative included (the product structure ties
+    distances exactly, so an index tie-break would depend on rounding).
+    Returns a dict of floats: x, y, w, degree, what."""
+    m = (degree + 3) // 2
+    X, Y, W = duffy_rule(m)
+    k = (degree + 2) // 2
+    best = mp.mpf(0)
+    n = len(X)
+    for e in range(3):
+        if e == 0:
+            dist = list(Y)
+        elif e == 1:
+            dist = list(X)
+        else:
+            dist = [(1 - X[i] - Y[i]) / mp.sqrt(2) for i in range(n)]
+        cut = sorted(dist)[k - 1] * (1 + mp.mpf(10) ** -9)
+        best = max(best, max(W[i] for i in range(n) if dist[i] <= cut))
+    return dict(degree=degree, x=[float(v) for v in X], y=[float(v) for v in Y], w=[float(v) for v in W],
+                what=float(best))
+
+
 def _shifted_legendre_coeffs(n):
     # P_n(2x-1) = sum_k (-1)^(n+k) C(n,k) C(n+k,k) x^k
     return [Fraction((-1) ** (n + k) * math.comb(n, k) * math.comb(n + k, k)) for k in range(n + 1)]

@@ -20,7 +20,7 @@
 
 #define NB 15 /* dim P_4 */
 #define TWO_PI 6.283185307179586476925286766559
-#define MAXQ 64
+#define MAXQ 1024
 
 typedef struct {
     /* far rule (Section 3.2): nq nodes on the reference simplex */

@@ -29,7 +29,7 @@ _BUILD = os.path.join(HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 NB = 15
-MAXQ = 64
+MAXQ = 1024
 
 
 class OrParams(C.Structure):
@@ -104,13 +104,16 @@ U8 = C.c_uint8
 
 
 class Oracle:
-    """FP64 reference evaluator for one far rule ('far16' or 'far19')."""
+    """FP64 reference evaluator for one far rule: 'far16', 'far19', or a rule
+    dict (x, y, w, degree, what) such as gen_rules.conical_rule(n)."""
 
-    def __init__(self, rule: str = "far19", eps: float = 1e-12, far_cn: float = 1.0, near_cn: float = 12.0,
+    def __init__(self, rule="far19", eps: float = 1e-12, far_cn: float = 1.0, near_cn: float = 12.0,
                  depth_cap: int = 30, nl: int = 16, tables=None):
         t = tables or load_tables()
         self.tables = t
-        fr, nr, gg = t[rule], t["near49"], t["ggq8"]
+        fr = t[rule] if isinstance(rule, str) else {k: (np.asarray(v, np.float64) if isinstance(v, list) else v)
+                                                    for k, v in rule.items()}
+        nr, gg = t["near49"], t["ggq8"]
         gl = t["gl16"] if nl == 16 else t["gl7"]
         p = OrParams()
         p.nq = len(fr["w"])

@@ -70,6 +70,26 @@ def test_f1_outside_target(cfg1, o16):
     assert np.abs(u[0] - ex).max() < 1e-11
 
 
+# C_N of Table "C_N values" for the far orders the conical rules stand in for
+CN_TABLE = {12: 12.0, 20: 6.8, 25: 3.0, 30: 2.5, 40: 2.0, 50: 1.0}
+
+
+@pytest.mark.parametrize("degree", [12, 30])
+def test_f1_conical_far_rule_closed_form(cfg1, tables, degree):
+    """The whole pipeline with a higher-order far rule (more than 32 nodes per
+    triangle) and the paper's C_N: f = 1 still matches the closed form."""
+    from oracle import gen_rules
+    from paper_2205_04401_gb300 import inputs
+    mesh, _ = cfg1
+    o = Oracle(gen_rules.conical_rule(degree), tables=tables, far_cn=CN_TABLE[degree])
+    extra = inputs.random_interior_points(mesh, 40, 5)
+    s = o.setup(mesh.vxy, mesh.tri, node_targets=False, extra=extra)
+    u, info = o.potential(s, np.ones((1, s["N"])))
+    ex = np.array([X.polygon_f1(s["vxy"], s["tri"], p) for p in extra])
+    assert np.abs(u[0] - ex).max() < 1e-11
+    assert info["capped"] == 0
+
+
 def _poly_cases():
     # (u_p, grad u_p, lap u_p) with lap of degree <= 4
     return [
@@ -92,6 +112,23 @@ def test_degree4_density_green_identity(disk_setup, o16, case):
     u, _ = o16.potential(s, f, targets=idx)
     edges = [(s["vxy"][a], s["vxy"][b]) for a, b in X.boundary_edges(s["tri"])]
     ex = np.array([X.green_volume(s["txy"][i], edges, up, gup) for i in idx])
+    assert np.abs(u[0] - ex).max() < 2e-11 * max(1.0, np.abs(ex).max())
+
+
+def test_degree4_density_green_identity_conical(cfg1, tables):
+    """Green's identity with a degree-20 conical far rule (121 nodes): the
+    P_4 projection through the larger rule is exact as well."""
+    from oracle import gen_rules
+    from paper_2205_04401_gb300 import inputs
+    mesh, _ = cfg1
+    o = Oracle(gen_rules.conical_rule(20), tables=tables, far_cn=CN_TABLE[20])
+    extra = inputs.random_interior_points(mesh, 12, 8)
+    s = o.setup(mesh.vxy, mesh.tri, node_targets=False, extra=extra)
+    up, gup, lap = _poly_cases()[1]
+    f = lap(s["yxy"])[None, :]
+    u, _ = o.potential(s, f)
+    edges = [(s["vxy"][a], s["vxy"][b]) for a, b in X.boundary_edges(s["tri"])]
+    ex = np.array([X.green_volume(p, edges, up, gup) for p in extra])
     assert np.abs(u[0] - ex).max() < 2e-11 * max(1.0, np.abs(ex).max())
 
 

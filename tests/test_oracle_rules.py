@@ -109,3 +109,50 @@ def test_far_rule_projection_exact(tables):
     fr = tables["far19"]
     K = o.basis(fr["x"], fr["y"])
     assert np.abs((K * fr["w"][:, None]).T @ K - np.eye(15)).max() < 1e-13
+
+
+CONICAL = [8, 12, 20, 25, 30, 40, 50]
+
+
+@pytest.mark.parametrize("degree", CONICAL)
+def test_conical_rule_exact(degree):
+    """Higher far orders for the offloading of Section 4.2: the conical-product
+    rule of total degree n integrates every monomial of degree <= n exactly
+    (closed form i! j! / (i + j + 2)!), has positive weights, interior nodes
+    and m^2 nodes, m = (n + 3) // 2, in the documented order (k = i m + j)."""
+    from oracle import gen_rules
+    r = gen_rules.conical_rule(degree)
+    x, y, w = (np.array(r[k]) for k in "xyw")
+    m = (degree + 3) // 2
+    assert len(w) == m * m and r["degree"] == degree
+    assert np.all(w > 0) and np.all(x > 0) and np.all(y > 0) and np.all(x + y < 1)
+    assert max_moment_error(x, y, w, degree) < 1e-15
+    # the row structure: x constant along j, y / (1 - x) the same along i
+    X, Y = x.reshape(m, m), y.reshape(m, m)
+    assert np.all(X == X[:, :1]) and np.all(np.diff(X[:, 0]) > 0)
+    assert np.abs(Y / (1 - X) - Y[0] / (1 - X[0])).max() < 1e-13
+
+
+@pytest.mark.parametrize("degree", CONICAL)
+def test_conical_what(degree):
+    """w-hat of a conical rule is one of its weights and at least the largest
+    weight of the row nearest the edge x = 0 (its (n + 2) // 2 nearest nodes
+    all lie on that row, at the same distance u_0)."""
+    from oracle import gen_rules
+    r = gen_rules.conical_rule(degree)
+    w = np.array(r["w"])
+    m = (degree + 3) // 2
+    assert r["what"] in set(w.tolist())
+    assert r["what"] >= w[:m].max()
+    assert r["what"] <= w.max()
+
+
+def test_conical_projection_exact():
+    """The P_4 projection with a conical far rule has an identity Gram matrix."""
+    from oracle import gen_rules
+    from oracle.oracle import Oracle
+    r = gen_rules.conical_rule(20)
+    o = Oracle(r)
+    x, y, w = (np.array(r[k]) for k in "xyw")
+    K = o.basis(x, y)
+    assert np.abs((K * w[:, None]).T @ K - np.eye(15)).max() < 1e-13
