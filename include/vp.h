@@ -57,10 +57,30 @@ typedef enum vp_status {
     VP_ERR_STATE = -8            /* handle used with the wrong context or after release */
 } vp_status;
 
-/* Far-field quadrature rules on the reference simplex (Section 3.2).  Both
- * are S3-symmetric positive-interior rules derived from their moment
- * equations: 16 nodes exact to degree 8, 19 nodes exact to degree 9. */
+/* Far-field quadrature rules on the reference simplex (Section 3.2).  The two
+ * built-in rules are S3-symmetric positive-interior rules derived from their
+ * moment equations: 16 nodes exact to degree 8, 19 nodes exact to degree 9.
+ * VP_RULE_CONICAL(n), n in [8, 50], is the conical-product Gauss rule of total
+ * degree n for raising the far order (offloading, Section 4.2): with the
+ * m = (n + 3)/2 (integer division) Gauss-Legendre points u_i and weights a_i
+ * on [0, 1], node k = i m + j (i, j < m) is
+ *   x_k = u_i,  y_k = (1 - u_i) u_j,  w_k = a_i a_j (1 - u_i),
+ * m^2 nodes, positive weights, all inside the simplex, exact to degree
+ * 2m - 2 >= n.  Its w-hat (Eq. rho0) is the largest weight among the
+ * (n + 2)/2 nodes nearest an edge, maximised over the three edges, with the
+ * nodes tied (to 1e-9 relative) with the last of them included.  The rule is
+ * made on the host on first use in a context and kept until vp_destroy. */
 typedef enum vp_rule { VP_RULE_16_D8 = 16, VP_RULE_19_D9 = 19 } vp_rule;
+#define VP_RULE_CONICAL(n) (1000 + (n))
+#define VP_RULE_CONICAL_MIN 8
+#define VP_RULE_CONICAL_MAX 50
+
+/* The nodes, weights, w-hat and degree of a far rule (host only, no device
+ * needed).  x, y, w: host arrays of cap entries (each may be NULL); *n gets
+ * the node count.  With cap < *n and any array non-NULL: INVALID_ARG.
+ * Errors: INVALID_ARG (unknown rule). */
+VP_API int vp_far_rule(int32_t rule, double* x, double* y, double* w, double* what, int32_t* degree, int32_t cap,
+                       int32_t* n);
 
 /* Arithmetic of vp_potential_eval.  VP_FP64: FP64 everywhere.  VP_MIXED: the
  * far sum in compensated FP32 (float-float coordinates and logarithm, FP64
@@ -139,8 +159,12 @@ VP_API int vp_last_error(const vp_ctx* ctx, char* buf, int32_t len);
  * vxy:  host, [nv][2] float64 vertex coordinates.
  * tri:  host, [nt][3] int32 vertex indices; clockwise triangles are made
  *       counter-clockwise by swapping their 2nd and 3rd vertex.
- * rule: VP_RULE_16_D8 or VP_RULE_19_D9.
- * Errors: INVALID_ARG (index out of range, nt < 1), NONFINITE, DEGENERATE_TRI.
+ * rule: VP_RULE_16_D8, VP_RULE_19_D9 or VP_RULE_CONICAL(n).  Meshes on a
+ *       conical rule are evaluated with the FP64 correction apply in every
+ *       precision, and VP_MIXED_TC, vp_nf_prepare_tc and the server refuse
+ *       them (INVALID_ARG).
+ * Errors: INVALID_ARG (index out of range, nt < 1, nt * nq > INT32_MAX),
+ * NONFINITE, DEGENERATE_TRI.
  * The call synchronises `stream` before returning (it validates on device). */
 VP_API int vp_mesh_upload(vp_ctx* ctx, const double* vxy, int64_t nv, const int32_t* tri, int64_t nt, int32_t rule,
                    void* stream, vp_mesh** out);

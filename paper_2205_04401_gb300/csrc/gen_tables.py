@@ -260,11 +260,9 @@ def _legendre_poly_coeffs(n):
     return p1
 
 
-def projection_matrix(pts):
-    """Q[k][i] = w_k sum_j Hinv[i][j] L_j(x_k, y_k): maps the moments
-    mu_i = int_T G L_i(rho_T^-1 y) dA to the nodal correction weights of the
-    discrete L2 projection onto P_4 with the far rule (exact Gram H, since
-    the rule has degree >= 8)."""
+def leg15_gram_inverse():
+    """Inverse of the Gram matrix H_ij = int L_i L_j dA of the tensor-Legendre
+    basis over the reference simplex (exact rationals, then inverted)."""
     from fractions import Fraction
     idx = legendre_tensor_index()
     # L_ab as polynomials in (x, y): P_a(3x - 1) expanded to monomials
@@ -298,6 +296,17 @@ def projection_matrix(pts):
             g = gram(i, j)
             H[i, j] = mp.mpf(g.numerator) / g.denominator
     Hinv = mp.inverse(H)
+    return Hinv
+
+
+def projection_matrix(pts):
+    """Q[k][i] = w_k sum_j Hinv[i][j] L_j(x_k, y_k): maps the moments
+    mu_i = int_T G L_i(rho_T^-1 y) dA to the nodal correction weights of the
+    discrete L2 projection onto P_4 with the far rule (exact Gram H, since
+    the rule has degree >= 8)."""
+    idx = legendre_tensor_index()
+    n = len(idx)
+    Hinv = leg15_gram_inverse()
     def L(x, y):
         def P(k, t):
             return sum(c * t ** e for e, c in enumerate(_legendre_poly_coeffs(k)))
@@ -334,6 +343,8 @@ def main():
         arr(f"VP_{name.upper()}_W", [p[2] for p in pts])
         out.append(f"static const double VP_{name.upper()}_WHAT = {cdbl(what(pts, deg))};")
         out.append(f"static const int VP_{name.upper()}_DEGREE = {deg};")
+    Hinv = leg15_gram_inverse()
+    arr("VP_LEG15_HINV", [Hinv[i, j] for i in range(Hinv.rows) for j in range(Hinv.cols)])
     pts = duffy(7)
     arr("VP_NEAR49_X", [p[0] for p in pts])
     arr("VP_NEAR49_Y", [p[1] for p in pts])

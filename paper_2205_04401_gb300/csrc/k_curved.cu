@@ -33,7 +33,7 @@ namespace {
 // straight node kernel; a curved triangle given clockwise is an error (its
 // curve would run along the wrong side).
 __global__ void k_mesh_nodes_curved(const double* __restrict__ vxy, int64_t nv, const int32_t* __restrict__ tri,
-                                    int64_t nt, CurveDev cv, const VpTables* __restrict__ tab, int rule,
+                                    int64_t nt, CurveDev cv, FarRuleDev fr,
                                     const double* __restrict__ tv, double* __restrict__ y, double* __restrict__ W,
                                     int32_t* flag) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -49,13 +49,13 @@ __global__ void k_mesh_nodes_curved(const double* __restrict__ vxy, int64_t nv, 
     double v[6];
 #pragma unroll
     for (int q = 0; q < 6; q++) v[q] = tv[6 * t + q];
-    const int nq = tab->nq[rule];
+    const int nq = fr.nq;
     for (int k = 0; k < nq; k++) {
         const int64_t j = t * nq + k;
         double det;
-        geom_map_rn(v, ax, cv.K, tab->fx[rule][k], tab->fy[rule][k], y + 2 * j, nullptr, &det);
+        geom_map_rn(v, ax, cv.K, fr.x[k], fr.y[k], y + 2 * j, nullptr, &det);
         if (!(det > 0.0)) atomicOr(flag, VP_DEV_ERR_DEGEN);
-        W[j] = rn_mul(tab->fw[rule][k], det);
+        W[j] = rn_mul(fr.w[k], det);
     }
 }
 
@@ -384,11 +384,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_self_curved(WeightsArgs 
 }  // namespace
 
 void launch_mesh_nodes_curved(const double* vxy, int64_t nv, const int32_t* tri, int64_t nt, CurveDev cv,
-                              const VpTables* tab, int rule, const double* tv, double* y, double* W, int32_t* flag,
-                              cudaStream_t s) {
+                              FarRuleDev fr, const double* tv, double* y, double* W, int32_t* flag, cudaStream_t s) {
     if (nt > 0)
-        k_mesh_nodes_curved<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(vxy, nv, tri, nt, cv, tab, rule, tv, y, W,
-                                                                          flag);
+        k_mesh_nodes_curved<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(vxy, nv, tri, nt, cv, fr, tv, y, W, flag);
 }
 
 void launch_curved_bbox(int64_t nt, CurveDev cv, double* bbox, cudaStream_t s) {

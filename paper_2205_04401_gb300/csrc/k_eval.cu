@@ -86,11 +86,14 @@ __global__ void k_reduce_splits(const double* __restrict__ partial, int splits, 
 // u[d0 + k][t] += sum C[e] f[d0 + k][T_p nq + node].  Eight entries per lane
 // are in flight (predicated, no tail loop) and u[t] is fetched before the
 // row, so a warp has up to 16 independent loads outstanding.
+// NQ = 0: nodes per triangle given at run time (generated far rules).
 template <int NQ, int D>
 __global__ void __launch_bounds__(256) k_apply_rows(const int64_t* __restrict__ row, const int32_t* __restrict__ ptri,
                                                     const double* __restrict__ C, const double* __restrict__ f,
-                                                    int64_t N, int d, int d0, int64_t M, double* __restrict__ u) {
+                                                    int64_t N, int d, int d0, int64_t M, double* __restrict__ u,
+                                                    int nq_rt) {
     constexpr int U = 8;
+    const int nq = NQ > 0 ? NQ : nq_rt;
     const int lane = threadIdx.x & 31;
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= M) return;
@@ -100,10 +103,10 @@ __global__ void __launch_bounds__(256) k_apply_rows(const int64_t* __restrict__ 
         for (int k = 0; k < D; k++)
             if (k == lane) u0[k] = d0 + k < d ? u[(int64_t)(d0 + k) * M + t] : 0.0;
     }
-    // row-local 32-bit indexing: entry r of the row is node r % NQ of pair r / NQ
+    // row-local 32-bit indexing: entry r of the row is node r % nq of pair r / nq
     const int64_t p0 = row[t];
-    const int len = (int)((row[t + 1] - p0) * NQ);
-    const double* __restrict__ Crow = C + p0 * NQ;
+    const int len = (int)((row[t + 1] - p0) * nq);
+    const double* __restrict__ Crow = C + p0 * nq;
     const int32_t* __restrict__ prow = ptri + p0;
     double s[D];
 #pragma unroll
@@ -115,9 +118,9 @@ __global__ void __launch_bounds__(256) k_apply_rows(const int64_t* __restrict__ 
         for (int i = 0; i < U; i++) {
             const int ri = r + 32 * i;
             const bool ok = ri < len;
-            const int pl = ri / NQ;
+            const int pl = ri / nq;
             c[i] = ok ? Crow[ri] : 0.0;
-            src[i] = ok ? prow[pl] * NQ + (ri - pl * NQ) : 0;
+            src[i] = ok ? prow[pl] * nq + (ri - pl * nq) : 0;
         }
 #pragma unroll
         for (int i = 0; i < U; i++)
@@ -248,11 +251,12 @@ __global__ void k_transpose_f(const double* __restrict__ f, int d, int64_t N, do
 template <int NQ, int DB>
 __global__ void __launch_bounds__(256) k_apply_many(const int64_t* __restrict__ row, const int32_t* __restrict__ ptri,
                                                     const double* __restrict__ C, const double* __restrict__ fT,
-                                                    int d, int64_t M, double* __restrict__ u) {
+                                                    int d, int64_t M, double* __restrict__ u, int nq_rt) {
     const int lane = threadIdx.x & 31;
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= M) return;
-    const int64_t e0 = row[t] * NQ, e1 = row[t + 1] * NQ;
+    const int nq = NQ > 0 ? NQ : nq_rt;
+    const int64_t e0 = row[t] * nq, e1 = row[t + 1] * nq;
     double s[DB];
 #pragma unroll
     for (int i = 0; i < DB; i++) s[i] = 0.0;
@@ -262,9 +266,9 @@ __global__ void __launch_bounds__(256) k_apply_many(const int64_t* __restrict__ 
         int64_t mysrc = 0;
         if (lane < n) {
             const int64_t e = base + lane;
-            const int64_t p = e / NQ;
+            const int64_t p = e / nq;
             myc = C[e];
-            mysrc = ((int64_t)ptri[p] * NQ + (e - p * NQ)) * d;
+            mysrc = ((int64_t)ptri[p] * nq + (e - p * nq)) * d;
         }
         for (int j = 0; j < n; j++) {
             const double c = __shfl_sync(0xffffffffu, myc, j);
@@ -285,15 +289,15 @@ __global__ void __launch_bounds__(256) k_apply_many(const int64_t* __restrict__ 
 
 template <int NQ>
 void apply_rows(const int64_t* row, const int32_t* ptri, const double* C, const double* f, int64_t N, int d,
-                int64_t M, double* u, cudaStream_t s) {
+                int64_t M, double* u, int nq, cudaStream_t s) {
     const unsigned grid = (unsigned)((M * 32 + 255) / 256);
     for (int d0 = 0; d0 < d;) {
         const int D = pick_chunk(d - d0);
         switch (D) {
-            case 8: k_apply_rows<NQ, 8><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u); break;
-            case 4: k_apply_rows<NQ, 4><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u); break;
-            case 2: k_apply_rows<NQ, 2><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u); break;
-            default: k_apply_rows<NQ, 1><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u); break;
+            case 8: k_apply_rows<NQ, 8><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u, nq); break;
+            case 4: k_apply_rows<NQ, 4><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u, nq); break;
+            case 2: k_apply_rows<NQ, 2><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u, nq); break;
+            default: k_apply_rows<NQ, 1><<<grid, 256, 0, s>>>(row, ptri, C, f, N, d, d0, M, u, nq); break;
         }
         d0 += D;
     }
@@ -317,13 +321,13 @@ void apply_rows_f2(const int64_t* row, const int32_t* ptri, const float2* C2, co
 
 template <int NQ>
 void apply_many(const int64_t* row, const int32_t* ptri, const double* C, const double* fT, int d, int64_t M,
-                double* u, cudaStream_t s) {
+                double* u, int nq, cudaStream_t s) {
     const unsigned grid = (unsigned)((M * 32 + 255) / 256);
     const int db = (d + 31) / 32;
-    if (db <= 1) k_apply_many<NQ, 1><<<grid, 256, 0, s>>>(row, ptri, C, fT, d, M, u);
-    else if (db <= 2) k_apply_many<NQ, 2><<<grid, 256, 0, s>>>(row, ptri, C, fT, d, M, u);
-    else if (db <= 4) k_apply_many<NQ, 4><<<grid, 256, 0, s>>>(row, ptri, C, fT, d, M, u);
-    else k_apply_many<NQ, 8><<<grid, 256, 0, s>>>(row, ptri, C, fT, d, M, u);
+    if (db <= 1) k_apply_many<NQ, 1><<<grid, 256, 0, s>>>(row, ptri, C, fT, d, M, u, nq);
+    else if (db <= 2) k_apply_many<NQ, 2><<<grid, 256, 0, s>>>(row, ptri, C, fT, d, M, u, nq);
+    else if (db <= 4) k_apply_many<NQ, 4><<<grid, 256, 0, s>>>(row, ptri, C, fT, d, M, u, nq);
+    else k_apply_many<NQ, 8><<<grid, 256, 0, s>>>(row, ptri, C, fT, d, M, u, nq);
 }
 
 // ------------------------------------------------------ float-float far
@@ -417,11 +421,13 @@ void launch_apply_fp64(const int64_t* row, const int32_t* ptri, const double* C,
     if (d >= APPLY_MANY_MIN_D && fT) {
         dim3 tg((unsigned)((N + 31) / 32), (unsigned)((d + 31) / 32)), tb(32, 8);
         k_transpose_f<<<tg, tb, 0, s>>>(f, d, N, fT);
-        if (nq == 19) apply_many<19>(row, ptri, C, fT, d, M, u, s);
-        else apply_many<16>(row, ptri, C, fT, d, M, u, s);
+        if (nq == 19) apply_many<19>(row, ptri, C, fT, d, M, u, nq, s);
+        else if (nq == 16) apply_many<16>(row, ptri, C, fT, d, M, u, nq, s);
+        else apply_many<0>(row, ptri, C, fT, d, M, u, nq, s);
     } else {
-        if (nq == 19) apply_rows<19>(row, ptri, C, f, N, d, M, u, s);
-        else apply_rows<16>(row, ptri, C, f, N, d, M, u, s);
+        if (nq == 19) apply_rows<19>(row, ptri, C, f, N, d, M, u, nq, s);
+        else if (nq == 16) apply_rows<16>(row, ptri, C, f, N, d, M, u, nq, s);
+        else apply_rows<0>(row, ptri, C, f, N, d, M, u, nq, s);
     }
 }
 

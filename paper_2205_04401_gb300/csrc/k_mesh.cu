@@ -8,7 +8,7 @@ namespace {
 //   y = A + (xi_k (B - A) + eta_k (C - A)),  W_j = w_k J_T,
 // evaluated with round-to-nearest operations in this order.
 __global__ void k_mesh_nodes(const double* __restrict__ vxy, int64_t nv, const int32_t* __restrict__ tri, int64_t nt,
-                             const VpTables* __restrict__ tab, int rule, double* __restrict__ tv, double* __restrict__ J,
+                             FarRuleDev fr, double* __restrict__ tv, double* __restrict__ J,
                              double* __restrict__ y, double* __restrict__ W, int32_t* flag) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
@@ -37,22 +37,22 @@ __global__ void k_mesh_nodes(const double* __restrict__ vxy, int64_t nv, const i
     double* v = tv + 6 * t;
     v[0] = Ax; v[1] = Ay; v[2] = Bx; v[3] = By; v[4] = Cx; v[5] = Cy;
     J[t] = o;
-    const int nq = tab->nq[rule];
+    const int nq = fr.nq;
     const double ex = rn_sub(Bx, Ax), ey = rn_sub(By, Ay);
     const double fx = rn_sub(Cx, Ax), fy = rn_sub(Cy, Ay);
     for (int k = 0; k < nq; k++) {
-        const double xi = tab->fx[rule][k], eta = tab->fy[rule][k];
+        const double xi = fr.x[k], eta = fr.y[k];
         int64_t j = t * nq + k;
         y[2 * j] = rn_add(Ax, rn_add(rn_mul(xi, ex), rn_mul(eta, fx)));
         y[2 * j + 1] = rn_add(Ay, rn_add(rn_mul(xi, ey), rn_mul(eta, fy)));
-        W[j] = rn_mul(tab->fw[rule][k], o);
+        W[j] = rn_mul(fr.w[k], o);
     }
 }
 
 }  // namespace
 
-void launch_mesh_nodes(const double* vxy, int64_t nv, const int32_t* tri, int64_t nt, const VpTables* tab, int rule,
-                       double* tv, double* J, double* y, double* W, int32_t* flag, cudaStream_t s) {
+void launch_mesh_nodes(const double* vxy, int64_t nv, const int32_t* tri, int64_t nt, FarRuleDev fr, double* tv,
+                       double* J, double* y, double* W, int32_t* flag, cudaStream_t s) {
     if (nt <= 0) return;
-    k_mesh_nodes<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(vxy, nv, tri, nt, tab, rule, tv, J, y, W, flag);
+    k_mesh_nodes<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(vxy, nv, tri, nt, fr, tv, J, y, W, flag);
 }

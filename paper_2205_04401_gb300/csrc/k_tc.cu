@@ -685,6 +685,8 @@ void tc_plan_free(TcPlan* p) {
 int tc_plan_build(vp_ctx* ctx, vp_nf* nf, int L, cudaStream_t s) {
     if (L < 3 || L > TC_LMAX) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_nf_prepare_tc: levels must be 3, 4 or 5");
     const vp_mesh* mesh = nf->mesh;
+    if (mesh->rule.builtin < 0)
+        return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_nf_prepare_tc: the tensor-core apply takes the 16- and 19-node rules");
     const int64_t M = nf->M;
     const int nq = mesh->nq;
     TcPlan* p = new TcPlan();

@@ -323,29 +323,31 @@ __device__ __forceinline__ void finish_pair_f2(const WeightsArgs& a, const Weigh
     for (int q = 0; q < VP_NB; q++) v[q] = f2_fast(mh[q], ml[q]);
     v[15] = {0.f, 0.f};
     const f2 mine = reduce_scatter16_f2(v, lane);
-    const int k = lane < a.nq ? lane : 0;
-    const float2* Qk = a.tab->Q2[a.rule][k];
-    f2 s = {0.f, 0.f};
+    for (int k0 = 0; k0 < a.nq; k0 += 32) {   // node k0 + lane of every group of 32
+        const int k = k0 + lane;
+        const float2* Qk = a.Q2 + (k < a.nq ? k : 0) * VP_NB;
+        f2 s = {0.f, 0.f};
 #pragma unroll
-    for (int q = 0; q < VP_NB; q++) {
-        const f2 mq = {__shfl_sync(0xffffffffu, mine.h, 2 * q), __shfl_sync(0xffffffffu, mine.l, 2 * q)};
-        const float2 Q = Qk[q];
-        s = f2_add(s, f2_mul({Q.x, Q.y}, mq));
-    }
-    if (lane < a.nq) {
-        if (lane != own) {
-            const int64_t j = (int64_t)T * a.nq + lane;
-            const float4 X = b.x2[t], Y = b.y2[j];
-            const f2 dx = f2_add({X.x, X.y}, {-Y.x, -Y.y}), dy = f2_add({X.z, X.w}, {-Y.z, -Y.w});
-            const f2 r2 = f2_add(f2_sqr(dx), f2_sqr(dy));
-            f2 lg;
-            if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);
-            else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
-            const float2 wq = b.wq2[j];
-            s = f2_add(s, f2_neg(f2_mul(lg, {wq.x, wq.y})));
+        for (int q = 0; q < VP_NB; q++) {
+            const f2 mq = {__shfl_sync(0xffffffffu, mine.h, 2 * q), __shfl_sync(0xffffffffu, mine.l, 2 * q)};
+            const float2 Q = Qk[q];
+            s = f2_add(s, f2_mul({Q.x, Q.y}, mq));
         }
-        a.C[p * a.nq + lane] = f2_to_d(s);
-        if (a.C2) a.C2[p * a.nq + lane] = make_float2(s.h, s.l);
+        if (k < a.nq) {
+            if (k != own) {
+                const int64_t j = (int64_t)T * a.nq + k;
+                const float4 X = b.x2[t], Y = b.y2[j];
+                const f2 dx = f2_add({X.x, X.y}, {-Y.x, -Y.y}), dy = f2_add({X.z, X.w}, {-Y.z, -Y.w});
+                const f2 r2 = f2_add(f2_sqr(dx), f2_sqr(dy));
+                f2 lg;
+                if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);
+                else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
+                const float2 wq = b.wq2[j];
+                s = f2_add(s, f2_neg(f2_mul(lg, {wq.x, wq.y})));
+            }
+            a.C[p * a.nq + k] = f2_to_d(s);
+            if (a.C2) a.C2[p * a.nq + k] = make_float2(s.h, s.l);
+        }
     }
 }
 

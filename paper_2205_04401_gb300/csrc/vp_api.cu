@@ -261,6 +261,7 @@ void vp_destroy(vp_ctx* ctx) {
     DevGuard g(ctx->device);
     cudaDeviceSynchronize();
     if (ctx->d_tables) cudaFree(ctx->d_tables);
+    far_rules_free(ctx);
     if (ctx->d_flag) cudaFree(ctx->d_flag);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->stage) cudaFree(ctx->stage);
@@ -298,10 +299,13 @@ static int mesh_upload_impl(vp_ctx* ctx, const double* d_vxy, int64_t nv, const 
     m->K = cin.K;
     m->nt = nt;
     m->nv = nv;
-    m->rule_index = rule == VP_RULE_16_D8 ? 0 : 1;
-    m->nq = rule;
+    int rc = far_rule_get(ctx, rule, &m->rule);
+    if (rc != VP_OK) {
+        vp_mesh_release(m);
+        return rc;
+    }
+    m->nq = m->rule.dev.nq;
     m->N = nt * m->nq;
-    int rc = VP_OK;
     double* d_red = nullptr;
     cudaError_t e = dev_alloc(&m->d_tv, 6 * nt);
     if (e == cudaSuccess) e = dev_alloc(&m->d_J, nt);
@@ -312,12 +316,11 @@ static int mesh_upload_impl(vp_ctx* ctx, const double* d_vxy, int64_t nv, const 
     if (rc == VP_OK) {
         cudaMemsetAsync(ctx->d_flag, 0, sizeof(int32_t), s);
         PROF(ctx, ST_MESH_NODES, s,
-             launch_mesh_nodes(d_vxy, nv, d_tri, nt, ctx->d_tables, m->rule_index, m->d_tv, m->d_J, m->d_y, m->d_W,
-                               ctx->d_flag, s));
+             launch_mesh_nodes(d_vxy, nv, d_tri, nt, m->rule.dev, m->d_tv, m->d_J, m->d_y, m->d_W, ctx->d_flag, s));
         if (m->d_cidx)
             PROF(ctx, ST_MESH_NODES, s,
-                 launch_mesh_nodes_curved(d_vxy, nv, d_tri, nt, mesh_curves(m), ctx->d_tables, m->rule_index, m->d_tv,
-                                          m->d_y, m->d_W, ctx->d_flag, s));
+                 launch_mesh_nodes_curved(d_vxy, nv, d_tri, nt, mesh_curves(m), m->rule.dev, m->d_tv, m->d_y, m->d_W,
+                                          ctx->d_flag, s));
         launch_bbox_reduce(d_vxy, nv, 2, d_red, s);
         if (m->d_cidx) launch_bbox_reduce(m->d_y, m->N, 2, d_red + 4, s);   // nodes on the curved sides' bulges
         cudaError_t le = cudaGetLastError();
@@ -349,9 +352,10 @@ int vp_mesh_upload(vp_ctx* ctx, const double* vxy, int64_t nv, const int32_t* tr
                    void* stream, vp_mesh** out) {
     if (out) *out = nullptr;
     if (!ctx_ok(ctx)) return VP_ERR_STATE;
-    if (!out || !vxy || !tri || nv < 3 || nt < 1 || (rule != VP_RULE_16_D8 && rule != VP_RULE_19_D9))
+    if (!out || !vxy || !tri || nv < 3 || nt < 1 || !far_rule_valid(rule))
         return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload: bad arguments");
-    if (nt > (int64_t)INT32_MAX / 19) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload: too many triangles");
+    if (nt > (int64_t)INT32_MAX / far_rule_nq(rule))
+        return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload: too many triangles");
     for (int64_t i = 0; i < 2 * nv; i++)
         if (!std::isfinite(vxy[i])) return vp_set_error(ctx, VP_ERR_NONFINITE, "vp_mesh_upload: non-finite vertex");
     for (int64_t i = 0; i < 3 * nt; i++)
@@ -372,9 +376,9 @@ int vp_mesh_upload_dev(vp_ctx* ctx, const double* vxy_dev, int64_t nv, const int
                        int32_t rule, void* stream, vp_mesh** out) {
     if (out) *out = nullptr;
     if (!ctx_ok(ctx)) return VP_ERR_STATE;
-    if (!out || !vxy_dev || !tri_dev || nv < 3 || nt < 1 || (rule != VP_RULE_16_D8 && rule != VP_RULE_19_D9))
+    if (!out || !vxy_dev || !tri_dev || nv < 3 || nt < 1 || !far_rule_valid(rule))
         return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload_dev: bad arguments");
-    if (nt > (int64_t)INT32_MAX / 19)
+    if (nt > (int64_t)INT32_MAX / far_rule_nq(rule))
         return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload_dev: too many triangles");
     DevGuard g(ctx->device);
     return mesh_upload_impl(ctx, vxy_dev, nv, tri_dev, nt, rule, (cudaStream_t)stream, out);
@@ -386,9 +390,9 @@ int vp_mesh_upload_curved(vp_ctx* ctx, const double* vxy, int64_t nv, const int3
     if (out) *out = nullptr;
     if (!ctx_ok(ctx)) return VP_ERR_STATE;
     if (!out || !vxy || !tri || !cidx || nv < 3 || nt < 1 || ncurve < 0 || (ncurve > 0 && !coef) || K < 0 ||
-        K > VP_MAX_CHEB || (rule != VP_RULE_16_D8 && rule != VP_RULE_19_D9))
+        K > VP_MAX_CHEB || !far_rule_valid(rule))
         return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload_curved: bad arguments");
-    if (nt > (int64_t)INT32_MAX / 19) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload_curved: too many triangles");
+    if (nt > (int64_t)INT32_MAX / far_rule_nq(rule)) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_mesh_upload_curved: too many triangles");
     for (int64_t i = 0; i < 2 * nv; i++)
         if (!std::isfinite(vxy[i])) return vp_set_error(ctx, VP_ERR_NONFINITE, "vp_mesh_upload_curved: non-finite vertex");
     for (int64_t i = 0; i < 3 * nt; i++)
@@ -503,8 +507,6 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
     nf->n_extra = m;
     nf->node_targets = node_targets ? 1 : 0;
     nf->params = prm;
-    const VpTables& tab = ctx->h_tables;
-    const int ri = mesh->rule_index;
     int rc = VP_OK;
 #define NF_FAIL(code, msg)                          \
     do {                                            \
@@ -550,7 +552,8 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         NF_CUDA(sc.alloc(&d_bbox, 4 * nt));
         NF_CUDA(sc.alloc(&d_red, 8));
         PROF(ctx, ST_TRI_GEOM, s,
-             launch_tri_geom(mesh->d_tv, mesh->d_J, nt, tab.far_what[ri], tab.far_degree[ri], prm.eps, prm.c_far, d_R, d_bbox, s));
+             launch_tri_geom(mesh->d_tv, mesh->d_J, nt, mesh->rule.what, mesh->rule.degree, prm.eps, prm.c_far, d_R,
+                             d_bbox, s));
         if (mesh->d_cidx) launch_curved_bbox(nt, mesh_curves(mesh), d_bbox, s);
         launch_bbox_reduce(d_bbox, nt, 4, d_red, s);
         launch_bbox_reduce(nf->d_txy, M, 2, d_red + 4, s);
@@ -629,7 +632,7 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
             PROF(ctx, ST_LOCATE, s, launch_locate(mesh->d_tv, nf->d_txy, d_order, d_tcell, M, gd, nf->d_tself, s));
         NF_CUDA(sc.alloc(&d_count, M));
         PROF(ctx, ST_LIST_COUNT, s,
-             launch_list_pass(mesh->d_tv, d_R, tab.far_degree[ri], nf->d_txy, nf->d_tself, d_order, d_tcell, M, gd,
+             launch_list_pass(mesh->d_tv, d_R, mesh->rule.degree, nf->d_txy, nf->d_tself, d_order, d_tcell, M, gd,
                               d_count, nullptr, nullptr, nullptr, nullptr, s));
         NF_CUDA(dev_alloc(&nf->d_row, M + 1));
         rc = vp_exclusive_scan_i32(ctx, d_count, nf->d_row, M, s);
@@ -644,7 +647,7 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         NF_CUDA(dev_alloc(&nf->d_pkind, nf->P));
         NF_CUDA(dev_alloc(&nf->d_C, nf->P * nq));
         PROF(ctx, ST_LIST_FILL, s,
-             launch_list_pass(mesh->d_tv, d_R, tab.far_degree[ri], nf->d_txy, nf->d_tself, d_order, d_tcell, M, gd,
+             launch_list_pass(mesh->d_tv, d_R, mesh->rule.degree, nf->d_txy, nf->d_tself, d_order, d_tcell, M, gd,
                               nullptr, nf->d_row, nf->d_ptri, nf->d_ptgt, nf->d_pkind, s));
         NF_CUDA(cudaGetLastError());
 
@@ -669,7 +672,8 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         n_near = (int64_t)h_u64[0];
         n_self = (int64_t)h_u64[1];
         wa.tab = ctx->d_tables;
-        wa.rule = ri;
+        wa.Q = mesh->rule.dev.Q;
+        wa.Q2 = mesh->rule.dev.Q2;
         wa.nq = nq;
         wa.tv = mesh->d_tv;
         wa.J = mesh->d_J;
@@ -880,6 +884,8 @@ int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, doub
             if (!profile) ctx->prof = prof_saved;
             return rc;
         }
+    } else if (mesh->rule.builtin < 0) {   // generated far rules: the FP64 apply for any node count
+        PROF(ctx, ST_APPLY, s, launch_apply_fp64(nf->d_row, nf->d_ptri, nf->d_C, mesh->nq, f_dev, N, d, M, u_dev, fT, s));
     } else if ((precision == VP_MIXED || fmm) && d == 1 && nf->d_C2) {
         PROF(ctx, ST_APPLY, s,
              launch_apply_stream(nf->d_row, nf->d_ptri, nf->d_ptgt, nf->d_C2, mesh->nq, f_dev, N, nf->P, M, u_dev,

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -21,6 +22,25 @@ enum VpStage {
     ST_MESH_NODES = 0, ST_TRI_GEOM, ST_TRI_CELLS, ST_CELL_SORT, ST_TARGET_CELLS, ST_LOCATE, ST_LIST_COUNT,
     ST_LIST_FILL, ST_WEIGHTS_SELF, ST_WEIGHTS_NEAR, ST_FF_SPLIT, ST_FAR_FP64, ST_FAR_FF, ST_REDUCE, ST_APPLY,
     ST_APPLY_TC, ST_WEIGHTS_CURVED, ST_FAR_FMM, ST_COUNT
+};
+
+// A far rule on the device: reference nodes and weights and the map Q from
+// the P_4 moments of a pair to its nodal correction weights (vp_rules.cu).
+struct FarRuleDev {
+    const double* x = nullptr;    // [nq]
+    const double* y = nullptr;    // [nq]
+    const double* w = nullptr;    // [nq]
+    const double* Q = nullptr;    // [nq][VP_NB]
+    const float2* Q2 = nullptr;   // [nq][VP_NB], float-float
+    int nq = 0;
+};
+struct FarRule {
+    FarRuleDev dev;
+    double what = 0.0;      // w-hat of Eq. rho0
+    int degree = 0;         // total degree N_f
+    int code = 0;           // vp_rule value
+    int builtin = -1;       // index into VpTables (0: 16 nodes, 1: 19 nodes), -1 generated
+    void* d_buf = nullptr;  // generated rules: device block owned by the context
 };
 
 struct ProfRec {
@@ -48,8 +68,17 @@ struct vp_ctx {
     double prof_ms[ST_COUNT] = {0};
     int ff_tpt[4] = {0, 0, 0, 0};   // autotuned targets per thread of the batched far sum, per chunk width
     int64_t prof_n[ST_COUNT] = {0};
+    // generated far rules, made on first use and kept until vp_destroy
+    std::vector<FarRule> gen_rules;
+    std::mutex rule_mu;
     int magic = 0x56504358;
 };
+
+// far rules (vp_rules.cu)
+bool far_rule_valid(int32_t rule);
+int far_rule_nq(int32_t rule);
+int far_rule_get(vp_ctx* ctx, int32_t rule, FarRule* out);
+void far_rules_free(vp_ctx* ctx);
 
 // Stage timing helpers (no-ops unless profiling is enabled).
 void prof_begin(vp_ctx* ctx, int stage, cudaStream_t s, ProfRec& r);
@@ -68,7 +97,8 @@ void prof_collect(vp_ctx* ctx);
 struct vp_mesh {
     vp_ctx* ctx = nullptr;
     int64_t nt = 0, nv = 0, N = 0;
-    int nq = 0, rule_index = 0;  // rule_index 0: 16 nodes, 1: 19 nodes
+    int nq = 0;
+    FarRule rule;                // far rule of the nodes (Section 3.2)
     double* d_tv = nullptr;      // [nt][6] counter-clockwise vertex coordinates
     double* d_J = nullptr;       // [nt] J_T = 2 area
     double* d_y = nullptr;       // [N][2]
@@ -154,8 +184,8 @@ int vp_exclusive_scan_i32(vp_ctx* ctx, const int32_t* in, int64_t* out, int64_t 
 int vp_exclusive_scan_i64(vp_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
 
 // mesh
-void launch_mesh_nodes(const double* vxy, int64_t nv, const int32_t* tri, int64_t nt, const VpTables* tab, int rule,
-                       double* tv, double* J, double* y, double* W, int32_t* flag, cudaStream_t s);
+void launch_mesh_nodes(const double* vxy, int64_t nv, const int32_t* tri, int64_t nt, FarRuleDev fr, double* tv,
+                       double* J, double* y, double* W, int32_t* flag, cudaStream_t s);
 
 // lists
 struct GridDev {
@@ -188,8 +218,7 @@ void launch_split_pairs(const uint8_t* pkind, int64_t P, int32_t* near_idx, int3
 // curved elements (k_curved.cu)
 inline CurveDev mesh_curves(const vp_mesh* m) { return CurveDev{m->d_cidx, m->d_coef, m->d_dcoef, m->K}; }
 void launch_mesh_nodes_curved(const double* vxy, int64_t nv, const int32_t* tri, int64_t nt, CurveDev cv,
-                              const VpTables* tab, int rule, const double* tv, double* y, double* W, int32_t* flag,
-                              cudaStream_t s);
+                              FarRuleDev fr, const double* tv, double* y, double* W, int32_t* flag, cudaStream_t s);
 void launch_curved_bbox(int64_t nt, CurveDev cv, double* bbox, cudaStream_t s);
 void launch_locate_curved(const double* tv, CurveDev cv, const double* txy, const int32_t* order,
                           const int32_t* tcell, int64_t M, GridDev g, int32_t* tself, cudaStream_t s);
@@ -201,7 +230,8 @@ void launch_split_pairs4(const uint8_t* pkind, const int32_t* ptri, CurveDev cv,
 // weights
 struct WeightsArgs {
     const VpTables* tab;
-    int rule;
+    const double* Q;    // far rule's moment-to-weight map [nq][VP_NB]
+    const float2* Q2;   // the same in float-float
     int nq;
     const double* tv;
     const double* J;

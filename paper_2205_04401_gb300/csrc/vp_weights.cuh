@@ -62,8 +62,8 @@ __device__ __forceinline__ double reduce_scatter16(double* v, int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// mu_i -> C_k for lanes k < nq, written to C[p*nq + k] (and to C2 when the
-// build keeps a float-float copy).
+// mu_i -> C_k, lane k of every group of 32 nodes, written to C[p*nq + k]
+// (and to C2 when the build keeps a float-float copy).
 __device__ __forceinline__ void finish_pair(const WeightsArgs& a, int64_t p, int T, int own, double xx, double xy,
                                             double* m, int lane, const double* rc, const double* lc, double ln2) {
     double v[16];
@@ -72,20 +72,23 @@ __device__ __forceinline__ void finish_pair(const WeightsArgs& a, int64_t p, int
     v[15] = 0.0;
     // index held by this lane after the reduce-scatter: bits 4..1 of the lane
     const double mine = reduce_scatter16(v, lane);
-    double s = 0.0;
-    const double* Qk = a.tab->Q[a.rule][lane < a.nq ? lane : 0];
+    for (int k0 = 0; k0 < a.nq; k0 += 32) {
+        const int k = k0 + lane;
+        double s = 0.0;
+        const double* Qk = a.Q + (k < a.nq ? k : 0) * VP_NB;
 #pragma unroll
-    for (int q = 0; q < VP_NB; q++) s = fma(Qk[q], __shfl_sync(0xffffffffu, mine, 2 * q), s);
-    if (lane < a.nq) {
-        if (lane != own) {
-            const int64_t j = (int64_t)T * a.nq + lane;
-            const double dx = xx - a.y[2 * j], dy = xy - a.y[2 * j + 1];
-            s -= a.W[j] * (vp_logd(dx * dx + dy * dy, rc, lc, ln2) * (0.5 * VP_INV_TWO_PI));
-        }
-        a.C[p * a.nq + lane] = s;
-        if (a.C2) {   // float-float copy (h, l = fl(s - h)) for builds that keep one
-            const float h = __double2float_rn(s);
-            a.C2[p * a.nq + lane] = make_float2(h, __double2float_rn(s - (double)h));
+        for (int q = 0; q < VP_NB; q++) s = fma(Qk[q], __shfl_sync(0xffffffffu, mine, 2 * q), s);
+        if (k < a.nq) {
+            if (k != own) {
+                const int64_t j = (int64_t)T * a.nq + k;
+                const double dx = xx - a.y[2 * j], dy = xy - a.y[2 * j + 1];
+                s -= a.W[j] * (vp_logd(dx * dx + dy * dy, rc, lc, ln2) * (0.5 * VP_INV_TWO_PI));
+            }
+            a.C[p * a.nq + k] = s;
+            if (a.C2) {   // float-float copy (h, l = fl(s - h)) for builds that keep one
+                const float h = __double2float_rn(s);
+                a.C2[p * a.nq + k] = make_float2(h, __double2float_rn(s - (double)h));
+            }
         }
     }
 }

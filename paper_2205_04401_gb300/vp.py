@@ -22,6 +22,13 @@ from . import build as _build
 VP_OK = 0
 VP_RULE_16_D8 = 16
 VP_RULE_19_D9 = 19
+VP_RULE_CONICAL_MIN = 8
+VP_RULE_CONICAL_MAX = 50
+
+
+def VP_RULE_CONICAL(n: int) -> int:
+    """Rule code of the conical-product Gauss far rule of total degree n (vp.h)."""
+    return 1000 + int(n)
 VP_FP64 = 0
 VP_MIXED = 1
 VP_MIXED_TC = 2
@@ -123,6 +130,8 @@ SIGNATURES = {
     "vp_server_destroy": (None, [C.c_void_p]),
     "vp_rule_table": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int32,
                                 C.POINTER(C.c_int32)]),
+    "vp_far_rule": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                              C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]),
 }
 
 
@@ -632,6 +641,21 @@ def pinned_empty(shape):
     """A page-locked host float64 array (numpy view of a pinned torch tensor)."""
     import torch
     return torch.empty(shape, dtype=torch.float64).pin_memory().numpy()
+
+
+def far_rule(rule: int):
+    """(x, y, w, what, degree) of a far rule: VP_RULE_16_D8, VP_RULE_19_D9 or VP_RULE_CONICAL(n)."""
+    lib = load()
+    n = C.c_int32()
+    what = C.c_double()
+    deg = C.c_int32()
+    _check(lib.vp_far_rule(rule, None, None, None, C.byref(what), C.byref(deg), 0, C.byref(n)), None, "vp_far_rule")
+    k = n.value
+    x, y, w = (np.zeros(k) for _ in range(3))
+    _check(lib.vp_far_rule(rule, x.ctypes.data_as(C.c_void_p), y.ctypes.data_as(C.c_void_p),
+                           w.ctypes.data_as(C.c_void_p), C.byref(what), C.byref(deg), k, C.byref(n)), None,
+           "vp_far_rule")
+    return x, y, w, what.value, deg.value
 
 
 def rule_table(which: int):

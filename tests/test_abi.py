@@ -69,3 +69,28 @@ def test_bad_arguments_return_codes(lib):
     assert rc == -7 and not h.value
     n = C.c_int32()
     assert lib.vp_rule_table(7, None, None, None, None, 64, C.byref(n)) == -1
+
+
+@pytest.mark.parametrize("degree", [8, 12, 20, 25, 30, 40, 50])
+def test_conical_rule_matches_oracle(degree):
+    """The library generates the conical-product far rules on the host (long
+    double), the oracle in 60-digit arithmetic: nodes and weights agree to one
+    unit in the last place, w-hat and the degree exactly."""
+    from oracle import gen_rules
+    from paper_2205_04401_gb300 import vp
+    x, y, w, what, deg = vp.far_rule(vp.VP_RULE_CONICAL(degree))
+    r = gen_rules.conical_rule(degree)
+    for a, k in ((x, "x"), (y, "y"), (w, "w")):
+        b = np.array(r[k])
+        assert len(a) == len(b)
+        assert np.all(np.abs(a - b) <= np.spacing(np.abs(b))), k
+    assert what == r["what"] and deg == degree
+
+
+def test_far_rule_codes():
+    from paper_2205_04401_gb300 import vp
+    x, y, w, what, deg = vp.far_rule(vp.VP_RULE_19_D9)
+    assert len(w) == 19 and deg == 9
+    for bad in (17, vp.VP_RULE_CONICAL(7), vp.VP_RULE_CONICAL(51)):
+        with pytest.raises(vp.VPError):
+            vp.far_rule(bad)
