@@ -299,6 +299,57 @@ def leg15_gram_inverse():
     return Hinv
 
 
+def mon15_gram_inverse():
+    """Inverse of the Gram matrix of the monomial basis M_ab(x, y) = u^a v^b,
+    u = 3x - 1, v = 3y - 1, a + b <= 4, in the order of the tensor-Legendre
+    basis (exact rationals, then inverted).  The float-float weight kernels
+    accumulate their moments in this basis (cheaper products, smaller values
+    on the simplex and a better-conditioned Gram matrix than L_ab)."""
+    from fractions import Fraction
+    idx = legendre_tensor_index()
+
+    def expand(a):      # (3x - 1)^a = sum_j C(a, j) 3^j (-1)^(a - j) x^j
+        return [Fraction(math.comb(a, j) * 3 ** j * (-1) ** (a - j)) for j in range(a + 1)]
+
+    ex = {a: expand(a) for a in range(5)}
+
+    def gram(i, j):
+        (a, b), (c, d) = idx[i], idx[j]
+        px = [Fraction(0)] * (a + c + 1)
+        for p1, c1 in enumerate(ex[a]):
+            for p2, c2 in enumerate(ex[c]):
+                px[p1 + p2] += c1 * c2
+        py = [Fraction(0)] * (b + d + 1)
+        for p1, c1 in enumerate(ex[b]):
+            for p2, c2 in enumerate(ex[d]):
+                py[p1 + p2] += c1 * c2
+        tot = Fraction(0)
+        for u, cu in enumerate(px):
+            for v, cv in enumerate(py):
+                tot += cu * cv * Fraction(math.factorial(u) * math.factorial(v), math.factorial(u + v + 2))
+        return tot
+    n = len(idx)
+    H = mp.matrix(n, n)
+    for i in range(n):
+        for j in range(n):
+            g = gram(i, j)
+            H[i, j] = mp.mpf(g.numerator) / g.denominator
+    return mp.inverse(H)
+
+
+def projection_matrix_mon(pts):
+    """QM[k][i] = w_k sum_j HMinv[i][j] M_j(x_k, y_k): the map of
+    projection_matrix for moments in the monomial basis M_ab."""
+    idx = legendre_tensor_index()
+    n = len(idx)
+    Hinv = mon15_gram_inverse()
+    Q = []
+    for x, y, w in pts:
+        m = [(3 * x - 1) ** a * (3 * y - 1) ** b for a, b in idx]
+        Q.append([w * mp.fsum(Hinv[i, j] * m[j] for j in range(n)) for i in range(n)])
+    return Q
+
+
 def projection_matrix(pts):
     """Q[k][i] = w_k sum_j Hinv[i][j] L_j(x_k, y_k): maps the moments
     mu_i = int_T G L_i(rho_T^-1 y) dA to the nodal correction weights of the
@@ -338,6 +389,8 @@ def main():
         pts = solve_symmetric(deg, c0, s21, s111)
         Q = projection_matrix(pts)
         arr(f"VP_{name.upper()}_Q", [v for row in Q for v in row])
+        QM = projection_matrix_mon(pts)
+        arr(f"VP_{name.upper()}_QM", [v for row in QM for v in row])
         arr(f"VP_{name.upper()}_X", [p[0] for p in pts])
         arr(f"VP_{name.upper()}_Y", [p[1] for p in pts])
         arr(f"VP_{name.upper()}_W", [p[2] for p in pts])
@@ -345,6 +398,8 @@ def main():
         out.append(f"static const int VP_{name.upper()}_DEGREE = {deg};")
     Hinv = leg15_gram_inverse()
     arr("VP_LEG15_HINV", [Hinv[i, j] for i in range(Hinv.rows) for j in range(Hinv.cols)])
+    Hinv = mon15_gram_inverse()
+    arr("VP_MON15_HINV", [Hinv[i, j] for i in range(Hinv.rows) for j in range(Hinv.cols)])
     pts = duffy(7)
     arr("VP_NEAR49_X", [p[0] for p in pts])
     arr("VP_NEAR49_Y", [p[1] for p in pts])

@@ -60,6 +60,7 @@ void fill_tables(VpTables& t) {
     const double* fy[2] = {VP_FAR16_Y, VP_FAR19_Y};
     const double* fw[2] = {VP_FAR16_W, VP_FAR19_W};
     const double* fq[2] = {VP_FAR16_Q, VP_FAR19_Q};
+    const double* fqm[2] = {VP_FAR16_QM, VP_FAR19_QM};
     const int nq[2] = {16, 19};
     t.far_what[0] = VP_FAR16_WHAT;
     t.far_what[1] = VP_FAR19_WHAT;
@@ -93,7 +94,7 @@ void fill_tables(VpTables& t) {
     }
     for (int r = 0; r < 2; r++)
         for (int k = 0; k < nq[r]; k++)
-            for (int a = 0; a < VP_NB; a++) t.Q2[r][k][a] = split(t.Q[r][k][a]);
+            for (int a = 0; a < VP_NB; a++) t.Q2[r][k][a] = split(fqm[r][k * VP_NB + a]);
     for (int j = 0; j < VP_NGL; j++) {
         t.lx2[j] = split(VP_GL16_X[j]);
         t.lw2[j] = split(VP_GL16_W[j]);

@@ -33,7 +33,7 @@ struct VpTables {
     // float-float quadratures
     float4 nz2[VP_NNEAR];               // near-rule nodes x (h, l), y (h, l)
     float2 nw2[VP_NNEAR];               // near-rule weights
-    float2 Q2[2][VP_MAXQ][VP_NB];       // Q
+    float2 Q2[2][VP_MAXQ][VP_NB];       // Q for moments in the monomial basis (f2_mon15_acc)
     float2 lx2[VP_NGL], lw2[VP_NGL];    // Gauss-Legendre nodes and weights on [0, 1]
     float2 gr2[VP_NGGQ], glr2[VP_NGGQ], gwl2[VP_NGGQ];   // GGQ nodes, their logs, weights / 2pi
 };

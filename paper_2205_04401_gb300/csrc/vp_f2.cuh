@@ -79,6 +79,33 @@ __device__ __forceinline__ void f2_acc1(float& ah, float& al, f2 g) {
     al = __fadd_rn(al, __fadd_rn(t, g.l));
 }
 
+// m += g M_ab(x, y) for the monomial basis M_ab = u^a v^b, u = 3x - 1,
+// v = 3y - 1, a + b <= 4, in the order of leg15: the terms g u^a v^b come from
+// one chain of 14 products (g u^a, then times v), each added by a two-sum.
+__device__ __forceinline__ void f2_mon15_acc(float* mh, float* ml, f2 g, f2 x, f2 y) {
+    const f2 u = f2_axpb(x, 3.0f, -1.0f), v = f2_axpb(y, 3.0f, -1.0f);
+    const f2 t1 = f2_mul(g, u), t2 = f2_mul(t1, u), t3 = f2_mul(t2, u), t4 = f2_mul(t3, u);
+    const f2 s01 = f2_mul(g, v), s02 = f2_mul(s01, v), s03 = f2_mul(s02, v), s04 = f2_mul(s03, v);
+    const f2 s11 = f2_mul(t1, v), s12 = f2_mul(s11, v), s13 = f2_mul(s12, v);
+    const f2 s21 = f2_mul(t2, v), s22 = f2_mul(s21, v);
+    const f2 s31 = f2_mul(t3, v);
+    f2_acc1(mh[0], ml[0], g);
+    f2_acc1(mh[1], ml[1], t1);
+    f2_acc1(mh[2], ml[2], s01);
+    f2_acc1(mh[3], ml[3], t2);
+    f2_acc1(mh[4], ml[4], s11);
+    f2_acc1(mh[5], ml[5], s02);
+    f2_acc1(mh[6], ml[6], t3);
+    f2_acc1(mh[7], ml[7], s21);
+    f2_acc1(mh[8], ml[8], s12);
+    f2_acc1(mh[9], ml[9], s03);
+    f2_acc1(mh[10], ml[10], t4);
+    f2_acc1(mh[11], ml[11], s31);
+    f2_acc1(mh[12], ml[12], s22);
+    f2_acc1(mh[13], ml[13], s13);
+    f2_acc1(mh[14], ml[14], s04);
+}
+
 // m += g L_ab(x, y) for the tensor-Legendre basis L_ab = P_a(3x - 1) P_b(3y - 1),
 // a + b <= 4, in the order of leg15 (n = a + b, then a from n down to 0).
 __device__ __forceinline__ void f2_leg15_acc(float* mh, float* ml, f2 g, f2 x, f2 y) {

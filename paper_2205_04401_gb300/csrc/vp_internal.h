@@ -30,8 +30,8 @@ struct FarRuleDev {
     const double* x = nullptr;    // [nq]
     const double* y = nullptr;    // [nq]
     const double* w = nullptr;    // [nq]
-    const double* Q = nullptr;    // [nq][VP_NB]
-    const float2* Q2 = nullptr;   // [nq][VP_NB], float-float
+    const double* Q = nullptr;    // [nq][VP_NB], moments in the tensor-Legendre basis (leg15)
+    const float2* Q2 = nullptr;   // [nq][VP_NB], float-float, moments in the monomial basis (f2_mon15_acc)
     int nq = 0;
 };
 struct FarRule {
@@ -230,8 +230,8 @@ void launch_split_pairs4(const uint8_t* pkind, const int32_t* ptri, CurveDev cv,
 // weights
 struct WeightsArgs {
     const VpTables* tab;
-    const double* Q;    // far rule's moment-to-weight map [nq][VP_NB]
-    const float2* Q2;   // the same in float-float
+    const double* Q;    // far rule's moment-to-weight map [nq][VP_NB] (tensor-Legendre moments)
+    const float2* Q2;   // float-float map for monomial-basis moments (the float-float kernels)
     int nq;
     const double* tv;
     const double* J;

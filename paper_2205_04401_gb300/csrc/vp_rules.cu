@@ -136,16 +136,37 @@ Rule conical_rule(int degree) {
     return r;
 }
 
-void projection_q(const Rule& r, std::vector<double>& Q) {
+// Monomial basis M_ab = u^a v^b, u = 3x - 1, v = 3y - 1, in the same order.
+void mon15_ld(long double x, long double y, long double* M) {
+    int i = 0;
+    const long double u = 3.0L * x - 1.0L, v = 3.0L * y - 1.0L;
+    for (int n = 0; n <= 4; n++)
+        for (int a = n; a >= 0; a--) {
+            long double t = 1.0L;
+            for (int e = 0; e < a; e++) t *= u;
+            for (int e = 0; e < n - a; e++) t *= v;
+            M[i++] = t;
+        }
+}
+
+// Q (tensor-Legendre moments, FP64 kernels) and QM (monomial moments,
+// float-float kernels) of a rule.
+void projection_q(const Rule& r, std::vector<double>& Q, std::vector<double>& QM) {
     const int nq = (int)r.w.size();
     Q.assign((size_t)nq * VP_NB, 0.0);
+    QM.assign((size_t)nq * VP_NB, 0.0);
     for (int k = 0; k < nq; k++) {
-        long double L[VP_NB];
+        long double L[VP_NB], M[VP_NB];
         leg15_ld(r.x[k], r.y[k], L);
+        mon15_ld(r.x[k], r.y[k], M);
         for (int i = 0; i < VP_NB; i++) {
-            long double s = 0.0L;
-            for (int j = 0; j < VP_NB; j++) s += (long double)VP_LEG15_HINV[i * VP_NB + j] * L[j];
+            long double s = 0.0L, sm = 0.0L;
+            for (int j = 0; j < VP_NB; j++) {
+                s += (long double)VP_LEG15_HINV[i * VP_NB + j] * L[j];
+                sm += (long double)VP_MON15_HINV[i * VP_NB + j] * M[j];
+            }
             Q[(size_t)k * VP_NB + i] = (double)((long double)r.w[k] * s);
+            QM[(size_t)k * VP_NB + i] = (double)((long double)r.w[k] * sm);
         }
     }
 }
@@ -193,8 +214,8 @@ int far_rule_get(vp_ctx* ctx, int32_t rule, FarRule* out) {
         }
     const Rule g = conical_rule(rule - VP_RULE_CONICAL(0));
     const int nq = (int)g.w.size();
-    std::vector<double> Q;
-    projection_q(g, Q);
+    std::vector<double> Q, QM;
+    projection_q(g, Q, QM);
     const size_t nd = (size_t)nq * (3 + VP_NB);
     std::vector<char> blob(nd * sizeof(double) + (size_t)nq * VP_NB * sizeof(float2));
     double* hd = (double*)blob.data();
@@ -203,9 +224,9 @@ int far_rule_get(vp_ctx* ctx, int32_t rule, FarRule* out) {
     std::copy(g.w.begin(), g.w.end(), hd + 2 * nq);
     std::copy(Q.begin(), Q.end(), hd + 3 * nq);
     float2* hq2 = (float2*)(blob.data() + nd * sizeof(double));
-    for (size_t i = 0; i < Q.size(); i++) {
-        const float h = (float)Q[i];
-        hq2[i] = make_float2(h, (float)(Q[i] - (double)h));
+    for (size_t i = 0; i < QM.size(); i++) {
+        const float h = (float)QM[i];
+        hq2[i] = make_float2(h, (float)(QM[i] - (double)h));
     }
     FarRule r;
     r.code = rule;
