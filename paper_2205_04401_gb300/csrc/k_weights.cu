@@ -326,13 +326,14 @@ __device__ __forceinline__ void finish_pair_f2(const WeightsArgs& a, const Weigh
     for (int k0 = 0; k0 < a.nq; k0 += 32) {   // node k0 + lane of every group of 32
         const int k = k0 + lane;
         const float2* Qk = a.Q2 + (k < a.nq ? k : 0) * VP_NB;
-        f2 s = {0.f, 0.f};
+        float ah = 0.f, al = 0.f;     // unnormalised, as the moment accumulators
 #pragma unroll
         for (int q = 0; q < VP_NB; q++) {
             const f2 mq = {__shfl_sync(0xffffffffu, mine.h, 2 * q), __shfl_sync(0xffffffffu, mine.l, 2 * q)};
             const float2 Q = Qk[q];
-            s = f2_add(s, f2_mul({Q.x, Q.y}, mq));
+            f2_acc(ah, al, {Q.x, Q.y}, mq);
         }
+        f2 s = f2_fast(ah, al);
         if (k < a.nq) {
             if (k != own) {
                 const int64_t j = (int64_t)T * a.nq + k;
@@ -367,16 +368,116 @@ __device__ VP_COLD bool near_stop_fp64(const double* v, SubTri S, double xx, dou
     return !tri_near_fast(ph, xx, xy, Nn, ldexp(R_root, -2 * S.L)) && !tri_contains_rn(ph, xx, xy);
 }
 
+// Per-pair float-float geometry of the near scheme, relative to the target.
+struct NearPairF2 {
+    f2 ax, ay;          // A - x
+    f2 ex, ey, fx, fy;  // B - A, C - A
+    f2 wj;              // J_T / 4pi
+    float cm;           // coordinate magnitude bound of the orientation filter
+};
+
+__device__ __forceinline__ NearPairF2 near_pair_f2(const WeightsF2& b, int T, int t) {
+    const float4 TA = b.tA[T], TE = b.te[T], TF = b.tf[T], TW = b.tw[T], X = b.x2[t];
+    NearPairF2 g;
+    g.ax = f2_add({TA.x, TA.y}, {-X.x, -X.y});
+    g.ay = f2_add({TA.z, TA.w}, {-X.z, -X.w});
+    g.ex = {TE.x, TE.y};
+    g.ey = {TE.z, TE.w};
+    g.fx = {TF.x, TF.y};
+    g.fy = {TF.z, TF.w};
+    g.wj = {TW.x, TW.y};
+    g.cm = fmaxf(TW.z, fmaxf(fabsf(X.x), fabsf(X.z)));
+    return g;
+}
+
+// The stop test of sub-triangle S of the pair's triangle (x outside every
+// near-rule edge ellipse of S and outside S): FP32 filters on the
+// float-float vertex offsets, the exact FP64 predicates when undecided.
+// Also gives the leaf data: offset D0 of S's first vertex, its reference
+// coordinates a0 and the scale 2^-L.
+__device__ __forceinline__ bool subtri_stop_f2(const WeightsArgs& a, const NearPairF2& g, const SubTri& S, int T,
+                                               int t, int Nn, double R_root, float Rf_root, float& scale, f2& d0x,
+                                               f2& d0y, f2& a0x, f2& a0y) {
+    scale = __int_as_float((127 - S.L) << 23);            // 2^-L
+    f2 dx[3], dy[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const f2 xi = dyadic_f2(S.v[2 * i], scale), eta = dyadic_f2(S.v[2 * i + 1], scale);
+        dx[i] = rel_coord(g.ax, xi, eta, g.ex, g.fx);
+        dy[i] = rel_coord(g.ay, xi, eta, g.ey, g.fy);
+        if (i == 0) {
+            a0x = xi;
+            a0y = eta;
+        }
+    }
+    d0x = dx[0];
+    d0y = dy[0];
+    const float Rf = __fmul_rn(Rf_root, __fmul_rn(scale, scale));
+    int near = 0;      // 1 near, 0 not near, -1 undecided
+    for (int e = 0; e < 3 && near != 1; e++) {
+        const int i0 = e, i1 = (e + 1) % 3;
+        const int r = edge_near_f32(dx[i0].h, dy[i0].h, dx[i1].h, dy[i1].h, Nn, Rf);
+        if (r == 1) near = 1;
+        else if (r == 2) near = -1;
+    }
+    int inside = 1;    // 1 inside, 0 outside, -1 undecided
+    if (near != 1) {
+        for (int e = 0; e < 3 && inside != 0; e++) {
+            const int i0 = e, i1 = (e + 1) % 3;
+            const int o = orient_filter(dx[i0].h, dy[i0].h, dx[i1].h, dy[i1].h, g.cm);
+            if (o < 0) inside = 0;
+            else if (o == 0) inside = -1;
+        }
+    }
+    if (near == 1) return false;
+    if (near == 0 && inside != -1) return inside == 0;
+    // undecided in FP32: the FP64 predicates on the FP64 vertices
+    return near_stop_fp64(a.tv + 6 * (int64_t)T, S, a.txy[2 * t], a.txy[2 * t + 1], Nn, R_root);
+}
+
+// One (leaf, near-rule node) term: node offset D0 + sh E_j from the target,
+// g = log|y - x|^2 W_j J_S / 4pi, moments += g M_ab(a0 + sh z_j).
+__device__ __forceinline__ void near_leaf_node(const LeafF2& lf, float4 E, float4 Z, float2 W,
+                                               const float4* ftab, const LogSmem& lt, double ln2, float* mh,
+                                               float* ml) {
+    const float sh = lf.sh;
+    const f2 dx = f2_add({lf.d0xh, lf.d0xl}, {__fmul_rn(E.x, sh), __fmul_rn(E.y, sh)});
+    const f2 dy = f2_add({lf.d0yh, lf.d0yl}, {__fmul_rn(E.z, sh), __fmul_rn(E.w, sh)});
+    const f2 r2 = f2_add(f2_sqr(dx), f2_sqr(dy));
+    f2 lg;
+    if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);              // log |y - x|^2
+    else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));        // far below any mesh scale
+    const f2 g = f2_mul(lg, f2_mul({W.x, W.y}, {lf.wjh, lf.wjl}));
+    const f2 xi = f2_add({lf.a0xh, lf.a0xl}, {__fmul_rn(Z.x, sh), __fmul_rn(Z.y, sh)});
+    const f2 eta = f2_add({lf.a0yh, lf.a0yl}, {__fmul_rn(Z.z, sh), __fmul_rn(Z.w, sh)});
+    f2_mon15_acc(mh, ml, g, xi, eta);
+}
+
+// E_j = z_j,x (B - A) + z_j,y (C - A) of the pair's triangle, per warp.
+__device__ __forceinline__ void near_exy(const NearPairF2& g, const float4* nz, float4* exy, int lane) {
+    for (int j = lane; j < VP_NNEAR; j += 32) {
+        const float4 Z = nz[j];
+        const f2 zx = {Z.x, Z.y}, zy = {Z.z, Z.w};
+        const f2 Ex = f2_add(f2_mul(zx, g.ex), f2_mul(zy, g.fx)), Ey = f2_add(f2_mul(zx, g.ey), f2_mul(zy, g.fy));
+        exy[j] = make_float4(Ex.h, Ex.l, Ey.h, Ey.l);
+    }
+}
+
 __global__ void __launch_bounds__(WARPS * 32, VP_NEAR_MINB) k_weights_near_f2(WeightsArgs a, WeightsF2 b, const int32_t* __restrict__ idx,
                                                               int64_t n) {
     __shared__ SubTri stack_all[WARPS][STK];
     __shared__ LeafF2 leaf_all[WARPS][LEAFCAP];
     __shared__ float4 exy_all[WARPS][VP_NNEAR];
     __shared__ float4 ftab[LOG_N];
+    __shared__ float4 nz_s[VP_NNEAR];    // near-rule nodes and weights, float-float
+    __shared__ float2 nw_s[VP_NNEAR];
     __shared__ LogSmem lt;
-    load_logtab(a.tab, lt);
     for (int i = threadIdx.x; i < LOG_N; i += blockDim.x) ftab[i] = g_logtab.e[i];
-    __syncthreads();
+    for (int i = threadIdx.x; i < VP_NNEAR; i += blockDim.x) {
+        nz_s[i] = a.tab->nz2[i];
+        nw_s[i] = a.tab->nw2[i];
+    }
+    load_logtab(a.tab, lt);              // ends with __syncthreads
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int64_t w = (int64_t)blockIdx.x * WARPS + wl;
     if (w >= n) return;
@@ -388,20 +489,12 @@ __global__ void __launch_bounds__(WARPS * 32, VP_NEAR_MINB) k_weights_near_f2(We
     const int T = a.ptri[p], t = a.ptgt[p];
     const int own = own_index(a, t, T);
     const int Nn = a.tab->near_degree;
-    const double R_root = ellipse_R_rn(a.tab->near_what, a.J[T], a.eps, a.c_near);
+    double R_root = 0.0;                 // warp-uniform: one lane's FP64 work
+    if (lane == 0) R_root = ellipse_R_rn(a.tab->near_what, a.J[T], a.eps, a.c_near);
+    R_root = __shfl_sync(0xffffffffu, R_root, 0);
     const float Rf_root = (float)R_root;
-    // float-float geometry relative to the target
-    const float4 TA = b.tA[T], TE = b.te[T], TF = b.tf[T], TW = b.tw[T], X = b.x2[t];
-    const f2 ax = f2_add({TA.x, TA.y}, {-X.x, -X.y}), ay = f2_add({TA.z, TA.w}, {-X.z, -X.w});
-    const f2 ex = {TE.x, TE.y}, ey = {TE.z, TE.w}, fx = {TF.x, TF.y}, fy = {TF.z, TF.w};
-    const f2 wj_pair = {TW.x, TW.y};
-    const float cm = fmaxf(TW.z, fmaxf(fabsf(X.x), fabsf(X.z)));
-    for (int j = lane; j < VP_NNEAR; j += 32) {
-        const float4 Z = a.tab->nz2[j];
-        const f2 zx = {Z.x, Z.y}, zy = {Z.z, Z.w};
-        const f2 Ex = f2_add(f2_mul(zx, ex), f2_mul(zy, fx)), Ey = f2_add(f2_mul(zx, ey), f2_mul(zy, fy));
-        exy[j] = make_float4(Ex.h, Ex.l, Ey.h, Ey.l);
-    }
+    const NearPairF2 g = near_pair_f2(b, T, t);
+    near_exy(g, nz_s, exy, lane);
 
     float mh[VP_NB], ml[VP_NB];
 #pragma unroll
@@ -432,47 +525,7 @@ __global__ void __launch_bounds__(WARPS * 32, VP_NEAR_MINB) k_weights_near_f2(We
             float scale = 1.f;
             if (lane < c) {
                 S = stack[sp - 1 - lane];
-                scale = __int_as_float((127 - S.L) << 23);            // 2^-L
-                // vertex offsets from the target, float-float
-                f2 dx[3], dy[3];
-#pragma unroll
-                for (int i = 0; i < 3; i++) {
-                    const f2 xi = dyadic_f2(S.v[2 * i], scale), eta = dyadic_f2(S.v[2 * i + 1], scale);
-                    dx[i] = rel_coord(ax, xi, eta, ex, fx);
-                    dy[i] = rel_coord(ay, xi, eta, ey, fy);
-                    if (i == 0) {
-                        a0x = xi;
-                        a0y = eta;
-                    }
-                }
-                d0x = dx[0];
-                d0y = dy[0];
-                // stop test: x outside every edge ellipse of S (near rule) and outside S
-                const float Rf = __fmul_rn(Rf_root, __fmul_rn(scale, scale));
-                int near = 0;      // 1 near, 0 not near, -1 undecided
-                for (int e = 0; e < 3 && near != 1; e++) {
-                    const int i0 = e, i1 = (e + 1) % 3;
-                    const int r = edge_near_f32(dx[i0].h, dy[i0].h, dx[i1].h, dy[i1].h, Nn, Rf);
-                    if (r == 1) near = 1;
-                    else if (r == 2) near = -1;
-                }
-                int inside = 1;    // 1 inside, 0 outside, -1 undecided
-                if (near != 1) {
-                    for (int e = 0; e < 3 && inside != 0; e++) {
-                        const int i0 = e, i1 = (e + 1) % 3;
-                        const int o = orient_filter(dx[i0].h, dy[i0].h, dx[i1].h, dy[i1].h, cm);
-                        if (o < 0) inside = 0;
-                        else if (o == 0) inside = -1;
-                    }
-                }
-                if (near == 1) {
-                    stop = false;
-                } else if (near == 0 && inside != -1) {
-                    stop = inside == 0;
-                } else {
-                    // undecided in FP32: the FP64 predicates on the FP64 vertices
-                    stop = near_stop_fp64(a.tv + 6 * (int64_t)T, S, a.txy[2 * t], a.txy[2 * t + 1], Nn, R_root);
-                }
+                stop = subtri_stop_f2(a, g, S, T, t, Nn, R_root, Rf_root, scale, d0x, d0y, a0x, a0y);
                 if (!stop && S.L >= a.depth_cap) {
                     stop = true;
                     capped++;
@@ -488,7 +541,7 @@ __global__ void __launch_bounds__(WARPS * 32, VP_NEAR_MINB) k_weights_near_f2(We
                     lf.d0xh = d0x.h; lf.d0xl = d0x.l; lf.d0yh = d0y.h; lf.d0yl = d0y.l;
                     lf.a0xh = a0x.h; lf.a0xl = a0x.l; lf.a0yh = a0y.h; lf.a0yl = a0y.l;
                     lf.sh = (S.v[2] - S.v[0]) > 0 ? scale : -scale;
-                    const f2 wj = f2_scale(wj_pair, __fmul_rn(scale, scale));
+                    const f2 wj = f2_scale(g.wj, __fmul_rn(scale, scale));
                     lf.wjh = wj.h; lf.wjl = wj.l; lf.pad = 0.f;
                     leaves[nleaf + __popc(lm & lower)] = lf;
                 } else {
@@ -502,20 +555,7 @@ __global__ void __launch_bounds__(WARPS * 32, VP_NEAR_MINB) k_weights_near_f2(We
             const int combos = nleaf * VP_NNEAR;
             for (int i = lane; i < combos; i += 32) {
                 const int li = i / VP_NNEAR, j = i - li * VP_NNEAR;
-                const LeafF2 lf = leaves[li];
-                const float4 E = exy[j], Z = a.tab->nz2[j];
-                const float2 W = a.tab->nw2[j];
-                const float sh = lf.sh;
-                const f2 dx = f2_add({lf.d0xh, lf.d0xl}, {__fmul_rn(E.x, sh), __fmul_rn(E.y, sh)});
-                const f2 dy = f2_add({lf.d0yh, lf.d0yl}, {__fmul_rn(E.z, sh), __fmul_rn(E.w, sh)});
-                const f2 r2 = f2_add(f2_sqr(dx), f2_sqr(dy));
-                f2 lg;
-                if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);              // log |y - x|^2
-                else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));        // far below any mesh scale
-                const f2 g = f2_mul(lg, f2_mul({W.x, W.y}, {lf.wjh, lf.wjl}));
-                const f2 xi = f2_add({lf.a0xh, lf.a0xl}, {__fmul_rn(Z.x, sh), __fmul_rn(Z.y, sh)});
-                const f2 eta = f2_add({lf.a0yh, lf.a0yl}, {__fmul_rn(Z.z, sh), __fmul_rn(Z.w, sh)});
-                f2_mon15_acc(mh, ml, g, xi, eta);
+                near_leaf_node(leaves[li], exy[j], nz_s[j], nw_s[j], ftab, lt, ln2, mh, ml);
             }
             total_leaves += nleaf;
             nleaf = 0;
@@ -530,6 +570,97 @@ __global__ void __launch_bounds__(WARPS * 32, VP_NEAR_MINB) k_weights_near_f2(We
         a.pstat[p] = total_leaves;
         a.pcap[p] = capped;
     }
+}
+
+// Near pairs whose whole triangle is already a leaf of the subdivision (about
+// three in four on graded meshes) need no traversal: one thread per pair
+// takes the depth-0 stop test of the traversal, writes the pair's leaf and
+// capped counts when the root is a leaf, and appends the pair to the root
+// list or to the list that the traversal kernel takes.
+__global__ void __launch_bounds__(256) k_near_root_split(WeightsArgs a, WeightsF2 b, const int32_t* __restrict__ idx,
+                                                         int64_t n, int32_t* __restrict__ root_idx,
+                                                         int32_t* __restrict__ deep_idx,
+                                                         unsigned long long* __restrict__ counters) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool root = false;
+    int32_t p = 0;
+    if (i < n) {
+        p = idx[i];
+        const int T = a.ptri[p], t = a.ptgt[p];
+        const double R_root = ellipse_R_rn(a.tab->near_what, a.J[T], a.eps, a.c_near);
+        const NearPairF2 g = near_pair_f2(b, T, t);
+        SubTri S;
+        S.v[0] = 0; S.v[1] = 0; S.v[2] = 1; S.v[3] = 0; S.v[4] = 0; S.v[5] = 1; S.L = 0;
+        float scale;
+        f2 d0x, d0y, a0x, a0y;
+        root = subtri_stop_f2(a, g, S, T, t, a.tab->near_degree, R_root, (float)R_root, scale, d0x, d0y, a0x, a0y);
+        int capped = 0;
+        if (!root && a.depth_cap <= 0) {
+            root = true;
+            capped = 1;
+        }
+        if (root) {
+            a.pstat[p] = 1;
+            a.pcap[p] = capped;
+        }
+    }
+    const unsigned mr = __ballot_sync(0xffffffffu, i < n && root);
+    const unsigned md = __ballot_sync(0xffffffffu, i < n && !root);
+    unsigned long long br = 0, bd = 0;
+    if (lane == 0) {
+        if (mr) br = atomicAdd(&counters[0], (unsigned long long)__popc(mr));
+        if (md) bd = atomicAdd(&counters[1], (unsigned long long)__popc(md));
+    }
+    br = __shfl_sync(0xffffffffu, br, 0);
+    bd = __shfl_sync(0xffffffffu, bd, 0);
+    const unsigned lower = (1u << lane) - 1u;
+    if (i < n) {
+        if (root) root_idx[br + __popc(mr & lower)] = p;
+        else deep_idx[bd + __popc(md & lower)] = p;
+    }
+}
+
+// Root-leaf near pairs: the near rule on the whole triangle (leaf D0 = A - x,
+// a0 = 0, scale 1), one warp per pair, then the moment-to-weight step.
+#ifndef VP_ROOT_MINB
+#define VP_ROOT_MINB 6
+#endif
+__global__ void __launch_bounds__(WARPS * 32, VP_ROOT_MINB) k_weights_near_root(WeightsArgs a, WeightsF2 b,
+                                                                                const int32_t* __restrict__ idx,
+                                                                                int64_t n) {
+    __shared__ float4 exy_all[WARPS][VP_NNEAR];
+    __shared__ float4 ftab[LOG_N];
+    __shared__ float4 nz_s[VP_NNEAR];
+    __shared__ float2 nw_s[VP_NNEAR];
+    __shared__ LogSmem lt;
+    for (int i = threadIdx.x; i < LOG_N; i += blockDim.x) ftab[i] = g_logtab.e[i];
+    for (int i = threadIdx.x; i < VP_NNEAR; i += blockDim.x) {
+        nz_s[i] = a.tab->nz2[i];
+        nw_s[i] = a.tab->nw2[i];
+    }
+    load_logtab(a.tab, lt);              // ends with __syncthreads
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t w = (int64_t)blockIdx.x * WARPS + wl;
+    if (w >= n) return;
+    const double ln2 = a.tab->ln2;
+    float4* exy = exy_all[wl];
+    const int64_t p = idx[w];
+    const int T = a.ptri[p], t = a.ptgt[p];
+    const int own = own_index(a, t, T);
+    const NearPairF2 g = near_pair_f2(b, T, t);
+    near_exy(g, nz_s, exy, lane);
+    LeafF2 lf;
+    lf.d0xh = g.ax.h; lf.d0xl = g.ax.l; lf.d0yh = g.ay.h; lf.d0yl = g.ay.l;
+    lf.a0xh = 0.f; lf.a0xl = 0.f; lf.a0yh = 0.f; lf.a0yl = 0.f;
+    lf.sh = 1.f;
+    lf.wjh = g.wj.h; lf.wjl = g.wj.l; lf.pad = 0.f;
+    __syncwarp();
+    float mh[VP_NB], ml[VP_NB];
+#pragma unroll
+    for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
+    for (int j = lane; j < VP_NNEAR; j += 32) near_leaf_node(lf, exy[j], nz_s[j], nw_s[j], ftab, lt, ln2, mh, ml);
+    finish_pair_f2(a, b, p, T, t, own, mh, ml, lane, ftab, lt, ln2);
 }
 
 // ---------------------------------------------------- self, float-float
@@ -579,20 +710,35 @@ __global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(We
     for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
     int panels = 0;
     for (int e = 0; e < 3; e++) {
-        const double Px = v[2 * e], Py = v[2 * e + 1];
-        const double Qx = v[(2 * e + 2) % 6], Qy = v[(2 * e + 3) % 6];
-        const double dx = rn_sub(Qx, Px), dy = rn_sub(Qy, Py);
-        const double L = rn_sqrt(rn_add(rn_mul(dx, dx), rn_mul(dy, dy)));
-        if (L == 0.0) continue;
-        const double h = rn_div(fabs(rn_sub(rn_mul(dx, rn_sub(xy, Py)), rn_mul(dy, rn_sub(xx, Px)))), L);
-        if (h == 0.0) continue;
-        double st = rn_div(rn_add(rn_mul(dx, rn_sub(xx, Px)), rn_mul(dy, rn_sub(xy, Py))), L);
-        if (st < 0.0) st = 0.0;
-        if (st > L) st = L;
-        const double fxp = rn_add(Px, rn_mul(rn_div(st, L), dx)), fyp = rn_add(Py, rn_mul(rn_div(st, L), dy));
-        const double ddx = rn_sub(xx, fxp), ddy = rn_sub(xy, fyp);
-        const double delta = rn_sqrt(rn_add(rn_mul(ddx, ddx), rn_mul(ddy, ddy)));
-        const double Lst = rn_sub(L, st);
+        // the side's FP64 geometry is warp-uniform: lane 0 computes it (the
+        // FP64 pipe runs 1/64 of the FP32 rate) and the warp receives it
+        double L = 0.0, h = 0.0, st = 0.0, Lst = 0.0;
+        int nd0 = 0, nd1 = 0;
+        if (lane == 0) {
+            const double Px = v[2 * e], Py = v[2 * e + 1];
+            const double Qx = v[(2 * e + 2) % 6], Qy = v[(2 * e + 3) % 6];
+            const double dx = rn_sub(Qx, Px), dy = rn_sub(Qy, Py);
+            L = rn_sqrt(rn_add(rn_mul(dx, dx), rn_mul(dy, dy)));
+            if (L != 0.0) h = rn_div(fabs(rn_sub(rn_mul(dx, rn_sub(xy, Py)), rn_mul(dy, rn_sub(xx, Px)))), L);
+            if (L != 0.0 && h != 0.0) {
+                st = rn_div(rn_add(rn_mul(dx, rn_sub(xx, Px)), rn_mul(dy, rn_sub(xy, Py))), L);
+                if (st < 0.0) st = 0.0;
+                if (st > L) st = L;
+                const double fxp = rn_add(Px, rn_mul(rn_div(st, L), dx)), fyp = rn_add(Py, rn_mul(rn_div(st, L), dy));
+                const double ddx = rn_sub(xx, fxp), ddy = rn_sub(xy, fyp);
+                const double delta = rn_sqrt(rn_add(rn_mul(ddx, ddx), rn_mul(ddy, ddy)));
+                Lst = rn_sub(L, st);
+                nd0 = st > 0.0 ? dyadic_count(st, delta) : 0;
+                nd1 = Lst > 0.0 ? dyadic_count(Lst, delta) : 0;
+            }
+        }
+        L = __shfl_sync(0xffffffffu, L, 0);
+        h = __shfl_sync(0xffffffffu, h, 0);
+        st = __shfl_sync(0xffffffffu, st, 0);
+        Lst = __shfl_sync(0xffffffffu, Lst, 0);
+        nd0 = __shfl_sync(0xffffffffu, nd0, 0);
+        nd1 = __shfl_sync(0xffffffffu, nd1, 0);
+        if (L == 0.0 || h == 0.0) continue;
         // the side in float-float: P - x, Q - P, and in reference coordinates
         const f2 pxr = e == 0 ? ax : f2_add(ax, e == 1 ? e2x : f2x);
         const f2 pyr = e == 0 ? ay : f2_add(ay, e == 1 ? e2y : f2y);
@@ -606,7 +752,7 @@ __global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(We
         for (int side = 0; side < 2; side++) {
             const double len = side == 0 ? st : Lst;
             if (!(len > 0.0)) continue;
-            const int Nd = dyadic_count(len, delta);
+            const int Nd = side == 0 ? nd0 : nd1;
             const f2 len2 = side == 0 ? st2 : f2_add(L2, f2_neg(st2));
             // panel boundaries: b_0 = end, b_i = end -/+ (1 - 2^-i) len, b_{Nd+1} = st
             f2 b0 = side == 0 ? f2{0.f, 0.f} : L2;
@@ -684,15 +830,16 @@ __global__ void k_weights_f2_pts(const double* __restrict__ xy, int64_t n, const
 
 }  // namespace
 
-size_t weights_f2_bytes(int64_t nt, int64_t M, int64_t N) {
-    // seven arrays, each rounded up to 256 bytes
+size_t weights_f2_bytes(int64_t nt, int64_t M, int64_t N, int64_t n_near) {
+    // seven arrays, the two near-pair lists and their counters, each rounded up to 256 bytes
     return (size_t)nt * 4 * sizeof(float4) + (size_t)M * sizeof(float4) + (size_t)N * (sizeof(float4) + sizeof(float2)) +
-           7 * 256;
+           (size_t)n_near * 2 * sizeof(int32_t) + 2 * sizeof(unsigned long long) + 10 * 256;
 }
 
-// float-float triangles, targets and nodes in the caller's scratch
-static WeightsF2 weights_f2_prepare(const WeightsArgs& a, cudaStream_t s) {
-    char* ws = (char*)a.f2_ws;
+// float-float triangles, targets and nodes in the caller's scratch; ws
+// points past them on return
+static WeightsF2 weights_f2_prepare(const WeightsArgs& a, cudaStream_t s, char*& ws) {
+    ws = (char*)a.f2_ws;
     auto take = [&](size_t bytes) {
         char* p = ws;
         ws += (bytes + 255) & ~(size_t)255;
@@ -722,7 +869,29 @@ void launch_weights(const WeightsArgs& a, const int32_t* self_idx, int64_t n_sel
         return;
     }
     ensure_logtab();
-    const WeightsF2 b = weights_f2_prepare(a, s);
+    char* ws = nullptr;
+    const WeightsF2 b = weights_f2_prepare(a, s, ws);
     PROF(ctx, ST_WEIGHTS_SELF, s, if (n_self > 0) k_weights_self_f2<<<gs, WARPS * 32, 0, s>>>(a, b, self_idx, n_self));
-    PROF(ctx, ST_WEIGHTS_NEAR, s, if (n_near > 0) k_weights_near_f2<<<gn, WARPS * 32, 0, s>>>(a, b, near_idx, n_near));
+    if (n_near <= 0) return;
+    auto take = [&](size_t bytes) {
+        char* q = ws;
+        ws += (bytes + 255) & ~(size_t)255;
+        return q;
+    };
+    int32_t* root_idx = (int32_t*)take(n_near * sizeof(int32_t));
+    int32_t* deep_idx = (int32_t*)take(n_near * sizeof(int32_t));
+    unsigned long long* cnt = (unsigned long long*)take(2 * sizeof(unsigned long long));
+    unsigned long long h_cnt[2] = {0, 0};
+    PROF(ctx, ST_WEIGHTS_NEAR, s, {
+        cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s);
+        k_near_root_split<<<(unsigned)((n_near + 255) / 256), 256, 0, s>>>(a, b, near_idx, n_near, root_idx, deep_idx,
+                                                                           cnt);
+        cudaMemcpyAsync(h_cnt, cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        const int64_t n_root = (int64_t)h_cnt[0], n_deep = (int64_t)h_cnt[1];
+        if (n_root > 0)
+            k_weights_near_root<<<(unsigned)((n_root + WARPS - 1) / WARPS), WARPS * 32, 0, s>>>(a, b, root_idx, n_root);
+        if (n_deep > 0)
+            k_weights_near_f2<<<(unsigned)((n_deep + WARPS - 1) / WARPS), WARPS * 32, 0, s>>>(a, b, deep_idx, n_deep);
+    });
 }

@@ -697,7 +697,7 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         wa.nt = nt;
         wa.M = M;
         wa.N = N;
-        NF_CUDA(sc.alloc(&d_f2ws, (int64_t)weights_f2_bytes(nt, M, N)));
+        NF_CUDA(sc.alloc(&d_f2ws, (int64_t)weights_f2_bytes(nt, M, N, n_near)));
         wa.f2_ws = d_f2ws;
         launch_weights(wa, d_self_idx, n_self, d_near_idx, n_near, s, ctx);
         if (mesh->d_cidx)

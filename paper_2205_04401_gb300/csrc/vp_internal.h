@@ -250,9 +250,9 @@ struct WeightsArgs {
     int depth_cap;
     int fp64;           // 1: node quadratures in FP64 (reference); 0: float-float
     int64_t nt, M, N;   // triangles, targets, nodes
-    void* f2_ws;        // scratch of weights_f2_bytes(nt, M, N) for the float-float kernels
+    void* f2_ws;        // scratch of weights_f2_bytes(nt, M, N, n_near) for the float-float kernels
 };
-size_t weights_f2_bytes(int64_t nt, int64_t M, int64_t N);
+size_t weights_f2_bytes(int64_t nt, int64_t M, int64_t N, int64_t n_near);
 // self and near weights (stages ST_WEIGHTS_SELF, ST_WEIGHTS_NEAR)
 void launch_weights(const WeightsArgs& a, const int32_t* self_idx, int64_t n_self, const int32_t* near_idx,
                     int64_t n_near, cudaStream_t s, vp_ctx* ctx);
