@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_weights_near(WeightsArgs a, cons
 // keeps its parent's orientation except the fourth, its point reflection).
 struct LeafF2 {
     float d0xh, d0xl, d0yh, d0yl;   // D0 = A + a0_x (B - A) + a0_y (C - A) - x
-    float a0xh, a0xl, a0yh, a0yl;   // a0
+    float u0h, u0l, v0h, v0l;       // (u, v) = 3 a0 - 1 of the first vertex
     float sh, wjh, wjl, pad;        // sh; J_T 4^-L / 4pi
 };
 
@@ -436,7 +436,8 @@ __device__ __forceinline__ bool subtri_stop_f2(const WeightsArgs& a, const NearP
 }
 
 // One (leaf, near-rule node) term: node offset D0 + sh E_j from the target,
-// g = log|y - x|^2 W_j J_S / 4pi, moments += g M_ab(a0 + sh z_j).
+// g = log|y - x|^2 W_j J_S / 4pi, moments += g M_ab at (u, v) = (u0, v0) +
+// sh Z, Z = 3 z_j (the node's (u, v) = 3 (a0 + sh z_j) - 1).
 __device__ __forceinline__ void near_leaf_node(const LeafF2& lf, float4 E, float4 Z, float2 W,
                                                const float4* ftab, const LogSmem& lt, double ln2, float* mh,
                                                float* ml) {
@@ -448,9 +449,9 @@ __device__ __forceinline__ void near_leaf_node(const LeafF2& lf, float4 E, float
     if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);              // log |y - x|^2
     else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));        // far below any mesh scale
     const f2 g = f2_mul(lg, f2_mul({W.x, W.y}, {lf.wjh, lf.wjl}));
-    const f2 xi = f2_add({lf.a0xh, lf.a0xl}, {__fmul_rn(Z.x, sh), __fmul_rn(Z.y, sh)});
-    const f2 eta = f2_add({lf.a0yh, lf.a0yl}, {__fmul_rn(Z.z, sh), __fmul_rn(Z.w, sh)});
-    f2_mon15_acc(mh, ml, g, xi, eta);
+    const f2 u = f2_add({lf.u0h, lf.u0l}, {__fmul_rn(Z.x, sh), __fmul_rn(Z.y, sh)});   // Z = 3 z_j
+    const f2 v = f2_add({lf.v0h, lf.v0l}, {__fmul_rn(Z.z, sh), __fmul_rn(Z.w, sh)});
+    f2_mon15_acc_uv(mh, ml, g, u, v);
 }
 
 // E_j = z_j,x (B - A) + z_j,y (C - A) of the pair's triangle, per warp.
@@ -469,12 +470,14 @@ __global__ void __launch_bounds__(WARPS * 32, VP_NEAR_MINB) k_weights_near_f2(We
     __shared__ LeafF2 leaf_all[WARPS][LEAFCAP];
     __shared__ float4 exy_all[WARPS][VP_NNEAR];
     __shared__ float4 ftab[LOG_N];
-    __shared__ float4 nz_s[VP_NNEAR];    // near-rule nodes and weights, float-float
+    __shared__ float4 nz_s[VP_NNEAR];
+    __shared__ float4 nz3_s[VP_NNEAR];   // 3 z_j, float-float    // near-rule nodes and weights, float-float
     __shared__ float2 nw_s[VP_NNEAR];
     __shared__ LogSmem lt;
     for (int i = threadIdx.x; i < LOG_N; i += blockDim.x) ftab[i] = g_logtab.e[i];
     for (int i = threadIdx.x; i < VP_NNEAR; i += blockDim.x) {
         nz_s[i] = a.tab->nz2[i];
+        nz3_s[i] = a.tab->nz3[i];
         nw_s[i] = a.tab->nw2[i];
     }
     load_logtab(a.tab, lt);              // ends with __syncthreads
@@ -539,7 +542,8 @@ __global__ void __launch_bounds__(WARPS * 32, VP_NEAR_MINB) k_weights_near_f2(We
                 if (stop) {
                     LeafF2 lf;
                     lf.d0xh = d0x.h; lf.d0xl = d0x.l; lf.d0yh = d0y.h; lf.d0yl = d0y.l;
-                    lf.a0xh = a0x.h; lf.a0xl = a0x.l; lf.a0yh = a0y.h; lf.a0yl = a0y.l;
+                    const f2 u0 = f2_axpb(a0x, 3.0f, -1.0f), v0 = f2_axpb(a0y, 3.0f, -1.0f);
+                    lf.u0h = u0.h; lf.u0l = u0.l; lf.v0h = v0.h; lf.v0l = v0.l;
                     lf.sh = (S.v[2] - S.v[0]) > 0 ? scale : -scale;
                     const f2 wj = f2_scale(g.wj, __fmul_rn(scale, scale));
                     lf.wjh = wj.h; lf.wjl = wj.l; lf.pad = 0.f;
@@ -555,7 +559,7 @@ __global__ void __launch_bounds__(WARPS * 32, VP_NEAR_MINB) k_weights_near_f2(We
             const int combos = nleaf * VP_NNEAR;
             for (int i = lane; i < combos; i += 32) {
                 const int li = i / VP_NNEAR, j = i - li * VP_NNEAR;
-                near_leaf_node(leaves[li], exy[j], nz_s[j], nw_s[j], ftab, lt, ln2, mh, ml);
+                near_leaf_node(leaves[li], exy[j], nz3_s[j], nw_s[j], ftab, lt, ln2, mh, ml);
             }
             total_leaves += nleaf;
             nleaf = 0;
@@ -632,11 +636,13 @@ __global__ void __launch_bounds__(WARPS * 32, VP_ROOT_MINB) k_weights_near_root(
     __shared__ float4 exy_all[WARPS][VP_NNEAR];
     __shared__ float4 ftab[LOG_N];
     __shared__ float4 nz_s[VP_NNEAR];
+    __shared__ float4 nz3_s[VP_NNEAR];   // 3 z_j, float-float
     __shared__ float2 nw_s[VP_NNEAR];
     __shared__ LogSmem lt;
     for (int i = threadIdx.x; i < LOG_N; i += blockDim.x) ftab[i] = g_logtab.e[i];
     for (int i = threadIdx.x; i < VP_NNEAR; i += blockDim.x) {
         nz_s[i] = a.tab->nz2[i];
+        nz3_s[i] = a.tab->nz3[i];
         nw_s[i] = a.tab->nw2[i];
     }
     load_logtab(a.tab, lt);              // ends with __syncthreads
@@ -652,14 +658,14 @@ __global__ void __launch_bounds__(WARPS * 32, VP_ROOT_MINB) k_weights_near_root(
     near_exy(g, nz_s, exy, lane);
     LeafF2 lf;
     lf.d0xh = g.ax.h; lf.d0xl = g.ax.l; lf.d0yh = g.ay.h; lf.d0yl = g.ay.l;
-    lf.a0xh = 0.f; lf.a0xl = 0.f; lf.a0yh = 0.f; lf.a0yl = 0.f;
+    lf.u0h = -1.f; lf.u0l = 0.f; lf.v0h = -1.f; lf.v0l = 0.f;
     lf.sh = 1.f;
     lf.wjh = g.wj.h; lf.wjl = g.wj.l; lf.pad = 0.f;
     __syncwarp();
     float mh[VP_NB], ml[VP_NB];
 #pragma unroll
     for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
-    for (int j = lane; j < VP_NNEAR; j += 32) near_leaf_node(lf, exy[j], nz_s[j], nw_s[j], ftab, lt, ln2, mh, ml);
+    for (int j = lane; j < VP_NNEAR; j += 32) near_leaf_node(lf, exy[j], nz3_s[j], nw_s[j], ftab, lt, ln2, mh, ml);
     finish_pair_f2(a, b, p, T, t, own, mh, ml, lane, ftab, lt, ln2);
 }
 
@@ -689,6 +695,7 @@ __global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(We
     const double xx = a.txy[2 * t], xy = a.txy[2 * t + 1];
     const double qx0 = xx - Ax, qy0 = xy - Ay;
     const f2 xi0 = f2_from_d((qx0 * fy - qy0 * fx) * invJ), eta0 = f2_from_d((ex * qy0 - ey * qx0) * invJ);
+    const f2 u0 = f2_axpb(xi0, 3.0f, -1.0f), v0 = f2_axpb(eta0, 3.0f, -1.0f);   // the target's (u, v)
     const int own = own_index(a, t, T);
     // float-float triangle relative to the target
     const float4 TA = b.tA[T], TE = b.te[T], TF = b.tf[T], X = b.x2[t];
@@ -708,36 +715,39 @@ __global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(We
     float mh[VP_NB], ml[VP_NB];
 #pragma unroll
     for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
+    // The three sides' FP64 geometry (it fixes the dyadic panels exactly as
+    // the FP64 scheme does), side e on lane e: the FP64 pipe is charged per
+    // warp instruction, so one instruction serves all three sides.
+    double gL = 0.0, gh = 0.0;
+    f2 ginvL = {0.f, 0.f}, gst = {0.f, 0.f};
+    int gnd0 = -1, gnd1 = -1;            // -1: no panels on that half of the side
+    if (lane < 3) {
+        const int e = lane;
+        const double Px = v[2 * e], Py = v[2 * e + 1];
+        const double Qx = v[(2 * e + 2) % 6], Qy = v[(2 * e + 3) % 6];
+        const double dx = rn_sub(Qx, Px), dy = rn_sub(Qy, Py);
+        gL = rn_sqrt(rn_add(rn_mul(dx, dx), rn_mul(dy, dy)));
+        if (gL != 0.0) gh = rn_div(fabs(rn_sub(rn_mul(dx, rn_sub(xy, Py)), rn_mul(dy, rn_sub(xx, Px)))), gL);
+        if (gL != 0.0 && gh != 0.0) {
+            double st = rn_div(rn_add(rn_mul(dx, rn_sub(xx, Px)), rn_mul(dy, rn_sub(xy, Py))), gL);
+            if (st < 0.0) st = 0.0;
+            if (st > gL) st = gL;
+            const double fxp = rn_add(Px, rn_mul(rn_div(st, gL), dx)), fyp = rn_add(Py, rn_mul(rn_div(st, gL), dy));
+            const double ddx = rn_sub(xx, fxp), ddy = rn_sub(xy, fyp);
+            const double delta = rn_sqrt(rn_add(rn_mul(ddx, ddx), rn_mul(ddy, ddy)));
+            const double Lst = rn_sub(gL, st);
+            gnd0 = st > 0.0 ? dyadic_count(st, delta) : -1;
+            gnd1 = Lst > 0.0 ? dyadic_count(Lst, delta) : -1;
+            ginvL = f2_from_d(1.0 / gL);
+            gst = f2_from_d(st);
+        }
+    }
     int panels = 0;
     for (int e = 0; e < 3; e++) {
-        // the side's FP64 geometry is warp-uniform: lane 0 computes it (the
-        // FP64 pipe runs 1/64 of the FP32 rate) and the warp receives it
-        double L = 0.0, h = 0.0, st = 0.0, Lst = 0.0;
-        int nd0 = 0, nd1 = 0;
-        if (lane == 0) {
-            const double Px = v[2 * e], Py = v[2 * e + 1];
-            const double Qx = v[(2 * e + 2) % 6], Qy = v[(2 * e + 3) % 6];
-            const double dx = rn_sub(Qx, Px), dy = rn_sub(Qy, Py);
-            L = rn_sqrt(rn_add(rn_mul(dx, dx), rn_mul(dy, dy)));
-            if (L != 0.0) h = rn_div(fabs(rn_sub(rn_mul(dx, rn_sub(xy, Py)), rn_mul(dy, rn_sub(xx, Px)))), L);
-            if (L != 0.0 && h != 0.0) {
-                st = rn_div(rn_add(rn_mul(dx, rn_sub(xx, Px)), rn_mul(dy, rn_sub(xy, Py))), L);
-                if (st < 0.0) st = 0.0;
-                if (st > L) st = L;
-                const double fxp = rn_add(Px, rn_mul(rn_div(st, L), dx)), fyp = rn_add(Py, rn_mul(rn_div(st, L), dy));
-                const double ddx = rn_sub(xx, fxp), ddy = rn_sub(xy, fyp);
-                const double delta = rn_sqrt(rn_add(rn_mul(ddx, ddx), rn_mul(ddy, ddy)));
-                Lst = rn_sub(L, st);
-                nd0 = st > 0.0 ? dyadic_count(st, delta) : 0;
-                nd1 = Lst > 0.0 ? dyadic_count(Lst, delta) : 0;
-            }
-        }
-        L = __shfl_sync(0xffffffffu, L, 0);
-        h = __shfl_sync(0xffffffffu, h, 0);
-        st = __shfl_sync(0xffffffffu, st, 0);
-        Lst = __shfl_sync(0xffffffffu, Lst, 0);
-        nd0 = __shfl_sync(0xffffffffu, nd0, 0);
-        nd1 = __shfl_sync(0xffffffffu, nd1, 0);
+        const double L = __shfl_sync(0xffffffffu, gL, e), h = __shfl_sync(0xffffffffu, gh, e);
+        const int nd0 = __shfl_sync(0xffffffffu, gnd0, e), nd1 = __shfl_sync(0xffffffffu, gnd1, e);
+        const f2 invL = {__shfl_sync(0xffffffffu, ginvL.h, e), __shfl_sync(0xffffffffu, ginvL.l, e)};
+        const f2 st2 = {__shfl_sync(0xffffffffu, gst.h, e), __shfl_sync(0xffffffffu, gst.l, e)};
         if (L == 0.0 || h == 0.0) continue;
         // the side in float-float: P - x, Q - P, and in reference coordinates
         const f2 pxr = e == 0 ? ax : f2_add(ax, e == 1 ? e2x : f2x);
@@ -748,11 +758,10 @@ __global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(We
         const float dref_x = e == 0 ? 1.f : (e == 1 ? -1.f : 0.f);                   // Q - P there
         const float dref_y = e == 0 ? 0.f : (e == 1 ? 1.f : -1.f);
         const f2 xiP = f2_add_f(f2_neg(xi0), pref_x), etaP = f2_add_f(f2_neg(eta0), pref_y);   // P - x, reference
-        const f2 invL = f2_from_d(1.0 / L), h2 = f2_from_d(h), L2 = f2_from_d(L), st2 = f2_from_d(st);
+        const f2 h2 = f2_from_d(h), L2 = f2_from_d(L);
         for (int side = 0; side < 2; side++) {
-            const double len = side == 0 ? st : Lst;
-            if (!(len > 0.0)) continue;
             const int Nd = side == 0 ? nd0 : nd1;
+            if (Nd < 0) continue;
             const f2 len2 = side == 0 ? st2 : f2_add(L2, f2_neg(st2));
             // panel boundaries: b_0 = end, b_i = end -/+ (1 - 2^-i) len, b_{Nd+1} = st
             f2 b0 = side == 0 ? f2{0.f, 0.f} : L2;
@@ -781,10 +790,11 @@ __global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(We
                 else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
                 const f2 lr0 = f2_scale(lg, 0.5f);                            // log r0
                 const f2 xig = f2_add(xiP, f2_scale(sl, dref_x)), etag = f2_add(etaP, f2_scale(sl, dref_y));
+                const f2 al = f2_mulf(xig, 3.0f), be = f2_mulf(etag, 3.0f);   // (u, v) = (u0, v0) + r (al, be)
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const f2 g = f2_mul(f2_add(lr0, glr[q]), f2_mul(ws, gwl[q]));
-                    f2_mon15_acc(mh, ml, g, f2_add(f2_mul(gr[q], xig), xi0), f2_add(f2_mul(gr[q], etag), eta0));
+                    f2_mon15_acc_uv(mh, ml, g, f2_add(f2_mul(gr[q], al), u0), f2_add(f2_mul(gr[q], be), v0));
                 }
                 b0 = b1;
             }

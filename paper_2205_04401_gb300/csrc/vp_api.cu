@@ -90,6 +90,8 @@ void fill_tables(VpTables& t) {
     for (int j = 0; j < VP_NNEAR; j++) {
         const float2 x = split(VP_NEAR49_X[j]), y = split(VP_NEAR49_Y[j]);
         t.nz2[j] = make_float4(x.x, x.y, y.x, y.y);
+        const float2 x3 = split(3.0 * VP_NEAR49_X[j]), y3 = split(3.0 * VP_NEAR49_Y[j]);
+        t.nz3[j] = make_float4(x3.x, x3.y, y3.x, y3.y);
         t.nw2[j] = split(VP_NEAR49_W[j]);
     }
     for (int r = 0; r < 2; r++)

@@ -32,6 +32,7 @@ struct VpTables {
     // the same constants as pairs of FP32 values (h, l = fl(x - h)) for the
     // float-float quadratures
     float4 nz2[VP_NNEAR];               // near-rule nodes x (h, l), y (h, l)
+    float4 nz3[VP_NNEAR];               // 3 x, 3 y of the near-rule nodes (h, l)
     float2 nw2[VP_NNEAR];               // near-rule weights
     float2 Q2[2][VP_MAXQ][VP_NB];       // Q for moments in the monomial basis (f2_mon15_acc)
     float2 lx2[VP_NGL], lw2[VP_NGL];    // Gauss-Legendre nodes and weights on [0, 1]

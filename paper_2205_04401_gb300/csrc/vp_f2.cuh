@@ -82,8 +82,7 @@ __device__ __forceinline__ void f2_acc1(float& ah, float& al, f2 g) {
 // m += g M_ab(x, y) for the monomial basis M_ab = u^a v^b, u = 3x - 1,
 // v = 3y - 1, a + b <= 4, in the order of leg15: the terms g u^a v^b come from
 // one chain of 14 products (g u^a, then times v), each added by a two-sum.
-__device__ __forceinline__ void f2_mon15_acc(float* mh, float* ml, f2 g, f2 x, f2 y) {
-    const f2 u = f2_axpb(x, 3.0f, -1.0f), v = f2_axpb(y, 3.0f, -1.0f);
+__device__ __forceinline__ void f2_mon15_acc_uv(float* mh, float* ml, f2 g, f2 u, f2 v) {
     const f2 t1 = f2_mul(g, u), t2 = f2_mul(t1, u), t3 = f2_mul(t2, u), t4 = f2_mul(t3, u);
     const f2 s01 = f2_mul(g, v), s02 = f2_mul(s01, v), s03 = f2_mul(s02, v), s04 = f2_mul(s03, v);
     const f2 s11 = f2_mul(t1, v), s12 = f2_mul(s11, v), s13 = f2_mul(s12, v);
@@ -104,6 +103,14 @@ __device__ __forceinline__ void f2_mon15_acc(float* mh, float* ml, f2 g, f2 x, f
     f2_acc1(mh[12], ml[12], s22);
     f2_acc1(mh[13], ml[13], s13);
     f2_acc1(mh[14], ml[14], s04);
+}
+__device__ __forceinline__ void f2_mon15_acc(float* mh, float* ml, f2 g, f2 x, f2 y) {
+    f2_mon15_acc_uv(mh, ml, g, f2_axpb(x, 3.0f, -1.0f), f2_axpb(y, 3.0f, -1.0f));
+}
+// a c for an FP32 constant c (product error kept)
+__device__ __forceinline__ f2 f2_mulf(f2 a, float c) {
+    const float p = __fmul_rn(c, a.h);
+    return f2_fast(p, __fmaf_rn(c, a.l, __fmaf_rn(c, a.h, -p)));
 }
 
 // m += g L_ab(x, y) for the tensor-Legendre basis L_ab = P_a(3x - 1) P_b(3y - 1),

@@ -75,9 +75,15 @@ def emulated_delta(C, row, ptri, kind, nq, f, L):
 
 
 def check_exact(um, ut, delta, mag):
+    """The tensor-core result equals the FP64 apply plus the emulated digit
+    rounding, up to the rounding of the two FP64 evaluations themselves: the
+    FP64 apply sums a row of up to ~10^3 weight-density products (rounding
+    ~sqrt(n) 2^-53 of sum |C f|), the emulation sums the same number of
+    differences and the tensor-core path combines its exact FP32 level sums
+    in float-float (~2^-48 per level): together a few 1e-15 of sum |C f|."""
     scale = np.abs(um).max(axis=1) + mag
     err = np.max(np.abs((ut - um) - delta), axis=1) / np.maximum(scale, 1e-300)
-    assert err.max() <= 2e-15, err.max()
+    assert err.max() <= 4e-15, err.max()
 
 
 def build(vp, ctx, mesh, rule, extra=None):
