@@ -1002,8 +1002,9 @@ def main():
     # smsp__thread_inst_executed.sum on the 2,048-triangle star,
     # profiles/far_sym_weights_star2048_counts.md): symmetric far sum 105.7 per
     # unordered node pair, its diagonal tiles 85.7 and the extra targets 83.5
-    # per ordered pair, near weights 954 per (leaf, node) evaluation including
-    # the per-pair work, self weights 72,500 per panel.
+    # per ordered pair, near weights 721 per (leaf, node) evaluation including
+    # the per-pair work (root classifier, root-leaf and traversal kernels),
+    # self weights 48,300 per panel.
     TI = 512                     # target tile of the symmetric far sum
     unord = diag = 0
     for lo in range(0, N, TI):
@@ -1012,8 +1013,8 @@ def main():
         diag += sz * sz
     far_inst = unord * 105.7 + diag * 85.7 + (M - N) * N * 83.5
     work = {
-        "weights_near": ("alu", stats["near_leaves"] * 49 * 954.0 * args.steps, issue_peak / 1e12, "Tinst/s"),
-        "weights_self": ("alu", stats["self_panels"] * 72500.0 * args.steps, issue_peak / 1e12, "Tinst/s"),
+        "weights_near": ("alu", stats["near_leaves"] * 49 * 721.4 * args.steps, issue_peak / 1e12, "Tinst/s"),
+        "weights_self": ("alu", stats["self_panels"] * 48328.0 * args.steps, issue_peak / 1e12, "Tinst/s"),
         "far_ff": ("alu", far_inst * args.steps, issue_peak / 1e12, "Tinst/s"),
         "far_fp64": ("alu", float(M) * N * 80.0 * args.steps, dfma_peak / 1e12, "FP64 TFLOP/s"),
         "apply": ("hbm", float(stats["n_pairs"] * (8 * nq + 4) + N * 8 + M * 8 + M * 8 * 2) * args.steps,
@@ -1075,7 +1076,7 @@ def main():
         }
         # library kernel launches per full step (upload + build + mixed evaluation of one density),
         # counted in the ncu launch list of this command (profiles/launches_star16384_mixed.md)
-        line["gpu_launches"] = 45 * args.steps if prec == vp.VP_MIXED else int(sum(v[0] for v in prof.values()))
+        line["gpu_launches"] = 47 * args.steps if prec == vp.VP_MIXED else int(sum(v[0] for v in prof.values()))
         print(json.dumps(line))
     nf.release()
     mh.release()

@@ -100,12 +100,15 @@ __global__ void k_fmm_count_up(int l, FmmGeo g, int32_t* cnt_all) {
     cnt_all[lvl_off(g, l) + b] = s;
 }
 
-// sorted sources: float-float coordinates and original index
-__global__ void k_fmm_sort_src(const int32_t* __restrict__ perm, int64_t n, FFCoords src, float4* __restrict__ sxy) {
+// sorted sources: float-float coordinates, and the sorted position of each
+// node (for the own-node test of node targets)
+__global__ void k_fmm_sort_src(const int32_t* __restrict__ perm, int64_t n, FFCoords src, float4* __restrict__ sxy,
+                               int32_t* __restrict__ spos) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int32_t j = perm[i];
     sxy[i] = make_float4(src.hi[2 * j], src.hi[2 * j + 1], src.lo[2 * j], src.lo[2 * j + 1]);
+    spos[j] = (int32_t)i;
 }
 
 // ------------------------------------------------------------ charges
@@ -290,64 +293,93 @@ __global__ void __launch_bounds__(FT) k_fmm_l2l(int l, FmmGeo g, const int32_t* 
 }
 
 // ------------------------------------------------------------ evaluation
-// Per target (in leaf order): the local expansion of its leaf (Horner) and
-// the direct sum over the sources of its leaf and the eight adjacent ones in
-// float-float (own node skipped).  u = P2P / 4pi (log r^2) + Re(L2P) / 2pi.
-__global__ void __launch_bounds__(128) k_fmm_eval(FmmGeo g, const int32_t* __restrict__ tperm,
-                                                  const int32_t* __restrict__ tleaf, int64_t M, const double* __restrict__ txy,
-                                                  FFCoords tgt, const int32_t* __restrict__ tnode,
-                                                  const int64_t* __restrict__ sstart, const int32_t* __restrict__ sperm,
-                                                  const float4* __restrict__ sxy, const float2* __restrict__ q2,
-                                                  int64_t N, const cd* __restrict__ Lc, int d, double* __restrict__ u) {
+// Block per leaf: its targets against the sources of the 3 x 3 leaves around
+// it, which are three contiguous runs of the leaf-sorted sources (one per
+// row of leaves), staged through shared memory in tiles; every staged source
+// is read by all threads at once.  The direct part runs in float-float
+// (the own node skipped by its sorted position), flushed into FP64 every 32
+// sources of a tile; then each target adds the local expansion of its leaf
+// (Horner).  u = P2P / 4pi (log r^2) + Re(L2P) / 2pi.
+constexpr int EV_THREADS = 128;
+constexpr int EV_TILE = 256;
+
+__global__ void __launch_bounds__(EV_THREADS) k_fmm_eval(FmmGeo g, const int64_t* __restrict__ tstart,
+                                                         const int32_t* __restrict__ tperm, int64_t M,
+                                                         const double* __restrict__ txy, FFCoords tgt,
+                                                         const int32_t* __restrict__ tnode,
+                                                         const int32_t* __restrict__ spos,
+                                                         const int64_t* __restrict__ sstart,
+                                                         const float4* __restrict__ sxy, const float2* __restrict__ q2,
+                                                         int64_t N, const cd* __restrict__ Lc, int d,
+                                                         double* __restrict__ u) {
     __shared__ float4 stab[LOG_N];
+    __shared__ float4 s_xy[EV_TILE];
+    __shared__ float2 s_q[EV_TILE];
+    const int b = blockIdx.x;
+    const int64_t t0 = tstart[b], t1 = tstart[b + 1];
+    if (t0 == t1) return;                                     // uniform in the block
     for (int i = threadIdx.x; i < LOG_N; i += blockDim.x) stab[i] = g_logtab.e[i];
-    __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M) return;
-    const int32_t t = tperm[i];
-    const int b = tleaf[t];
     const int nb = 1 << g.L;
     const int ix = b % nb, iy = b / nb;
+    const int jx0 = max(ix - 1, 0), jx1 = min(ix + 1, nb - 1);
+    int64_t r0[3], r1[3];
+    int nr = 0;
+    for (int jy = max(iy - 1, 0); jy <= min(iy + 1, nb - 1); jy++) {
+        r0[nr] = sstart[(int64_t)jy * nb + jx0];
+        r1[nr] = sstart[(int64_t)jy * nb + jx1 + 1];
+        nr++;
+    }
     const double r = ldexp(g.side, -g.L);
     const cd c = box_center(g, g.L, ix, iy);
-    const cd z = {(txy[2 * t] - c.x) / r, (txy[2 * t + 1] - c.y) / r};
-    const float thx = tgt.hi[2 * t], thy = tgt.hi[2 * t + 1], tlx = tgt.lo[2 * t], tly = tgt.lo[2 * t + 1];
-    const int32_t own = tnode[t];
     const int64_t tot = g.lvl_off[g.L + 1];
-    for (int dd = 0; dd < d; dd++) {
-        // local expansion
-        const cd* B = Lc + ((int64_t)dd * tot + g.lvl_off[g.L] + b) * NC;
-        cd phi = B[FP];
-        for (int k = FP - 1; k >= 0; k--) phi = cfma(phi, z, B[k]);
-        // direct part: float-float partial sums of up to FLUSH sources,
-        // flushed into an FP64 accumulator (as the direct far sum does per tile)
-        constexpr int FLUSH = 32;
-        double acc = 0.0;
-        for (int jy = max(iy - 1, 0); jy <= min(iy + 1, nb - 1); jy++) {
-            for (int jx = max(ix - 1, 0); jx <= min(ix + 1, nb - 1); jx++) {
-                const int64_t lb = (int64_t)jy * nb + jx;
-                const int64_t s1 = sstart[lb + 1];
-                for (int64_t k0 = sstart[lb]; k0 < s1; k0 += FLUSH) {
-                    const int64_t k1 = min(k0 + FLUSH, s1);
-                    float sh = 0.f, sl = 0.f;
-#pragma unroll 4
-                    for (int64_t k = k0; k < k1; k++) {
-                        float s, corr;
-                        ff_dist2<true>(thx, thy, tlx, tly, sxy[k], s, corr);
-                        if (sperm[k] == own) {   // own node: log 1 = 0
-                            s = 1.0f;
-                            corr = 0.0f;
-                        }
-                        float lh, ll;
-                        ff_log(stab, s, corr, lh, ll);
-                        const float2 qv = q2[(int64_t)dd * N + k];
-                        ff_madd(qv.x, qv.y, lh, ll, sh, sl);
+    for (int64_t tb = t0; tb < t1; tb += EV_THREADS) {
+        const int64_t ti = tb + threadIdx.x;
+        const bool live = ti < t1;
+        const int32_t t = live ? tperm[ti] : 0;
+        const float thx = tgt.hi[2 * t], thy = tgt.hi[2 * t + 1], tlx = tgt.lo[2 * t], tly = tgt.lo[2 * t + 1];
+        const int32_t own = tnode[t];
+        const int64_t kown = (live && own >= 0) ? (int64_t)spos[own] : -1;
+        for (int dd = 0; dd < d; dd++) {
+            double acc = 0.0;
+            for (int q = 0; q < nr; q++) {
+                for (int64_t k0 = r0[q]; k0 < r1[q]; k0 += EV_TILE) {
+                    const int n = (int)min((int64_t)EV_TILE, r1[q] - k0);
+                    __syncthreads();
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                        s_xy[i] = sxy[k0 + i];
+                        s_q[i] = q2[(int64_t)dd * N + k0 + i];
                     }
-                    acc += (double)sh + (double)sl;
+                    __syncthreads();
+                    if (!live) continue;
+                    const int kl = (int)(kown - k0);              // own node's slot in this tile, if any
+                    for (int i0 = 0; i0 < n; i0 += 32) {
+                        const int i1 = min(i0 + 32, n);
+                        float sh = 0.f, sl = 0.f;
+#pragma unroll 4
+                        for (int i = i0; i < i1; i++) {
+                            float s2, corr;
+                            ff_dist2<true>(thx, thy, tlx, tly, s_xy[i], s2, corr);
+                            if (i == kl) {                        // own node: log 1 = 0
+                                s2 = 1.0f;
+                                corr = 0.0f;
+                            }
+                            float lh, ll;
+                            ff_log(stab, s2, corr, lh, ll);
+                            const float2 qv = s_q[i];
+                            ff_madd(qv.x, qv.y, lh, ll, sh, sl);
+                        }
+                        acc += (double)sh + (double)sl;
+                    }
                 }
             }
+            if (live) {
+                const cd z = {(txy[2 * t] - c.x) / r, (txy[2 * t + 1] - c.y) / r};
+                const cd* B = Lc + ((int64_t)dd * tot + g.lvl_off[g.L] + b) * NC;
+                cd phi = B[FP];
+                for (int k = FP - 1; k >= 0; k--) phi = cfma(phi, z, B[k]);
+                u[(int64_t)dd * M + t] = acc * VP_INV_FOUR_PI + phi.x * VP_INV_TWO_PI;
+            }
         }
-        u[(int64_t)dd * M + t] = acc * VP_INV_FOUR_PI + phi.x * VP_INV_TWO_PI;
     }
 }
 
@@ -366,6 +398,7 @@ struct FmmPlan {
     int32_t* d_sperm = nullptr;     // [N] sources by leaf, ascending inside
     int64_t* d_tstart = nullptr;
     int32_t* d_tperm = nullptr;
+    int32_t* d_spos = nullptr;      // [N] sorted position of each node
     int32_t* d_scnt = nullptr;      // [nbox_tot] sources per box, all levels
     int32_t* d_tcnt = nullptr;      // [nbox_tot] targets per box
     float4* d_sxy = nullptr;        // [N] sorted sources, float-float
@@ -377,7 +410,7 @@ struct FmmPlan {
 void fmm_plan_free(FmmPlan* p) {
     if (!p) return;
     void* ps[] = {p->d_lvl_off, p->d_sleaf, p->d_tleaf, p->d_sstart, p->d_sperm, p->d_tstart, p->d_tperm,
-                  p->d_scnt, p->d_tcnt, p->d_sxy, p->d_binom, p->d_wpow, p->d_T};
+                  p->d_spos, p->d_scnt, p->d_tcnt, p->d_sxy, p->d_binom, p->d_wpow, p->d_T};
     for (void* q : ps)
         if (q) cudaFree(q);
     delete p;
@@ -531,6 +564,7 @@ int fmm_plan_build(vp_ctx* ctx, vp_nf* nf, cudaStream_t s) {
     al(&p->d_tstart, nleaf + 1);
     al(&p->d_sperm, N);
     al(&p->d_tperm, M);
+    al(&p->d_spos, N);
     al(&p->d_scnt, p->nbox_tot);
     al(&p->d_tcnt, p->nbox_tot);
     al(&p->d_sxy, N);
@@ -601,7 +635,7 @@ int fmm_plan_build(vp_ctx* ctx, vp_nf* nf, cudaStream_t s) {
         return rc;
     }
     ensure_logtab();
-    k_fmm_sort_src<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(p->d_sperm, N, nf->src_ff, p->d_sxy);
+    k_fmm_sort_src<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(p->d_sperm, N, nf->src_ff, p->d_sxy, p->d_spos);
     if (cudaGetLastError() != cudaSuccess) return fail(VP_ERR_CUDA, "fmm plan: launch failed");
     int32_t h_flag = 0;
     if (cudaMemcpyAsync(&h_flag, ctx->d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -647,9 +681,8 @@ int fmm_far(vp_ctx* ctx, const vp_nf* nf, const double* f, int d, double* u, voi
     for (int l = 3; l <= L; l++)
         k_fmm_l2l<<<dim3((unsigned)((int64_t)1 << (2 * l)), (unsigned)d), FT, 0, s>>>(l, g, p->d_tcnt, p->d_binom,
                                                                                     p->d_wpow, Lc);
-    k_fmm_eval<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(g, p->d_tperm, p->d_tleaf, M, nf->d_txy, nf->tgt_ff,
-                                                           nf->d_tnode, p->d_sstart, p->d_sperm, p->d_sxy, q2, N, Lc, d,
-                                                           u);
+    k_fmm_eval<<<(unsigned)nleaf, EV_THREADS, 0, s>>>(g, p->d_tstart, p->d_tperm, M, nf->d_txy, nf->tgt_ff,
+                                                      nf->d_tnode, p->d_spos, p->d_sstart, p->d_sxy, q2, N, Lc, d, u);
     VP_LAUNCH_CHECK(ctx);
     return VP_OK;
 }

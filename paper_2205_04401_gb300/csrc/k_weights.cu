@@ -502,14 +502,16 @@ __global__ void __launch_bounds__(WARPS * 32, VP_NEAR_MINB) k_weights_near_f2(We
     float mh[VP_NB], ml[VP_NB];
 #pragma unroll
     for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
+    // the pairs here are those whose root is not a leaf (k_near_root_split):
+    // the traversal starts from the root's four children
     if (lane == 0) {
         SubTri r;
         r.v[0] = 0; r.v[1] = 0; r.v[2] = 1; r.v[3] = 0; r.v[4] = 0; r.v[5] = 1; r.L = 0;
-        stack[0] = r;
+        push_children(r, stack, 0);
     }
     __syncwarp();
-    int sp = 1, nleaf = 0, total_leaves = 0, capped = 0;
-    int visited = 0;
+    int sp = 4, nleaf = 0, total_leaves = 0, capped = 0;
+    int visited = 1;
     bool overflow = false;
     const unsigned lower = (1u << lane) - 1u;
     while (sp > 0 || nleaf > 0) {
