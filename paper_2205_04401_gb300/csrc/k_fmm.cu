@@ -293,17 +293,20 @@ __global__ void __launch_bounds__(FT) k_fmm_l2l(int l, FmmGeo g, const int32_t* 
 }
 
 // ------------------------------------------------------------ evaluation
-// Block per leaf: its targets against the sources of the 3 x 3 leaves around
-// it, which are three contiguous runs of the leaf-sorted sources (one per
-// row of leaves), staged through shared memory in tiles; every staged source
-// is read by all threads at once.  The direct part runs in float-float
+// Block per (leaf, run of up to EV_THREADS of its targets): the targets
+// against the sources of the 3 x 3 leaves around the leaf, which are three
+// contiguous runs of the leaf-sorted sources (one per row of leaves), staged
+// through shared memory in tiles; every staged source is read by all threads
+// at once.  (A block per leaf would serialise the many targets of the dense
+// leaves of a graded mesh on one SM.)  The direct part runs in float-float
 // (the own node skipped by its sorted position), flushed into FP64 every 32
 // sources of a tile; then each target adds the local expansion of its leaf
 // (Horner).  u = P2P / 4pi (log r^2) + Re(L2P) / 2pi.
 constexpr int EV_THREADS = 128;
 constexpr int EV_TILE = 256;
 
-__global__ void __launch_bounds__(EV_THREADS) k_fmm_eval(FmmGeo g, const int64_t* __restrict__ tstart,
+__global__ void __launch_bounds__(EV_THREADS) k_fmm_eval(FmmGeo g, const int2* __restrict__ units,
+                                                         const int64_t* __restrict__ tstart,
                                                          const int32_t* __restrict__ tperm, int64_t M,
                                                          const double* __restrict__ txy, FFCoords tgt,
                                                          const int32_t* __restrict__ tnode,
@@ -315,9 +318,9 @@ __global__ void __launch_bounds__(EV_THREADS) k_fmm_eval(FmmGeo g, const int64_t
     __shared__ float4 stab[LOG_N];
     __shared__ float4 s_xy[EV_TILE];
     __shared__ float2 s_q[EV_TILE];
-    const int b = blockIdx.x;
-    const int64_t t0 = tstart[b], t1 = tstart[b + 1];
-    if (t0 == t1) return;                                     // uniform in the block
+    const int2 un = units[blockIdx.x];
+    const int b = un.x;
+    const int64_t t0 = tstart[b] + (int64_t)un.y * EV_THREADS, t1 = min(t0 + EV_THREADS, tstart[b + 1]);
     for (int i = threadIdx.x; i < LOG_N; i += blockDim.x) stab[i] = g_logtab.e[i];
     const int nb = 1 << g.L;
     const int ix = b % nb, iy = b / nb;
@@ -399,6 +402,8 @@ struct FmmPlan {
     int64_t* d_tstart = nullptr;
     int32_t* d_tperm = nullptr;
     int32_t* d_spos = nullptr;      // [N] sorted position of each node
+    int2* d_units = nullptr;        // evaluation blocks: (leaf, run of EV_THREADS targets)
+    int64_t n_units = 0;
     int32_t* d_scnt = nullptr;      // [nbox_tot] sources per box, all levels
     int32_t* d_tcnt = nullptr;      // [nbox_tot] targets per box
     float4* d_sxy = nullptr;        // [N] sorted sources, float-float
@@ -410,7 +415,7 @@ struct FmmPlan {
 void fmm_plan_free(FmmPlan* p) {
     if (!p) return;
     void* ps[] = {p->d_lvl_off, p->d_sleaf, p->d_tleaf, p->d_sstart, p->d_sperm, p->d_tstart, p->d_tperm,
-                  p->d_spos, p->d_scnt, p->d_tcnt, p->d_sxy, p->d_binom, p->d_wpow, p->d_T};
+                  p->d_spos, p->d_units, p->d_scnt, p->d_tcnt, p->d_sxy, p->d_binom, p->d_wpow, p->d_T};
     for (void* q : ps)
         if (q) cudaFree(q);
     delete p;
@@ -642,6 +647,21 @@ int fmm_plan_build(vp_ctx* ctx, vp_nf* nf, cudaStream_t s) {
         cudaStreamSynchronize(s) != cudaSuccess)
         return fail(VP_ERR_CUDA, "fmm plan: build failed");
     if (h_flag) return fail(VP_ERR_CUDA, "fmm plan: leaf sort exceeded its capacity");
+    // evaluation blocks: every leaf's targets in runs of EV_THREADS
+    {
+        std::vector<int64_t> ts(nleaf + 1);
+        if (cudaMemcpy(ts.data(), p->d_tstart, (nleaf + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(VP_ERR_CUDA, "fmm plan: copy failed");
+        std::vector<int2> un;
+        for (int64_t b = 0; b < nleaf; b++)
+            for (int64_t k = 0; k * EV_THREADS < ts[b + 1] - ts[b]; k++) un.push_back(make_int2((int)b, (int)k));
+        p->n_units = (int64_t)un.size();
+        if (cudaMalloc(&p->d_units, std::max<size_t>(1, un.size()) * sizeof(int2)) != cudaSuccess)
+            return fail(VP_ERR_OOM, "fmm plan: device allocation failed");
+        if (!un.empty() &&
+            cudaMemcpy(p->d_units, un.data(), un.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(VP_ERR_CUDA, "fmm plan: copy failed");
+    }
     nf->fmm = p;
     return VP_OK;
 }
@@ -681,8 +701,10 @@ int fmm_far(vp_ctx* ctx, const vp_nf* nf, const double* f, int d, double* u, voi
     for (int l = 3; l <= L; l++)
         k_fmm_l2l<<<dim3((unsigned)((int64_t)1 << (2 * l)), (unsigned)d), FT, 0, s>>>(l, g, p->d_tcnt, p->d_binom,
                                                                                     p->d_wpow, Lc);
-    k_fmm_eval<<<(unsigned)nleaf, EV_THREADS, 0, s>>>(g, p->d_tstart, p->d_tperm, M, nf->d_txy, nf->tgt_ff,
-                                                      nf->d_tnode, p->d_spos, p->d_sstart, p->d_sxy, q2, N, Lc, d, u);
+    if (p->n_units > 0)
+        k_fmm_eval<<<(unsigned)p->n_units, EV_THREADS, 0, s>>>(g, p->d_units, p->d_tstart, p->d_tperm, M, nf->d_txy,
+                                                               nf->tgt_ff, nf->d_tnode, p->d_spos, p->d_sstart,
+                                                               p->d_sxy, q2, N, Lc, d, u);
     VP_LAUNCH_CHECK(ctx);
     return VP_OK;
 }
