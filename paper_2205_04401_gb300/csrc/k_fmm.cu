@@ -9,7 +9,8 @@
 //   local about c:      phi(z) = sum_l b_l ((z - c)/r)^l;
 // with the translations of Greengard and Rokhlin: M2M (child to parent),
 // M2L between the well-separated boxes of a level (children of the parent's
-// neighbours that are not neighbours), L2L (parent to child).  The leaves'
+// neighbours that are not neighbours; its products in float-float, the
+// expansions stored in FP64), L2L (parent to child).  The leaves'
 // own and adjacent boxes are summed directly (P2P) in the float-float
 // arithmetic of the direct far sum, skipping the target's own node.  With
 // one box of separation the translation error of a point source at the
@@ -24,6 +25,7 @@
 #include <vector>
 
 #include "vp_internal.h"
+#include "vp_f2.cuh"
 #include "vp_ff.cuh"
 
 #ifndef VP_FMM_P
@@ -129,18 +131,25 @@ __global__ void k_fmm_charges(const int32_t* __restrict__ perm, int64_t n, const
 
 // ------------------------------------------------------------ P2M
 // One block per (leaf, density): nodes in chunks of CH; thread j < CH forms
-// the powers of its node, thread k sums column k in node order.
+// the terms -q_j z_j^k / k of its node in float-float complex arithmetic
+// (36 complex products per node would occupy the FP64 pipe), thread k sums
+// column k of the chunk in node order in float-float and adds it into FP64.
 constexpr int CH = 64;
-__constant__ double c_inv[NC];   // 1/k
+__constant__ float2 c_inv2[NC];   // 1/k, float-float
+
+__device__ __forceinline__ void c2_mul(f2 ar, f2 ai, f2 br, f2 bi, f2& cr, f2& ci) {
+    cr = f2_add(f2_mul(ar, br), f2_neg(f2_mul(ai, bi)));
+    ci = f2_add(f2_mul(ar, bi), f2_mul(ai, br));
+}
+
 __global__ void __launch_bounds__(FT) k_fmm_p2m(FmmGeo g, const int64_t* __restrict__ start,
                                                 const int32_t* __restrict__ perm, const double* __restrict__ yxy,
-                                                const double* __restrict__ q, int64_t N, cd* __restrict__ M) {
-    __shared__ cd T[CH][NC + 1];
+                                                const float2* __restrict__ q2, int64_t N, cd* __restrict__ M) {
+    __shared__ float4 T[CH][NC + 1];
     const int64_t b = blockIdx.x;
     const int dd = blockIdx.y;
     const int64_t s0 = start[b], s1 = start[b + 1];
     const int nb = 1 << g.L;
-    const int64_t nbox = (int64_t)nb * nb;
     cd* out = M + ((int64_t)dd * g.lvl_off[g.L + 1] + lvl_off(g, g.L) + b) * NC;
     const int tid = threadIdx.x;
     if (s1 == s0) {
@@ -149,28 +158,40 @@ __global__ void __launch_bounds__(FT) k_fmm_p2m(FmmGeo g, const int64_t* __restr
     }
     const double r = ldexp(g.side, -g.L);
     const cd c = box_center(g, g.L, (int)(b % nb), (int)(b / nb));
-    cd acc = {0.0, 0.0};
+    double accx = 0.0, accy = 0.0;
     for (int64_t c0 = s0; c0 < s1; c0 += CH) {
         const int64_t i = c0 + tid;
         if (tid < CH && i < s1) {
             const int32_t j = perm[i];
-            const double qi = q[(int64_t)dd * N + i];
-            const cd z = {(yxy[2 * j] - c.x) / r, (yxy[2 * j + 1] - c.y) / r};
-            T[tid][0] = {qi, 0.0};
-            cd zk = {1.0, 0.0};
+            const float2 qv = q2[(int64_t)dd * N + i];
+            const f2 q = {qv.x, qv.y};
+            const f2 zr = f2_from_d((yxy[2 * j] - c.x) / r), zi = f2_from_d((yxy[2 * j + 1] - c.y) / r);
+            T[tid][0] = make_float4(q.h, q.l, 0.f, 0.f);
+            f2 kr = {1.f, 0.f}, ki = {0.f, 0.f};
+            const f2 nq = f2_neg(q);
             for (int k = 1; k <= FP; k++) {
-                zk = cmul(zk, z);
-                T[tid][k] = cscale(zk, -qi * c_inv[k]);
+                c2_mul(kr, ki, zr, zi, kr, ki);
+                const float2 iv = c_inv2[k];
+                const f2 sc = f2_mul(nq, {iv.x, iv.y});
+                const f2 tr = f2_mul(kr, sc), ti = f2_mul(ki, sc);
+                T[tid][k] = make_float4(tr.h, tr.l, ti.h, ti.l);
             }
         }
         __syncthreads();
         const int cnt = (int)min((int64_t)CH, s1 - c0);
-        if (tid < NC)
-            for (int jj = 0; jj < cnt; jj++) acc = cadd(acc, T[jj][tid]);
+        if (tid < NC) {
+            f2 sr = {0.f, 0.f}, si = {0.f, 0.f};
+            for (int jj = 0; jj < cnt; jj++) {
+                const float4 t = T[jj][tid];
+                sr = f2_add(sr, {t.x, t.y});
+                si = f2_add(si, {t.z, t.w});
+            }
+            accx += f2_to_d(sr);
+            accy += f2_to_d(si);
+        }
         __syncthreads();
     }
-    (void)nbox;
-    if (tid < NC) out[tid] = acc;
+    if (tid < NC) out[tid] = {accx, accy};
 }
 
 // ------------------------------------------------------------ M2M
@@ -224,10 +245,24 @@ __global__ void __launch_bounds__(FT) k_fmm_m2m(int l, FmmGeo g, const int32_t* 
 // v = (source centre - target centre) / r, and b_0 += a_0 log r; the
 // matrices (level independent with scaled expansions) are built on the host.
 // One block per (target box, density) over the boxes of every level 2..L.
+// Multipoles as float-float complex values (re h, re l, im h, im l) for the
+// M2L products.
+__global__ void k_fmm_m_f2(const cd* __restrict__ M, int64_t n, float4* __restrict__ M2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const f2 re = f2_from_d(M[i].x), im = f2_from_d(M[i].y);
+    M2[i] = make_float4(re.h, re.l, im.h, im.l);
+}
+
+// The products run in float-float (the FP64 pipe would bound them at 4 DFMA
+// per complex multiply-add; the FP32 pipe does the float-float ones about five
+// times faster): each source box's 37-term sum is accumulated in float-float,
+// renormalised after every term, and added into FP64; the local expansion is
+// stored in FP64.
 __global__ void __launch_bounds__(FT) k_fmm_m2l(FmmGeo g, const int32_t* __restrict__ cnt_src,
-                                                const int32_t* __restrict__ cnt_tgt, const cd* __restrict__ T,
-                                                const cd* __restrict__ M, cd* __restrict__ Lc) {
-    __shared__ cd A[NC];
+                                                const int32_t* __restrict__ cnt_tgt, const float4* __restrict__ T2,
+                                                const float4* __restrict__ M2, cd* __restrict__ Lc) {
+    __shared__ float4 A[NC];
     const int64_t gb = blockIdx.x + g.lvl_off[2];   // global box index (levels >= 2)
     const int dd = blockIdx.y;
     int l = 2;
@@ -237,9 +272,9 @@ __global__ void __launch_bounds__(FT) k_fmm_m2l(FmmGeo g, const int32_t* __restr
     const int ix = (int)(b % nb), iy = (int)(b / nb);
     const int64_t tot = g.lvl_off[g.L + 1];
     const int tid = threadIdx.x;
-    cd acc = {0.0, 0.0};
+    double accx = 0.0, accy = 0.0;
     if (cnt_tgt[gb] > 0) {
-        const double logr = log(ldexp(g.side, -l));
+        const f2 logr = f2_from_d(log(ldexp(g.side, -l)));
         const int px = ix >> 1, py = iy >> 1;
         for (int cy = 2 * (py - 1); cy <= 2 * (py + 1) + 1; cy++) {
             if (cy < 0 || cy >= nb) continue;
@@ -250,18 +285,29 @@ __global__ void __launch_bounds__(FT) k_fmm_m2l(FmmGeo g, const int32_t* __restr
                 const int64_t sb = (int64_t)cy * nb + cx;
                 if (cnt_src[g.lvl_off[l] + sb] == 0) continue;
                 __syncthreads();
-                if (tid < NC) A[tid] = M[((int64_t)dd * tot + g.lvl_off[l] + sb) * NC + tid];
+                if (tid < NC) A[tid] = M2[((int64_t)dd * tot + g.lvl_off[l] + sb) * NC + tid];
                 __syncthreads();
                 if (tid < NC) {
-                    const cd* To = T + (int64_t)((dy + 3) * 7 + (dx + 3)) * NC * NC + tid;   // column tid, k-major
-                    if (tid == 0) acc.x += A[0].x * logr;
+                    const float4* To = T2 + (int64_t)((dy + 3) * 7 + (dx + 3)) * NC * NC + tid;   // column tid, k-major
+                    float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;   // re, im
+                    if (tid == 0) f2_acc(ah, al, {A[0].x, A[0].y}, logr);
 #pragma unroll 4
-                    for (int k = 0; k <= FP; k++) acc = cfma(A[k], To[(int64_t)k * NC], acc);
+                    for (int k = 0; k <= FP; k++) {
+                        const float4 a = A[k], t = To[(int64_t)k * NC];
+                        f2_acc(ah, al, {a.x, a.y}, {t.x, t.y});
+                        f2_acc(ah, al, {-a.z, -a.w}, {t.z, t.w});
+                        f2_acc(bh, bl, {a.x, a.y}, {t.z, t.w});
+                        f2_acc(bh, bl, {a.z, a.w}, {t.x, t.y});
+                        const f2 ra = f2_fast(ah, al), rb = f2_fast(bh, bl);
+                        ah = ra.h; al = ra.l; bh = rb.h; bl = rb.l;
+                    }
+                    accx += (double)ah + (double)al;
+                    accy += (double)bh + (double)bl;
                 }
             }
         }
     }
-    if (tid < NC) Lc[((int64_t)dd * tot + gb) * NC + tid] = acc;
+    if (tid < NC) Lc[((int64_t)dd * tot + gb) * NC + tid] = {accx, accy};
 }
 
 // ------------------------------------------------------------ L2L
@@ -409,13 +455,13 @@ struct FmmPlan {
     float4* d_sxy = nullptr;        // [N] sorted sources, float-float
     double* d_binom = nullptr;      // [2NC][2NC] binomial coefficients
     cd* d_wpow = nullptr;           // [4][2NC] powers of the child offsets
-    cd* d_T = nullptr;              // [49][NC][NC] M2L matrices of the offsets, k-major
+    float4* d_T2 = nullptr;         // [49][NC][NC] M2L matrices of the offsets, k-major, float-float (re h, re l, im h, im l)
 };
 
 void fmm_plan_free(FmmPlan* p) {
     if (!p) return;
     void* ps[] = {p->d_lvl_off, p->d_sleaf, p->d_tleaf, p->d_sstart, p->d_sperm, p->d_tstart, p->d_tperm,
-                  p->d_spos, p->d_units, p->d_scnt, p->d_tcnt, p->d_sxy, p->d_binom, p->d_wpow, p->d_T};
+                  p->d_spos, p->d_units, p->d_scnt, p->d_tcnt, p->d_sxy, p->d_binom, p->d_wpow, p->d_T2};
     for (void* q : ps)
         if (q) cudaFree(q);
     delete p;
@@ -575,7 +621,7 @@ int fmm_plan_build(vp_ctx* ctx, vp_nf* nf, cudaStream_t s) {
     al(&p->d_sxy, N);
     al(&p->d_binom, binom.size());
     al(&p->d_wpow, wpow.size());
-    al(&p->d_T, Tm.size());
+    al(&p->d_T2, Tm.size());
     int64_t* d_cursor = nullptr;
     al(&d_cursor, nleaf + 1);
     if (e != cudaSuccess) {
@@ -585,12 +631,21 @@ int fmm_plan_build(vp_ctx* ctx, vp_nf* nf, cudaStream_t s) {
     cudaMemcpyAsync(p->d_lvl_off, p->h_lvl_off.data(), (L + 2) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(p->d_binom, binom.data(), binom.size() * sizeof(double), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(p->d_wpow, wpow.data(), wpow.size() * sizeof(cd), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(p->d_T, Tm.data(), Tm.size() * sizeof(cd), cudaMemcpyHostToDevice, s);
+    std::vector<float4> T2(Tm.size());
+    for (size_t i = 0; i < Tm.size(); i++) {
+        const float rh = (float)Tm[i].x, ih = (float)Tm[i].y;
+        T2[i] = make_float4(rh, (float)(Tm[i].x - (double)rh), ih, (float)(Tm[i].y - (double)ih));
+    }
+    cudaMemcpy(p->d_T2, T2.data(), T2.size() * sizeof(float4), cudaMemcpyHostToDevice);
     {
-        double inv[NC];
-        inv[0] = 0.0;
-        for (int k = 1; k < NC; k++) inv[k] = 1.0 / k;
-        cudaMemcpyToSymbolAsync(c_inv, inv, sizeof(inv), 0, cudaMemcpyHostToDevice, s);
+        float2 inv[NC];
+        inv[0] = make_float2(0.f, 0.f);
+        for (int k = 1; k < NC; k++) {
+            const double v = 1.0 / k;
+            const float h = (float)v;
+            inv[k] = make_float2(h, (float)(v - (double)h));
+        }
+        cudaMemcpyToSymbolAsync(c_inv2, inv, sizeof(inv), 0, cudaMemcpyHostToDevice, s);
     }
     const FmmGeo g = fmm_geo(p);
     int rc = VP_OK;
@@ -669,7 +724,7 @@ int fmm_plan_build(vp_ctx* ctx, vp_nf* nf, cudaStream_t s) {
 size_t fmm_ws_bytes(const vp_nf* nf, int d) {
     if (!nf->fmm) return 0;
     const int64_t N = nf->mesh->N;
-    return 2 * ((size_t)d * nf->fmm->nbox_tot * NC * sizeof(cd) + 256) + (size_t)d * N * (sizeof(double) + sizeof(float2)) +
+    return 3 * ((size_t)d * nf->fmm->nbox_tot * NC * sizeof(cd) + 256) + (size_t)d * N * (sizeof(double) + sizeof(float2)) +
            512;
 }
 
@@ -687,17 +742,21 @@ int fmm_far(vp_ctx* ctx, const vp_nf* nf, const double* f, int d, double* u, voi
     };
     cd* Mp = (cd*)take((size_t)d * p->nbox_tot * NC * sizeof(cd));
     cd* Lc = (cd*)take((size_t)d * p->nbox_tot * NC * sizeof(cd));
+    float4* M2 = (float4*)take((size_t)d * p->nbox_tot * NC * sizeof(float4));
     double* q = (double*)take((size_t)d * N * sizeof(double));
     float2* q2 = (float2*)take((size_t)d * N * sizeof(float2));
     const int64_t nleaf = (int64_t)1 << (2 * L);
     k_fmm_charges<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(p->d_sperm, N, mesh->d_W, f, d, q, q2);
-    k_fmm_p2m<<<dim3((unsigned)nleaf, (unsigned)d), FT, 0, s>>>(g, p->d_sstart, p->d_sperm, mesh->d_y, q, N, Mp);
+    k_fmm_p2m<<<dim3((unsigned)nleaf, (unsigned)d), FT, 0, s>>>(g, p->d_sstart, p->d_sperm, mesh->d_y, q2, N, Mp);
     for (int l = L - 1; l >= 2; l--)
         k_fmm_m2m<<<dim3((unsigned)((int64_t)1 << (2 * l)), (unsigned)d), FT, 0, s>>>(l, g, p->d_scnt, p->d_binom,
                                                                                     p->d_wpow, Mp);
     const int64_t n_m2l = p->nbox_tot - p->h_lvl_off[2];
-    if (L >= 2)
-        k_fmm_m2l<<<dim3((unsigned)n_m2l, (unsigned)d), FT, 0, s>>>(g, p->d_scnt, p->d_tcnt, p->d_T, Mp, Lc);
+    if (L >= 2) {
+        const int64_t nm = (int64_t)d * p->nbox_tot * NC;
+        k_fmm_m_f2<<<(unsigned)((nm + 255) / 256), 256, 0, s>>>(Mp, nm, M2);
+        k_fmm_m2l<<<dim3((unsigned)n_m2l, (unsigned)d), FT, 0, s>>>(g, p->d_scnt, p->d_tcnt, p->d_T2, M2, Lc);
+    }
     for (int l = 3; l <= L; l++)
         k_fmm_l2l<<<dim3((unsigned)((int64_t)1 << (2 * l)), (unsigned)d), FT, 0, s>>>(l, g, p->d_tcnt, p->d_binom,
                                                                                     p->d_wpow, Lc);

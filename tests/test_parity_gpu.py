@@ -301,3 +301,27 @@ def test_errors_are_reported(vp, ctx):
     with pytest.raises(vp.VPError) as e:
         vp.mesh_upload(ctx, np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]]), np.array([[0, 1, 3]], np.int32))
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("cap", [0, 1, 2])
+def test_depth_cap_trees_match_oracle(vp, ctx, tables, cfg1, cap):
+    """Shallow depth caps (Section 3.3's subdivision stopped at depth `cap`):
+    cap 0 makes every near pair a root leaf (the root classifier's capped
+    branch), caps 1 and 2 stop the traversal kernel early; the capped counts,
+    leaf counts and weights match the oracle's for the same cap."""
+    mesh, dens = cfg1
+    o = Oracle("far16", tables=tables, depth_cap=cap)
+    s = o.setup(mesh.vxy, mesh.tri)
+    f = np.stack([d(s["yxy"]) for d in dens])
+    u_or, info = o.potential(s, f)
+    m = vp.mesh_upload(ctx, mesh.vxy, mesh.tri, 16)
+    nf = vp.nearfield_build(ctx, m, node_targets=True, depth_cap=cap)
+    st = vp.nf_stats(nf)
+    C = vp.nf_weights(nf).cpu().numpy()
+    u = vp.potential_eval(ctx, nf, torch.from_numpy(f).cuda(), precision=0).cpu().numpy()
+    assert st["depth_capped"] == info["capped"]
+    if cap == 0:
+        assert info["capped"] > 0
+    assert st["near_leaves"] == int(info["stats"][info["pkind"] == 0].sum())
+    compare_weights(C, info["C"], s["J"], info["ptri"])
+    assert rel_err(u, u_or).max() <= 1e-12
