@@ -279,7 +279,6 @@ struct WeightsF2 {
     const float2* wq2;    // [N] W_j / 4pi
 };
 
-__device__ __forceinline__ f2 f2_neg(f2 a) { return {-a.h, -a.l}; }
 
 // Warp-wide reduce-scatter of 16 float-float values (the FP64 version's
 // pattern): afterwards lane l holds the warp total of value (l >> 1).

@@ -17,6 +17,7 @@ __device__ __forceinline__ f2 f2_from_d(double d) {
     return {h, __double2float_rn(d - (double)h)};
 }
 __device__ __forceinline__ double f2_to_d(f2 a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ f2 f2_neg(f2 a) { return {-a.h, -a.l}; }
 
 // s + e = a + b exactly (Knuth)
 __device__ __forceinline__ void f2_two_sum(float a, float b, float& s, float& e) {
