@@ -233,10 +233,13 @@ static int64_t sym_units(int64_t N, std::vector<int32_t>* uI, std::vector<int64_
     return units;
 }
 
+// Source splits of the extra-target sum: about 16 blocks per SM (two waves at
+// eight resident blocks), so that few targets still fill the GPU and the last
+// wave is short (4 per SM left half the block slots empty).
 static int extra_splits(int64_t N, int64_t m, int sm_count) {
     if (m <= 0) return 0;
     const int64_t blocks = (m + SYM_TI - 1) / SYM_TI;
-    int64_t sp = (4LL * sm_count + blocks - 1) / blocks;
+    int64_t sp = (16LL * sm_count + blocks - 1) / blocks;
     sp = std::min<int64_t>(sp, std::max<int64_t>(1, N / 1024));
     return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 256));
 }
