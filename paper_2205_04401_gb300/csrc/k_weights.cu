@@ -313,6 +313,26 @@ __device__ __forceinline__ f2 reduce_scatter16_f2(f2* v, int lane) {
     return f2_add(v[0], {__shfl_xor_sync(0xffffffffu, v[0].h, 1), __shfl_xor_sync(0xffffffffu, v[0].l, 1)});
 }
 
+// C_k = s - [k != own] W_k G(x, y_k) for node k of the pair's triangle, stored
+// in FP64 and float-float.
+__device__ __forceinline__ void far_subtract_store(const WeightsArgs& a, const WeightsF2& b, int64_t p, int T, int t,
+                                                   int own, int k, f2 s, const float4* ftab, const LogSmem& lt,
+                                                   double ln2) {
+    if (k != own) {
+        const int64_t j = (int64_t)T * a.nq + k;
+        const float4 X = b.x2[t], Y = b.y2[j];
+        const f2 dx = f2_add({X.x, X.y}, {-Y.x, -Y.y}), dy = f2_add({X.z, X.w}, {-Y.z, -Y.w});
+        const f2 r2 = f2_add(f2_sqr(dx), f2_sqr(dy));
+        f2 lg;
+        if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);
+        else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
+        const float2 wq = b.wq2[j];
+        s = f2_add(s, f2_neg(f2_mul(lg, {wq.x, wq.y})));
+    }
+    a.C[p * a.nq + k] = f2_to_d(s);
+    if (a.C2) a.C2[p * a.nq + k] = make_float2(s.h, s.l);
+}
+
 // mu (float-float accumulators) -> C_k = sum_i Q_ki mu_i - [k != own] W_k G(x, y_k)
 __device__ __forceinline__ void finish_pair_f2(const WeightsArgs& a, const WeightsF2& b, int64_t p, int T, int t,
                                                int own, const float* mh, const float* ml, int lane,
@@ -332,22 +352,7 @@ __device__ __forceinline__ void finish_pair_f2(const WeightsArgs& a, const Weigh
             const float2 Q = Qk[q];
             f2_acc(ah, al, {Q.x, Q.y}, mq);
         }
-        f2 s = f2_fast(ah, al);
-        if (k < a.nq) {
-            if (k != own) {
-                const int64_t j = (int64_t)T * a.nq + k;
-                const float4 X = b.x2[t], Y = b.y2[j];
-                const f2 dx = f2_add({X.x, X.y}, {-Y.x, -Y.y}), dy = f2_add({X.z, X.w}, {-Y.z, -Y.w});
-                const f2 r2 = f2_add(f2_sqr(dx), f2_sqr(dy));
-                f2 lg;
-                if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);
-                else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
-                const float2 wq = b.wq2[j];
-                s = f2_add(s, f2_neg(f2_mul(lg, {wq.x, wq.y})));
-            }
-            a.C[p * a.nq + k] = f2_to_d(s);
-            if (a.C2) a.C2[p * a.nq + k] = make_float2(s.h, s.l);
-        }
+        if (k < a.nq) far_subtract_store(a, b, p, T, t, own, k, f2_fast(ah, al), ftab, lt, ln2);
     }
 }
 
@@ -626,24 +631,26 @@ __global__ void __launch_bounds__(256) k_near_root_split(WeightsArgs a, WeightsF
     }
 }
 
-// Root-leaf near pairs: the near rule on the whole triangle (leaf D0 = A - x,
-// a0 = 0, scale 1), one warp per pair, then the moment-to-weight step.
+// Root-leaf near pairs: the near rule on the whole triangle.  Its nodes sit at
+// fixed reference points z_j, so the moments and the moment-to-weight map
+// fold into one constant matrix of the far rule, C_k = sum_j B_jk g_j with
+// g_j = log|y_j - x|^2 w_j J_T / 4pi (B = QM M(z)^T, tabulated per rule):
+// one warp per pair forms the 49 g_j in shared memory, lane k the dot
+// product of node k (32 nodes per pass), then the far-rule subtraction.
 #ifndef VP_ROOT_MINB
 #define VP_ROOT_MINB 6
 #endif
 __global__ void __launch_bounds__(WARPS * 32, VP_ROOT_MINB) k_weights_near_root(WeightsArgs a, WeightsF2 b,
                                                                                 const int32_t* __restrict__ idx,
                                                                                 int64_t n) {
-    __shared__ float4 exy_all[WARPS][VP_NNEAR];
+    __shared__ float2 g_all[WARPS][VP_NNEAR];
     __shared__ float4 ftab[LOG_N];
     __shared__ float4 nz_s[VP_NNEAR];
-    __shared__ float4 nz3_s[VP_NNEAR];   // 3 z_j, float-float
     __shared__ float2 nw_s[VP_NNEAR];
     __shared__ LogSmem lt;
     for (int i = threadIdx.x; i < LOG_N; i += blockDim.x) ftab[i] = g_logtab.e[i];
     for (int i = threadIdx.x; i < VP_NNEAR; i += blockDim.x) {
         nz_s[i] = a.tab->nz2[i];
-        nz3_s[i] = a.tab->nz3[i];
         nw_s[i] = a.tab->nw2[i];
     }
     load_logtab(a.tab, lt);              // ends with __syncthreads
@@ -651,23 +658,41 @@ __global__ void __launch_bounds__(WARPS * 32, VP_ROOT_MINB) k_weights_near_root(
     const int64_t w = (int64_t)blockIdx.x * WARPS + wl;
     if (w >= n) return;
     const double ln2 = a.tab->ln2;
-    float4* exy = exy_all[wl];
+    float2* gs = g_all[wl];
     const int64_t p = idx[w];
     const int T = a.ptri[p], t = a.ptgt[p];
     const int own = own_index(a, t, T);
     const NearPairF2 g = near_pair_f2(b, T, t);
-    near_exy(g, nz_s, exy, lane);
-    LeafF2 lf;
-    lf.d0xh = g.ax.h; lf.d0xl = g.ax.l; lf.d0yh = g.ay.h; lf.d0yl = g.ay.l;
-    lf.u0h = -1.f; lf.u0l = 0.f; lf.v0h = -1.f; lf.v0l = 0.f;
-    lf.sh = 1.f;
-    lf.wjh = g.wj.h; lf.wjl = g.wj.l; lf.pad = 0.f;
+    for (int j = lane; j < VP_NNEAR; j += 32) {
+        const float4 Z = nz_s[j];
+        const f2 zx = {Z.x, Z.y}, zy = {Z.z, Z.w};
+        const f2 dx = f2_add(g.ax, f2_add(f2_mul(zx, g.ex), f2_mul(zy, g.fx)));   // y_j - x
+        const f2 dy = f2_add(g.ay, f2_add(f2_mul(zx, g.ey), f2_mul(zy, g.fy)));
+        const f2 r2 = f2_add(f2_sqr(dx), f2_sqr(dy));
+        f2 lg;
+        if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);
+        else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
+        const float2 W = nw_s[j];
+        const f2 gj = f2_mul(lg, f2_mul({W.x, W.y}, g.wj));
+        gs[j] = make_float2(gj.h, gj.l);
+    }
     __syncwarp();
-    float mh[VP_NB], ml[VP_NB];
-#pragma unroll
-    for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
-    for (int j = lane; j < VP_NNEAR; j += 32) near_leaf_node(lf, exy[j], nz3_s[j], nw_s[j], ftab, lt, ln2, mh, ml);
-    finish_pair_f2(a, b, p, T, t, own, mh, ml, lane, ftab, lt, ln2);
+    for (int k0 = 0; k0 < a.nq; k0 += 32) {
+        const int k = k0 + lane;
+        const float2* Bk = a.B2 + (k < a.nq ? k : 0);
+        float ah = 0.f, al = 0.f;
+#pragma unroll 7
+        for (int j = 0; j < VP_NNEAR; j++) {
+            const float2 gj = gs[j], B = Bk[(int64_t)j * a.nq];
+            f2_acc(ah, al, {B.x, B.y}, {gj.x, gj.y});
+            if ((j & 7) == 7) {
+                const f2 r = f2_fast(ah, al);
+                ah = r.h;
+                al = r.l;
+            }
+        }
+        if (k < a.nq) far_subtract_store(a, b, p, T, t, own, k, f2_fast(ah, al), ftab, lt, ln2);
+    }
 }
 
 // ---------------------------------------------------- self, float-float

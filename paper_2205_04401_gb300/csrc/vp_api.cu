@@ -97,6 +97,7 @@ void fill_tables(VpTables& t) {
     for (int r = 0; r < 2; r++)
         for (int k = 0; k < nq[r]; k++)
             for (int a = 0; a < VP_NB; a++) t.Q2[r][k][a] = split(fqm[r][k * VP_NB + a]);
+    for (int r = 0; r < 2; r++) root_leaf_map(fqm[r], nq[r], t.B2[r]);
     for (int j = 0; j < VP_NGL; j++) {
         t.lx2[j] = split(VP_GL16_X[j]);
         t.lw2[j] = split(VP_GL16_W[j]);
@@ -677,6 +678,7 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         wa.tab = ctx->d_tables;
         wa.Q = mesh->rule.dev.Q;
         wa.Q2 = mesh->rule.dev.Q2;
+        wa.B2 = mesh->rule.dev.B2;
         wa.nq = nq;
         wa.tv = mesh->d_tv;
         wa.J = mesh->d_J;

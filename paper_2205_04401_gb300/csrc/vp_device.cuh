@@ -35,6 +35,9 @@ struct VpTables {
     float4 nz3[VP_NNEAR];               // 3 x, 3 y of the near-rule nodes (h, l)
     float2 nw2[VP_NNEAR];               // near-rule weights
     float2 Q2[2][VP_MAXQ][VP_NB];       // Q for moments in the monomial basis (f2_mon15_acc)
+    // root-leaf map of rule r: a near pair whose triangle is a leaf has
+    // C_k = sum_j B[j nq + k] g_j over the near-rule nodes j (B = QM M^T)
+    float2 B2[2][VP_NNEAR * VP_MAXQ];
     float2 lx2[VP_NGL], lw2[VP_NGL];    // Gauss-Legendre nodes and weights on [0, 1]
     float2 gr2[VP_NGGQ], glr2[VP_NGGQ], gwl2[VP_NGGQ];   // GGQ nodes, their logs, weights / 2pi
 };

@@ -32,6 +32,7 @@ struct FarRuleDev {
     const double* w = nullptr;    // [nq]
     const double* Q = nullptr;    // [nq][VP_NB], moments in the tensor-Legendre basis (leg15)
     const float2* Q2 = nullptr;   // [nq][VP_NB], float-float, moments in the monomial basis (f2_mon15_acc)
+    const float2* B2 = nullptr;   // [VP_NNEAR][nq], float-float: root-leaf map, C_k = sum_j B2[j nq + k] g_j
     int nq = 0;
 };
 struct FarRule {
@@ -76,6 +77,8 @@ struct vp_ctx {
 
 // far rules (vp_rules.cu)
 bool far_rule_valid(int32_t rule);
+// B2[j nq + k] = sum_i QM[k][i] M_i(u_j, v_j) at the near-rule nodes (float-float)
+void root_leaf_map(const double* QM, int nq, float2* B2);
 int far_rule_nq(int32_t rule);
 int far_rule_get(vp_ctx* ctx, int32_t rule, FarRule* out);
 void far_rules_free(vp_ctx* ctx);
@@ -232,6 +235,7 @@ struct WeightsArgs {
     const VpTables* tab;
     const double* Q;    // far rule's moment-to-weight map [nq][VP_NB] (tensor-Legendre moments)
     const float2* Q2;   // float-float map for monomial-basis moments (the float-float kernels)
+    const float2* B2;   // root-leaf map of the far rule (k_weights_near_root)
     int nq;
     const double* tv;
     const double* J;

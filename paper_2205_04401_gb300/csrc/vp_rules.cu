@@ -171,6 +171,24 @@ void projection_q(const Rule& r, std::vector<double>& Q, std::vector<double>& QM
     }
 }
 
+}  // namespace
+
+void root_leaf_map(const double* QM, int nq, float2* B2) {
+    for (int j = 0; j < VP_NNEAR; j++) {
+        long double M[VP_NB];
+        mon15_ld(VP_NEAR49_X[j], VP_NEAR49_Y[j], M);
+        for (int k = 0; k < nq; k++) {
+            long double b = 0.0L;
+            for (int i = 0; i < VP_NB; i++) b += (long double)QM[(size_t)k * VP_NB + i] * M[i];
+            const double bd = (double)b;
+            const float h = (float)bd;
+            B2[(size_t)j * nq + k] = make_float2(h, (float)(bd - (double)h));
+        }
+    }
+}
+
+namespace {
+
 bool conical_code(int32_t rule) {
     return rule >= VP_RULE_CONICAL(VP_RULE_CONICAL_MIN) && rule <= VP_RULE_CONICAL(VP_RULE_CONICAL_MAX);
 }
@@ -202,6 +220,7 @@ int far_rule_get(vp_ctx* ctx, int32_t rule, FarRule* out) {
         r.dev.w = (const double*)(base + offsetof(VpTables, fw) + ri * sizeof(t.fw[0]));
         r.dev.Q = (const double*)(base + offsetof(VpTables, Q) + ri * sizeof(t.Q[0]));
         r.dev.Q2 = (const float2*)(base + offsetof(VpTables, Q2) + ri * sizeof(t.Q2[0]));
+        r.dev.B2 = (const float2*)(base + offsetof(VpTables, B2) + ri * sizeof(t.B2[0]));
         *out = r;
         return VP_OK;
     }
@@ -217,7 +236,7 @@ int far_rule_get(vp_ctx* ctx, int32_t rule, FarRule* out) {
     std::vector<double> Q, QM;
     projection_q(g, Q, QM);
     const size_t nd = (size_t)nq * (3 + VP_NB);
-    std::vector<char> blob(nd * sizeof(double) + (size_t)nq * VP_NB * sizeof(float2));
+    std::vector<char> blob(nd * sizeof(double) + (size_t)nq * (VP_NB + VP_NNEAR) * sizeof(float2));
     double* hd = (double*)blob.data();
     std::copy(g.x.begin(), g.x.end(), hd);
     std::copy(g.y.begin(), g.y.end(), hd + nq);
@@ -228,6 +247,7 @@ int far_rule_get(vp_ctx* ctx, int32_t rule, FarRule* out) {
         const float h = (float)QM[i];
         hq2[i] = make_float2(h, (float)(QM[i] - (double)h));
     }
+    root_leaf_map(QM.data(), nq, hq2 + (size_t)nq * VP_NB);
     FarRule r;
     r.code = rule;
     r.degree = g.degree;
@@ -246,6 +266,7 @@ int far_rule_get(vp_ctx* ctx, int32_t rule, FarRule* out) {
     r.dev.w = dd + 2 * nq;
     r.dev.Q = dd + 3 * nq;
     r.dev.Q2 = (const float2*)((const char*)r.d_buf + nd * sizeof(double));
+    r.dev.B2 = r.dev.Q2 + (size_t)nq * VP_NB;
     ctx->gen_rules.push_back(r);
     *out = r;
     return VP_OK;
