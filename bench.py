@@ -1002,7 +1002,7 @@ def main():
     # smsp__thread_inst_executed.sum on the 2,048-triangle star,
     # profiles/far_sym_weights_star2048_counts.md): symmetric far sum 105.7 per
     # unordered node pair, its diagonal tiles 85.7 and the extra targets 83.5
-    # per ordered pair, near weights 721 per (leaf, node) evaluation including
+    # per ordered pair, near weights 749 per (leaf, node) evaluation including
     # the per-pair work (root classifier, root-leaf and traversal kernels),
     # self weights 48,300 per panel.
     TI = 512                     # target tile of the symmetric far sum
@@ -1013,7 +1013,7 @@ def main():
         diag += sz * sz
     far_inst = unord * 105.7 + diag * 85.7 + (M - N) * N * 83.5
     work = {
-        "weights_near": ("alu", stats["near_leaves"] * 49 * 721.4 * args.steps, issue_peak / 1e12, "Tinst/s"),
+        "weights_near": ("alu", stats["near_leaves"] * 49 * 748.7 * args.steps, issue_peak / 1e12, "Tinst/s"),
         "weights_self": ("alu", stats["self_panels"] * 48328.0 * args.steps, issue_peak / 1e12, "Tinst/s"),
         "far_ff": ("alu", far_inst * args.steps, issue_peak / 1e12, "Tinst/s"),
         "far_fp64": ("alu", float(M) * N * 80.0 * args.steps, dfma_peak / 1e12, "FP64 TFLOP/s"),
