@@ -348,7 +348,10 @@ __global__ void __launch_bounds__(FT) k_fmm_l2l(int l, FmmGeo g, const int32_t* 
 // (the own node skipped by its sorted position), flushed into FP64 every 32
 // sources of a tile; then each target adds the local expansion of its leaf
 // (Horner).  u = P2P / 4pi (log r^2) + Re(L2P) / 2pi.
-constexpr int EV_THREADS = 128;
+#ifndef VP_FMM_EV_THREADS
+#define VP_FMM_EV_THREADS 128
+#endif
+constexpr int EV_THREADS = VP_FMM_EV_THREADS;   // targets (and threads) per evaluation block
 constexpr int EV_TILE = 256;
 
 __global__ void __launch_bounds__(EV_THREADS) k_fmm_eval(FmmGeo g, const int2* __restrict__ units,
@@ -702,14 +705,32 @@ int fmm_plan_build(vp_ctx* ctx, vp_nf* nf, cudaStream_t s) {
         cudaStreamSynchronize(s) != cudaSuccess)
         return fail(VP_ERR_CUDA, "fmm plan: build failed");
     if (h_flag) return fail(VP_ERR_CUDA, "fmm plan: leaf sort exceeded its capacity");
-    // evaluation blocks: every leaf's targets in runs of EV_THREADS
+    // evaluation blocks: every leaf's targets in runs of EV_THREADS, heaviest
+    // first (targets x sources of the 3 x 3 leaves), so that the blocks that
+    // start last are short and the last wave ends together
     {
-        std::vector<int64_t> ts(nleaf + 1);
-        if (cudaMemcpy(ts.data(), p->d_tstart, (nleaf + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        std::vector<int64_t> ts(nleaf + 1), ss(nleaf + 1);
+        if (cudaMemcpy(ts.data(), p->d_tstart, (nleaf + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(ss.data(), p->d_sstart, (nleaf + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
             return fail(VP_ERR_CUDA, "fmm plan: copy failed");
+        const int nb = 1 << L;
+        std::vector<std::pair<int64_t, int2>> wu;
+        for (int64_t b = 0; b < nleaf; b++) {
+            const int64_t nt = ts[b + 1] - ts[b];
+            if (nt == 0) continue;
+            const int ix = (int)(b % nb), iy = (int)(b / nb);
+            int64_t src = 0;
+            for (int jy = std::max(iy - 1, 0); jy <= std::min(iy + 1, nb - 1); jy++)
+                src += ss[(int64_t)jy * nb + std::min(ix + 1, nb - 1) + 1] - ss[(int64_t)jy * nb + std::max(ix - 1, 0)];
+            for (int64_t k = 0; k * EV_THREADS < nt; k++)
+                wu.push_back({std::min<int64_t>(EV_THREADS, nt - k * EV_THREADS) * src, make_int2((int)b, (int)k)});
+        }
+        std::stable_sort(wu.begin(), wu.end(), [](const std::pair<int64_t, int2>& x, const std::pair<int64_t, int2>& y) {
+            return x.first > y.first;
+        });
         std::vector<int2> un;
-        for (int64_t b = 0; b < nleaf; b++)
-            for (int64_t k = 0; k * EV_THREADS < ts[b + 1] - ts[b]; k++) un.push_back(make_int2((int)b, (int)k));
+        un.reserve(wu.size());
+        for (const auto& w : wu) un.push_back(w.second);
         p->n_units = (int64_t)un.size();
         if (cudaMalloc(&p->d_units, std::max<size_t>(1, un.size()) * sizeof(int2)) != cudaSuccess)
             return fail(VP_ERR_OOM, "fmm plan: device allocation failed");

@@ -123,3 +123,21 @@ def test_fmm_batch_matches_single_evaluations(vp, ctx):
     for (nf, _, _), (_, _, m) in zip(items, refs):
         nf.release()
         m.release()
+
+
+def test_fmm_far_outside_targets(vp, ctx, tables):
+    """Targets far outside the mesh stretch the tree's square (most leaves
+    empty, the nodes in a few of them): the FMM still matches the oracle."""
+    mesh, dens = inputs.config1()
+    extra = np.array([[30.0, -20.0], [-25.0, 40.0], [0.3, 0.2], [1.5, 0.0], [0.999, 0.001]])
+    o = Oracle("far16", tables=tables)
+    s = o.setup(mesh.vxy, mesh.tri, node_targets=True, extra=extra)
+    f = np.stack([d(s["yxy"]) for d in dens])
+    u_or, _ = o.potential(s, f)
+    m = vp.mesh_upload(ctx, mesh.vxy, mesh.tri, 16)
+    nf = vp.nearfield_build(ctx, m, node_targets=True, txy=torch.from_numpy(extra).cuda())
+    u = vp.potential_eval(ctx, nf, torch.from_numpy(f).cuda(), precision=vp.VP_MIXED_FMM).cpu().numpy()
+    assert rel(u, u_or) <= 1e-12
+    assert np.abs(u[:, -5:] - u_or[:, -5:]).max() <= 1e-12 * np.abs(u_or).max()
+    nf.release()
+    m.release()
