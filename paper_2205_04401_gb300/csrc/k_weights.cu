@@ -10,14 +10,21 @@
 // radius-arclength coordinates on three fans, generalized Gaussian rule in
 // the radius, graded Gauss-Legendre panels in the arc length).
 //
-// Per quadrature point the kernels accumulate the moments mu_i of the
-// tensor-Legendre basis leg15 (20 operations instead of ~60 for the
-// orthonormal basis); the constant matrix Q (generated in high precision)
-// maps mu to the nodal weights: C_k = sum_i Q_ki mu_i - [k != own] W_k G.
+// Per quadrature point the kernels accumulate the moments mu_i of a basis of
+// P_4 (the tensor-Legendre basis leg15 in FP64, monomials in (3x - 1, 3y - 1)
+// in float-float); a constant matrix Q (generated in high precision) maps mu
+// to the nodal weights: C_k = sum_i Q_ki mu_i - [k != own] W_k G.
 // The node loops run in float-float (vp_f2.cuh: the near loop entirely, the
 // self loop from the FP64 panel quantities on) or, with VP_NF_FP64_WEIGHTS,
 // in FP64 with the table-driven vp_logd; the subdivision tree, the stop test
 // and the panel construction are FP64 in both.
+//
+// Float-float near pairs take three routes: a classifier (one thread per
+// pair) takes the stop test of the whole triangle; pairs whose triangle is a
+// leaf go through a constant map of the far rule (k_weights_near_root); the
+// others have their leaves listed by a depth-first subdivision (one thread
+// per pair, counted, scanned, written) and evaluated 32 at a time
+// (k_weights_near_deep).
 #include "vp_internal.h"
 #include "vp_f2.cuh"
 #include "vp_ff.cuh"
@@ -468,119 +475,6 @@ __device__ __forceinline__ void near_exy(const NearPairF2& g, const float4* nz, 
     }
 }
 
-__global__ void __launch_bounds__(WARPS * 32, VP_NEAR_MINB) k_weights_near_f2(WeightsArgs a, WeightsF2 b, const int32_t* __restrict__ idx,
-                                                              int64_t n) {
-    __shared__ SubTri stack_all[WARPS][STK];
-    __shared__ LeafF2 leaf_all[WARPS][LEAFCAP];
-    __shared__ float4 exy_all[WARPS][VP_NNEAR];
-    __shared__ float4 ftab[LOG_N];
-    __shared__ float4 nz_s[VP_NNEAR];
-    __shared__ float4 nz3_s[VP_NNEAR];   // 3 z_j, float-float    // near-rule nodes and weights, float-float
-    __shared__ float2 nw_s[VP_NNEAR];
-    __shared__ LogSmem lt;
-    for (int i = threadIdx.x; i < LOG_N; i += blockDim.x) ftab[i] = g_logtab.e[i];
-    for (int i = threadIdx.x; i < VP_NNEAR; i += blockDim.x) {
-        nz_s[i] = a.tab->nz2[i];
-        nz3_s[i] = a.tab->nz3[i];
-        nw_s[i] = a.tab->nw2[i];
-    }
-    load_logtab(a.tab, lt);              // ends with __syncthreads
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int64_t w = (int64_t)blockIdx.x * WARPS + wl;
-    if (w >= n) return;
-    const double ln2 = a.tab->ln2;
-    SubTri* stack = stack_all[wl];
-    LeafF2* leaves = leaf_all[wl];
-    float4* exy = exy_all[wl];
-    const int64_t p = idx[w];
-    const int T = a.ptri[p], t = a.ptgt[p];
-    const int own = own_index(a, t, T);
-    const int Nn = a.tab->near_degree;
-    double R_root = 0.0;                 // warp-uniform: one lane's FP64 work
-    if (lane == 0) R_root = ellipse_R_rn(a.tab->near_what, a.J[T], a.eps, a.c_near);
-    R_root = __shfl_sync(0xffffffffu, R_root, 0);
-    const float Rf_root = (float)R_root;
-    const NearPairF2 g = near_pair_f2(b, T, t);
-    near_exy(g, nz_s, exy, lane);
-
-    float mh[VP_NB], ml[VP_NB];
-#pragma unroll
-    for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
-    // the pairs here are those whose root is not a leaf (k_near_root_split):
-    // the traversal starts from the root's four children
-    if (lane == 0) {
-        SubTri r;
-        r.v[0] = 0; r.v[1] = 0; r.v[2] = 1; r.v[3] = 0; r.v[4] = 0; r.v[5] = 1; r.L = 0;
-        push_children(r, stack, 0);
-    }
-    __syncwarp();
-    int sp = 4, nleaf = 0, total_leaves = 0, capped = 0;
-    int visited = 1;
-    bool overflow = false;
-    const unsigned lower = (1u << lane) - 1u;
-    while (sp > 0 || nleaf > 0) {
-        bool flush = nleaf > 0 && (sp == 0 || nleaf + 32 > LEAFCAP || nleaf >= 32);
-        if (!flush) {
-            int c = min(sp, 32);
-            c = min(c, (STK - sp) / 3);
-            if (c <= 0 || visited > MAX_VISITED) {
-                overflow = true;
-                break;
-            }
-            visited += c;
-            SubTri S;
-            bool stop = false;
-            f2 d0x, d0y, a0x, a0y;
-            float scale = 1.f;
-            if (lane < c) {
-                S = stack[sp - 1 - lane];
-                stop = subtri_stop_f2(a, g, S, T, t, Nn, R_root, Rf_root, scale, d0x, d0y, a0x, a0y);
-                if (!stop && S.L >= a.depth_cap) {
-                    stop = true;
-                    capped++;
-                }
-            }
-            __syncwarp();
-            const unsigned lm = __ballot_sync(0xffffffffu, lane < c && stop);
-            const unsigned sm = __ballot_sync(0xffffffffu, lane < c && !stop);
-            sp -= c;
-            if (lane < c) {
-                if (stop) {
-                    LeafF2 lf;
-                    lf.d0xh = d0x.h; lf.d0xl = d0x.l; lf.d0yh = d0y.h; lf.d0yl = d0y.l;
-                    const f2 u0 = f2_axpb(a0x, 3.0f, -1.0f), v0 = f2_axpb(a0y, 3.0f, -1.0f);
-                    lf.u0h = u0.h; lf.u0l = u0.l; lf.v0h = v0.h; lf.v0l = v0.l;
-                    lf.sh = (S.v[2] - S.v[0]) > 0 ? scale : -scale;
-                    const f2 wj = f2_scale(g.wj, __fmul_rn(scale, scale));
-                    lf.wjh = wj.h; lf.wjl = wj.l; lf.pad = 0.f;
-                    leaves[nleaf + __popc(lm & lower)] = lf;
-                } else {
-                    push_children(S, stack, sp + 4 * __popc(sm & lower));
-                }
-            }
-            nleaf += __popc(lm);
-            sp += 4 * __popc(sm);
-            __syncwarp();
-        } else {
-            const int combos = nleaf * VP_NNEAR;
-            for (int i = lane; i < combos; i += 32) {
-                const int li = i / VP_NNEAR, j = i - li * VP_NNEAR;
-                near_leaf_node(leaves[li], exy[j], nz3_s[j], nw_s[j], ftab, lt, ln2, mh, ml);
-            }
-            total_leaves += nleaf;
-            nleaf = 0;
-            __syncwarp();
-        }
-    }
-    if (overflow && lane == 0) atomicOr(a.flag, VP_DEV_ERR_STACK);
-    finish_pair_f2(a, b, p, T, t, own, mh, ml, lane, ftab, lt, ln2);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) capped += __shfl_xor_sync(0xffffffffu, capped, o);
-    if (lane == 0) {
-        a.pstat[p] = total_leaves;
-        a.pcap[p] = capped;
-    }
-}
 
 // Near pairs whose whole triangle is already a leaf of the subdivision (about
 // three in four on graded meshes) need no traversal: one thread per pair
@@ -693,6 +587,143 @@ __global__ void __launch_bounds__(WARPS * 32, VP_ROOT_MINB) k_weights_near_root(
         }
         if (k < a.nq) far_subtract_store(a, b, p, T, t, own, k, f2_fast(ah, al), ftab, lt, ln2);
     }
+}
+
+// Near pairs whose root is not a leaf, in three steps.  One thread per pair
+// runs the subdivision depth first from the root's four children with the
+// traversal's stop test, counting its leaves (pass 0) and, after a scan,
+// writing them (pass 1) as (first vertex, level, orientation) records; then a
+// warp per pair evaluates its leaves 32 at a time (k_weights_near_deep).
+struct LeafRec {
+    int32_t x, y;    // first vertex, numerators at scale 2^-L
+    int32_t L;
+    int32_t flip;    // 1: the inverted child (m12, m20, m01), sh = -2^-L
+};
+constexpr int DSTK = 128;   // per-thread stack: 3 per level of depth + 4
+
+__global__ void __launch_bounds__(128) k_near_deep_leaves(WeightsArgs a, WeightsF2 b, const int32_t* __restrict__ idx,
+                                                          int64_t n, int pass, int32_t* __restrict__ cnt,
+                                                          const int64_t* __restrict__ off, LeafRec* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t p = idx[i];
+    const int T = a.ptri[p], t = a.ptgt[p];
+    const int Nn = a.tab->near_degree;
+    const double R_root = ellipse_R_rn(a.tab->near_what, a.J[T], a.eps, a.c_near);
+    const float Rf_root = (float)R_root;
+    const NearPairF2 g = near_pair_f2(b, T, t);
+    SubTri stk[DSTK];
+    SubTri r;
+    r.v[0] = 0; r.v[1] = 0; r.v[2] = 1; r.v[3] = 0; r.v[4] = 0; r.v[5] = 1; r.L = 0;
+    push_children(r, stk, 0);
+    int sp = 4, capped = 0, visited = 1;
+    int64_t nleaf = 0;
+    bool overflow = false;
+    const int64_t base = pass ? off[i] : 0;
+    while (sp > 0) {
+        if (++visited > MAX_VISITED) {
+            overflow = true;
+            break;
+        }
+        const SubTri S = stk[--sp];
+        float scale;
+        f2 d0x, d0y, a0x, a0y;
+        bool stop = subtri_stop_f2(a, g, S, T, t, Nn, R_root, Rf_root, scale, d0x, d0y, a0x, a0y);
+        if (!stop && S.L >= a.depth_cap) {
+            stop = true;
+            capped++;
+        }
+        if (stop) {
+            if (pass) {
+                LeafRec lr;
+                lr.x = S.v[0];
+                lr.y = S.v[1];
+                lr.L = S.L;
+                lr.flip = (S.v[2] - S.v[0]) > 0 ? 0 : 1;
+                out[base + nleaf] = lr;
+            }
+            nleaf++;
+        } else {
+            if (sp + 4 > DSTK) {
+                overflow = true;
+                break;
+            }
+            push_children(S, stk, sp);
+            sp += 4;
+        }
+    }
+    if (overflow) atomicOr(a.flag, VP_DEV_ERR_STACK);
+    if (pass == 0) {
+        cnt[i] = (int32_t)nleaf;
+    } else {
+        a.pstat[p] = (int32_t)nleaf;
+        a.pcap[p] = capped;
+    }
+}
+
+#ifndef VP_DEEP_MINB
+#define VP_DEEP_MINB 6
+#endif
+__global__ void __launch_bounds__(WARPS * 32, VP_DEEP_MINB) k_weights_near_deep(WeightsArgs a, WeightsF2 b,
+                                                                                const int32_t* __restrict__ idx,
+                                                                                int64_t n,
+                                                                                const int64_t* __restrict__ off,
+                                                                                const LeafRec* __restrict__ recs) {
+    __shared__ LeafF2 leaf_all[WARPS][32];
+    __shared__ float4 exy_all[WARPS][VP_NNEAR];
+    __shared__ float4 ftab[LOG_N];
+    __shared__ float4 nz_s[VP_NNEAR];
+    __shared__ float4 nz3_s[VP_NNEAR];   // 3 z_j, float-float
+    __shared__ float2 nw_s[VP_NNEAR];
+    __shared__ LogSmem lt;
+    for (int i = threadIdx.x; i < LOG_N; i += blockDim.x) ftab[i] = g_logtab.e[i];
+    for (int i = threadIdx.x; i < VP_NNEAR; i += blockDim.x) {
+        nz_s[i] = a.tab->nz2[i];
+        nz3_s[i] = a.tab->nz3[i];
+        nw_s[i] = a.tab->nw2[i];
+    }
+    load_logtab(a.tab, lt);              // ends with __syncthreads
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t w = (int64_t)blockIdx.x * WARPS + wl;
+    if (w >= n) return;
+    const double ln2 = a.tab->ln2;
+    LeafF2* leaves = leaf_all[wl];
+    float4* exy = exy_all[wl];
+    const int64_t p = idx[w];
+    const int T = a.ptri[p], t = a.ptgt[p];
+    const int own = own_index(a, t, T);
+    const NearPairF2 g = near_pair_f2(b, T, t);
+    near_exy(g, nz_s, exy, lane);
+    float mh[VP_NB], ml[VP_NB];
+#pragma unroll
+    for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
+    const int64_t l0 = off[w], l1 = off[w + 1];
+    for (int64_t c0 = l0; c0 < l1; c0 += 32) {
+        const int nl = (int)min((int64_t)32, l1 - c0);
+        __syncwarp();
+        if (lane < nl) {
+            // the leaf data exactly as the traversal forms it (subtri_stop_f2)
+            const LeafRec lr = recs[c0 + lane];
+            const float scale = __int_as_float((127 - lr.L) << 23);
+            const f2 xi = dyadic_f2(lr.x, scale), eta = dyadic_f2(lr.y, scale);
+            const f2 d0x = rel_coord(g.ax, xi, eta, g.ex, g.fx), d0y = rel_coord(g.ay, xi, eta, g.ey, g.fy);
+            const f2 u0 = f2_axpb(xi, 3.0f, -1.0f), v0 = f2_axpb(eta, 3.0f, -1.0f);
+            const f2 wj = f2_scale(g.wj, __fmul_rn(scale, scale));
+            LeafF2 lf;
+            lf.d0xh = d0x.h; lf.d0xl = d0x.l; lf.d0yh = d0y.h; lf.d0yl = d0y.l;
+            lf.u0h = u0.h; lf.u0l = u0.l; lf.v0h = v0.h; lf.v0l = v0.l;
+            lf.sh = lr.flip ? -scale : scale;
+            lf.wjh = wj.h; lf.wjl = wj.l; lf.pad = 0.f;
+            leaves[lane] = lf;
+        }
+        __syncwarp();
+        const int combos = nl * VP_NNEAR;
+        for (int i = lane; i < combos; i += 32) {
+            const int li = i / VP_NNEAR, j = i - li * VP_NNEAR;
+            near_leaf_node(leaves[li], exy[j], nz3_s[j], nw_s[j], ftab, lt, ln2, mh, ml);
+        }
+    }
+    finish_pair_f2(a, b, p, T, t, own, mh, ml, lane, ftab, lt, ln2);
 }
 
 // ---------------------------------------------------- self, float-float
@@ -896,6 +927,41 @@ static WeightsF2 weights_f2_prepare(const WeightsArgs& a, cudaStream_t s, char*&
     return b;
 }
 
+static __global__ void k_set_flag(int32_t* flag, int32_t bits) { atomicOr(flag, bits); }
+
+// The deep near pairs: leaf counts, their scan, the leaf records, the
+// evaluation (k_near_deep_leaves, k_weights_near_deep).
+static void near_deep(const WeightsArgs& a, const WeightsF2& b, const int32_t* deep_idx, int64_t n_deep, cudaStream_t s,
+                      vp_ctx* ctx) {
+    int32_t* cnt = nullptr;
+    int64_t* off = nullptr;
+    LeafRec* recs = nullptr;
+    if (cudaMalloc(&cnt, n_deep * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&off, (n_deep + 1) * sizeof(int64_t)) != cudaSuccess) {
+        k_set_flag<<<1, 1, 0, s>>>(a.flag, VP_DEV_ERR_ALLOC);
+        cudaFree(cnt);
+        cudaFree(off);
+        return;
+    }
+    const unsigned gt = (unsigned)((n_deep + 127) / 128);
+    k_near_deep_leaves<<<gt, 128, 0, s>>>(a, b, deep_idx, n_deep, 0, cnt, nullptr, nullptr);
+    int64_t total = 0;
+    if (vp_exclusive_scan_i32(ctx, cnt, off, n_deep, s) == VP_OK &&
+        cudaMemcpyAsync(&total, off + n_deep, sizeof(int64_t), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+        cudaStreamSynchronize(s) == cudaSuccess &&
+        cudaMalloc(&recs, std::max<int64_t>(total, 1) * sizeof(LeafRec)) == cudaSuccess) {
+        k_near_deep_leaves<<<gt, 128, 0, s>>>(a, b, deep_idx, n_deep, 1, cnt, off, recs);
+        k_weights_near_deep<<<(unsigned)((n_deep + WARPS - 1) / WARPS), WARPS * 32, 0, s>>>(a, b, deep_idx, n_deep, off,
+                                                                                         recs);
+    } else {
+        k_set_flag<<<1, 1, 0, s>>>(a.flag, VP_DEV_ERR_ALLOC);
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(recs);
+    cudaFree(cnt);
+    cudaFree(off);
+}
+
 void launch_weights(const WeightsArgs& a, const int32_t* self_idx, int64_t n_self, const int32_t* near_idx,
                     int64_t n_near, cudaStream_t s, vp_ctx* ctx) {
     const unsigned gs = (unsigned)((n_self + WARPS - 1) / WARPS), gn = (unsigned)((n_near + WARPS - 1) / WARPS);
@@ -927,7 +993,6 @@ void launch_weights(const WeightsArgs& a, const int32_t* self_idx, int64_t n_sel
         const int64_t n_root = (int64_t)h_cnt[0], n_deep = (int64_t)h_cnt[1];
         if (n_root > 0)
             k_weights_near_root<<<(unsigned)((n_root + WARPS - 1) / WARPS), WARPS * 32, 0, s>>>(a, b, root_idx, n_root);
-        if (n_deep > 0)
-            k_weights_near_f2<<<(unsigned)((n_deep + WARPS - 1) / WARPS), WARPS * 32, 0, s>>>(a, b, deep_idx, n_deep);
+        if (n_deep > 0) near_deep(a, b, deep_idx, n_deep, s, ctx);
     });
 }

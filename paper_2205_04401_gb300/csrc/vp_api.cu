@@ -140,6 +140,7 @@ int check_flag(vp_ctx* ctx, int32_t* d_flag, cudaStream_t s) {
     if (h & VP_DEV_ERR_CELL) return vp_set_error(ctx, VP_ERR_CUDA, "grid cell list exceeds sort capacity");
     if (h & VP_DEV_ERR_TIMEOUT) return vp_set_error(ctx, VP_ERR_TIMEOUT, "a pipelined kernel timed out waiting for its copies");
     if (h & VP_DEV_ERR_CURVED_CW) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "a curved element is clockwise");
+    if (h & VP_DEV_ERR_ALLOC) return vp_set_error(ctx, VP_ERR_OOM, "device allocation failed in the near-field build");
     return VP_OK;
 }
 

@@ -228,3 +228,4 @@ __host__ __device__ __forceinline__ void koornwinder4(double x, double y, double
 #define VP_DEV_ERR_CELL 16
 #define VP_DEV_ERR_TIMEOUT 32   // a bounded wait of a pipelined kernel gave up
 #define VP_DEV_ERR_CURVED_CW 64 // a curved element given clockwise
+#define VP_DEV_ERR_ALLOC 128    // a device allocation inside a pipelined step failed

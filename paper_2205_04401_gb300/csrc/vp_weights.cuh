@@ -8,14 +8,12 @@
 namespace {
 
 
-// Stack depth and resident blocks per SM of the float-float kernels (chosen
-// by timing the 16,384-triangle star build: 5 and 6 blocks beat the
-// unconstrained register allocation by 14% and 17%).
+// Stack depth of the warp-wide traversals (FP64 and curved kernels) and
+// resident blocks per SM of the float-float self kernel (chosen by timing
+// the 16,384-triangle star build: 6 blocks beat the unconstrained register
+// allocation by 17%, 5 and 4 were slower).
 #ifndef VP_NEAR_STK
 #define VP_NEAR_STK 128
-#endif
-#ifndef VP_NEAR_MINB
-#define VP_NEAR_MINB 5
 #endif
 #ifndef VP_SELF_MINB
 #define VP_SELF_MINB 6
