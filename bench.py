@@ -1002,8 +1002,9 @@ def main():
     # smsp__thread_inst_executed.sum on the 2,048-triangle star,
     # profiles/far_sym_weights_star2048_counts.md): symmetric far sum 105.7 per
     # unordered node pair, its diagonal tiles 85.7 and the extra targets 83.5
-    # per ordered pair, near weights 749 per (leaf, node) evaluation including
-    # the per-pair work (root classifier, root-leaf and traversal kernels),
+    # per ordered pair, near weights 755 per (leaf, node) evaluation including
+    # the per-pair work (root classifier, root-leaf kernel, leaf lists and
+    # their evaluation),
     # self weights 48,300 per panel.
     TI = 512                     # target tile of the symmetric far sum
     unord = diag = 0
@@ -1013,7 +1014,7 @@ def main():
         diag += sz * sz
     far_inst = unord * 105.7 + diag * 85.7 + (M - N) * N * 83.5
     work = {
-        "weights_near": ("alu", stats["near_leaves"] * 49 * 748.7 * args.steps, issue_peak / 1e12, "Tinst/s"),
+        "weights_near": ("alu", stats["near_leaves"] * 49 * 755.0 * args.steps, issue_peak / 1e12, "Tinst/s"),
         "weights_self": ("alu", stats["self_panels"] * 48328.0 * args.steps, issue_peak / 1e12, "Tinst/s"),
         "far_ff": ("alu", far_inst * args.steps, issue_peak / 1e12, "Tinst/s"),
         "far_fp64": ("alu", float(M) * N * 80.0 * args.steps, dfma_peak / 1e12, "FP64 TFLOP/s"),
@@ -1076,7 +1077,7 @@ def main():
         }
         # library kernel launches per full step (upload + build + mixed evaluation of one density),
         # counted in the ncu launch list of this command (profiles/launches_star16384_mixed.md)
-        line["gpu_launches"] = 47 * args.steps if prec == vp.VP_MIXED else int(sum(v[0] for v in prof.values()))
+        line["gpu_launches"] = 53 * args.steps if prec == vp.VP_MIXED else int(sum(v[0] for v in prof.values()))
         print(json.dumps(line))
     nf.release()
     mh.release()
