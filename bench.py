@@ -1076,8 +1076,9 @@ def main():
             "stage_share": stage_share,
         }
         # library kernel launches per full step (upload + build + mixed evaluation of one density),
-        # counted in the ncu launch list of this command (profiles/launches_star16384_mixed.md)
-        line["gpu_launches"] = 53 * args.steps if prec == vp.VP_MIXED else int(sum(v[0] for v in prof.values()))
+        # counted in the ncu launch list of this command (profiles/launches_star16384_mixed.md);
+        # the other precisions' steps have not been counted and report none
+        line["gpu_launches"] = 53 * args.steps if prec == vp.VP_MIXED else None
         print(json.dumps(line))
     nf.release()
     mh.release()
