@@ -126,6 +126,20 @@ def oracle_baseline(mesh, fun, extra, budget_s=12.0, seed=1):
     return dict(value=n2 / dt, seconds=dt, targets=n2, s=s, f=f, sample=sample, u=u)
 
 
+# ------------------------------------------------------------ multi-rank
+def whole_job(t_local_ms, units_per_rank, world, device=None):
+    """The slowest rank's timed total (max over ranks) and the whole-job
+    throughput: every rank processed units_per_rank units of its own replica
+    in that time.  Needs torch.distributed initialised when world > 1."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    t = float(tt.item())
+    return t, world * units_per_rank / (t / 1e3)
+
+
 # --------------------------------------------------------------- reference
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -908,12 +922,7 @@ def main():
     prof = vp.profile_read(ctx)
     vp.profile_enable(ctx, False)
     t_steps = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    t_total = sum(t_steps)
-    tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    t_total = float(tt.item())
-    value = world * args.steps * M / (t_total / 1e3)
+    t_total, value = whole_job(sum(t_steps), args.steps * M, world, dev)
 
     # resident evaluation (weights cached, serving mode) and FP64 comparison
     mh = vp.mesh_upload_dev(ctx, vxy_d, tri_d, vp.VP_RULE_19_D9)
