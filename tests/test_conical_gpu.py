@@ -161,3 +161,38 @@ def test_conical_refused_where_unsupported(vp, ctx):
         vp.nf_prepare_tc(nf)
     with pytest.raises(vp.VPError):
         vp.mesh_upload(ctx, mesh.vxy, mesh.tri, vp.VP_RULE_CONICAL(51))
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+def test_conical_rules_in_a_batch(vp, ctx, prec):
+    """Meshes on different far rules (a conical rule of degree 20 among the
+    built-in ones) in one graph-captured batch, direct (run-time node count
+    in the batched apply) and with the FMM: each item equals its single
+    evaluation (FMM: bit for bit; direct: to 1e-13, the batched far sum is
+    one-sided and sums in another order)."""
+    meshes = [(inputs.disk_uniform_mesh(300, 11, 2), vp.VP_RULE_CONICAL(20)),
+              (inputs.lshape_mesh(400, 12, 2), 19), (inputs.disk_mesh(n_b=10, n_i=5), vp.VP_RULE_CONICAL(30))]
+    items, refs, keep = [], [], []
+    for k, (mesh, rule) in enumerate(meshes):
+        m = vp.mesh_upload(ctx, mesh.vxy, mesh.tri, rule)
+        nf = vp.nearfield_build(ctx, m, node_targets=True, c_far=CN_TABLE.get(rule - 1000, 1.0) if rule > 1000 else 1.0)
+        y, _ = vp.mesh_nodes(m)
+        yn = y.cpu().numpy()
+        f = torch.from_numpy(np.stack([np.cos(2 * yn[:, 0] + k) * yn[:, 1] + 1.0])).cuda()
+        u = torch.full((1, nf.M), float("nan"), dtype=torch.float64, device="cuda")
+        items.append((nf, f, u))
+        refs.append(vp.potential_eval(ctx, nf, f, precision=prec).cpu().numpy())
+        keep.append(m)
+    batch = vp.Batch(ctx, items, precision=prec)
+    batch.launch()
+    torch.cuda.synchronize()
+    for (nf, f, u), ref in zip(items, refs):
+        ub = u.cpu().numpy()
+        if prec == 3:
+            assert np.array_equal(ub, ref)
+        else:
+            assert rel_err(ub, ref).max() <= 1e-13
+    batch.release()
+    for (nf, _, _), m in zip(items, keep):
+        nf.release()
+        m.release()
