@@ -196,3 +196,40 @@ def test_conical_rules_in_a_batch(vp, ctx, prec):
     for (nf, _, _), m in zip(items, keep):
         nf.release()
         m.release()
+
+
+def test_conical_rule_on_curved_disk(vp, ctx, tables):
+    """A degree-12 conical far rule (49 nodes) on the curved unit disk: the
+    blending-map nodes, the curved near and self weights (node-group loop of
+    the FP64 curved kernels) and the closed form (|x|^2 - 1)/4 of f = 1."""
+    mesh = inputs.disk_mesh()
+    tri, cur = inputs.curved_boundary(mesh, [(0.0, 0.0, 1.0)])
+    rng = np.random.default_rng(21)
+    r = np.sqrt(rng.random(200)) * 0.999
+    th = rng.random(200) * 2 * np.pi
+    extra = np.concatenate([np.stack([r * np.cos(th), r * np.sin(th)], 1),
+                            [[0.999999, 0.0], [0.0, -0.9999], [0.70710678, 0.70710677]]])
+    o = Oracle(gen_rules.conical_rule(12), tables=tables, far_cn=CN_TABLE[12])
+    s = o.setup(mesh.vxy, tri, node_targets=False, extra=extra, curves=cur)
+    f = np.ones((1, s["N"]))
+    u_or, info = o.potential(s, f)
+    m = vp.mesh_upload_curved(ctx, mesh.vxy, tri, cur, vp.VP_RULE_CONICAL(12))
+    nf = vp.nearfield_build(ctx, m, node_targets=False, txy=torch.from_numpy(extra).cuda(), c_far=CN_TABLE[12])
+    y, w = vp.mesh_nodes(m)
+    row, ptri, kind, tself = vp.nf_lists(nf)
+    C = vp.nf_weights(nf).cpu().numpy()
+    fd = torch.from_numpy(f).cuda()
+    u0 = vp.potential_eval(ctx, nf, fd, precision=vp.VP_FP64).cpu().numpy()
+    u1 = vp.potential_eval(ctx, nf, fd, precision=vp.VP_MIXED).cpu().numpy()
+    yy = y.cpu().numpy()
+    assert np.abs(yy - s["yxy"]).max() <= 16 * np.spacing(1.0)
+    assert np.array_equal(tself.cpu().numpy(), s["tself"])
+    assert np.array_equal(row.cpu().numpy(), info["row"]) and np.array_equal(ptri.cpu().numpy(), info["ptri"])
+    check_weights(C, info["C"], s["J"], info["ptri"], 1e-13)
+    assert rel_err(u0, u_or).max() <= 1e-12
+    assert rel_err(u1, u_or).max() <= 1e-10
+    ex = (np.sum(extra ** 2, 1) - 1) / 4
+    for u in (u0[0], u1[0]):
+        assert np.abs(u - ex).max() / np.abs(ex).max() <= 1e-11
+    nf.release()
+    m.release()
