@@ -187,15 +187,33 @@ __global__ void k_locate(const double* __restrict__ tv, const double* __restrict
 }
 
 // Count (row == nullptr) or fill the target-major list of each target:
-// kind 1 for S(x), kind 0 for T != S(x) whose ellipses hold x.
+// kind 1 for S(x), kind 0 for T != S(x) whose ellipses hold x.  With a
+// cache, the counting pass also keeps up to `cap` entries per target (T, and
+// the kind in the top bit) and the filling pass copies them instead of
+// testing again; targets with more entries are tested again.
 __global__ void k_list_pass(const double* __restrict__ tv, const double* __restrict__ R, int N,
                             const double* __restrict__ txy, const int32_t* __restrict__ tself,
                             const int32_t* __restrict__ order, const int32_t* __restrict__ tcell, int64_t M, GridDev g,
                             int32_t* __restrict__ count, const int64_t* __restrict__ row, int32_t* __restrict__ ptri,
-                            int32_t* __restrict__ ptgt, uint8_t* __restrict__ pkind) {
+                            int32_t* __restrict__ ptgt, uint8_t* __restrict__ pkind, uint32_t* __restrict__ cache,
+                            int cap) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     int32_t t = order[i];
+    if (row && cache) {
+        const int64_t o0 = row[t];
+        const int32_t cnt = (int32_t)(row[t + 1] - o0);
+        if (cnt <= cap) {
+            const uint32_t* ce = cache + (int64_t)t * cap;
+            for (int32_t k = 0; k < cnt; k++) {
+                const uint32_t e = ce[k];
+                ptri[o0 + k] = (int32_t)(e & 0x7fffffffu);
+                ptgt[o0 + k] = t;
+                pkind[o0 + k] = (uint8_t)(e >> 31);
+            }
+            return;
+        }
+    }
     double xx = txy[2 * t], xy = txy[2 * t + 1];
     int32_t S = tself[t];
     int32_t c = tcell[t];
@@ -217,6 +235,8 @@ __global__ void k_list_pass(const double* __restrict__ tv, const double* __restr
                 ptri[out + n] = T;
                 ptgt[out + n] = t;
                 pkind[out + n] = (uint8_t)kind;
+            } else if (cache && n < cap) {
+                cache[(int64_t)t * cap + n] = (uint32_t)T | ((uint32_t)kind << 31);
             }
             n++;
         }
@@ -274,8 +294,9 @@ void launch_locate(const double* tv, const double* txy, const int32_t* order, co
 
 void launch_list_pass(const double* tv, const double* R, int N, const double* txy, const int32_t* tself,
                       const int32_t* order, const int32_t* tcell, int64_t M, GridDev g, int32_t* count,
-                      const int64_t* row, int32_t* ptri, int32_t* ptgt, uint8_t* pkind, cudaStream_t s) {
+                      const int64_t* row, int32_t* ptri, int32_t* ptgt, uint8_t* pkind, uint32_t* cache, int cap,
+                      cudaStream_t s) {
     if (M > 0)
         k_list_pass<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(tv, R, N, txy, tself, order, tcell, M, g, count, row,
-                                                                ptri, ptgt, pkind);
+                                                                ptri, ptgt, pkind, cache, cap);
 }

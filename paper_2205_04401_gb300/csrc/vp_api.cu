@@ -537,6 +537,8 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         unsigned long long* d_u64;
         unsigned long long h_u64[4] = {0, 0, 0, 0};
         int32_t *d_cnear_idx = nullptr, *d_cself_idx = nullptr;
+        uint32_t* d_lcache = nullptr;
+        constexpr int LIST_CAP = 48;
         char* d_f2ws;
         int32_t h_max = 0;
         std::vector<double> hb;
@@ -636,9 +638,14 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         else
             PROF(ctx, ST_LOCATE, s, launch_locate(mesh->d_tv, nf->d_txy, d_order, d_tcell, M, gd, nf->d_tself, s));
         NF_CUDA(sc.alloc(&d_count, M));
+        // the counting pass keeps up to LIST_CAP entries per target for the filling pass
+        if (sc.alloc(&d_lcache, (size_t)M * LIST_CAP) != cudaSuccess) {
+            cudaGetLastError();
+            d_lcache = nullptr;
+        }
         PROF(ctx, ST_LIST_COUNT, s,
              launch_list_pass(mesh->d_tv, d_R, mesh->rule.degree, nf->d_txy, nf->d_tself, d_order, d_tcell, M, gd,
-                              d_count, nullptr, nullptr, nullptr, nullptr, s));
+                              d_count, nullptr, nullptr, nullptr, nullptr, d_lcache, LIST_CAP, s));
         NF_CUDA(dev_alloc(&nf->d_row, M + 1));
         rc = vp_exclusive_scan_i32(ctx, d_count, nf->d_row, M, s);
         if (rc) goto fail;
@@ -653,7 +660,7 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
         NF_CUDA(dev_alloc(&nf->d_C, nf->P * nq));
         PROF(ctx, ST_LIST_FILL, s,
              launch_list_pass(mesh->d_tv, d_R, mesh->rule.degree, nf->d_txy, nf->d_tself, d_order, d_tcell, M, gd,
-                              nullptr, nf->d_row, nf->d_ptri, nf->d_ptgt, nf->d_pkind, s));
+                              nullptr, nf->d_row, nf->d_ptri, nf->d_ptgt, nf->d_pkind, d_lcache, LIST_CAP, s));
         NF_CUDA(cudaGetLastError());
 
         // correction weights

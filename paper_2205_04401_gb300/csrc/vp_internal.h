@@ -214,7 +214,8 @@ void launch_locate(const double* tv, const double* txy, const int32_t* order, co
                    GridDev g, int32_t* tself, cudaStream_t s);
 void launch_list_pass(const double* tv, const double* R, int N, const double* txy, const int32_t* tself,
                       const int32_t* order, const int32_t* tcell, int64_t M, GridDev g, int32_t* count,
-                      const int64_t* row, int32_t* ptri, int32_t* ptgt, uint8_t* pkind, cudaStream_t s);
+                      const int64_t* row, int32_t* ptri, int32_t* ptgt, uint8_t* pkind, uint32_t* cache, int cap,
+                      cudaStream_t s);
 void launch_split_pairs(const uint8_t* pkind, int64_t P, int32_t* near_idx, int32_t* self_idx,
                         unsigned long long* counters, cudaStream_t s);
 
