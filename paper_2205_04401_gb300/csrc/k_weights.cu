@@ -284,6 +284,7 @@ struct WeightsF2 {
     const float4* x2;     // [M] target x, y
     const float4* y2;     // [N] node x, y
     const float2* wq2;    // [N] W_j / 4pi
+    const double* Rn;     // [nt] near-rule ellipse parameter R = w J_T / (eps C_N) of the root
 };
 
 
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(256) k_near_root_split(WeightsArgs a, WeightsF
     if (i < n) {
         p = idx[i];
         const int T = a.ptri[p], t = a.ptgt[p];
-        const double R_root = ellipse_R_rn(a.tab->near_what, a.J[T], a.eps, a.c_near);
+        const double R_root = b.Rn[T];
         const NearPairF2 g = near_pair_f2(b, T, t);
         SubTri S;
         S.v[0] = 0; S.v[1] = 0; S.v[2] = 1; S.v[3] = 0; S.v[4] = 0; S.v[5] = 1; S.L = 0;
@@ -609,7 +610,7 @@ __global__ void __launch_bounds__(128) k_near_deep_leaves(WeightsArgs a, Weights
     const int64_t p = idx[i];
     const int T = a.ptri[p], t = a.ptgt[p];
     const int Nn = a.tab->near_degree;
-    const double R_root = ellipse_R_rn(a.tab->near_what, a.J[T], a.eps, a.c_near);
+    const double R_root = b.Rn[T];
     const float Rf_root = (float)R_root;
     const NearPairF2 g = near_pair_f2(b, T, t);
     SubTri stk[DSTK];
@@ -867,7 +868,8 @@ __global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(We
 // float-float geometry of the weights kernels
 __global__ void k_weights_f2_tri(const double* __restrict__ tv, const double* __restrict__ J, int64_t nt,
                                  float4* __restrict__ tA, float4* __restrict__ te, float4* __restrict__ tf,
-                                 float4* __restrict__ tw) {
+                                 float4* __restrict__ tw, const VpTables* __restrict__ tab, double eps,
+                                 double cn, double* __restrict__ Rn) {
     const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (T >= nt) return;
     const double* v = tv + 6 * T;
@@ -881,6 +883,7 @@ __global__ void k_weights_f2_tri(const double* __restrict__ tv, const double* __
     te[T] = make_float4(ex.h, ex.l, ey.h, ey.l);
     tf[T] = make_float4(fx.h, fx.l, fy.h, fy.l);
     tw[T] = make_float4(wj.h, wj.l, (float)(cm * 1.0000001), 0.f);
+    Rn[T] = ellipse_R_rn(tab->near_what, J[T], eps, cn);
 }
 
 __global__ void k_weights_f2_pts(const double* __restrict__ xy, int64_t n, const double* __restrict__ W,
@@ -898,9 +901,10 @@ __global__ void k_weights_f2_pts(const double* __restrict__ xy, int64_t n, const
 }  // namespace
 
 size_t weights_f2_bytes(int64_t nt, int64_t M, int64_t N, int64_t n_near) {
-    // seven arrays, the two near-pair lists and their counters, each rounded up to 256 bytes
-    return (size_t)nt * 4 * sizeof(float4) + (size_t)M * sizeof(float4) + (size_t)N * (sizeof(float4) + sizeof(float2)) +
-           (size_t)n_near * 2 * sizeof(int32_t) + 2 * sizeof(unsigned long long) + 10 * 256;
+    // eight arrays, the two near-pair lists and their counters, each rounded up to 256 bytes
+    return (size_t)nt * (4 * sizeof(float4) + sizeof(double)) + (size_t)M * sizeof(float4) +
+           (size_t)N * (sizeof(float4) + sizeof(float2)) + (size_t)n_near * 2 * sizeof(int32_t) +
+           2 * sizeof(unsigned long long) + 11 * 256;
 }
 
 // float-float triangles, targets and nodes in the caller's scratch; ws
@@ -920,10 +924,13 @@ static WeightsF2 weights_f2_prepare(const WeightsArgs& a, cudaStream_t s, char*&
     float4* x2 = (float4*)take(a.M * sizeof(float4));
     float4* y2 = (float4*)take(a.N * sizeof(float4));
     float2* wq2 = (float2*)take(a.N * sizeof(float2));
-    if (a.nt > 0) k_weights_f2_tri<<<(unsigned)((a.nt + 255) / 256), 256, 0, s>>>(a.tv, a.J, a.nt, tA, te, tf, tw);
+    double* Rn = (double*)take(a.nt * sizeof(double));
+    if (a.nt > 0)
+        k_weights_f2_tri<<<(unsigned)((a.nt + 255) / 256), 256, 0, s>>>(a.tv, a.J, a.nt, tA, te, tf, tw, a.tab, a.eps,
+                                                                      a.c_near, Rn);
     if (a.M > 0) k_weights_f2_pts<<<(unsigned)((a.M + 255) / 256), 256, 0, s>>>(a.txy, a.M, nullptr, x2, nullptr);
     if (a.N > 0) k_weights_f2_pts<<<(unsigned)((a.N + 255) / 256), 256, 0, s>>>(a.y, a.N, a.W, y2, wq2);
-    b.tA = tA; b.te = te; b.tf = tf; b.tw = tw; b.x2 = x2; b.y2 = y2; b.wq2 = wq2;
+    b.tA = tA; b.te = te; b.tf = tf; b.tw = tw; b.x2 = x2; b.y2 = y2; b.wq2 = wq2; b.Rn = Rn;
     return b;
 }
 
