@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--extra", type=int, default=10000)
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--fp64-weights", action="store_true",
+                    help="correction-weight node quadratures in FP64 (VP_NF_FP64_WEIGHTS) instead of float-float")
     ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5, 6, 7, 8],
                     help="2: the 16,384-triangle star (default); 3: 64 densities; 4: 200 uneven meshes in one "
                          "batched launch; 5: serving loop with Poisson arrivals; 6: annulus with curved boundary "
@@ -124,6 +126,30 @@ def oracle_baseline(mesh, fun, extra, budget_s=12.0, seed=1):
     u, _ = o.potential(s, f, targets=sample)
     dt = time.perf_counter() - t0
     return dict(value=n2 / dt, seconds=dt, targets=n2, s=s, f=f, sample=sample, u=u)
+
+
+# ------------------------------------------------------------ launches
+def count_launches(fn):
+    """Kernel launches of this library (its kernels are named k_*) while fn
+    runs, from the profiler's CUDA activity records; None if the profiler
+    cannot record device activity here."""
+    import re
+
+    import torch
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        torch.cuda.synchronize()
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        pat = re.compile(r"(^|[\s:])k_[A-Za-z0-9_]+")
+        n = 0
+        for e in prof.events():
+            if str(getattr(e, "device_type", "")).endswith("CUDA") and pat.search(e.name or ""):
+                n += 1
+        return n if n > 0 else None
+    except Exception:
+        return None
 
 
 # ------------------------------------------------------------ multi-rank
@@ -887,7 +913,7 @@ def main():
 
     def step():
         mh = vp.mesh_upload_dev(ctx, vxy_d, tri_d, vp.VP_RULE_19_D9)
-        nf = vp.nearfield_build(ctx, mh, node_targets=True, txy=extra_d)
+        nf = vp.nearfield_build(ctx, mh, node_targets=True, txy=extra_d, fp64_weights=args.fp64_weights)
         vp.potential_eval(ctx, nf, f_d, precision=prec, out=u_d)
         return mh, nf
 
@@ -923,6 +949,10 @@ def main():
     vp.profile_enable(ctx, False)
     t_steps = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     t_total, value = whole_job(sum(t_steps), args.steps * M, world, dev)
+    # the library's kernel launches in one more step of the same kind, listed
+    # by the profiler (CUPTI); times the timed steps
+    per_step = count_launches(lambda: [h.release() for h in reversed(step())])
+    launches = per_step * args.steps if per_step is not None else None
 
     # resident evaluation (weights cached, serving mode) and FP64 comparison
     mh = vp.mesh_upload_dev(ctx, vxy_d, tri_d, vp.VP_RULE_19_D9)
@@ -969,8 +999,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         mh2 = vp.mesh_upload(ctx, mesh.vxy, mesh.tri, vp.VP_RULE_19_D9)
-        xd = x_pin.to(dev, non_blocking=True)
-        nf2 = vp.nearfield_build(ctx, mh2, node_targets=True, txy=xd)
+        nf2 = vp.nearfield_build_host(ctx, mh2, node_targets=True, txy=x_pin.numpy(), fp64_weights=args.fp64_weights)
         vp.potential_eval_host(ctx, nf2, f_pin.numpy(), precision=prec, out=u_host)
         t1 = time.perf_counter()
         nf2.release()
@@ -999,62 +1028,66 @@ def main():
     except Exception:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    dfma_peak = 1.186e12        # measured FP64 FMA throughput on this GB300 (flop/s), profiles/peaks_gb300.md
-    # Issue peak of the float-float kernels (bound "alu"): every SM sub-partition
-    # issues one warp instruction per clock, so 152 SMs x 4 x 32 lanes x the
-    # maximum SM clock thread-instructions per second (FP32, integer, shared
-    # memory and shuffle instructions all take an issue slot).
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    issue_peak = 152 * 4 * 32 * sm_mhz * 1e6
+    # FP32 pipe peak (bound "alu"): 152 SMs x 128 FP32 lanes x the maximum SM
+    # clock, in thread-instructions per second (no FP32 peak is measured in the
+    # peaks file; this is derived from the unit counts and the clock)
+    fp32_peak = 152 * 128 * sm_mhz * 1e6
     nq = 19
-    # thread-instructions per unit of the float-float kernels (ncu
-    # smsp__thread_inst_executed.sum on the 2,048-triangle star,
-    # profiles/far_sym_weights_star2048_counts.md): symmetric far sum 105.7 per
-    # unordered node pair, its diagonal tiles 85.7 and the extra targets 83.5
-    # per ordered pair, near weights 755 per (leaf, node) evaluation including
-    # the per-pair work (root classifier, root-leaf kernel, leaf lists and
-    # their evaluation),
-    # self weights 48,300 per panel.
-    TI = 512                     # target tile of the symmetric far sum
-    unord = diag = 0
-    for lo in range(0, N, TI):
-        sz = min(TI, N - lo)
-        unord += sz * max(0, N - lo - sz)
-        diag += sz * sz
-    far_inst = unord * 105.7 + diag * 85.7 + (M - N) * N * 83.5
+    # Far sum, algorithmic work per ordered (target, source) pair of the 1e-10
+    # float-float path: 45 FP32-pipe instructions, the estimate for one pair
+    # evaluated on its own (float-float dx, dy and r^2 from split coordinates
+    # ~15; a table logarithm of the float-float r^2 with a short log1p series
+    # and its error terms ~22; the float-float charge product and compensated
+    # accumulation ~8).  Pairs = N M ordered pairs, whatever the kernel's own
+    # scheme (the symmetric kernel shares a pair's distance and logarithm
+    # between its two directions and so can exceed this count's roofline).
+    ALG_FAR_PER_PAIR = 45.0
+    pairs = float(N) * float(M)
     work = {
-        "weights_near": ("alu", stats["near_leaves"] * 49 * 755.0 * args.steps, issue_peak / 1e12, "Tinst/s"),
-        "weights_self": ("alu", stats["self_panels"] * 48328.0 * args.steps, issue_peak / 1e12, "Tinst/s"),
-        "far_ff": ("alu", far_inst * args.steps, issue_peak / 1e12, "Tinst/s"),
-        "far_fp64": ("alu", float(M) * N * 80.0 * args.steps, dfma_peak / 1e12, "FP64 TFLOP/s"),
+        "far_ff": ("alu", pairs * ALG_FAR_PER_PAIR * args.steps, fp32_peak / 1e12, "Tinst/s",
+                   "algorithmic: 45 FP32-pipe instructions per ordered pair x N M pairs"),
         "apply": ("hbm", float(stats["n_pairs"] * (8 * nq + 4) + N * 8 + M * 8 + M * 8 * 2) * args.steps,
-                       hbm, "GB/s"),
-        # list passes: targets read (16 B), per pair triangle + target + kind written (9 B), row pointers
-        "list_fill": ("hbm", float(M * 16 + stats["n_pairs"] * 9 + (M + 1) * 8) * args.steps, hbm, "GB/s"),
-        "list_count": ("hbm", float(M * 16 + M * 4) * args.steps, hbm, "GB/s"),
+                  hbm, "GB/s", "algorithmic: P (8 nq + 4) + 8 N + 24 M bytes"),
+        # list filling copies the counting pass's entries: targets read (16 B), per pair triangle +
+        # target + kind written (9 B), row pointers
+        "list_fill": ("hbm", float(M * 16 + stats["n_pairs"] * 9 + (M + 1) * 8) * args.steps, hbm, "GB/s",
+                      "algorithmic: 16 M + 9 P + 8 (M + 1) bytes"),
     }
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     dname, (dn, dms) = dom
     roof = None
     if dname in work and dn > 0:
-        bound, units, peak, unit = work[dname]
+        bound, units, peak, unit, model = work[dname]
         scale = 1e9 if unit == "GB/s" else 1e12
         achieved = units / (dms / 1e3) / scale
-        # DRAM bytes per far-sum stage (k_far_sym + its combine + k_far_extra), one ncu capture of
-        # this workload (profiles/dram_star16384_far_sum.md); other stages: not captured at this size
-        traffic = 1.8719e9 if (dname == "far_ff" and args.ntri == 16384 and args.extra == 10000) else None
         roof = {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": traffic, "launches": dn, "ms_per_launch": dms / dn}
+                "frac": achieved / peak, "traffic": None, "launches": dn, "ms_per_launch": dms / dn,
+                "model": model, "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock" if bound == "alu"
+                else "MEASURED_PEAKS.json hbm_gbs"}
     stage_share = {k: round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4) for k, v in prof.items() if v[0]}
     # every modelled stage against its own bound (the dominant one is "roofline")
     rooflines = {}
-    for k, (bound, units, peak, unit) in work.items():
+    for k, (bound, units, peak, unit, model) in work.items():
         n_l, ms_l = prof.get(k, (0, 0.0))
         if n_l and ms_l > 0:
             sc = 1e9 if unit == "GB/s" else 1e12
             a = units / (ms_l / 1e3) / sc
             rooflines[k] = {"bound": bound, "achieved": round(a, 3), "peak": peak, "unit": unit,
-                            "frac": round(a / peak, 4), "ms_per_launch": round(ms_l / n_l, 4)}
+                            "frac": round(a / peak, 4), "ms_per_launch": round(ms_l / n_l, 4), "model": model}
+    # correction weights: the paper's work counters per second (no roofline
+    # fraction: their float-float instruction mix has no algorithmic count)
+    for k, cnt, what in (("weights_near", stats["near_leaves"] * 49, "near-rule node evaluations (leaves x 49)"),
+                         ("weights_self", stats["self_panels"] * 16 * 8, "self panel points (panels x 16 x 8)")):
+        n_l, ms_l = prof.get(k, (0, 0.0))
+        if n_l and ms_l > 0:
+            rooflines[k] = {"bound": "alu", "units_per_s": round(cnt * args.steps / (ms_l / 1e3), 1),
+                            "unit": what, "frac": None, "ms_per_launch": round(ms_l / n_l, 4)}
+    # list counting: FP64 ellipse predicates per (target, candidate) behind FP32 pre-tests; no algorithmic model
+    n_l, ms_l = prof.get("list_count", (0, 0.0))
+    if n_l and ms_l > 0:
+        rooflines["list_count"] = {"bound": "fp64 predicates / latency", "frac": None,
+                                   "ms_per_launch": round(ms_l / n_l, 4)}
 
     if rank == 0:
         line = {
@@ -1063,12 +1096,14 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == vp.VP_FP64 else "f32x2+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "targets": M, "nodes": N, "densities": 1, "precision": args.precision,
+                       "weights": ("FP64 node quadratures (VP_NF_FP64_WEIGHTS)" if args.fp64_weights else
+                                   "float-float node quadratures; FP64 trees and predicates"),
                        "step": "mesh_upload+nearfield_build+potential_eval", "l2": "256 MiB flush between steps",
                        "parallelism": f"replicas{world}"},
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "target-evals/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": None,
+            "gpu_launches": launches,
             "roofline": roof,
             "rooflines_by_stage": rooflines,
             "cpu_baseline": cpu,
@@ -1084,10 +1119,6 @@ def main():
             "stage_ms": {k: round(v[1] / max(1, args.steps), 3) for k, v in prof.items() if v[0]},
             "stage_share": stage_share,
         }
-        # library kernel launches per full step (upload + build + mixed evaluation of one density),
-        # counted in the ncu launch list of this command (profiles/launches_star16384_mixed.md);
-        # the other precisions' steps have not been counted and report none
-        line["gpu_launches"] = 53 * args.steps if prec == vp.VP_MIXED else None
         print(json.dumps(line))
     nf.release()
     mh.release()

@@ -112,6 +112,13 @@ typedef struct vp_nf_params {
     int32_t flags;     /* 0, or VP_NF_FP64_WEIGHTS */
 } vp_nf_params;
 
+/* Fill *out with the defaults vp_nearfield_build uses when params is NULL:
+ * eps 1e-12 (reading of the paper's experiments), c_far 1 (the provable
+ * superset E' of Section 4.1), c_near 12 (Table "C_N values", C_12 = 12),
+ * depth_cap 30, flags 0.  Host only; needs no device.  Errors: INVALID_ARG
+ * (out NULL). */
+VP_API int vp_nf_params_default(vp_nf_params* out);
+
 /* vp_nf_params.flags: evaluate the node quadratures of the correction
  * weights in FP64.  By default they run in float-float arithmetic (pairs of
  * FP32 values with error-free transformations, ~2^-48 per operation), which
@@ -137,11 +144,29 @@ typedef struct vp_nf_stats_t {
 /* ---------------------------------------------------------------- context */
 
 /* Create a context on CUDA device `device` (must be compute capability 10.3).
- * Allocates small constant tables.  *out receives the handle. */
+ * Allocates small constant tables, copies the log tables of the float-float
+ * kernels and resolves the fixed scratch of vp_potential_eval_noalloc (so
+ * that no later call loads a module or blocks on a table copy).  *out
+ * receives the handle.  Errors: NO_DEVICE, OOM, CUDA. */
 VP_API int vp_create(vp_ctx** out, int device);
 
 /* Release the context.  NULL is ignored. */
 VP_API void vp_destroy(vp_ctx* ctx);
+
+/* Device memory held by the context itself: the evaluation workspace (grown
+ * on demand by vp_potential_eval and kept for reuse) and the staging buffer
+ * of vp_potential_eval_host.  Host only.  Errors: STATE. */
+VP_API int vp_ctx_memory(const vp_ctx* ctx, int64_t* workspace_bytes, int64_t* staging_bytes);
+
+/* Bound on the column scratch of the symmetric far sum (the node-target far
+ * sum of VP_MIXED with one density, Section 3.6): the target tiles are
+ * processed in bands whose column partial sums fit `bytes` (default 256 MiB;
+ * accepted 1 MiB .. 1 TiB), so its workspace is about 1.25 x bytes + 40 N
+ * bytes whatever the node count N.  Smaller caps mean more, shorter launches
+ * and the same result up to the order of the FP64 additions.  Applies to
+ * near fields whose first symmetric evaluation comes after the call.  Host
+ * only.  Errors: STATE, INVALID_ARG. */
+VP_API int vp_set_far_sym_cap(vp_ctx* ctx, int64_t bytes);
 
 /* Human-readable name of a status code (static storage). */
 VP_API const char* vp_status_str(int status);
@@ -240,6 +265,12 @@ VP_API void vp_mesh_release(vp_mesh* mesh);
 VP_API int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, const double* txy_dev, int64_t m,
                        const vp_nf_params* params, void* stream, vp_nf** out);
 
+/* Same as vp_nearfield_build with the extra targets in a HOST buffer
+ * (txy_host [m][2], may be NULL when m = 0): copied to the device through the
+ * context's staging buffer on `stream`, then built.  Synchronises `stream`. */
+VP_API int vp_nearfield_build_host(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, const double* txy_host,
+                                   int64_t m, const vp_nf_params* params, void* stream, vp_nf** out);
+
 /* Counters and sizes of a build (host struct). */
 VP_API int vp_nf_stats(const vp_nf* nf, vp_nf_stats_t* out);
 
@@ -314,8 +345,10 @@ VP_API int vp_potential_eval_host(vp_ctx* ctx, const vp_nf* nf, const double* f_
  * loads the library holds until the process exits.  A call that would need
  * more (about splits * d * M * 8 + N * 2 * min(d, 8) * 4 bytes) is rejected
  * with VP_ERR_INVALID_ARG and a message; use vp_potential_eval then.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * vp_create has already resolved the array's device address
+ * (cudaGetSymbolAddress, which loads the module that holds it) and copied the
+ * float-float log tables, so this call allocates nothing, copies no table and
+ * looks up no symbol, on its first call as on every later one.
  * All calls share the one array and it keeps the last call's contents:
  * calls whose work overlaps on the GPU (other streams, other contexts on the
  * same device) race on it and must be serialised by the caller.  Nothing in
@@ -353,6 +386,18 @@ VP_API int vp_batch_create(vp_ctx* ctx, const vp_eval_item* items, int32_t n, in
                            vp_batch** out);
 VP_API int vp_batch_launch(vp_batch* batch, void* stream);
 VP_API void vp_batch_release(vp_batch* batch);
+
+/* Tile of the batched far sum for density-chunk width `width` (1, 2, 4 or 8):
+ * targets_per_thread 1, 2 or 4 fixes it for batches created afterwards on
+ * this context; 0 (the default) lets vp_batch_create's autotuner choose.
+ * Every tile sums each target's sources in the same order, so the results do
+ * not depend on it.  Host only.  Errors: STATE, INVALID_ARG. */
+VP_API int vp_set_batch_tile(vp_ctx* ctx, int32_t width, int32_t targets_per_thread);
+
+/* The tile and the work-unit count of each density-chunk width of a batch
+ * (index 0..3 for widths 1, 2, 4, 8; 0 where the batch has no such chunk or
+ * runs the multipole path).  Either pointer may be NULL.  Errors: STATE. */
+VP_API int vp_batch_info(const vp_batch* batch, int32_t* targets_per_thread, int64_t* work_units);
 
 /* Evaluate n items at once: vp_batch_create + vp_batch_launch + release
  * (synchronises `stream`). */

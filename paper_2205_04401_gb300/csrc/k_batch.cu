@@ -382,7 +382,8 @@ extern "C" int vp_batch_create(vp_ctx* ctx, const vp_eval_item* items, int32_t n
         if (far[g].empty()) continue;
         const int D = 1 << g;
         b->nent[g] = (int)far[g].size();
-        b->tpt[g] = ctx->ff_tpt[g] ? ctx->ff_tpt[g] : 2;
+        const int fixed = ctx->ff_tpt_fixed[g];
+        b->tpt[g] = fixed ? fixed : (ctx->ff_tpt[g] ? ctx->ff_tpt[g] : 2);
         auto fill_units = [&](int tpt) {
             int64_t u = 0;
             for (size_t i = 0; i < far[g].size(); i++) {
@@ -398,7 +399,7 @@ extern "C" int vp_batch_create(vp_ctx* ctx, const vp_eval_item* items, int32_t n
             !upload((void**)&b->d_far_begin[g], far_begin[g].data(), far_begin[g].size() * sizeof(int64_t)))
             rc = VP_ERR_OOM;
         b->grid[g] = ctx->sm_count * occupancy(D, b->tpt[g]);
-        if (rc == VP_OK && !ctx->ff_tpt[g] && precision == VP_MIXED) {
+        if (rc == VP_OK && !fixed && !ctx->ff_tpt[g] && precision == VP_MIXED) {
             // autotune on this batch: charges first, then each variant timed
             for (const auto& p : b->preps)
                 if (p.D == D) {
@@ -479,6 +480,26 @@ extern "C" int vp_batch_create(vp_ctx* ctx, const vp_eval_item* items, int32_t n
     return VP_OK;
 }
 
+extern "C" int vp_set_batch_tile(vp_ctx* ctx, int32_t width, int32_t targets_per_thread) {
+    if (!ctx || ctx->magic != 0x56504358) return VP_ERR_STATE;
+    const int g = width == 1 ? 0 : width == 2 ? 1 : width == 4 ? 2 : width == 8 ? 3 : -1;
+    if (g < 0 || (targets_per_thread != 0 && targets_per_thread != 1 && targets_per_thread != 2 &&
+                  targets_per_thread != 4))
+        return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_set_batch_tile: width 1/2/4/8, targets per thread 0/1/2/4");
+    ctx->ff_tpt_fixed[g] = targets_per_thread;
+    return VP_OK;
+}
+
+extern "C" int vp_batch_info(const vp_batch* b, int32_t* targets_per_thread, int64_t* work_units) {
+    if (!b || b->magic != 0x56504254) return VP_ERR_STATE;
+    for (int g = 0; g < 4; g++) {
+        const bool used = b->nent[g] > 0 && b->precision != VP_MIXED_FMM;
+        if (targets_per_thread) targets_per_thread[g] = used ? b->tpt[g] : 0;
+        if (work_units) work_units[g] = used ? b->units[g] : 0;
+    }
+    return VP_OK;
+}
+
 extern "C" int vp_batch_launch(vp_batch* b, void* stream) {
     if (!b || b->magic != 0x56504254) return VP_ERR_STATE;
     DevGuardB guard(b->ctx->device);
@@ -506,3 +527,6 @@ extern "C" int vp_potential_eval_batch(vp_ctx* ctx, const vp_eval_item* items, i
     vp_batch_release(b);
     return rc;
 }
+
+// Loads this unit's log table on the current device (vp_create).
+cudaError_t batch_module_prepare() { return ensure_logtab(); }

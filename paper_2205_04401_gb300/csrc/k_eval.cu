@@ -446,3 +446,27 @@ void launch_apply_f2(const int64_t* row, const int32_t* ptri, const float2* C2, 
 void launch_ff_split(const double* xy, int64_t n, double ox, double oy, double q, FFCoords out, cudaStream_t s) {
     if (n > 0) k_ff_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xy, n, ox, oy, q, out.hi, out.lo);
 }
+
+// Loads this unit's log table on the current device (vp_create), and the
+// kernels of the one-sided evaluation (far sums, split reduction, row apply):
+// under lazy loading a kernel is otherwise loaded, possibly with a device
+// allocation, at its first launch, which vp_potential_eval_noalloc must not do.
+cudaError_t eval_module_prepare() {
+    cudaError_t e = ensure_logtab();
+    if (e != cudaSuccess) return e;
+    const void* kernels[] = {
+        (const void*)k_far_fp64<1>, (const void*)k_far_fp64<2>, (const void*)k_far_fp64<4>, (const void*)k_far_fp64<8>,
+        (const void*)k_prep_q_ff<1>, (const void*)k_prep_q_ff<2>, (const void*)k_prep_q_ff<4>, (const void*)k_prep_q_ff<8>,
+        (const void*)k_far_ff<1>, (const void*)k_far_ff<2>, (const void*)k_far_ff<4>, (const void*)k_far_ff<8>,
+        (const void*)k_reduce_splits,
+        (const void*)k_apply_rows<19, 1>, (const void*)k_apply_rows<19, 2>, (const void*)k_apply_rows<19, 4>,
+        (const void*)k_apply_rows<19, 8>, (const void*)k_apply_rows<16, 1>, (const void*)k_apply_rows<16, 2>,
+        (const void*)k_apply_rows<16, 4>, (const void*)k_apply_rows<16, 8>, (const void*)k_apply_rows<0, 1>,
+        (const void*)k_apply_rows<0, 2>, (const void*)k_apply_rows<0, 4>, (const void*)k_apply_rows<0, 8>};
+    for (const void* k : kernels) {
+        cudaFuncAttributes a;
+        e = cudaFuncGetAttributes(&a, k);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}

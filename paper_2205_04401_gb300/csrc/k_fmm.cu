@@ -791,3 +791,6 @@ int fmm_far(vp_ctx* ctx, const vp_nf* nf, const double* f, int d, double* u, voi
 
 int fmm_level(const vp_nf* nf) { return nf->fmm ? nf->fmm->L : 0; }
 int64_t fmm_boxes(const vp_nf* nf) { return nf->fmm ? nf->fmm->nbox_tot : 0; }
+
+// Loads this unit's log table on the current device (vp_create).
+cudaError_t fmm_module_prepare() { return ensure_logtab(); }

@@ -1003,3 +1003,6 @@ void launch_weights(const WeightsArgs& a, const int32_t* self_idx, int64_t n_sel
         if (n_deep > 0) near_deep(a, b, deep_idx, n_deep, s, ctx);
     });
 }
+
+// Loads this unit's log table on the current device (vp_create).
+cudaError_t weights_module_prepare() { return ensure_logtab(); }

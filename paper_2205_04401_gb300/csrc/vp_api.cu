@@ -257,7 +257,37 @@ int vp_create(vp_ctx** out, int device) {
         vp_destroy(ctx);
         return VP_ERR_OOM;
     }
+    // log tables of the float-float units and the no-alloc scratch address:
+    // done here so that evaluations never block on a table copy or a module load
+    cudaError_t (*const prep[])() = {eval_module_prepare, far_sym_module_prepare, batch_module_prepare,
+                                     fmm_module_prepare, weights_module_prepare};
+    for (auto fn : prep) {
+        const cudaError_t e = fn();
+        if (e != cudaSuccess) {
+            vp_destroy(ctx);
+            return e == cudaErrorMemoryAllocation ? VP_ERR_OOM : VP_ERR_CUDA;
+        }
+    }
+    if (int rc = noalloc_prepare(ctx)) {
+        vp_destroy(ctx);
+        return rc;
+    }
     *out = ctx;
+    return VP_OK;
+}
+
+int vp_set_far_sym_cap(vp_ctx* ctx, int64_t bytes) {
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    if (bytes < ((int64_t)1 << 20) || bytes > ((int64_t)1 << 40))
+        return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_set_far_sym_cap: bytes outside [1 MiB, 1 TiB]");
+    ctx->far_sym_cap_bytes = bytes;
+    return VP_OK;
+}
+
+int vp_ctx_memory(const vp_ctx* ctx, int64_t* workspace_bytes, int64_t* staging_bytes) {
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    if (workspace_bytes) *workspace_bytes = (int64_t)ctx->ws_bytes;
+    if (staging_bytes) *staging_bytes = (int64_t)ctx->stage_bytes;
     return VP_OK;
 }
 
@@ -481,6 +511,16 @@ void vp_mesh_release(vp_mesh* mesh) {
 }
 
 // -------------------------------------------------------------- near field
+int vp_nf_params_default(vp_nf_params* out) {
+    if (!out) return VP_ERR_INVALID_ARG;
+    out->eps = 1e-12;
+    out->c_far = 1.0;
+    out->c_near = 12.0;   // Table "C_N values": C_12 = 12 for the order-12 near rule
+    out->depth_cap = 30;
+    out->flags = 0;
+    return VP_OK;
+}
+
 int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, const double* txy_dev, int64_t m,
                        const vp_nf_params* params, void* stream, vp_nf** out) {
     if (out) *out = nullptr;
@@ -492,11 +532,7 @@ int vp_nearfield_build(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, c
     const int64_t M = (node_targets ? N : 0) + m;
     if (M < 1 || M > (int64_t)INT32_MAX) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_nearfield_build: no targets");
     vp_nf_params prm;
-    prm.eps = 1e-12;
-    prm.c_far = 1.0;
-    prm.c_near = 12.0;
-    prm.depth_cap = 30;
-    prm.flags = 0;
+    vp_nf_params_default(&prm);
     if (params) prm = *params;
     if (!(prm.eps >= 1e-15 && prm.eps <= 1e-2) || !(prm.c_far > 0) || !(prm.c_near > 0) || prm.depth_cap < 0 ||
         prm.depth_cap > 30 || (prm.flags & ~VP_NF_FP64_WEIGHTS))
@@ -782,6 +818,31 @@ fail:
 #undef NF_CUDA
 }
 
+int vp_nearfield_build_host(vp_ctx* ctx, const vp_mesh* mesh, int32_t node_targets, const double* txy_host,
+                            int64_t m, const vp_nf_params* params, void* stream, vp_nf** out) {
+    if (out) *out = nullptr;
+    if (!ctx_ok(ctx)) return VP_ERR_STATE;
+    if (m < 0 || (m > 0 && !txy_host))
+        return vp_set_error(ctx, VP_ERR_INVALID_ARG, "vp_nearfield_build_host: bad arguments");
+    if (m == 0) return vp_nearfield_build(ctx, mesh, node_targets, nullptr, 0, params, stream, out);
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t tb = (size_t)m * 2 * sizeof(double);
+    if (tb > ctx->stage_bytes) {
+        if (ctx->stage) {
+            cudaStreamSynchronize(s);
+            cudaFree(ctx->stage);
+            ctx->stage = nullptr;
+            ctx->stage_bytes = 0;
+        }
+        VP_CUDA_TRY(ctx, cudaMalloc(&ctx->stage, tb));
+        ctx->stage_bytes = tb;
+    }
+    VP_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->stage, txy_host, tb, cudaMemcpyHostToDevice, s));
+    // the build copies the targets into its own arrays and synchronises `stream`
+    return vp_nearfield_build(ctx, mesh, node_targets, ctx->stage, m, params, stream, out);
+}
+
 int vp_nf_stats(const vp_nf* nf, vp_nf_stats_t* out) {
     if (!nf_ok(nf)) return VP_ERR_STATE;
     if (!out) return VP_ERR_INVALID_ARG;
@@ -824,7 +885,7 @@ void vp_nf_release(vp_nf* nf) {
 // ------------------------------------------------------------- evaluation
 }  // extern "C"
 
-static int eval_splits(const vp_ctx* ctx, int64_t M, int64_t N, int threads) {
+int eval_splits(const vp_ctx* ctx, int64_t M, int64_t N, int threads) {
     const int64_t blocks = (M + threads - 1) / threads;
     const int64_t want = 4LL * ctx->sm_count;
     int64_t s = (want + blocks - 1) / blocks;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <mutex>
 
 // Log table in shared memory: c_i = 1 + (i + 1/2)/512, rc_i = fl(1/c_i),
 // log c_i = lh_i + ll_i (two floats).  Error-free transformations below use
@@ -239,12 +240,20 @@ __global__ void k_prep_q_ff(const double* __restrict__ W, const double* __restri
     }
 }
 
-// Fill this unit's g_logtab on the current device (once per device).
-static void ensure_logtab() {
-    static int loaded_mask[4] = {0, 0, 0, 0};   // devices 0..127
+// Fill this unit's g_logtab on the current device (once per device).  Safe to
+// call from several host threads; a device is marked loaded only after its
+// copy succeeded, and the copy's error is returned.  vp_create calls it (through
+// each unit's *_prepare function) so that no evaluation pays for the blocking
+// copy or the module load it triggers.
+static cudaError_t ensure_logtab() {
+    static std::mutex mu;
+    static unsigned loaded_mask[4] = {0, 0, 0, 0};   // devices 0..127
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 128 && (loaded_mask[dev >> 5] >> (dev & 31)) & 1) return;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((loaded_mask[dev >> 5] >> (dev & 31)) & 1u) return cudaSuccess;
     static LogTab h;
     for (int i = 0; i < LOG_N; i++) {
         const double c = 1.0 + (i + 0.5) / LOG_N;
@@ -254,6 +263,7 @@ static void ensure_logtab() {
         const float lh = (float)L;
         h.e[i] = make_float4((float)(1.0 / c), lh, (float)(L - (double)lh), (float)c);   // c is exact in float
     }
-    cudaMemcpyToSymbol(g_logtab, &h, sizeof(h));
-    if (dev >= 0 && dev < 128) loaded_mask[dev >> 5] |= 1 << (dev & 31);
+    e = cudaMemcpyToSymbol(g_logtab, &h, sizeof(h));
+    if (e == cudaSuccess) loaded_mask[dev >> 5] |= 1u << (dev & 31);
+    return e;
 }

@@ -68,6 +68,8 @@ struct vp_ctx {
     std::vector<cudaEvent_t> prof_pool;
     double prof_ms[ST_COUNT] = {0};
     int ff_tpt[4] = {0, 0, 0, 0};   // autotuned targets per thread of the batched far sum, per chunk width
+    int ff_tpt_fixed[4] = {0, 0, 0, 0};   // vp_set_batch_tile: fixed targets per thread (0: autotune)
+    int64_t far_sym_cap_bytes = int64_t(256) << 20;   // column scratch per band of the symmetric far sum
     int64_t prof_n[ST_COUNT] = {0};
     // generated far rules, made on first use and kept until vp_destroy
     std::vector<FarRule> gen_rules;
@@ -175,6 +177,21 @@ struct vp_nf {
 #define VP_LAUNCH_CHECK(ctx) VP_CUDA_TRY(ctx, cudaGetLastError())
 
 int vp_set_error(vp_ctx* ctx, int code, const std::string& msg);
+
+// Per-unit device set-up run by vp_create with the context's device current:
+// each float-float unit copies its log table (vp_ff.cuh), and the
+// allocation-free evaluation resolves its fixed scratch array, so that no
+// later call loads a module, copies a table or looks up a symbol.
+cudaError_t eval_module_prepare();
+cudaError_t far_sym_module_prepare();
+cudaError_t batch_module_prepare();
+cudaError_t fmm_module_prepare();
+cudaError_t weights_module_prepare();
+int noalloc_prepare(vp_ctx* ctx);
+
+// Source splits of the one-sided far sum for M targets and N sources
+// (blocks of `threads` targets, about four blocks per SM in all).
+int eval_splits(const vp_ctx* ctx, int64_t M, int64_t N, int threads);
 
 // Evaluation with explicit workspace (vp_potential_eval's body).
 size_t eval_ws_bytes(const vp_ctx* ctx, const vp_nf* nf, int d, int precision);

@@ -38,7 +38,7 @@ struct CurrentDevice {
     }
 };
 
-// Called with ctx->device current.
+// Called with ctx->device current (vp_create, then every call: a lookup).
 int scratch_address(vp_ctx* ctx, unsigned char** out) {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     const int dev = ctx->device;
@@ -56,17 +56,15 @@ int scratch_address(vp_ctx* ctx, unsigned char** out) {
     return VP_OK;
 }
 
-// The same split of the sources over blocks as vp_potential_eval.
-int far_splits(const vp_ctx* ctx, int64_t M, int64_t N) {
-    const int threads = 128;
-    const int64_t blocks = (M + threads - 1) / threads;
-    const int64_t want = 4LL * ctx->sm_count;
-    int64_t s = (want + blocks - 1) / blocks;
-    s = std::min<int64_t>(s, std::max<int64_t>(1, N / 1024));
-    return (int)std::max<int64_t>(1, std::min<int64_t>(s, 64));
-}
-
 }  // namespace
+
+// Run by vp_create with the device current: resolving the address loads this
+// unit's module, which reserves the array, so the entry point itself never
+// does (under lazy module loading the first use of the symbol would).
+int noalloc_prepare(vp_ctx* ctx) {
+    unsigned char* p = nullptr;
+    return scratch_address(ctx, &p);
+}
 
 extern "C" int vp_potential_eval_noalloc(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, double* u_dev,
                                          int32_t precision, void* stream) {
@@ -79,7 +77,7 @@ extern "C" int vp_potential_eval_noalloc(vp_ctx* ctx, const vp_nf* nf, const dou
     cudaStream_t s = (cudaStream_t)stream;
     const vp_mesh* mesh = nf->mesh;
     const int64_t N = mesh->N, M = nf->M;
-    const int splits = far_splits(ctx, M, N);
+    const int splits = eval_splits(ctx, M, N, 128);   // the split vp_potential_eval uses
     const int dmax = d >= 8 ? 8 : (d >= 4 ? 4 : (d >= 2 ? 2 : 1));   // largest density chunk of the far sum
     const size_t partial_bytes = splits > 1 ? (size_t)splits * d * M * sizeof(double) : 0;
     const size_t off_q = (partial_bytes + 255) & ~(size_t)255;

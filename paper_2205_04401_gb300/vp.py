@@ -75,6 +75,8 @@ class EvalItem(C.Structure):
 SIGNATURES = {
     "vp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
     "vp_destroy": (None, [C.c_void_p]),
+    "vp_ctx_memory": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "vp_set_far_sym_cap": (C.c_int, [C.c_void_p, C.c_int64]),
     "vp_status_str": (C.c_char_p, [C.c_int]),
     "vp_last_error": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int32]),
     "vp_mesh_upload": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
@@ -101,6 +103,9 @@ SIGNATURES = {
     "vp_nearfield_build": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.POINTER(NfParams),
                                      C.c_void_p, C.POINTER(C.c_void_p)]),
     "vp_nf_stats": (C.c_int, [C.c_void_p, C.POINTER(NfStats)]),
+    "vp_nearfield_build_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int64,
+                                          C.POINTER(NfParams), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "vp_nf_params_default": (C.c_int, [C.POINTER(NfParams)]),
     "vp_nf_lists": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vp_nf_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "vp_nf_release": (None, [C.c_void_p]),
@@ -119,6 +124,8 @@ SIGNATURES = {
                                   C.POINTER(C.c_void_p)]),
     "vp_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "vp_batch_release": (None, [C.c_void_p]),
+    "vp_set_batch_tile": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "vp_batch_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "vp_server_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_void_p)]),
     "vp_server_register": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
     "vp_server_register_cold": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
@@ -202,6 +209,21 @@ class Context:
             raise VPError(rc, f"vp_create(device={device}): {lib.vp_status_str(rc).decode()}")
         self.handle = h
         self.device = device
+
+    def memory(self) -> dict:
+        """vp_ctx_memory: device bytes of the context's evaluation workspace and staging buffer."""
+        ws, st = C.c_int64(), C.c_int64()
+        _check(load().vp_ctx_memory(self.handle, C.byref(ws), C.byref(st)), self, "vp_ctx_memory")
+        return {"workspace_bytes": ws.value, "staging_bytes": st.value}
+
+    def set_batch_tile(self, width: int, targets_per_thread: int):
+        """vp_set_batch_tile: fix the batched far sum's tile for a density-chunk width (0: autotune)."""
+        _check(load().vp_set_batch_tile(self.handle, C.c_int32(width), C.c_int32(targets_per_thread)), self,
+               "vp_set_batch_tile")
+
+    def set_far_sym_cap(self, nbytes: int):
+        """vp_set_far_sym_cap: bound on the column scratch of the symmetric far sum."""
+        _check(load().vp_set_far_sym_cap(self.handle, C.c_int64(int(nbytes))), self, "vp_set_far_sym_cap")
 
     def close(self):
         if getattr(self, "handle", None):
@@ -409,19 +431,56 @@ def mesh_nodes(mesh: Mesh, stream=None):
 VP_NF_FP64_WEIGHTS = 1
 
 
-def nearfield_build(ctx: Context, mesh: Mesh, node_targets: bool = True, txy=None, eps: float = 1e-12,
-                    c_far: float = 1.0, c_near: float = 12.0, depth_cap: int = 30, fp64_weights: bool = False,
-                    stream=None) -> NearField:
-    """vp_nearfield_build; fp64_weights sets VP_NF_FP64_WEIGHTS (node
+def nf_params_default() -> dict:
+    """vp_nf_params_default: the parameters vp_nearfield_build uses when none are given."""
+    p = NfParams()
+    _check(load().vp_nf_params_default(C.byref(p)), None, "vp_nf_params_default")
+    return {k: getattr(p, k) for k, _ in NfParams._fields_}
+
+
+def nearfield_build(ctx: Context, mesh: Mesh, node_targets: bool = True, txy=None, eps: float | None = None,
+                    c_far: float | None = None, c_near: float | None = None, depth_cap: int | None = None,
+                    fp64_weights: bool = False, stream=None) -> NearField:
+    """vp_nearfield_build; parameters left as None take the library defaults
+    (vp_nf_params_default); fp64_weights sets VP_NF_FP64_WEIGHTS (node
     quadratures in FP64 instead of float-float)."""
     lib = load()
     m = 0 if txy is None else int(txy.shape[0])
-    p = NfParams(eps, c_far, c_near, depth_cap, VP_NF_FP64_WEIGHTS if fp64_weights else 0)
+    p = NfParams()
+    _check(lib.vp_nf_params_default(C.byref(p)), ctx, "vp_nf_params_default")
+    if eps is not None:
+        p.eps = eps
+    if c_far is not None:
+        p.c_far = c_far
+    if c_near is not None:
+        p.c_near = c_near
+    if depth_cap is not None:
+        p.depth_cap = depth_cap
+    p.flags = VP_NF_FP64_WEIGHTS if fp64_weights else 0
     h = C.c_void_p()
     rc = lib.vp_nearfield_build(ctx.handle, mesh.handle, C.c_int32(1 if node_targets else 0),
                                 _dptr(txy, "float64") if m else None, C.c_int64(m), C.byref(p), _stream(stream),
                                 C.byref(h))
     _check(rc, ctx, "vp_nearfield_build")
+    M = (mesh.N if node_targets else 0) + m
+    return NearField(ctx, mesh, h, M)
+
+
+def nearfield_build_host(ctx: Context, mesh: Mesh, node_targets: bool = True, txy: np.ndarray | None = None,
+                         fp64_weights: bool = False, stream=None) -> NearField:
+    """vp_nearfield_build_host: extra targets from a host array [m][2] (default parameters)."""
+    lib = load()
+    m = 0 if txy is None else int(txy.shape[0])
+    if m:
+        txy = np.ascontiguousarray(txy, dtype=np.float64)
+    p = NfParams()
+    _check(lib.vp_nf_params_default(C.byref(p)), ctx, "vp_nf_params_default")
+    p.flags = VP_NF_FP64_WEIGHTS if fp64_weights else 0
+    h = C.c_void_p()
+    rc = lib.vp_nearfield_build_host(ctx.handle, mesh.handle, C.c_int32(1 if node_targets else 0),
+                                     txy.ctypes.data_as(C.c_void_p) if m else None, C.c_int64(m), C.byref(p),
+                                     _stream(stream), C.byref(h))
+    _check(rc, ctx, "vp_nearfield_build_host")
     M = (mesh.N if node_targets else 0) + m
     return NearField(ctx, mesh, h, M)
 
@@ -560,6 +619,13 @@ class Batch:
 
     def launch(self, stream=None):
         _check(load().vp_batch_launch(self.handle, _stream(stream)), self.ctx, "vp_batch_launch")
+
+    def info(self) -> dict:
+        """vp_batch_info: targets-per-thread tile and work units per density-chunk width (1, 2, 4, 8)."""
+        tpt = (C.c_int32 * 4)()
+        units = (C.c_int64 * 4)()
+        _check(load().vp_batch_info(self.handle, tpt, units), self.ctx, "vp_batch_info")
+        return {w: (tpt[i], units[i]) for i, w in enumerate((1, 2, 4, 8))}
 
     def release(self):
         if getattr(self, "handle", None):

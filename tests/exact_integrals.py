@@ -69,29 +69,45 @@ def _poly_along_ray(qfun, x, e, deg, scale):
     return c / scale ** np.arange(deg + 1)
 
 
-def fan_poly(x, A, B, C, qfun, deg=4, epsabs=1e-15, epsrel=1e-14):
-    """int_T log|x - y| q(y) dA, q a polynomial of degree <= deg."""
+def fan_poly(x, A, B, C, qfun, deg=4, epsabs=3e-15, epsrel=3e-14):
+    """int_T log|x - y| q(y) dA, q a polynomial of degree <= deg.
+
+    Each fan (x, P, Q) is integrated along its edge: the ray to P + t (Q - P)
+    has length R(t) = |a + t d| (a = P - x, d = Q - P) and sweeps the angle
+    at the rate cross(a, d) / R(t)^2, so the fan is
+        int_0^1 [int_0^R(t) r log r q(x + r e(t)) dr] cross(a, d) / R(t)^2 dt.
+    The t-integrand peaks at the foot of the perpendicular from x with a width
+    of about the distance h from x to the line; the interval is cut there and
+    at geometric offsets h 10^j on either side."""
     x = np.asarray(x, float)
     total = 0.0
     scale = max(np.linalg.norm(v - x) for v in (A, B, C))
     for P, Q in ((A, B), (B, C), (C, A)):
-        a, b = P - x, Q - x
-        cross = a[0] * b[1] - a[1] * b[0]
+        a, d = P - x, Q - P
+        cross = a[0] * d[1] - a[1] * d[0]
         if abs(cross) < 1e-300:
             continue
-        th0 = math.atan2(a[1], a[0])
-        dth = math.atan2(cross, a @ b)            # signed angle P -> Q seen from x
-        d = Q - P
-        # distance along direction theta to the line PQ: r = cross / (e x d)
-        def f(t):
-            th = th0 + t
-            e = np.array([math.cos(th), math.sin(th)])
-            den = e[0] * d[1] - e[1] * d[0]
-            R = (a[0] * d[1] - a[1] * d[0]) / den
-            c = _poly_along_ray(qfun, x, e, deg, scale)
-            return sum(c[k] * _radial_moment(k, R) for k in range(deg + 1))
-        val, _ = integrate.quad(f, 0.0, dth, epsabs=epsabs, epsrel=epsrel, limit=400)
-        total += val
+        dd = float(d @ d)
+
+        def g(t):
+            v = a + t * d
+            R = math.sqrt(float(v @ v))
+            c = _poly_along_ray(qfun, x, v / R, deg, scale)
+            return sum(c[k] * _radial_moment(k, R) for k in range(deg + 1)) * cross / (R * R)
+        t_foot = float(-(a @ d) / dd)
+        width = abs(cross) / dd            # h / |d|
+        cuts = {0.0, 1.0}
+        for j in range(6):
+            for sgn in (-1.0, 1.0):
+                c = t_foot + sgn * width * 10.0 ** j
+                if 0.0 < c < 1.0:
+                    cuts.add(c)
+        if 0.0 < t_foot < 1.0:
+            cuts.add(t_foot)
+        cuts = sorted(cuts)
+        for lo, hi in zip(cuts, cuts[1:]):
+            val, _ = integrate.quad(g, lo, hi, epsabs=epsabs, epsrel=epsrel, limit=400)
+            total += val
     return total
 
 

@@ -93,12 +93,15 @@ def test_fmm_curved_annulus_closed_form(vp, ctx):
     m.release()
 
 
-def test_fmm_batch_matches_single_evaluations(vp, ctx):
+def test_fmm_batch_matches_single_evaluations(vp, ctx, tables):
     """A graph-captured batch of uneven meshes with VP_MIXED_FMM gives each
     item's single VP_MIXED_FMM evaluation bit for bit (same kernels, same
-    order), and stays within 1e-12 of the direct mixed result."""
+    order), stays within 1e-12 of the direct mixed result, and within 1e-12
+    of the FP64 oracle on sampled targets of every item."""
     meshes = [inputs.disk_uniform_mesh(600, 5, 2), inputs.lobed_mesh(1500, 6, 5, 0.25, 2),
               inputs.lshape_mesh(900, 7, 2)]
+    o = Oracle("far19", tables=tables)
+    rng = np.random.default_rng(95)
     items, refs = [], []
     for k, mesh in enumerate(meshes):
         m = vp.mesh_upload(ctx, mesh.vxy, mesh.tri, 19)
@@ -106,23 +109,28 @@ def test_fmm_batch_matches_single_evaluations(vp, ctx):
         y, _ = vp.mesh_nodes(m)
         yn = y.cpu().numpy()
         d = k + 1
-        f = torch.from_numpy(np.stack([inputs.gaussian_mix(mesh, 90 + 7 * k + j)(yn) for j in range(d)])).cuda()
+        fn = np.stack([inputs.gaussian_mix(mesh, 90 + 7 * k + j)(yn) for j in range(d)])
+        f = torch.from_numpy(fn).cuda()
         u = torch.full((d, nf.M), float("nan"), dtype=torch.float64, device="cuda")
+        s = o.setup(mesh.vxy, mesh.tri)
+        sample = np.sort(rng.choice(s["N"], 150, replace=False))
+        u_or, _ = o.potential(s, fn, targets=sample)
         items.append((nf, f, u))
         refs.append((vp.potential_eval(ctx, nf, f, precision=vp.VP_MIXED_FMM).cpu().numpy(),
-                     vp.potential_eval(ctx, nf, f, precision=vp.VP_MIXED).cpu().numpy(), m))
+                     vp.potential_eval(ctx, nf, f, precision=vp.VP_MIXED).cpu().numpy(), m, sample, u_or))
     batch = vp.Batch(ctx, items, precision=vp.VP_MIXED_FMM)
     for _ in range(2):
         batch.launch()
         torch.cuda.synchronize()
-        for (nf, f, u), (uf, um, _) in zip(items, refs):
+        for (nf, f, u), (uf, um, _, sample, u_or) in zip(items, refs):
             ub = u.cpu().numpy()
             assert np.array_equal(ub, uf)
             assert rel(ub, um) <= 1e-12
+            assert rel(ub[:, sample], u_or) <= 1e-12
     batch.release()
-    for (nf, _, _), (_, _, m) in zip(items, refs):
+    for (nf, _, _), ref in zip(items, refs):
         nf.release()
-        m.release()
+        ref[2].release()
 
 
 def test_fmm_far_outside_targets(vp, ctx, tables):

@@ -37,7 +37,7 @@ def _rank_main(rank, world, port, out):
 def test_whole_job_takes_the_slowest_rank_and_all_units():
     world = 2
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
