@@ -101,65 +101,43 @@ __global__ void __launch_bounds__(AS_WARPS * 32, 1)
         }
         const int64_t p0 = tile * AS_TILE;
         const int n = (int)min((int64_t)AS_TILE, P - p0);
-        // entry-parallel pass: entry e = 32 i + lane of the tile (pair e / NQ,
-        // node e % NQ), so that the density gathers of consecutive lanes are
-        // consecutive addresses; the float-float product C_e f_e replaces C_e
-        // in shared memory
-        float2* C = st[s].C;
-        // all density gathers first (independent loads in flight together),
-        // then the products
-        constexpr int NI = (AS_TILE * NQ + 31) / 32;   // entries per lane
-        float2 fv[NI];
-#pragma unroll
-        for (int i = 0; i < NI; i++) {
-            const int e = 32 * i + lane;
-            const int j = e / NQ;
-            const int64_t src = j < n ? (int64_t)st[s].tri[j] * NQ + (e - j * NQ) : 0;
-            fv[i] = __ldg(fd2 + src);
-        }
-        // this lane's pair (lane mod AS_TILE): target, row bounds and current
-        // value, loaded early so that their latency overlaps the products
+        // pair-parallel: with 32-pair tiles lane l takes pair p0 + l (with
+        // 16-pair tiles the two half-warps take the first and the second half
+        // of its nodes).  Its weights come from the tile in shared memory,
+        // its density values straight from the L2-resident float-float
+        // density (the nq values of one triangle are contiguous, so a lane's
+        // successive gathers fall in the same few sectors); each product is
+        // split exactly and added into one of four float-float partial sums
+        // (hi by two-sum, lo collecting the errors) in a fixed order.
         const int pl = lane & (AS_TILE - 1);
         int t = INT_MAX;   // padding lanes form their own segment
         int64_t r0 = 0, r1 = 0;
         double u0 = 0.0;
+        f2 ps = {0.f, 0.f};
         if (pl < n) {
             t = st[s].tgt[pl];
+            constexpr int HQ = AS_TILE == 32 ? NQ : (NQ + 1) / 2;
+            const int q0 = AS_TILE == 32 ? 0 : (lane >> 4) * HQ;
+            const float2* fp = fd2 + (int64_t)st[s].tri[pl] * NQ + q0;
+            float2 fv[HQ];
+#pragma unroll
+            for (int q = 0; q < HQ; q++) fv[q] = (q0 + q < NQ) ? __ldg(fp + q) : make_float2(0.f, 0.f);
             if (lane == pl) {
                 r0 = row[t];
                 r1 = row[t + 1];
                 u0 = u[t];
             }
-        }
-#pragma unroll
-        for (int i = 0; i < NI; i++) {
-            const int e = 32 * i + lane;
-            if (e / NQ < n) {
-                const float2 c = C[e];
-                const float p = __fmul_rn(c.x, fv[i].x);
-                float er = __fmaf_rn(c.x, fv[i].x, -p);
-                er = __fmaf_rn(c.x, fv[i].y, __fmaf_rn(c.y, fv[i].x, er));
-                C[e] = make_float2(p, er);
-            }
-        }
-        __syncwarp();
-        // pair-parallel pass: the NQ products of pair p0 + pl, in interleaved
-        // float-float partial sums combined in a fixed order (with 16-pair
-        // tiles the two half-warps take the first and second half of them)
-        f2 ps = {0.f, 0.f};
-        if (pl < n) {
-            constexpr int HQ = AS_TILE == 32 ? NQ : (NQ + 1) / 2;
-            const int q0 = AS_TILE == 32 ? 0 : (lane >> 4) * HQ;
-            const float2* c = C + pl * NQ;
-            f2 a4[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            const float2* c = st[s].C + pl * NQ + q0;
+            float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int q = 0; q < HQ; q++) {
                 if (q0 + q < NQ) {
-                    const float2 v = c[q0 + q];
-                    a4[q & 3] = f2_add(a4[q & 3], {v.x, v.y});
+                    const float2 cv = c[q];
+                    f2_acc(ah[q & 3], al[q & 3], f2{cv.x, cv.y}, f2{fv[q].x, fv[q].y});
                 }
             }
-            ps = f2_add(f2_add(a4[0], a4[1]), f2_add(a4[2], a4[3]));
+            ps = f2_add(f2_add(f2_fast(ah[0], al[0]), f2_fast(ah[1], al[1])),
+                        f2_add(f2_fast(ah[2], al[2]), f2_fast(ah[3], al[3])));
         }
         if (AS_TILE == 16) {
             // both halves: (first half) + (second half), the same on both
@@ -246,12 +224,12 @@ size_t apply_stream_ws_bytes(int64_t N, int64_t P) {
 
 void launch_apply_stream(const int64_t* row, const int32_t* ptri, const int32_t* ptgt, const float2* C2, int nq,
                          const double* f, int64_t N, int64_t P, int64_t M, double* u, void* ws, int32_t* flag,
-                         int sm_count, cudaStream_t s) {
+                         int sm_count, cudaStream_t s, bool f2_ready) {
     if (P <= 0 || M <= 0) return;
     // the density as float-float pairs, then the slots
     float2* fd2 = (float2*)ws;
     double* slots = (double*)((char*)ws + (((size_t)N * sizeof(float2) + 255) & ~(size_t)255));
-    launch_to_f2(f, N, fd2, s);
+    if (!f2_ready) launch_to_f2(f, N, fd2, s);
     if (nq == 19) apply_stream<19>(row, ptri, ptgt, C2, fd2, P, M, u, slots, flag, sm_count, s);
     else apply_stream<16>(row, ptri, ptgt, C2, fd2, P, M, u, slots, flag, sm_count, s);
 }

@@ -354,7 +354,7 @@ int far_sym_plan(vp_ctx* ctx, vp_nf* nf) {
 // u_far for one density: the symmetric pass over the node targets, the
 // one-sided pass over the extra targets.  out: [M] (node targets first).
 void launch_far_sym(const vp_ctx* ctx, const vp_nf* nf, const double* W, const double* f, double* out, void* ws,
-                    cudaStream_t s) {
+                    cudaStream_t s, float2* f2out) {
     ensure_logtab();
     const SymPlan* p = nf->sym;
     const int64_t N = p->N, M = nf->M, m = M - N;
@@ -374,7 +374,7 @@ void launch_far_sym(const vp_ctx* ctx, const vp_nf* nf, const double* W, const d
     double* xpart = (double*)w;
     const float* shi = nf->src_ff.hi;
     const float* slo = nf->src_ff.lo;
-    k_prep_q_ff<1><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(W, f, N, 1, 0, q);
+    k_prep_q_ff<1><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(W, f, N, 1, 0, q, f2out);
     for (size_t b = 0; b < p->bands.size(); b++) {
         const SymBand& bd = p->bands[b];
         if (bd.u1 > bd.u0)

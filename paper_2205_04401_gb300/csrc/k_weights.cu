@@ -529,16 +529,28 @@ __global__ void __launch_bounds__(256) k_near_root_split(WeightsArgs a, WeightsF
 // Root-leaf near pairs: the near rule on the whole triangle.  Its nodes sit at
 // fixed reference points z_j, so the moments and the moment-to-weight map
 // fold into one constant matrix of the far rule, C_k = sum_j B_jk g_j with
-// g_j = log|y_j - x|^2 w_j J_T / 4pi (B = QM M(z)^T, tabulated per rule):
-// one warp per pair forms the 49 g_j in shared memory, lane k the dot
-// product of node k (32 nodes per pass), then the far-rule subtraction.
+// g_j = log|y_j - x|^2 w_j J_T / 4pi (B = QM M(z)^T, tabulated per rule).
+// A warp takes RPW pairs at once, so that its lanes stay busy: the RPW x 49
+// values g_j are spread over the lanes into shared memory, then the RPW x nq
+// dot products (one (pair, node) per lane) and the far-rule subtraction.
+// Each (pair, node) result is computed by the same operations in the same
+// order whatever lane takes it.
 #ifndef VP_ROOT_MINB
 #define VP_ROOT_MINB 6
 #endif
+#ifndef VP_ROOT_PPW
+#define VP_ROOT_PPW 5
+#endif
+constexpr int RPW = VP_ROOT_PPW;
+struct RootPair {
+    NearPairF2 g;
+    int32_t p, T, t, own;
+};
 __global__ void __launch_bounds__(WARPS * 32, VP_ROOT_MINB) k_weights_near_root(WeightsArgs a, WeightsF2 b,
                                                                                 const int32_t* __restrict__ idx,
                                                                                 int64_t n) {
-    __shared__ float2 g_all[WARPS][VP_NNEAR];
+    __shared__ float2 g_all[WARPS][RPW][VP_NNEAR];
+    __shared__ RootPair rp_all[WARPS][RPW];
     __shared__ float4 ftab[LOG_N];
     __shared__ float4 nz_s[VP_NNEAR];
     __shared__ float2 nw_s[VP_NNEAR];
@@ -550,15 +562,24 @@ __global__ void __launch_bounds__(WARPS * 32, VP_ROOT_MINB) k_weights_near_root(
     }
     load_logtab(a.tab, lt);              // ends with __syncthreads
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int64_t w = (int64_t)blockIdx.x * WARPS + wl;
-    if (w >= n) return;
+    const int64_t w0 = ((int64_t)blockIdx.x * WARPS + wl) * RPW;
+    if (w0 >= n) return;
+    const int np = (int)min((int64_t)RPW, n - w0);
     const double ln2 = a.tab->ln2;
-    float2* gs = g_all[wl];
-    const int64_t p = idx[w];
-    const int T = a.ptri[p], t = a.ptgt[p];
-    const int own = own_index(a, t, T);
-    const NearPairF2 g = near_pair_f2(b, T, t);
-    for (int j = lane; j < VP_NNEAR; j += 32) {
+    RootPair* rp = rp_all[wl];
+    if (lane < np) {
+        RootPair r;
+        r.p = idx[w0 + lane];
+        r.T = a.ptri[r.p];
+        r.t = a.ptgt[r.p];
+        r.own = own_index(a, r.t, r.T);
+        r.g = near_pair_f2(b, r.T, r.t);
+        rp[lane] = r;
+    }
+    __syncwarp();
+    for (int e = lane; e < np * VP_NNEAR; e += 32) {
+        const int q = e / VP_NNEAR, j = e - q * VP_NNEAR;
+        const NearPairF2 g = rp[q].g;
         const float4 Z = nz_s[j];
         const f2 zx = {Z.x, Z.y}, zy = {Z.z, Z.w};
         const f2 dx = f2_add(g.ax, f2_add(f2_mul(zx, g.ex), f2_mul(zy, g.fx)));   // y_j - x
@@ -569,12 +590,13 @@ __global__ void __launch_bounds__(WARPS * 32, VP_ROOT_MINB) k_weights_near_root(
         else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
         const float2 W = nw_s[j];
         const f2 gj = f2_mul(lg, f2_mul({W.x, W.y}, g.wj));
-        gs[j] = make_float2(gj.h, gj.l);
+        g_all[wl][q][j] = make_float2(gj.h, gj.l);
     }
     __syncwarp();
-    for (int k0 = 0; k0 < a.nq; k0 += 32) {
-        const int k = k0 + lane;
-        const float2* Bk = a.B2 + (k < a.nq ? k : 0);
+    for (int sl = lane; sl < np * a.nq; sl += 32) {
+        const int q = sl / a.nq, k = sl - q * a.nq;
+        const float2* gs = g_all[wl][q];
+        const float2* Bk = a.B2 + k;
         float ah = 0.f, al = 0.f;
 #pragma unroll 7
         for (int j = 0; j < VP_NNEAR; j++) {
@@ -586,7 +608,8 @@ __global__ void __launch_bounds__(WARPS * 32, VP_ROOT_MINB) k_weights_near_root(
                 al = r.l;
             }
         }
-        if (k < a.nq) far_subtract_store(a, b, p, T, t, own, k, f2_fast(ah, al), ftab, lt, ln2);
+        const RootPair& r = rp[q];
+        far_subtract_store(a, b, r.p, r.T, r.t, r.own, k, f2_fast(ah, al), ftab, lt, ln2);
     }
 }
 
@@ -999,7 +1022,8 @@ void launch_weights(const WeightsArgs& a, const int32_t* self_idx, int64_t n_sel
         cudaStreamSynchronize(s);
         const int64_t n_root = (int64_t)h_cnt[0], n_deep = (int64_t)h_cnt[1];
         if (n_root > 0)
-            k_weights_near_root<<<(unsigned)((n_root + WARPS - 1) / WARPS), WARPS * 32, 0, s>>>(a, b, root_idx, n_root);
+            k_weights_near_root<<<(unsigned)((n_root + WARPS * RPW - 1) / (WARPS * RPW)), WARPS * 32, 0, s>>>(
+                a, b, root_idx, n_root);
         if (n_deep > 0) near_deep(a, b, deep_idx, n_deep, s, ctx);
     });
 }

@@ -935,6 +935,11 @@ int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, doub
     double* fT = apply_ws_bytes(N, d) ? (double*)apply_ws : nullptr;
     const bool prof_saved = ctx->prof;
     if (!profile) ctx->prof = false;
+    // the streamed apply (one density, mixed) gathers the density as
+    // float-float pairs: the direct far sum's charge preparation writes them
+    const bool stream_apply = precision != VP_MIXED_TC && mesh->rule.builtin >= 0 &&
+                              (precision == VP_MIXED || fmm) && d == 1 && nf->d_C2;
+    float2* f2out = stream_apply && !fmm ? (float2*)apply_ws : nullptr;
     if (precision == VP_FP64)
         PROF(ctx, ST_FAR_FP64, s,
              launch_far_fp64(mesh->d_y, mesh->d_W, N, f_dev, d, nf->d_txy, nf->d_tnode, M, partial, splits, s));
@@ -946,10 +951,11 @@ int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, doub
             return rc;
         }
     } else if (sym)
-        PROF(ctx, ST_FAR_FF, s, launch_far_sym(ctx, nf, mesh->d_W, f_dev, u_dev, qbuf, s));
+        PROF(ctx, ST_FAR_FF, s, launch_far_sym(ctx, nf, mesh->d_W, f_dev, u_dev, qbuf, s, f2out));
     else
         PROF(ctx, ST_FAR_FF, s,
-             launch_far_ff(nf->src_ff, mesh->d_W, N, f_dev, d, nf->tgt_ff, nf->d_tnode, M, partial, qbuf, splits, s));
+             launch_far_ff(nf->src_ff, mesh->d_W, N, f_dev, d, nf->tgt_ff, nf->d_tnode, M, partial, qbuf, splits, s,
+                           f2out));
     if (splits > 1) PROF(ctx, ST_REDUCE, s, launch_reduce_splits(partial, splits, (int64_t)d * M, u_dev, s));
     if (precision == VP_MIXED_TC) {
         int rc = VP_OK;
@@ -963,7 +969,7 @@ int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, doub
     } else if ((precision == VP_MIXED || fmm) && d == 1 && nf->d_C2) {
         PROF(ctx, ST_APPLY, s,
              launch_apply_stream(nf->d_row, nf->d_ptri, nf->d_ptgt, nf->d_C2, mesh->nq, f_dev, N, nf->P, M, u_dev,
-                                 apply_ws, ctx->d_flag, ctx->sm_count, s));
+                                 apply_ws, ctx->d_flag, ctx->sm_count, s, f2out != nullptr));
     } else if ((precision == VP_MIXED || fmm) && d < APPLY_MANY_MIN_D && nf->d_C2) {
         PROF(ctx, ST_APPLY, s,
              launch_apply_f2(nf->d_row, nf->d_ptri, nf->d_C2, mesh->nq, f_dev, N, d, M, u_dev, (float2*)apply_ws, s));

@@ -299,8 +299,11 @@ void launch_sum_by_kind(const int32_t* a, const uint8_t* kind, const int32_t* b,
 // evaluation
 void launch_far_fp64(const double* y, const double* W, int64_t N, const double* f, int d, const double* txy,
                      const int32_t* tnode, int64_t M, double* partial, int splits, cudaStream_t s);
+// f2out (d = 1 only, may be nullptr): also write the density as float-float
+// pairs for the streamed correction apply (fused into the charge preparation)
 void launch_far_ff(const FFCoords& src, const double* W, int64_t N, const double* f, int d, const FFCoords& tgt,
-                   const int32_t* tnode, int64_t M, double* partial, float* qbuf, int splits, cudaStream_t s);
+                   const int32_t* tnode, int64_t M, double* partial, float* qbuf, int splits, cudaStream_t s,
+                   float2* f2out = nullptr);
 void launch_reduce_splits(const double* partial, int splits, int64_t count, double* out, cudaStream_t s);
 // Densities from which the correction is applied with densities across lanes
 // (needs a node-major copy of f: apply_ws_bytes); fewer, or fT == nullptr,
@@ -315,7 +318,7 @@ int far_sym_plan(vp_ctx* ctx, vp_nf* nf);
 void far_sym_plan_free(SymPlan* p);
 size_t far_sym_ws_bytes(const vp_ctx* ctx, const vp_nf* nf);
 void launch_far_sym(const vp_ctx* ctx, const vp_nf* nf, const double* W, const double* f, double* out, void* ws,
-                    cudaStream_t s);
+                    cudaStream_t s, float2* f2out = nullptr);
 
 // fast multipole far sum (k_fmm.cu): plan on first use, workspace, evaluation
 // (writes u = far sum, d densities), leaf level of a plan
@@ -339,6 +342,8 @@ void launch_apply_f2(const int64_t* row, const int32_t* ptri, const float2* C2, 
 // streamed float-float apply of one density (k_apply_stream.cu), workspace of
 // apply_stream_ws_bytes(N, P); ptri, ptgt and C2 carry 16 bytes of padding
 size_t apply_stream_ws_bytes(int64_t N, int64_t P);
+// f2_ready: the workspace already holds the float-float density (written by
+// the far sum's charge preparation), else it is converted first
 void launch_apply_stream(const int64_t* row, const int32_t* ptri, const int32_t* ptgt, const float2* C2, int nq,
                          const double* f, int64_t N, int64_t P, int64_t M, double* u, void* ws, int32_t* flag,
-                         int sm_count, cudaStream_t s);
+                         int sm_count, cudaStream_t s, bool f2_ready = false);

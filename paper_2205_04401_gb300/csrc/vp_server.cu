@@ -117,6 +117,14 @@ static int build_cold(vp_server* sv, ServedMesh& m) {
             return rc;
         }
     }
+    if (sv->precision == VP_MIXED && far_sym_applicable(nf, 1)) {
+        rc = far_sym_plan(sv->ctx, nf);
+        if (rc) {
+            vp_nf_release(nf);
+            vp_mesh_release(mesh);
+            return rc;
+        }
+    }
     m.mesh = mesh;
     m.nf = nf;
     m.owned = true;
@@ -285,6 +293,11 @@ int vp_server_register(vp_server* sv, int64_t key, const vp_nf* nf) {
     if (sv->precision == VP_MIXED_FMM && !nf->fmm) {
         // the multipole plan is built here, before requests reach the mesh
         const int rc = fmm_plan_build(sv->ctx, const_cast<vp_nf*>(nf), sv->build_stream);
+        if (rc) return rc;
+    }
+    if (sv->precision == VP_MIXED && far_sym_applicable(nf, 1) && !nf->sym) {
+        // the symmetric far sum's unit tables, for its one-density requests
+        const int rc = far_sym_plan(sv->ctx, const_cast<vp_nf*>(nf));
         if (rc) return rc;
     }
     ServedMesh m;
