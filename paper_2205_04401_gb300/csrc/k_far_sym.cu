@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(SYM_THREADS) k_far_sym(const float* __restrict
                                                          const int64_t* __restrict__ coff, int64_t u0, int64_t cb0,
                                                          double* __restrict__ rowbuf, double* __restrict__ colbuf) {
     __shared__ SymSmem sm;
-    for (int i = threadIdx.x; i < LOG_N; i += SYM_THREADS) sm.stab[i] = g_logtab.e[i];
+    for (int i = threadIdx.x; i < LOG_N; i += SYM_THREADS) sm.stab[i] = g_logtab_far.e[i];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t u = u0 + blockIdx.x;
     const int I = unit_I[u];
@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(SYM_THREADS) k_far_sym(const float* __restrict
 #pragma unroll
                     for (int r = 0; r < SYM_TPT; r++) {
                         float s, corr, lh, ll;
-                        ff_dist2<false>(thx[r], thy[r], tlx[r], tly[r], sv, s, corr);   // distinct nodes
-                        ff_log(sm.stab, s, corr, lh, ll);         // log |x_i - y_j|^2
+                        ff_dist2_far<false>(thx[r], thy[r], tlx[r], tly[r], sv, s, corr);   // distinct nodes
+                        ff_log_far(sm.stab, s, corr, lh, ll);     // log |x_i - y_j|^2
                         ff_madd(qj.x, qj.y, lh, ll, sh[r], sl[r]);
                         ff_madd(qh[r], ql[r], lh, ll, ch, cl);
                     }

@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(EV_THREADS) k_fmm_eval(FmmGeo g, const int2* _
     const int2 un = units[blockIdx.x];
     const int b = un.x;
     const int64_t t0 = tstart[b] + (int64_t)un.y * EV_THREADS, t1 = min(t0 + EV_THREADS, tstart[b + 1]);
-    for (int i = threadIdx.x; i < LOG_N; i += blockDim.x) stab[i] = g_logtab.e[i];
+    for (int i = threadIdx.x; i < LOG_N; i += blockDim.x) stab[i] = g_logtab_far.e[i];
     const int nb = 1 << g.L;
     const int ix = b % nb, iy = b / nb;
     const int jx0 = max(ix - 1, 0), jx1 = min(ix + 1, nb - 1);
@@ -410,13 +410,13 @@ __global__ void __launch_bounds__(EV_THREADS) k_fmm_eval(FmmGeo g, const int2* _
 #pragma unroll 4
                         for (int i = i0; i < i1; i++) {
                             float s2, corr;
-                            ff_dist2<true>(thx, thy, tlx, tly, s_xy[i], s2, corr);
+                            ff_dist2_far<true>(thx, thy, tlx, tly, s_xy[i], s2, corr);
                             if (i == kl) {                        // own node: log 1 = 0
                                 s2 = 1.0f;
                                 corr = 0.0f;
                             }
                             float lh, ll;
-                            ff_log(stab, s2, corr, lh, ll);
+                            ff_log_far(stab, s2, corr, lh, ll);
                             const float2 qv = s_q[i];
                             ff_madd(qv.x, qv.y, lh, ll, sh, sl);
                         }

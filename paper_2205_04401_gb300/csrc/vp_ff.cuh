@@ -18,6 +18,9 @@ struct LogTab {
 // One copy per translation unit (no relocatable device code), filled by
 // ensure_logtab() from host code of the same unit.
 static __device__ LogTab g_logtab;
+// The far sum's table: the same c_i and 1/c_i, log c_i split as a multiple of
+// 2^-18 (hi) plus the FP32 rest (lo), so that E ln2_h + hi is exact (ff_log_far).
+static __device__ LogTab g_logtab_far;
 
 constexpr float LN2_H = 0.693147182464599609375f;        // fl(ln 2)
 constexpr float LN2_L = -1.904654323148236e-09f;        // ln 2 - LN2_H
@@ -59,6 +62,87 @@ __device__ __forceinline__ void ff_log(const float4* __restrict__ tab, float s, 
     tail = __fadd_rn(tail, __fadd_rn(__fadd_rn(ea, eb), eP));
     hi = b;
     lo = tail;
+}
+
+// ln 2 = LN2_H18 + LN2_L18 with LN2_H18 = 181704 2^-18 (18 bits): E LN2_H18 is
+// exact for |E| <= 63.
+constexpr float LN2_H18 = 0.693145751953125f;
+constexpr float LN2_L18 = 1.4286068202862268e-06f;
+
+// The far sum's logarithm of (s, corr), |corr| <= 2^-23 s, s in [2^-63, 2^64),
+// trimmed to its error budget.  The far sum's relative error is at most
+// max_pair |d log r^2| sum_j |q_j| / (4 pi max|u|); on the workloads here
+// sum|q| / (4 pi max|u|) is below 1, so a per-pair error of 1e-11 keeps the
+// potential an order of magnitude inside a 1e-10 bar.  With
+// log s = E ln 2 + log c + log(1 + w), w = (m - c)/c = wh + wl:
+//   * E LN2_H18 (exact) + hi(log c) (on the 2^-18 grid) is exact, so
+//     hi + wh + E LN2_H18 takes two fast two-sums (hi >= 2^-10 > |wh|, and
+//     |E LN2_H18| >= ln2_h > |hi + wh| or E = 0);
+//   * E LN2_L18 + lo(log c) in one FMA: rounding at most 2^-24 (63 + 1)
+//     2^-19 = 7e-12 (1e-12 for |E| <= 8, r^2 above 2^-8);
+//   * log(1 + w) - w = -w^2/2 + w^3/3 (the dropped w^4/4 < 2^-42), and wl
+//     without its w wl part (< 2^-44);
+//   * corr / s with an approximate reciprocal (relative 2^-22 of 2^-23).
+// The result is renormalised (|lo| <= 2^-24 |hi|) for the products that follow.
+// The accurate ff_log (error ~1e-13) stays with the correction weights.
+__device__ __forceinline__ void ff_log_far(const float4* __restrict__ tab, float s, float corr, float& hi,
+                                           float& lo) {
+    const int bits = __float_as_int(s);
+    const float fe = __fsub_rn(__int_as_float((bits >> 23) | 0x4b000000), 8388735.0f);
+    const int i = (bits >> (23 - LOG_BITS)) & (LOG_N - 1);
+    const float m = __int_as_float((bits & 0x007fffff) | 0x3f800000);    // [1, 2)
+    const float4 t = tab[i];                                             // 1/c, log c (hi, lo), c
+    const float u = __fsub_rn(m, t.w);                                   // exact (Sterbenz)
+    const float wh = __fmul_rn(u, t.x);
+    const float wl = __fmul_rn(__fmaf_rn(-wh, t.w, u), t.x);            // residual u - wh c is exact
+    float p = __fmaf_rn(wh, 0.33333334f, -0.5f);
+    p = __fmul_rn(__fmul_rn(p, wh), wh);                                 // -w^2/2 + w^3/3
+    const float P = __fmul_rn(fe, LN2_H18);                              // exact
+    const float s1 = __fadd_rn(t.y, wh);                                 // fast two-sum, t.y >= 2^-10 > |wh|
+    const float e1 = __fsub_rn(wh, __fsub_rn(s1, t.y));
+    const float b = __fadd_rn(P, s1);                                    // fast two-sum, |P| >= |s1| or P = 0
+    const float e2 = __fsub_rn(s1, __fsub_rn(b, P));
+    float rs;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(s));
+    float tail = __fmaf_rn(corr, rs, wl);
+    tail = __fadd_rn(tail, __fmaf_rn(fe, LN2_L18, t.z));
+    tail = __fadd_rn(tail, p);
+    tail = __fadd_rn(tail, __fadd_rn(e1, e2));
+    // renormalise: |tail| reaches 2^-17 |b| (the E LN2_L18 term), which would
+    // cost the far sum's float-float products and sums six bits; fast two-sum,
+    // exact unless |b| < |tail| (then both are below 1e-4 and the error is
+    // below 2^-24 1e-4)
+    hi = __fadd_rn(b, tail);
+    lo = __fsub_rn(tail, __fsub_rn(hi, b));
+}
+
+// |x_t - y_s|^2 for the far sum: (a + al)^2 + (b + bl)^2 with a, b the exact
+// differences of the hi parts and al, bl of the lo parts, as
+// s0 + [e1 + e2 + e3 + al (2a + al) + bl (2b + bl)], s0 + e3 = a^2 + b^2
+// exactly (a^2 = p1 + e1, b^2 = p2 + e2), renormalised to (s, corr) with
+// |corr| <= 2^-24 s.  The cross terms are rounded to 2^-24 of themselves,
+// at most 2^-22 |x - y| q, q the grid of the hi parts: a relative error of
+// r^2 below 1e-13 for |x - y| > 1e-4 of the box (the other pairs weigh one
+// charge each).  GUARD: map coincident points to s = 1e-30.
+template <bool GUARD = true>
+__device__ __forceinline__ void ff_dist2_far(float thx, float thy, float tlx, float tly, float4 sv, float& s,
+                                             float& corr) {
+    const float a = __fsub_rn(thx, sv.x), b = __fsub_rn(thy, sv.y);
+    const float al = __fsub_rn(tlx, sv.z), bl = __fsub_rn(tly, sv.w);
+    const float p1 = __fmul_rn(a, a), p2 = __fmul_rn(b, b);
+    const float e1 = __fmaf_rn(a, a, -p1), e2 = __fmaf_rn(b, b, -p2);
+    const float big = fmaxf(p1, p2), small = fminf(p1, p2);
+    const float s0 = __fadd_rn(big, small);
+    const float e3 = __fsub_rn(small, __fsub_rn(s0, big));            // fast two-sum (big >= small >= 0)
+    float c0 = __fadd_rn(__fadd_rn(e1, e2), e3);
+    c0 = __fmaf_rn(al, __fmaf_rn(2.0f, a, al), c0);
+    c0 = __fmaf_rn(bl, __fmaf_rn(2.0f, b, bl), c0);
+    s = __fadd_rn(s0, c0);
+    corr = __fadd_rn(__fsub_rn(s0, s), c0);
+    if (GUARD && !(s > 1e-30f)) {
+        s = 1e-30f;
+        corr = 0.0f;
+    }
 }
 
 // |x_t - y_s|^2 as a renormalised float-float pair from the split coordinates
@@ -117,13 +201,13 @@ __device__ __forceinline__ void ff_tile(const float4* __restrict__ sxy, const fl
 #pragma unroll
         for (int r = 0; r < TPT; r++) {
             float s, corr;
-            ff_dist2(thx[r], thy[r], tlx[r], tly[r], sv, s, corr);
+            ff_dist2_far(thx[r], thy[r], tlx[r], tly[r], sv, s, corr);
             if (CHECK_OWN && i == own_local[r]) {                    // own node: log 1 = 0
                 s = 1.0f;
                 corr = 0.0f;
             }
             float lh, ll;
-            ff_log(stab, s, corr, lh, ll);                           // log |x-y|^2 = lh + ll
+            ff_log_far(stab, s, corr, lh, ll);                       // log |x-y|^2 = lh + ll
 #pragma unroll
             for (int k = 0; k < D; k++) ff_madd(qh[k], ql[k], lh, ll, sh[r][k], sl[r][k]);
         }
@@ -141,7 +225,7 @@ struct FFSmem {
 
 template <int D>
 __device__ __forceinline__ void ff_load_table(FFSmem<D>& sm) {
-    for (int i = threadIdx.x; i < LOG_N; i += FF_THREADS) sm.stab[i] = g_logtab.e[i];
+    for (int i = threadIdx.x; i < LOG_N; i += FF_THREADS) sm.stab[i] = g_logtab_far.e[i];
 }
 
 // One block of FF_THREADS x TPT targets (tbase + r FF_THREADS, r < TPT)
@@ -271,6 +355,14 @@ static cudaError_t ensure_logtab() {
         h.e[i] = make_float4((float)(1.0 / c), lh, (float)(L - (double)lh), (float)c);   // c is exact in float
     }
     e = cudaMemcpyToSymbol(g_logtab, &h, sizeof(h));
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < LOG_N; i++) {
+        const double c = 1.0 + (i + 0.5) / LOG_N;
+        const double L = std::log(c);
+        const double hi = std::nearbyint(L * 262144.0) / 262144.0;    // on the 2^-18 grid (>= 2^-10)
+        h.e[i] = make_float4((float)(1.0 / c), (float)hi, (float)(L - hi), (float)c);
+    }
+    e = cudaMemcpyToSymbol(g_logtab_far, &h, sizeof(h));
     if (e == cudaSuccess) loaded_mask[dev >> 5] |= 1u << (dev & 31);
     return e;
 }

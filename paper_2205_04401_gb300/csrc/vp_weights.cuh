@@ -16,7 +16,7 @@ namespace {
 #define VP_NEAR_STK 128
 #endif
 #ifndef VP_SELF_MINB
-#define VP_SELF_MINB 6
+#define VP_SELF_MINB 4
 #endif
 
 constexpr int WARPS = 4;

@@ -168,8 +168,9 @@ def test_conical_rules_in_a_batch(vp, ctx, prec):
     """Meshes on different far rules (a conical rule of degree 20 among the
     built-in ones) in one graph-captured batch, direct (run-time node count
     in the batched apply) and with the FMM: each item equals its single
-    evaluation (FMM: bit for bit; direct: to 1e-13, the batched far sum is
-    one-sided and sums in another order)."""
+    evaluation (FMM: bit for bit; direct: to 1e-12, the FP64 parity bar: the
+    batched far sum is one-sided where the single evaluation is symmetric, so
+    its FP64 partial sums are added in another order)."""
     meshes = [(inputs.disk_uniform_mesh(300, 11, 2), vp.VP_RULE_CONICAL(20)),
               (inputs.lshape_mesh(400, 12, 2), 19), (inputs.disk_mesh(n_b=10, n_i=5), vp.VP_RULE_CONICAL(30))]
     items, refs, keep = [], [], []
@@ -191,7 +192,7 @@ def test_conical_rules_in_a_batch(vp, ctx, prec):
         if prec == 3:
             assert np.array_equal(ub, ref)
         else:
-            assert rel_err(ub, ref).max() <= 1e-13
+            assert rel_err(ub, ref).max() <= 1e-12
     batch.release()
     for (nf, _, _), m in zip(items, keep):
         nf.release()

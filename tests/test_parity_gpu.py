@@ -215,8 +215,8 @@ def test_forty_densities_on_the_star_mesh(vp, ctx, tables, star):
 def test_symmetric_far_sum_single_density(vp, ctx, tables, star, which):
     """One density with node targets takes the symmetric far sum (each pair
     of nodes in different tiles evaluated once, used both ways): equal to
-    the one-sided batch kernel to rounding and to the oracle within the
-    mixed bar.  The L-shape has N = 13,300 nodes (ragged last tile) and
+    the one-sided batch kernel within the FP64 parity bar (the same pair
+    values summed in another order) and to the oracle within the mixed bar.  The L-shape has N = 13,300 nodes (ragged last tile) and
     extra targets."""
     if which == "star":
         s, f3, sample, u_or3, _, _, g = star
@@ -238,7 +238,8 @@ def test_symmetric_far_sum_single_density(vp, ctx, tables, star, which):
     u = vp.potential_eval(ctx, nf, fd, precision=1).cpu().numpy()
     ub = torch.empty((1, nf.M), dtype=torch.float64, device="cuda")
     vp.potential_eval_batch(ctx, [(nf, fd, ub)], precision=1)
-    assert rel_err(u, ub.cpu().numpy()).max() <= 1e-13
+    # same pair values, FP64 partial sums in another order: the FP64 parity bar
+    assert rel_err(u, ub.cpu().numpy()).max() <= 1e-12
     assert rel_err(u[:, sample], u_or).max() <= 1e-10
 
 
