@@ -42,7 +42,7 @@ constexpr int TC_CH_TRI = 2;       // triangles per K chunk
 constexpr int TC_CH_K = TC_KPT * TC_CH_TRI;   // 48
 constexpr int TC_KSTEPS = TC_CH_K / 16;        // 3 MMAs of K = 16 per digit per chunk
 constexpr int TC_STAGES = 3;
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 192;   // producer warp, MMA warp, four epilogue warps
 constexpr int TC_TMEM_COLS = 512;
 constexpr int TC_PAIR_CAP = 16384;  // near pairs per tile the plan can hold
 
@@ -475,32 +475,71 @@ struct TcArgs {
     const unsigned long long* fmaxb;   // [dn]
     int64_t nT, M, n_tiles;
     int L, dn, d, d0;
-    int* counter;               // tile counter (zero before the launch)
     int32_t* flag;              // device error flags
     double* u;                  // [d][M]
 };
 
-// Persistent: one CTA per SM takes tiles from a counter.  Thread 0 issues the
-// A copies (one bulk copy per chunk) and the MMAs; all threads gather the
-// density digits (16-byte cp.async) and read the accumulators back.
+__device__ __forceinline__ void mbar_arrive1(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Chunk c of a tile with n_near near chunks and nch in all: its run (near or
+// self, cut every sc chunks) and whether it opens or closes that run.
+struct ChunkPos {
+    bool self_run, first, last;
+};
+__device__ __forceinline__ ChunkPos chunk_pos(int64_t c, int64_t n_near, int64_t nch, int sc) {
+    ChunkPos r;
+    r.self_run = c >= n_near;
+    const int64_t pos = r.self_run ? c - n_near : c, len = r.self_run ? nch - n_near : n_near;
+    r.first = (pos % sc) == 0;
+    r.last = (pos % sc) == sc - 1 || pos == len - 1;
+    return r;
+}
+
+// Persistent and warp-specialised: one CTA per SM walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... (Morton order, so neighbouring
+// tiles have similar chunk counts).
+//   warp 0 (producer): per chunk, waits for the stage to be free, one lane
+//     bulk-copies the weight-digit image (complete_tx on the stage's full
+//     barrier), all lanes gather the density digits with 16-byte cp.async;
+//     one chunk later (its copies done, made visible to the tensor cores'
+//     proxy) lane 0 arrives on the full barrier;
+//   warp 1 (MMA): per chunk, waits for the stage, issues the L x 3 MMAs and
+//     commits them to the stage's empty barrier; at the end of a run it
+//     commits to acc_full and, before the next run, waits for acc_empty;
+//   warps 2-5 (epilogue, TMEM lanes 32 (w mod 4) ..): zero the accumulator
+//     columns, and after each run read the level sums, combine them in
+//     float-float and add them to u, zero the columns again and arrive on
+//     acc_empty.
+// No CTA-wide barrier inside the loop; every wait is bounded and an abort
+// (a wait that gave up) is shared through shared memory, drained, reported.
+constexpr int TC_PROD_LAG = 1;   // chunks between issuing a stage's gathers and declaring it full
+template <int DN>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(TcArgs a) {
     extern __shared__ unsigned char tc_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
-    const int L = a.L, dn = a.dn;
-    const uint32_t abytes = a_chunk_bytes(L), bstep = b_step_bytes(L), bbytes = b_chunk_bytes(L);
-    const uint32_t stage_bytes = abytes + bbytes;
-    uint64_t* bars = (uint64_t*)(base + TC_STAGES * stage_bytes);   // full[3], mma[3]
-    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * TC_STAGES);
-    int* tile_slot = (int*)(tmem_slot + 1);
-    int* abort_flag = tile_slot + 1;
-    int* tau = abort_flag + 1;                                       // [dn]
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int L = a.L;
+    constexpr int dn = DN;   // densities per pass (dens_per_pass(L))
+    const uint32_t abytes = a_chunk_bytes(L), bstep = b_step_bytes(L);
+    const uint32_t stage_bytes = abytes + b_chunk_bytes(L);
+    uint64_t* bars = (uint64_t*)(base + TC_STAGES * stage_bytes);   // full[S], empty[S], acc_full, acc_empty
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * TC_STAGES + 2);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    int* tau = (int*)(tmem_slot + 2);                                // [dn]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = smem_u32(base);
     auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
-    auto mma_bar = [&](int s) { return smem_u32(&bars[TC_STAGES + s]); };
+    auto empty_bar = [&](int s) { return smem_u32(&bars[TC_STAGES + s]); };
+    const uint32_t acc_full = smem_u32(&bars[2 * TC_STAGES]), acc_empty = smem_u32(&bars[2 * TC_STAGES + 1]);
 
     if (tid == 0) {
-        for (int s = 0; s < 2 * TC_STAGES; s++) mbar_init(smem_u32(&bars[s]), 1);
+        for (int s = 0; s < TC_STAGES; s++) {
+            mbar_init(full_bar(s), 2);     // lane 0's expect_tx arrival + its arrival once the gathers landed
+            mbar_init(empty_bar(s), 1);    // the MMA warp's commit
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 4);           // one arrival per epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *abort_flag = 0;
     }
@@ -515,147 +554,202 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(TcArgs a) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const int nlev = 2 * L - 1;
-    const int sc_chunks = super_chunks(L);
-    const uint32_t idesc = idesc_bf16(TC_M, dn * L);
-    const int kgroups = TC_CH_K / 8;                                 // 16-byte column groups per chunk
+    const int sc = super_chunks(L);
 
-    uint32_t q = 0;                // chunks of this CTA so far (pipeline sequence)
-    uint32_t fills = 0, full_waits = 0;   // thread 0: A copies issued / consumed
-    bool ok = true;
-
-    // fill stage of chunk sequence number qq with global chunk c
-    auto fill = [&](uint32_t qq, int64_t c) {
-        const int s = (int)(qq % TC_STAGES);
-        if (qq >= TC_STAGES && !mbar_wait(mma_bar(s), ((qq - TC_STAGES) / TC_STAGES) & 1)) ok = false;
-        const uint32_t sa = sbase + s * stage_bytes, sb = sa + abytes;
-        if (tid == 0) {
-            mbar_expect_tx(full_bar(s), abytes);
-            bulk_g2s(sa, (const unsigned char*)a.A + (size_t)c * abytes, abytes, full_bar(s));
-            fills++;
-        }
-        const int32_t t0 = a.chunk_tri[2 * c], t1 = a.chunk_tri[2 * c + 1];
-        const int pieces = L * dn * kgroups;
-        for (int pc = tid; pc < pieces; pc += TC_THREADS) {
-            const int np = pc / kgroups, kg = pc % kgroups;
-            const int32_t tri = kg < 3 ? t0 : t1;
-            const uint16_t* src = a.B + ((size_t)np * a.nT + tri) * TC_KPT + 8 * (kg % 3);
-            const int ks = kg >> 1, h = kg & 1;
-            cp16(sb + ks * bstep + (np >> 3) * 256 + h * 128 + (np & 7) * 16, src);
-        }
-        cp_commit();
-    };
-
-    for (;;) {
-        if (tid == 0) *tile_slot = atomicAdd(a.counter, 1);
-        __syncthreads();
-        const int b = *tile_slot;
-        const bool stop = b >= a.n_tiles || *abort_flag;
-        __syncthreads();
-        if (stop) break;
-        const int64_t c0 = a.chunk_ptr[b];
-        const int64_t nch = a.chunk_ptr[b + 1] - c0;
-        if (nch == 0) continue;
-        const int64_t n_near = a.chunk_near[b];
-        const int32_t t = a.perm[(int64_t)b * TC_M + tid];
-        fill(q, c0);
-        if (nch > 1) fill(q + 1, c0 + 1);
-        bool aborted = false;
-        for (int64_t c = 0; c < nch; c++) {
-            const uint32_t qc = q + (uint32_t)c;
-            const int s = (int)(qc % TC_STAGES);
-            if (c + 2 < nch) fill(qc + 2, c0 + c + 2);
-            const int64_t ahead = min((int64_t)2, nch - 1 - c);
-            if (ahead == 2) cp_wait<2>();
-            else if (ahead == 1) cp_wait<1>();
-            else cp_wait<0>();
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        const int kgroups = TC_CH_K / 8;   // 16-byte column groups per chunk
+        uint32_t k = 0;                    // chunks issued
+        bool ok = true;
+        auto declare_full = [&](uint32_t j) {   // chunk j's gathers have landed (this lane): visible, then arrive
             fence_async_smem();
-            // runs: the near chunks, then the self chunks, cut every sc_chunks
-            const bool self_run = c >= n_near;
-            const int64_t pos = self_run ? c - n_near : c, run_len = self_run ? nch - n_near : n_near;
-            const bool sc_first = (pos % sc_chunks) == 0;
-            const bool sc_last = (pos % sc_chunks) == sc_chunks - 1 || pos == run_len - 1;
-            if (sc_first) {
-                for (int l = 0; l < nlev; l++)
-                    for (int g = 0; g < dn / 16; g++) tmem_st16_zero(tmem + lane_base + dn * l + 16 * g);
-                tmem_wait_st();
-            }
-            if (!ok) atomicOr(abort_flag, 1);
-            tc_fence_before();
-            __syncthreads();
-            if (*abort_flag) {
-                aborted = true;
-                break;
-            }
-            if (tid == 0) {
-                if (!mbar_wait(full_bar(s), (qc / TC_STAGES) & 1)) ok = false;
-                full_waits++;
-                tc_fence_after();
-                const uint32_t sa = sbase + s * stage_bytes, sb = sa + abytes;
-#pragma unroll
-                for (int ks = 0; ks < TC_KSTEPS; ks++) {
-                    const uint64_t bdesc = smem_desc(sb + ks * bstep, 128, 256);
-                    for (int sd = 0; sd < L; sd++) {
-                        const uint64_t adesc = smem_desc(sa + (sd * TC_KSTEPS + ks) * 4096, 128, 256);
-                        mma_bf16(tmem + dn * sd, adesc, bdesc, idesc, 1u);
+            __syncwarp();
+            if (lane == 0) mbar_arrive1(full_bar((int)(j % TC_STAGES)));
+        };
+        for (int64_t b = blockIdx.x; b < a.n_tiles && ok; b += gridDim.x) {
+            const int64_t c0 = a.chunk_ptr[b], nch = a.chunk_ptr[b + 1] - c0;
+            for (int64_t c = 0; c < nch; c++) {
+                const int s = (int)(k % TC_STAGES);
+                int stop = 0;                      // decided by lane 0, the same for the whole warp
+                if (lane == 0) {
+                    stop = *abort_flag;
+                    if (!stop && k >= TC_STAGES && !mbar_wait(empty_bar(s), ((k / TC_STAGES) - 1) & 1)) {
+                        stop = 1;
+                        *abort_flag = 1;
                     }
                 }
-                mma_commit(mma_bar(s));
+                if (__shfl_sync(0xffffffffu, stop, 0)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t sa = sbase + s * stage_bytes, sb = sa + abytes;
+                if (lane == 0) {
+                    mbar_expect_tx(full_bar(s), abytes);
+                    bulk_g2s(sa, (const unsigned char*)a.A + (size_t)(c0 + c) * abytes, abytes, full_bar(s));
+                }
+                const int32_t t0 = a.chunk_tri[2 * (c0 + c)], t1 = a.chunk_tri[2 * (c0 + c) + 1];
+                const int pieces = L * dn * kgroups;
+                for (int pc = lane; pc < pieces; pc += 32) {
+                    const int np = pc / kgroups, kg = pc % kgroups;
+                    const int32_t tri = kg < 3 ? t0 : t1;
+                    const uint16_t* src = a.B + ((size_t)np * a.nT + tri) * TC_KPT + 8 * (kg % 3);
+                    const int ks = kg >> 1, h = kg & 1;
+                    cp16(sb + ks * bstep + (np >> 3) * 256 + h * 128 + (np & 7) * 16, src);
+                }
+                cp_commit();
+                if (k >= TC_PROD_LAG) {
+                    cp_wait<TC_PROD_LAG>();
+                    declare_full(k - TC_PROD_LAG);
+                }
+                k++;
             }
-            if (sc_last) {
-                // level sums of this run of chunks -> float-float -> FP64 u
-                if (!mbar_wait(mma_bar(s), (qc / TC_STAGES) & 1)) ok = false;
-                tc_fence_after();
-                const int et = t >= 0 ? a.rexp[(self_run ? a.M : 0) + t] - 12 : 0;
-#pragma unroll 1
-                for (int g = 0; g < dn / 16; g++) {
-                    float H[16], Lo[16];
+        }
+        // the last chunks' gathers, and (after an abort) the bulk copies still in flight
+        cp_wait<0>();
+        for (uint32_t j = k > TC_PROD_LAG ? k - TC_PROD_LAG : 0; j < k; j++) declare_full(j);
+        if (!ok && lane == 0)
+            for (uint32_t j = k > TC_STAGES ? k - TC_STAGES : 0; j < k; j++)
+                mbar_wait(full_bar((int)(j % TC_STAGES)), (j / TC_STAGES) & 1);
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(TC_M, dn * L);
+            uint32_t k = 0, runs = 0;
+            bool ok = true;
+            for (int64_t b = blockIdx.x; b < a.n_tiles && ok; b += gridDim.x) {
+                const int64_t c0 = a.chunk_ptr[b], nch = a.chunk_ptr[b + 1] - c0, n_near = a.chunk_near[b];
+                for (int64_t c = 0; c < nch; c++) {
+                    const ChunkPos cp = chunk_pos(c, n_near, nch, sc);
+                    if (*abort_flag || (cp.first && !mbar_wait(acc_empty, runs & 1))) {
+                        ok = false;
+                        *abort_flag = 1;
+                        break;
+                    }
+                    const int s = (int)(k % TC_STAGES);
+                    if (!mbar_wait(full_bar(s), (k / TC_STAGES) & 1)) {
+                        ok = false;
+                        *abort_flag = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = sbase + s * stage_bytes, sb = sa + abytes;
 #pragma unroll
-                    for (int j = 0; j < 16; j++) H[j] = Lo[j] = 0.f;
-                    for (int l = 0; l < nlev; l++) {
+                    for (int ks = 0; ks < TC_KSTEPS; ks++) {
+                        const uint64_t bdesc = smem_desc(sb + ks * bstep, 128, 256);
+                        for (int sd = 0; sd < L; sd++) {
+                            const uint64_t adesc = smem_desc(sa + (sd * TC_KSTEPS + ks) * 4096, 128, 256);
+                            mma_bf16(tmem + dn * sd, adesc, bdesc, idesc, 1u);
+                        }
+                    }
+                    mma_commit(empty_bar(s));
+                    if (cp.last) {
+                        mma_commit(acc_full);
+                        runs++;
+                    }
+                    k++;
+                }
+            }
+            if (k > 0) mbar_wait(empty_bar((int)((k - 1) % TC_STAGES)), ((k - 1) / TC_STAGES) & 1);
+            if (!ok) atomicOr(a.flag, VP_DEV_ERR_TIMEOUT);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int q = warp & 3;                                      // TMEM lane quarter of this warp
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        const int row = q * 32 + lane;
+        auto zero_acc = [&]() {
+            for (int l = 0; l < nlev; l++)
+                for (int g = 0; g < dn / 16; g++) tmem_st16_zero(tmem + lane_base + dn * l + 16 * g);
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive1(acc_empty);
+        };
+        zero_acc();
+        uint32_t runs = 0;
+        bool ok = true;
+        for (int64_t b = blockIdx.x; b < a.n_tiles && ok; b += gridDim.x) {
+            const int64_t c0 = a.chunk_ptr[b], nch = a.chunk_ptr[b + 1] - c0, n_near = a.chunk_near[b];
+            const int32_t t = a.perm[b * TC_M + row];
+            // with 32 densities per pass this tile's corrections of the target
+            // are summed over its runs in registers (FP64) and written once
+            constexpr int NACC = DN == 32 ? 32 : 1;
+            double acc[NACC];
+#pragma unroll
+            for (int n = 0; n < NACC; n++) acc[n] = 0.0;
+            double* ut = a.u + (int64_t)a.d0 * a.M + (t >= 0 ? t : 0);
+            for (int64_t c = 0; c < nch; c++) {
+                const ChunkPos cp = chunk_pos(c, n_near, nch, sc);
+                if (!cp.last) continue;
+                int stop = 0;
+                if (lane == 0) stop = *abort_flag || !mbar_wait(acc_full, runs & 1);
+                if (__shfl_sync(0xffffffffu, stop, 0)) {
+                    ok = false;
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                // the level sums of this run, combined in float-float as they are read
+                float H[DN], Lo[DN];
+#pragma unroll
+                for (int j = 0; j < DN; j++) H[j] = Lo[j] = 0.f;
+                for (int l = 0; l < nlev; l++) {
+                    const float scl = __int_as_float((127 - 7 * l) << 23);   // 2^(-7 l), exact
+#pragma unroll
+                    for (int g = 0; g < DN / 16; g++) {
                         uint32_t v[16];
                         tmem_ld16(tmem + lane_base + dn * l + 16 * g, v);
                         tmem_wait_ld();
-                        const float scl = __int_as_float((127 - 7 * l) << 23);   // 2^(-7 l), exact
 #pragma unroll
                         for (int j = 0; j < 16; j++) {
                             float sm, er;
-                            two_sum_f(H[j], __fmul_rn(__int_as_float((int)v[j]), scl), sm, er);
-                            H[j] = sm;
-                            Lo[j] = __fadd_rn(Lo[j], er);
-                        }
-                    }
-                    if (t >= 0) {
-#pragma unroll
-                        for (int j = 0; j < 16; j++) {
-                            const int n = 16 * g + j;
-                            if (a.d0 + n < a.d) {
-                                double* up = a.u + (int64_t)(a.d0 + n) * a.M + t;
-                                *up += ldexp((double)H[j] + (double)Lo[j], et + tau[n]);
-                            }
+                            two_sum_f(H[16 * g + j], __fmul_rn(__int_as_float((int)v[j]), scl), sm, er);
+                            H[16 * g + j] = sm;
+                            Lo[16 * g + j] = __fadd_rn(Lo[16 * g + j], er);
                         }
                     }
                 }
+                // free the accumulator at once: the MMAs of the next run overlap the rest
+                zero_acc();
+                runs++;
+                const int et = t >= 0 ? a.rexp[(cp.self_run ? a.M : 0) + t] - 12 : 0;
+                if (DN == 32) {
+#pragma unroll
+                    for (int j = 0; j < NACC; j++) acc[j] += ldexp((double)H[j] + (double)Lo[j], et + tau[j]);
+                } else if (t >= 0) {
+                    // read-modify-write in groups of 8 densities: the loads first, then the stores
+#pragma unroll
+                    for (int j0 = 0; j0 < DN; j0 += 8) {
+                        double old[8];
+#pragma unroll
+                        for (int j = 0; j < 8; j++)
+                            if (a.d0 + j0 + j < a.d) old[j] = ut[(int64_t)(j0 + j) * a.M];
+#pragma unroll
+                        for (int j = 0; j < 8; j++)
+                            if (a.d0 + j0 + j < a.d)
+                                ut[(int64_t)(j0 + j) * a.M] =
+                                    old[j] + ldexp((double)H[j0 + j] + (double)Lo[j0 + j], et + tau[j0 + j]);
+                    }
+                }
+            }
+            if (DN != 32 || !ok || t < 0) continue;
+            // one read-modify-write per (target, density) and tile, in groups of 8 (loads, then stores)
+#pragma unroll
+            for (int j0 = 0; j0 < NACC; j0 += 8) {
+                double old[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (a.d0 + j0 + j < a.d) old[j] = ut[(int64_t)(j0 + j) * a.M];
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (a.d0 + j0 + j < a.d) ut[(int64_t)(j0 + j) * a.M] = old[j] + acc[j0 + j];
             }
         }
-        if (aborted) break;
-        q += (uint32_t)nch;
+        if (!ok && lane == 0) atomicOr(a.flag, VP_DEV_ERR_TIMEOUT);
     }
-    // drain: outstanding copies and MMAs of an aborted tile, then free TMEM
-    cp_wait<0>();
-    if (tid == 0) {
-        while (full_waits < fills) {
-            const uint32_t qq = full_waits;
-            mbar_wait(full_bar((int)(qq % TC_STAGES)), (qq / TC_STAGES) & 1);
-            full_waits++;
-        }
-        if (fills > 0) {
-            const uint32_t last = fills - 1;
-            mbar_wait(mma_bar((int)(last % TC_STAGES)), (last / TC_STAGES) & 1);
-        }
-        if (!ok || *abort_flag) atomicOr(a.flag, VP_DEV_ERR_TIMEOUT);
-    }
+    // all roles done (the MMA warp waited for its last commit): free TMEM
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -664,7 +758,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(TcArgs a) {
 }
 
 size_t tc_smem_bytes(int L) {
-    return (size_t)TC_STAGES * (a_chunk_bytes(L) + b_chunk_bytes(L)) + 1024 + 2 * TC_STAGES * 8 + 16 + 4 * TC_DN;
+    return (size_t)TC_STAGES * (a_chunk_bytes(L) + b_chunk_bytes(L)) + 1024 + (2 * TC_STAGES + 2) * 8 + 8 + 4 * TC_DN;
 }
 
 }  // namespace
@@ -806,9 +900,9 @@ int tc_apply(vp_ctx* ctx, const vp_nf* nf, const double* f, int d, double* u, vo
     uint16_t* B = (uint16_t*)ws;
     unsigned char* tail = (unsigned char*)ws + ((bbytes + 255) & ~(size_t)255);
     unsigned long long* fmaxb = (unsigned long long*)tail;                  // [dn]
-    int* counter = (int*)(tail + TC_DN * sizeof(unsigned long long));       // tile counter
     const size_t smem = tc_smem_bytes(L);
-    VP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_apply<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_apply<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<int64_t>(p->n_tiles, ctx->sm_count);
     for (int d0 = 0; d0 < d; d0 += dn) {
         VP_CUDA_TRY(ctx, cudaMemsetAsync(tail, 0, TC_DN * sizeof(unsigned long long) + sizeof(int), s));
@@ -833,10 +927,10 @@ int tc_apply(vp_ctx* ctx, const vp_nf* nf, const double* f, int d, double* u, vo
         a.dn = dn;
         a.d = d;
         a.d0 = d0;
-        a.counter = counter;
         a.flag = ctx->d_flag;
         a.u = u;
-        k_tc_apply<<<grid, TC_THREADS, smem, s>>>(a);
+        if (dn == 32) k_tc_apply<32><<<grid, TC_THREADS, smem, s>>>(a);
+        else k_tc_apply<64><<<grid, TC_THREADS, smem, s>>>(a);
         VP_LAUNCH_CHECK(ctx);
     }
     return VP_OK;
