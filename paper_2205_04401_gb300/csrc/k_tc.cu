@@ -25,10 +25,13 @@
 // are read back and combined in float-float,
 //   sum_l 2^(-7 l) Acc_l,
 // and scaled by 2^(e_t + tau_n - 12) into FP64 u.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "vp_internal.h"
 #include "vp_async.cuh"
@@ -41,15 +44,27 @@ constexpr int TC_KPT = 24;         // K columns per triangle
 constexpr int TC_CH_TRI = 2;       // triangles per K chunk
 constexpr int TC_CH_K = TC_KPT * TC_CH_TRI;   // 48
 constexpr int TC_KSTEPS = TC_CH_K / 16;        // 3 MMAs of K = 16 per digit per chunk
-constexpr int TC_STAGES = 3;
+#ifndef VP_TC_KPS
+#define VP_TC_KPS 3
+#endif
+constexpr int TC_KPS = VP_TC_KPS;                 // k-steps per pipeline stage (1 or 3: a whole chunk)
+static_assert(TC_KPS == 1 || TC_KPS == TC_KSTEPS, "a stage is one k-step or a whole chunk");
+constexpr int TC_STAGES = TC_KPS == 1 ? 8 : 3;    // stages that fit 227 KB of shared memory
 constexpr int TC_THREADS = 192;   // producer warp, MMA warp, four epilogue warps
 constexpr int TC_TMEM_COLS = 512;
 constexpr int TC_PAIR_CAP = 16384;  // near pairs per tile the plan can hold
 
-__host__ __device__ constexpr uint32_t a_chunk_bytes(int L) { return (uint32_t)L * TC_KSTEPS * 4096u; }
+// one row group (8 targets) of a chunk: [k-step][digit][2 column halves][8 rows x 16 B]
+__host__ __device__ constexpr uint32_t a_group_bytes(int L) { return (uint32_t)L * TC_KSTEPS * 256u; }
+// one k-step of a row group: [digit][2 column halves][8 rows x 16 B]
+__host__ __device__ constexpr uint32_t a_gstep_bytes(int L) { return (uint32_t)L * 256u; }
 __host__ __device__ constexpr int dens_per_pass(int L) { return L <= 4 ? 64 : 32; }   // dn (2L - 1) <= 512 columns
 __host__ __device__ constexpr uint32_t b_step_bytes(int L) { return (uint32_t)L * dens_per_pass(L) * 16u * 2u; }
-__host__ __device__ constexpr uint32_t b_chunk_bytes(int L) { return TC_KSTEPS * b_step_bytes(L); }
+// a pipeline stage: one k-step of a chunk, the 16 row groups of weight digits
+// and the density digits of its 16 columns
+__host__ __device__ constexpr uint32_t stage_bytes_of(int L) {
+    return TC_KPS * (16u * a_gstep_bytes(L) + b_step_bytes(L));
+}
 // chunks per exact FP32 accumulation: K L 2^12 < 2^24
 __host__ __device__ constexpr int super_chunks(int L) { return (1 << 24) / (L * 4096 * TC_CH_K); }
 
@@ -334,10 +349,30 @@ __global__ void k_row_exp(const int64_t* __restrict__ row, const uint8_t* __rest
 
 // warp per target: digits of its weights scattered into the dense A images
 // (per chunk: [digit s][k-step][16 row groups x 2 column halves][8 rows x 16 B])
+// warp per target: the row group of the target in its tile, marked in every
+// chunk that holds one of its pairs
+__global__ void k_group_mask(const int64_t* __restrict__ row, const int32_t* __restrict__ pslot,
+                             const int32_t* __restrict__ pos, const int64_t* __restrict__ chunk_ptr, int64_t M,
+                             uint32_t* __restrict__ gmask) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= M) return;
+    const int ps = pos[t];
+    const int b = ps / TC_M, i = ps % TC_M;
+    const int64_t cb = chunk_ptr[b];
+    for (int64_t p = row[t] + lane; p < row[t + 1]; p += 32) atomicOr(&gmask[cb + pslot[p] / TC_CH_TRI], 1u << (i >> 3));
+}
+
+__global__ void k_popc(const uint32_t* __restrict__ m, int64_t n, int32_t* __restrict__ cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cnt[i] = __popc(m[i]);
+}
+
 template <int NQ>
 __global__ void k_scatter_a(const int64_t* __restrict__ row, const uint8_t* __restrict__ pkind,
                             const double* __restrict__ C, const int32_t* __restrict__ pslot,
                             const int32_t* __restrict__ pos, const int64_t* __restrict__ chunk_ptr,
+                            const uint32_t* __restrict__ gmask, const int64_t* __restrict__ gptr,
                             const int32_t* __restrict__ rexp, int64_t M, int L, uint16_t* __restrict__ A) {
     const int lane = threadIdx.x & 31;
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -347,7 +382,8 @@ __global__ void k_scatter_a(const int64_t* __restrict__ row, const uint8_t* __re
     const int64_t cb = chunk_ptr[b];
     if (chunk_ptr[b + 1] == cb) return;             // no pairs
     const int sh_near = 7 * L - 1 - rexp[t], sh_self = 7 * L - 1 - rexp[M + t];
-    const size_t abytes = a_chunk_bytes(L);
+    const size_t gbytes = a_group_bytes(L);
+    const int g = i >> 3;
     const int64_t e0 = row[t] * NQ, e1 = row[t + 1] * NQ;
     for (int64_t e = e0 + lane; e < e1; e += 32) {
         const int64_t p = e / NQ;
@@ -359,11 +395,11 @@ __global__ void k_scatter_a(const int64_t* __restrict__ row, const uint8_t* __re
         const long long X = __double2ll_rn(ldexp(C[e], pkind[p] ? sh_self : sh_near));
         int a[TC_LMAX];
         digits128(X, L, a);
-        const size_t base = (size_t)chunk * abytes + (size_t)(i >> 3) * 256 + (size_t)(kc >> 3) * 128 +
-                            (size_t)(i & 7) * 16 + (size_t)(kc & 7) * 2;
+        const int64_t blk = gptr[chunk] + __popc(gmask[chunk] & ((1u << g) - 1u));   // stored row group
+        const size_t base = (size_t)blk * gbytes + (size_t)(kc >> 3) * 128 + (size_t)(i & 7) * 16 + (size_t)(kc & 7) * 2;
 #pragma unroll
         for (int s = 0; s < TC_LMAX; s++)
-            if (s < L) A[(base + (size_t)(s * TC_KSTEPS + ks) * 4096) / 2] = bf16_bits(a[s]);
+            if (s < L) A[(base + (size_t)(ks * L + s) * 256) / 2] = bf16_bits(a[s]);
     }
 }
 
@@ -410,13 +446,17 @@ __global__ void k_fdigits(const double* __restrict__ f, int64_t N, int64_t nT, i
 }
 
 // ------------------------------------------------------------ tcgen05 glue
-__device__ __forceinline__ void cp16(uint32_t dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+// zeros for the row groups a stage must clear (copied like data, so that no
+// generic-proxy store has to be fenced before the tensor cores read the stage)
+__device__ __align__(128) unsigned char g_tc_zero[4096];
+
+// tiled TMA load of a 3-D box at (x, y, z) into shared memory, completing on an mbarrier
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -470,7 +510,9 @@ struct TcArgs {
     const int32_t* chunk_near;  // [n_tiles] near chunks of each tile (self chunks follow)
     const int32_t* chunk_tri;   // [n_chunks][2]
     const int32_t* rexp;        // [2][M] near and self row exponents
-    const uint16_t* A;          // [n_chunks] digit images
+    const uint16_t* A;          // [stored row groups] digit images
+    const uint32_t* gmask;      // [n_chunks] stored row groups of each chunk
+    const int64_t* gptr;        // [n_chunks] first stored row group of each chunk
     const uint16_t* B;          // [L dn][nT][24] density digits
     const unsigned long long* fmaxb;   // [dn]
     int64_t nT, M, n_tiles;
@@ -500,11 +542,11 @@ __device__ __forceinline__ ChunkPos chunk_pos(int64_t c, int64_t n_near, int64_t
 // Persistent and warp-specialised: one CTA per SM walks the tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ... (Morton order, so neighbouring
 // tiles have similar chunk counts).
-//   warp 0 (producer): per chunk, waits for the stage to be free, one lane
-//     bulk-copies the weight-digit image (complete_tx on the stage's full
-//     barrier), all lanes gather the density digits with 16-byte cp.async;
-//     one chunk later (its copies done, made visible to the tensor cores'
-//     proxy) lane 0 arrives on the full barrier;
+//   warp 0 (producer): per chunk, waits for the stage to be free, zeroes the
+//     row groups the stage still holds from an earlier chunk, and issues the
+//     copies: the chunk's stored row groups of weight digits (bulk copies)
+//     and its two triangles' density digits (six TMA tensor boxes), all
+//     completing on the stage's full barrier;
 //   warp 1 (MMA): per chunk, waits for the stage, issues the L x 3 MMAs and
 //     commits them to the stage's empty barrier; at the end of a run it
 //     commits to acc_full and, before the next run, waits for acc_empty;
@@ -514,15 +556,16 @@ __device__ __forceinline__ ChunkPos chunk_pos(int64_t c, int64_t n_near, int64_t
 //     acc_empty.
 // No CTA-wide barrier inside the loop; every wait is bounded and an abort
 // (a wait that gave up) is shared through shared memory, drained, reported.
-constexpr int TC_PROD_LAG = 1;   // chunks between issuing a stage's gathers and declaring it full
 template <int DN>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(TcArgs a, const __grid_constant__ CUtensorMap tmB) {
     extern __shared__ unsigned char tc_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
     const int L = a.L;
     constexpr int dn = DN;   // densities per pass (dens_per_pass(L))
-    const uint32_t abytes = a_chunk_bytes(L), bstep = b_step_bytes(L);
-    const uint32_t stage_bytes = abytes + b_chunk_bytes(L);
+    // stage: [16 row groups][TC_KPS k-steps][L digits][2 halves][8 rows x 16 B], then
+    // [TC_KPS k-steps][2 halves][L dn density rows x 16 B]
+    const uint32_t gstep = a_gstep_bytes(L), gst = TC_KPS * gstep, abytes = 16u * gst, bstep = b_step_bytes(L);
+    const uint32_t stage_bytes = stage_bytes_of(L);
     uint64_t* bars = (uint64_t*)(base + TC_STAGES * stage_bytes);   // full[S], empty[S], acc_full, acc_empty
     uint32_t* tmem_slot = (uint32_t*)(bars + 2 * TC_STAGES + 2);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
@@ -535,7 +578,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(TcArgs a) {
 
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; s++) {
-            mbar_init(full_bar(s), 2);     // lane 0's expect_tx arrival + its arrival once the gathers landed
+            mbar_init(full_bar(s), 1);     // lane 0's expect_tx arrival; the copies complete the transactions
             mbar_init(empty_bar(s), 1);    // the MMA warp's commit
         }
         mbar_init(acc_full, 1);
@@ -559,55 +602,83 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(TcArgs a) {
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
-        const int kgroups = TC_CH_K / 8;   // 16-byte column groups per chunk
-        uint32_t k = 0;                    // chunks issued
+        // Per k-step of a chunk (one stage): the k-step of its stored row
+        // groups of weight digits (bulk copies, lanes 0-15) and the density
+        // digits of its two column halves (TMA boxes of L dn rows x 16 B, lanes
+        // 16-17), all completing on the stage's full barrier; row groups the
+        // stage still holds from an earlier chunk are zeroed first.  Chunk
+        // metadata is loaded 32 chunks at a time.
+        const uint32_t gbytes = a_group_bytes(L);
+        const uint32_t kbox = (uint32_t)(L * dn) * 16u;   // one density-digit box
+        uint32_t held[TC_STAGES];          // row groups each stage holds nonzero digits of (unknown at first)
+#pragma unroll
+        for (int s = 0; s < TC_STAGES; s++) held[s] = 0xFFFFu;
+        uint32_t k = 0;                    // stages issued
         bool ok = true;
-        auto declare_full = [&](uint32_t j) {   // chunk j's gathers have landed (this lane): visible, then arrive
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive1(full_bar((int)(j % TC_STAGES)));
-        };
         for (int64_t b = blockIdx.x; b < a.n_tiles && ok; b += gridDim.x) {
             const int64_t c0 = a.chunk_ptr[b], nch = a.chunk_ptr[b + 1] - c0;
+            int32_t mt0 = 0, mt1 = 0;
+            uint32_t mm = 0;
+            int64_t mg = 0;
             for (int64_t c = 0; c < nch; c++) {
-                const int s = (int)(k % TC_STAGES);
-                int stop = 0;                      // decided by lane 0, the same for the whole warp
-                if (lane == 0) {
-                    stop = *abort_flag;
-                    if (!stop && k >= TC_STAGES && !mbar_wait(empty_bar(s), ((k / TC_STAGES) - 1) & 1)) {
-                        stop = 1;
-                        *abort_flag = 1;
+                if ((c & 31) == 0) {       // metadata of the next 32 chunks, one per lane
+                    const int64_t cc = c0 + c + lane;
+                    if (c + lane < nch) {
+                        mt0 = a.chunk_tri[2 * cc];
+                        mt1 = a.chunk_tri[2 * cc + 1];
+                        mm = a.gmask[cc];
+                        mg = a.gptr[cc];
                     }
                 }
-                if (__shfl_sync(0xffffffffu, stop, 0)) {
-                    ok = false;
-                    break;
+                const int src = (int)(c & 31);
+                const int32_t t0 = __shfl_sync(0xffffffffu, mt0, src), t1 = __shfl_sync(0xffffffffu, mt1, src);
+                const uint32_t m = __shfl_sync(0xffffffffu, mm, src);
+                const int64_t gp = __shfl_sync(0xffffffffu, mg, src);
+                for (int ks = 0; ks < TC_KSTEPS && ok; ks += TC_KPS) {
+                    const int s = (int)(k % TC_STAGES);
+                    int stop = 0;                  // decided by lane 0, the same for the whole warp
+                    if (lane == 0) {
+                        stop = *abort_flag;
+                        if (!stop && k >= TC_STAGES && !mbar_wait(empty_bar(s), ((k / TC_STAGES) - 1) & 1)) {
+                            stop = 1;
+                            *abort_flag = 1;
+                        }
+                    }
+                    if (__shfl_sync(0xffffffffu, stop, 0)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sa = sbase + s * stage_bytes, sb = sa + abytes;
+                    uint32_t z = 0;
+#pragma unroll
+                    for (int q = 0; q < TC_STAGES; q++)
+                        if (q == s) {
+                            z = held[q] & ~m;
+                            held[q] = m;
+                        }
+                    if (lane == 0) mbar_expect_tx(full_bar(s), (uint32_t)__popc(m | z) * gst + 2u * TC_KPS * kbox);
+                    __syncwarp();
+                    if (lane < 16) {
+                        if ((m >> lane) & 1u)
+                            bulk_g2s(sa + lane * gst,
+                                     (const unsigned char*)a.A +
+                                         (size_t)(gp + __popc(m & ((1u << lane) - 1u))) * gbytes + ks * gstep,
+                                     gst, full_bar(s));
+                        else if ((z >> lane) & 1u)
+                            bulk_g2s(sa + lane * gst, g_tc_zero, gst, full_bar(s));
+                    } else if (lane < 16 + 2 * TC_KPS) {
+                        // column half h of k-step ks + j: column group kg = 2 (ks + j) + h,
+                        // triangle kg / 3, columns 8 (kg % 3) .. + 7
+                        const int j = (lane - 16) >> 1, h = (lane - 16) & 1, kg = 2 * (ks + j) + h;
+                        tma_load3(sb + j * bstep + h * (bstep / 2), &tmB, 8 * (kg % 3), kg < 3 ? t0 : t1, 0,
+                                  full_bar(s));
+                    }
+                    k++;
                 }
-                const uint32_t sa = sbase + s * stage_bytes, sb = sa + abytes;
-                if (lane == 0) {
-                    mbar_expect_tx(full_bar(s), abytes);
-                    bulk_g2s(sa, (const unsigned char*)a.A + (size_t)(c0 + c) * abytes, abytes, full_bar(s));
-                }
-                const int32_t t0 = a.chunk_tri[2 * (c0 + c)], t1 = a.chunk_tri[2 * (c0 + c) + 1];
-                const int pieces = L * dn * kgroups;
-                for (int pc = lane; pc < pieces; pc += 32) {
-                    const int np = pc / kgroups, kg = pc % kgroups;
-                    const int32_t tri = kg < 3 ? t0 : t1;
-                    const uint16_t* src = a.B + ((size_t)np * a.nT + tri) * TC_KPT + 8 * (kg % 3);
-                    const int ks = kg >> 1, h = kg & 1;
-                    cp16(sb + ks * bstep + (np >> 3) * 256 + h * 128 + (np & 7) * 16, src);
-                }
-                cp_commit();
-                if (k >= TC_PROD_LAG) {
-                    cp_wait<TC_PROD_LAG>();
-                    declare_full(k - TC_PROD_LAG);
-                }
-                k++;
+                if (!ok) break;
             }
         }
-        // the last chunks' gathers, and (after an abort) the bulk copies still in flight
-        cp_wait<0>();
-        for (uint32_t j = k > TC_PROD_LAG ? k - TC_PROD_LAG : 0; j < k; j++) declare_full(j);
+        // after an abort: the copies still in flight into the stages
         if (!ok && lane == 0)
             for (uint32_t j = k > TC_STAGES ? k - TC_STAGES : 0; j < k; j++)
                 mbar_wait(full_bar((int)(j % TC_STAGES)), (j / TC_STAGES) & 1);
@@ -626,28 +697,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(TcArgs a) {
                         *abort_flag = 1;
                         break;
                     }
-                    const int s = (int)(k % TC_STAGES);
-                    if (!mbar_wait(full_bar(s), (k / TC_STAGES) & 1)) {
-                        ok = false;
-                        *abort_flag = 1;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t sa = sbase + s * stage_bytes, sb = sa + abytes;
-#pragma unroll
-                    for (int ks = 0; ks < TC_KSTEPS; ks++) {
-                        const uint64_t bdesc = smem_desc(sb + ks * bstep, 128, 256);
-                        for (int sd = 0; sd < L; sd++) {
-                            const uint64_t adesc = smem_desc(sa + (sd * TC_KSTEPS + ks) * 4096, 128, 256);
-                            mma_bf16(tmem + dn * sd, adesc, bdesc, idesc, 1u);
+                    for (int ks = 0; ks < TC_KSTEPS; ks += TC_KPS) {
+                        const int s = (int)(k % TC_STAGES);
+                        if (!mbar_wait(full_bar(s), (k / TC_STAGES) & 1)) {
+                            ok = false;
+                            *abort_flag = 1;
+                            break;
                         }
+                        tc_fence_after();
+                        const uint32_t sa = sbase + s * stage_bytes, sb = sa + abytes;
+#pragma unroll
+                        for (int j = 0; j < TC_KPS; j++) {
+                            // density rows 16 B apart (8-row groups 128 B apart), the column halves bstep / 2 apart
+                            const uint64_t bdesc = smem_desc(sb + j * bstep, bstep / 2, 128);
+                            for (int sd = 0; sd < L; sd++) {
+                                // row groups gst apart, the two column halves 128 B apart
+                                const uint64_t adesc = smem_desc(sa + j * gstep + sd * 256, 128, gst);
+                                mma_bf16(tmem + dn * sd, adesc, bdesc, idesc, 1u);
+                            }
+                        }
+                        mma_commit(empty_bar(s));
+                        k++;
                     }
-                    mma_commit(empty_bar(s));
+                    if (!ok) break;
                     if (cp.last) {
                         mma_commit(acc_full);
                         runs++;
                     }
-                    k++;
                 }
             }
             if (k > 0) mbar_wait(empty_bar((int)((k - 1) % TC_STAGES)), ((k - 1) / TC_STAGES) & 1);
@@ -734,17 +810,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(TcArgs a) {
                     }
                 }
             }
-            if (DN != 32 || !ok || t < 0) continue;
-            // one read-modify-write per (target, density) and tile, in groups of 8 (loads, then stores)
+            if constexpr (DN == 32) {
+                if (!ok || t < 0) continue;
+                // one read-modify-write per (target, density) and tile, in groups of 8 (loads, then stores)
 #pragma unroll
-            for (int j0 = 0; j0 < NACC; j0 += 8) {
-                double old[8];
+                for (int j0 = 0; j0 < NACC; j0 += 8) {
+                    double old[8];
 #pragma unroll
-                for (int j = 0; j < 8; j++)
-                    if (a.d0 + j0 + j < a.d) old[j] = ut[(int64_t)(j0 + j) * a.M];
+                    for (int j = 0; j < 8; j++)
+                        if (a.d0 + j0 + j < a.d) old[j] = ut[(int64_t)(j0 + j) * a.M];
 #pragma unroll
-                for (int j = 0; j < 8; j++)
-                    if (a.d0 + j0 + j < a.d) ut[(int64_t)(j0 + j) * a.M] = old[j] + acc[j0 + j];
+                    for (int j = 0; j < 8; j++)
+                        if (a.d0 + j0 + j < a.d) ut[(int64_t)(j0 + j) * a.M] = old[j] + acc[j0 + j];
+                }
             }
         }
         if (!ok && lane == 0) atomicOr(a.flag, VP_DEV_ERR_TIMEOUT);
@@ -758,7 +836,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(TcArgs a) {
 }
 
 size_t tc_smem_bytes(int L) {
-    return (size_t)TC_STAGES * (a_chunk_bytes(L) + b_chunk_bytes(L)) + 1024 + (2 * TC_STAGES + 2) * 8 + 8 + 4 * TC_DN;
+    return (size_t)TC_STAGES * stage_bytes_of(L) + 1024 + (2 * TC_STAGES + 2) * 8 + 8 + 4 * TC_DN;
 }
 
 }  // namespace
@@ -773,6 +851,8 @@ void tc_plan_free(TcPlan* p) {
     cudaFree(p->d_chunk_near);
     cudaFree(p->d_rexp);
     cudaFree(p->d_A);
+    cudaFree(p->d_gmask);
+    cudaFree(p->d_gptr);
     delete p;
 }
 
@@ -793,11 +873,13 @@ int tc_plan_build(vp_ctx* ctx, vp_nf* nf, int L, cudaStream_t s) {
     int32_t* ucount = nullptr;
     int32_t* dflag = nullptr;
     int32_t* pslot = nullptr;
+    int32_t* gcount = nullptr;
     auto fail = [&](int code, const char* msg) {
         cudaFree(keys);
         cudaFree(ucount);
         cudaFree(dflag);
         cudaFree(pslot);
+        cudaFree(gcount);
         tc_plan_free(p);
         return vp_set_error(ctx, code, msg);
     };
@@ -854,20 +936,33 @@ int tc_plan_build(vp_ctx* ctx, vp_nf* nf, int L, cudaStream_t s) {
                                                             p->d_chunk_near, p->d_chunk_ptr, p->d_chunk_tri, pslot,
                                                             dflag);
     TC_TRY(cudaGetLastError());
-    // weight digits
-    p->a_bytes = (size_t)p->n_chunks * a_chunk_bytes(L);
+    // which row groups (8 targets) of each chunk hold weights: only those are stored
+    const unsigned wg = (unsigned)((M * 32 + 255) / 256);
+    const int64_t nc1 = std::max<int64_t>(p->n_chunks, 1);
+    TC_TRY(cudaMalloc(&p->d_gmask, nc1 * sizeof(uint32_t)));
+    TC_TRY(cudaMalloc(&p->d_gptr, (nc1 + 1) * sizeof(int64_t)));
+    TC_TRY(cudaMalloc(&gcount, nc1 * sizeof(int32_t)));
+    TC_TRY(cudaMemsetAsync(p->d_gmask, 0, nc1 * sizeof(uint32_t), s));
+    if (M > 0) k_group_mask<<<wg, 256, 0, s>>>(nf->d_row, pslot, p->d_pos, p->d_chunk_ptr, M, p->d_gmask);
+    if (p->n_chunks > 0) k_popc<<<(unsigned)((p->n_chunks + 255) / 256), 256, 0, s>>>(p->d_gmask, p->n_chunks, gcount);
+    TC_TRY(cudaGetLastError());
+    rc = vp_exclusive_scan_i32(ctx, gcount, p->d_gptr, p->n_chunks, s);
+    if (rc) return fail(rc, "vp_nf_prepare_tc: scan");
+    TC_TRY(cudaMemcpyAsync(&p->n_groups, p->d_gptr + p->n_chunks, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TC_TRY(cudaStreamSynchronize(s));
+    // weight digits of the stored row groups
+    p->a_bytes = (size_t)p->n_groups * a_group_bytes(L);
     TC_TRY(cudaMalloc(&p->d_A, std::max<size_t>(p->a_bytes, 16)));
     TC_TRY(cudaMemsetAsync(p->d_A, 0, p->a_bytes, s));
-    const unsigned wg = (unsigned)((M * 32 + 255) / 256);
     if (M > 0) {
         if (nq == 19) {
             k_row_exp<19><<<wg, 256, 0, s>>>(nf->d_row, nf->d_pkind, nf->d_C, M, p->d_rexp);
             k_scatter_a<19><<<wg, 256, 0, s>>>(nf->d_row, nf->d_pkind, nf->d_C, pslot, p->d_pos, p->d_chunk_ptr,
-                                               p->d_rexp, M, L, p->d_A);
+                                               p->d_gmask, p->d_gptr, p->d_rexp, M, L, p->d_A);
         } else {
             k_row_exp<16><<<wg, 256, 0, s>>>(nf->d_row, nf->d_pkind, nf->d_C, M, p->d_rexp);
             k_scatter_a<16><<<wg, 256, 0, s>>>(nf->d_row, nf->d_pkind, nf->d_C, pslot, p->d_pos, p->d_chunk_ptr,
-                                               p->d_rexp, M, L, p->d_A);
+                                               p->d_gmask, p->d_gptr, p->d_rexp, M, L, p->d_A);
         }
     }
     TC_TRY(cudaGetLastError());
@@ -876,8 +971,9 @@ int tc_plan_build(vp_ctx* ctx, vp_nf* nf, int L, cudaStream_t s) {
     cudaFree(ucount);
     cudaFree(dflag);
     cudaFree(pslot);
+    cudaFree(gcount);
 #undef TC_TRY
-    p->bytes = p->a_bytes + n_slots * 4 + M * 4 + (p->n_tiles + 1) * 12 + p->n_chunks * 8 + M * 8;
+    p->bytes = p->a_bytes + n_slots * 4 + M * 4 + (p->n_tiles + 1) * 12 + p->n_chunks * 20 + M * 8;
     tc_plan_free(nf->tc);
     nf->tc = p;
     return VP_OK;
@@ -888,6 +984,21 @@ size_t tc_ws_bytes(const vp_nf* nf) {
     const int L = nf->tc->levels;
     const size_t bbytes = (size_t)L * dens_per_pass(L) * nf->mesh->nt * TC_KPT * sizeof(uint16_t);
     return ((bbytes + 255) & ~(size_t)255) + TC_DN * sizeof(unsigned long long) + 256;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
 }
 
 int tc_apply(vp_ctx* ctx, const vp_nf* nf, const double* f, int d, double* u, void* ws, cudaStream_t s) {
@@ -901,6 +1012,19 @@ int tc_apply(vp_ctx* ctx, const vp_nf* nf, const double* f, int d, double* u, vo
     unsigned char* tail = (unsigned char*)ws + ((bbytes + 255) & ~(size_t)255);
     unsigned long long* fmaxb = (unsigned long long*)tail;                  // [dn]
     const size_t smem = tc_smem_bytes(L);
+    // the density digits B[(r dn + n)][T][24] as a 3-D tensor (k, T, r dn + n) of
+    // bf16; a box is 8 columns of one triangle for all L dn rows (16 B each)
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return vp_set_error(ctx, VP_ERR_CUDA, "tensor-core apply: cuTensorMapEncodeTiled unavailable");
+    CUtensorMap tmB;
+    const cuuint64_t gdim[3] = {(cuuint64_t)TC_KPT, (cuuint64_t)nT, (cuuint64_t)(L * dn)};
+    const cuuint64_t gstride[2] = {(cuuint64_t)TC_KPT * 2, (cuuint64_t)nT * TC_KPT * 2};
+    const cuuint32_t box[3] = {8, 1, (cuuint32_t)(L * dn)};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (encode(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)B, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return vp_set_error(ctx, VP_ERR_CUDA, "tensor-core apply: cuTensorMapEncodeTiled failed");
     VP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_apply<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     VP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_apply<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<int64_t>(p->n_tiles, ctx->sm_count);
@@ -918,6 +1042,8 @@ int tc_apply(vp_ctx* ctx, const vp_nf* nf, const double* f, int d, double* u, vo
         a.chunk_tri = p->d_chunk_tri;
         a.rexp = p->d_rexp;
         a.A = p->d_A;
+        a.gmask = p->d_gmask;
+        a.gptr = p->d_gptr;
         a.B = B;
         a.fmaxb = fmaxb;
         a.nT = nT;
@@ -929,8 +1055,8 @@ int tc_apply(vp_ctx* ctx, const vp_nf* nf, const double* f, int d, double* u, vo
         a.d0 = d0;
         a.flag = ctx->d_flag;
         a.u = u;
-        if (dn == 32) k_tc_apply<32><<<grid, TC_THREADS, smem, s>>>(a);
-        else k_tc_apply<64><<<grid, TC_THREADS, smem, s>>>(a);
+        if (dn == 32) k_tc_apply<32><<<grid, TC_THREADS, smem, s>>>(a, tmB);
+        else k_tc_apply<64><<<grid, TC_THREADS, smem, s>>>(a, tmB);
         VP_LAUNCH_CHECK(ctx);
     }
     return VP_OK;

@@ -131,7 +131,10 @@ struct TcPlan {
     int32_t* d_chunk_near = nullptr;// [n_tiles] near-pair chunks of each tile (its self chunks follow)
     int32_t* d_chunk_tri = nullptr; // [n_chunks][2] triangles of each chunk
     int32_t* d_rexp = nullptr;      // [2][M] row exponents of the near and the self weights
-    uint16_t* d_A = nullptr;        // [n_chunks] digit images (bf16 bits)
+    uint32_t* d_gmask = nullptr;    // [n_chunks] row groups (8 targets) with weights in the chunk
+    int64_t* d_gptr = nullptr;      // [n_chunks + 1] first stored row group of each chunk
+    uint16_t* d_A = nullptr;        // [stored row groups] digit images (bf16 bits)
+    int64_t n_groups = 0;           // stored row groups
     size_t a_bytes = 0, bytes = 0;
 };
 
