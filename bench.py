@@ -832,8 +832,9 @@ def run_offload(args):
     (curved, h0 = 0.1: 721 triangles), its two-Gaussian density, targets = the
     interpolation nodes of a staggered mesh of order N_s = 12 or 20, eps =
     1e-10 or 1e-14; far rules: the built-in degree-8 (16 nodes) and degree-9
-    (19 nodes) ones (C_N = 1) and the conical-product rules of degree 12, 20,
-    25, 30, 40, 50 with C_N of Table "C_N values".  Per point: near
+    (19 nodes) ones (C_N = 1), and the S3-symmetric rules (33-453 nodes) and
+    the conical-product rules (49-676 nodes) of degree 12, 20, 25, 30, 40, 50
+    with C_N of Table "C_N values".  Per point: near
     corrections c, sub-triangles s_n and panels s_l per target, the near-field
     build (T_N with the apply), the far sum T_F by the FMM and directly, and
     the error of the FMM result for f = 1 against (|x|^2 - 1)/4."""
@@ -848,7 +849,9 @@ def run_offload(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     cn = {12: 12.0, 20: 6.8, 25: 3.0, 30: 2.5, 40: 2.0, 50: 1.0}
-    rules = [(16, 8, 1.0), (19, 9, 1.0)] + [(vp.VP_RULE_CONICAL(n), n, cn[n]) for n in (12, 20, 25, 30, 40, 50)]
+    rules = [(16, 8, 1.0, "builtin"), (19, 9, 1.0, "builtin")] + \
+        [(vp.VP_RULE_SYM(n), n, cn[n], "symmetric") for n in vp.VP_RULE_SYM_DEGREES] + \
+        [(vp.VP_RULE_CONICAL(n), n, cn[n], "conical") for n in (12, 20, 25, 30, 40, 50)]
     targets = {}
     for Ns in (12, 20):
         it = vp.Interp(ctx, st.vxy, ts, Ns, curves=cs)
@@ -872,7 +875,7 @@ def run_offload(args):
 
     rows = []
     clocks = Clocks(0)
-    for rule, deg, c_far in rules:
+    for rule, deg, c_far, family in rules:
         mesh = vp.mesh_upload_curved(ctx, q.vxy, tq, cq, rule)
         y, _ = vp.mesh_nodes(mesh)
         yn = y.cpu().numpy()
@@ -888,7 +891,7 @@ def run_offload(args):
                 nf = vp.nearfield_build(ctx, mesh, node_targets=False, txy=txy, eps=eps, c_far=c_far)
                 sts = vp.nf_stats(nf)
                 M = nf.M
-                rec = {"degree": deg, "nq": mesh.N // len(tq), "c_far": c_far, "eps": eps, "N_s": Ns, "targets": M,
+                rec = {"degree": deg, "family": family, "nq": mesh.N // len(tq), "c_far": c_far, "eps": eps, "N_s": Ns, "targets": M,
                        "nodes": mesh.N, "c": sts["n_near"] / M, "s_n": sts["near_leaves"] / M,
                        "s_l": sts["self_panels"] / M, "build_ms": sts["build_ms"],
                        "weights_gb": sts["n_pairs"] * mesh.N // len(tq) * 16 / 1e9}
@@ -916,7 +919,7 @@ def run_offload(args):
         "config": {"workload": "disk_curved_h0.1_721tri_staggered_interp_targets_Ns12_20_two_gaussian_"
                                "far_orders_8_to_50_eps1e-10_1e-14",
                    "step": "near-field build + resident FMM evaluation at the best far order (eps 1e-14, N_s 20)"},
-        "clocks": ck, "best": {k: best[k] for k in ("degree", "nq", "T_N_ms", "T_F_ms")},
+        "clocks": ck, "best": {k: best[k] for k in ("degree", "family", "nq", "T_N_ms", "T_F_ms")},
         "sweep": rows,
     }
     print(json.dumps(line))
@@ -1135,7 +1138,9 @@ def main():
                             "frac": round(a / peak, 4), "ms_per_launch": round(ms_l / n_l, 4), "model": model}
     # correction weights: the paper's work counters per second (no roofline
     # fraction: their float-float instruction mix has no algorithmic count)
-    for k, cnt, what in (("weights_near", stats["near_leaves"] * 49, "near-rule node evaluations (leaves x 49)"),
+    n_near = len(vp.rule_table(33)[2])           # the near rule's length
+    for k, cnt, what in (("weights_near", stats["near_leaves"] * n_near,
+                          f"near-rule node evaluations (leaves x {n_near})"),
                          ("weights_self", stats["self_panels"] * 16 * 8, "self panel points (panels x 16 x 8)")):
         n_l, ms_l = prof.get(k, (0, 0.0))
         if n_l and ms_l > 0:

@@ -74,6 +74,17 @@ typedef enum vp_rule { VP_RULE_16_D8 = 16, VP_RULE_19_D9 = 19 } vp_rule;
 #define VP_RULE_CONICAL(n) (1000 + (n))
 #define VP_RULE_CONICAL_MIN 8
 #define VP_RULE_CONICAL_MAX 50
+/* VP_RULE_SYM(n), n in {12, 20, 25, 30, 40}: S3-symmetric rules of degree n
+ * with positive weights and all nodes inside the simplex, about half the
+ * nodes of the conical rule of the same degree (33, 81, 124, 175 and 295
+ * nodes; the Xiao-Gimbutas rules the paper takes have 32 at degree 12 and
+ * 290 at 40).  Each is the root of its S3-invariant moment
+ * equations next to an orbit structure found by orbit elimination (a
+ * symmetrised product rule reduced one orbit at a time, the equations
+ * restored by Gauss-Newton after each step), computed in 90-digit
+ * arithmetic and rounded once; nodes in orbit order (centroid, S21, S111).
+ * w-hat as for the built-in rules. */
+#define VP_RULE_SYM(n) (2000 + (n))
 
 /* The nodes, weights, w-hat and degree of a far rule (host only, no device
  * needed).  x, y, w: host arrays of cap entries (each may be NULL); *n gets
@@ -514,8 +525,8 @@ VP_API void vp_interp_release(vp_interp* interp);
 /* ---------------------------------------------------------------- tables */
 
 /* The compiled quadrature tables, for inspection (host buffers of capacity
- * cap; *n receives the node count).  which: 16 / 19 (far rules), 49 (near
- * rule), 8 (radial generalized Gaussian rule: x = r, y unused), 116 (the
+ * cap; *n receives the node count).  which: 16 / 19 (far rules), 33 (near
+ * rule: the S3-symmetric rule of degree 12), 8 (radial generalized Gaussian rule: x = r, y unused), 116 (the
  * arc-length Gauss-Legendre rule on [0,1]).  *what receives w of Eq. rho0
  * (0 for the 1-D rules). */
 VP_API int vp_rule_table(int32_t which, double* x, double* y, double* w, double* what, int32_t cap, int32_t* n);

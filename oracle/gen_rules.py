@@ -9,15 +9,17 @@ every rule from its defining moment equations in 60-digit arithmetic
 (mpmath) and rounds each value once to double:
 
 * gl16 / gl7 : Gauss-Legendre on [0,1] (Newton on the Legendre recurrence).
-* near49     : the collapsed ("Duffy") product of two 7-point Gauss-Legendre
-               rules, x = u, y = (1-u) v, weight a_i a_j (1-u_i); exact for
-               total degree 12 on the reference simplex, standing in for the
-               order-12 near rule of Section 5.1.
+* near33     : the S3-symmetric 33-point rule of degree 12 (the order-12
+               near rule of Section 5.1), the same rule as sym12 below.
 * far16      : S3-symmetric, degree 8, orbits [centroid, 3 x S21, 1 x S111].
 * far19      : S3-symmetric, degree 9, orbits [centroid, 4 x S21, 1 x S111].
                Both solved by Gauss-Newton on all monomial moments
                x^i y^j (i+j <= degree), from the starting orbit parameters
                listed in FAR_START below (they define which root is meant).
+* sym<n>     : S3-symmetric far rules of degree n = 12, 20, 25, 30, 40, 50
+               (Section 4.2), Newton's method on the S3-invariant moment
+               equations from the orbit definitions in far_sym_defs.py
+               (90 digits; see symmetric_far_rule).
 * ggq8       : 8 nodes r_j, weights om_j on [0,1] with
                sum_j om_j r_j^k = int_0^1 r r^k dr and
                sum_j om_j r_j^k log r_j = int_0^1 r r^k log r dr, k = 0..7,
@@ -162,6 +164,140 @@ def symmetric_rule(spec):
     res = max(abs(x) for x in _moment_residual(p, deg, n21, n111))
     assert res < mp.mpf(10) ** (-45), res
     return _expand(p, n21, n111)
+
+
+# --------------------------------------------------- S3-symmetric far rules
+# Far rules of degree 12-50 for the order sweep of Section 4.2 (the paper
+# takes Xiao-Gimbutas rules; none is available here).  Each rule is named by
+# its orbit structure and approximate orbit parameters in far_sym_defs.py;
+# the exact rule is the root of its moment equations next to them, reached
+# here by Newton's method in 90-digit arithmetic.  The moment equations are
+# taken on the S3-invariant polynomials, which for a symmetric rule are all
+# the conditions there are: with the centred barycentric coordinates
+# u_i = l_i - 1/3 and the power sums p2 = sum u_i^2, p3 = sum u_i^3, the
+# products p2^i p3^j, 2i + 3j <= degree, span the invariant polynomials of
+# that degree, and one node per orbit gives the orbit's sum.  Their exact
+# integrals come from the collapsed Gauss rule of degree // 2 + 2 points
+# (exact to total degree >= degree + 2).  A parameter listed in `fixed` is
+# held at its listed value, which makes the system square where the orbit
+# structure has one parameter more than there are equations.
+
+def _far_sym_defs():
+    try:
+        from .far_sym_defs import FAR_SYM
+    except ImportError:          # run as a script from this folder
+        from far_sym_defs import FAR_SYM
+    return FAR_SYM
+
+
+def _sym_pairs(deg):
+    return [(i, j) for j in range(deg // 3 + 1) for i in range((deg - 3 * j) // 2 + 1)]
+
+
+def _p2p3(l1, l2, l3):
+    t = mp.mpf(1) / 3
+    u = (l1 - t, l2 - t, l3 - t)
+    return u[0] ** 2 + u[1] ** 2 + u[2] ** 2, u[0] ** 3 + u[1] ** 3 + u[2] ** 3, u
+
+
+def _sym_exact(deg):
+    X, Y, W = duffy_rule(deg // 2 + 2)
+    pairs = _sym_pairs(deg)
+    out = [mp.mpf(0)] * len(pairs)
+    for x, y, w in zip(X, Y, W):
+        p2, p3, _ = _p2p3(1 - x - y, x, y)
+        for k, (i, j) in enumerate(pairs):
+            out[k] += w * p2 ** i * p3 ** j
+    return out
+
+
+def _sym_params(spec):
+    p = [] if spec["w0"] is None else [mp.mpf(spec["w0"])]
+    for a, w in spec["s21"]:
+        p += [mp.mpf(a), mp.mpf(w)]
+    for a, b, w in spec["s111"]:
+        p += [mp.mpf(a), mp.mpf(b), mp.mpf(w)]
+    return p
+
+
+def _sym_system(p, spec, pairs, exact):
+    """Residuals sum_orbits |orbit| w p2^i p3^j - exact and their Jacobian."""
+    R = [-v for v in exact]
+    J = [[mp.mpf(0)] * len(p) for _ in pairs]
+    c = 0
+    kinds = ([0] if spec["w0"] is not None else []) + [1] * len(spec["s21"]) + [2] * len(spec["s111"])
+    for kind in kinds:
+        if kind == 0:                 # centroid: p2 = p3 = 0
+            R[0] += p[c]
+            J[0][c] += 1
+            c += 1
+            continue
+        if kind == 1:                 # S21(a): barycentric (a, a, 1 - 2a)
+            a, w = p[c], p[c + 1]
+            lam, dirs, mult = (a, a, 1 - 2 * a), [(1, 1, -2)], 3
+        else:                         # S111(a, b): (a, b, 1 - a - b)
+            a, b, w = p[c], p[c + 1], p[c + 2]
+            lam, dirs, mult = (a, b, 1 - a - b), [(1, 0, -1), (0, 1, -1)], 6
+        p2, p3, u = _p2p3(*lam)
+        dp2 = [sum(2 * u[q] * d[q] for q in range(3)) for d in dirs]
+        dp3 = [sum(3 * u[q] ** 2 * d[q] for q in range(3)) for d in dirs]
+        for k, (i, j) in enumerate(pairs):
+            psi = p2 ** i * p3 ** j
+            R[k] += mult * w * psi
+            gi = i * p2 ** (i - 1) * p3 ** j if i > 0 else 0
+            gj = j * p2 ** i * p3 ** (j - 1) if j > 0 else 0
+            for s, _ in enumerate(dirs):
+                J[k][c + s] += mult * w * (gi * dp2[s] + gj * dp3[s])
+            J[k][c + len(dirs)] += mult * psi
+        c += len(dirs) + 1
+    return R, J
+
+
+def symmetric_far_rule(degree):
+    """The S3-symmetric far rule of the given degree (far_sym_defs.FAR_SYM):
+    dict of floats x, y, w, degree, what, with the nodes in orbit order."""
+    spec = _far_sym_defs()[degree]
+    with mp.workdps(90):
+        pairs = _sym_pairs(degree)
+        exact = _sym_exact(degree)
+        p = _sym_params(spec)
+        free = [c for c in range(len(p)) if c not in spec["fixed"]]
+        assert len(free) == len(pairs), (len(free), len(pairs))
+        for _ in range(40):
+            R, J = _sym_system(p, spec, pairs, exact)
+            step = mp.lu_solve(mp.matrix([[J[k][c] for c in free] for k in range(len(pairs))]), mp.matrix(R))
+            for s, c in enumerate(free):
+                p[c] -= step[s]
+            if max(abs(v) for v in step) < mp.mpf(10) ** -70:
+                break
+        R, _ = _sym_system(p, spec, pairs, exact)
+        assert max(abs(v) for v in R) < mp.mpf(10) ** -70
+        n21, n111 = len(spec["s21"]), len(spec["s111"])
+        X, Y, W = [], [], []
+        c = 0
+        if spec["w0"] is not None:
+            X.append(mp.mpf(1) / 3)
+            Y.append(mp.mpf(1) / 3)
+            W.append(p[0])
+            c = 1
+        for _ in range(n21):
+            a, w = p[c], p[c + 1]
+            c += 2
+            for (l2, l3) in [(a, 1 - 2 * a), (1 - 2 * a, a), (a, a)]:
+                X.append(l2)
+                Y.append(l3)
+                W.append(w)
+        for _ in range(n111):
+            a, b, w = p[c], p[c + 1], p[c + 2]
+            c += 3
+            cc = 1 - a - b
+            for (l1, l2, l3) in [(a, b, cc), (a, cc, b), (b, a, cc), (b, cc, a), (cc, a, b), (cc, b, a)]:
+                X.append(l2)
+                Y.append(l3)
+                W.append(w)
+        assert all(w > 0 for w in W) and all(x > 0 and y > 0 and 1 - x - y > 0 for x, y in zip(X, Y))
+        return dict(degree=degree, x=[float(v) for v in X], y=[float(v) for v in Y], w=[float(v) for v in W],
+                    what=float(what_for(X, Y, W, degree)))
 
 
 def _ggq_residual(z, t):
@@ -314,13 +450,17 @@ def main(path=None):
     for name, n in [("gl16", 16), ("gl7", 7)]:
         x, w = gauss_legendre01(n)
         out[name] = dict(x=[_hx(v) for v in x], w=[_hx(v) for v in w])
-    X, Y, W = duffy_rule(7)
-    out["near49"] = dict(degree=12, x=[_hx(v) for v in X], y=[_hx(v) for v in Y], w=[_hx(v) for v in W],
-                         what=_hx(what_for(X, Y, W, 12)))
+    r = symmetric_far_rule(12)
+    out["near33"] = dict(degree=12, x=[_hx(v) for v in r["x"]], y=[_hx(v) for v in r["y"]],
+                         w=[_hx(v) for v in r["w"]], what=_hx(r["what"]))
     for name, spec in FAR_START.items():
         X, Y, W = symmetric_rule(spec)
         out[name] = dict(degree=spec["degree"], x=[_hx(v) for v in X], y=[_hx(v) for v in Y],
                          w=[_hx(v) for v in W], what=_hx(what_for(X, Y, W, spec["degree"])))
+    for d in sorted(_far_sym_defs()):
+        r = symmetric_far_rule(d)
+        out[f"sym{d}"] = dict(degree=d, x=[_hx(v) for v in r["x"]], y=[_hx(v) for v in r["y"]],
+                              w=[_hx(v) for v in r["w"]], what=_hx(r["what"]))
     r, om = ggq8()
     out["ggq8"] = dict(r=[_hx(v) for v in r], w=[_hx(v) for v in om])
     idx, Linv = oracle_basis(4)

@@ -113,7 +113,7 @@ class Oracle:
         self.tables = t
         fr = t[rule] if isinstance(rule, str) else {k: (np.asarray(v, np.float64) if isinstance(v, list) else v)
                                                     for k, v in rule.items()}
-        nr, gg = t["near49"], t["ggq8"]
+        nr, gg = t["near33"], t["ggq8"]
         gl = t["gl16"] if nl == 16 else t["gl7"]
         p = OrParams()
         p.nq = len(fr["w"])

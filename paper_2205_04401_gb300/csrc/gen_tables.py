@@ -6,7 +6,9 @@ Serkh, arXiv 2205.04401), derived here from their moment equations in
 
   far16   S3-symmetric 16-point rule of degree 8 on the reference simplex
   far19   S3-symmetric 19-point rule of degree 9
-  near49  collapsed 7x7 Gauss-Legendre rule (x = u, y = (1-u) v), degree 12
+  near33  the S3-symmetric 33-point rule of degree 12 (the near rule, Section 5.1)
+  sym<n>  S3-symmetric far rules of degree n = 12, 20, 25, 30, 40, 50 (Section 4.2),
+          from the orbit definitions in sym_rule_defs.py
   ggq8    8-point generalized Gaussian rule on [0,1] for r p(r), r log(r) p(r), p in P_7
   gl16    16-point Gauss-Legendre rule on [0,1]
   what    largest weight among the ceil((N+1)/2) nodes nearest an edge (max over edges)
@@ -20,6 +22,7 @@ Run once when a rule changes:  python paper_2205_04401_gb300/csrc/gen_tables.py
 (needs mpmath; the generated header is committed).
 """
 import math
+from fractions import Fraction
 import os
 
 import mpmath as mp
@@ -167,6 +170,126 @@ def solve_symmetric(deg, c0, s21, s111):
     assert mp.norm(R) < mp.mpf(10) ** -40
     c0_, s2, s3 = unpack(p)
     return orbit_points(c0_, s2, s3)
+
+
+def _sym_defs():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "sym_rule_defs", os.path.join(os.path.dirname(os.path.abspath(__file__)), "sym_rule_defs.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.SYM_RULES
+
+
+def e23_moment(i, j):
+    """Exact integral over the reference simplex of e2^i e3^j, e2 = l1 l2 +
+    l1 l3 + l2 l3 and e3 = l1 l2 l3 of the barycentric coordinates, from
+    int l1^a l2^b l3^c = a! b! c! / (a + b + c + 2)! and the multinomial
+    expansion of e2^i."""
+    f = math.factorial
+    tot = Fraction(0)
+    for p1 in range(i + 1):
+        for p2 in range(i - p1 + 1):
+            p3 = i - p1 - p2
+            mult = f(i) // (f(p1) * f(p2) * f(p3))
+            tot += Fraction(mult * f(p1 + p2 + j) * f(p1 + p3 + j) * f(p2 + p3 + j), f(2 * i + 3 * j + 2))
+    return tot
+
+
+def solve_sym_e23(deg, rule):
+    """S3-symmetric rule of degree deg from its orbit definition (sym_rule_defs):
+    Newton's method in 90-digit arithmetic on the moment equations of the
+    invariant basis e2^i e3^j, 2i + 3j <= deg (on the plane l1 + l2 + l3 = 1
+    these span the S3-invariant polynomials of degree <= deg, so they are all
+    the conditions of a symmetric rule).  Orbit sums by one representative:
+    centroid (weight w0), S21(a) = (a, a, 1 - 2a) x 3, S111(a, b) =
+    (a, b, 1 - a - b) x 6.  Parameters listed in rule["fixed"] keep their
+    listed values.  Returns [(x, y, w)] in orbit order."""
+    with mp.workdps(90):
+        idx = [(i, j) for i in range(deg // 2 + 1) for j in range((deg - 2 * i) // 3 + 1)]
+        exact = []
+        for i, j in idx:
+            q = e23_moment(i, j)
+            exact.append(mp.mpf(q.numerator) / q.denominator)
+        kinds = ([0] if rule["w0"] is not None else []) + [1] * len(rule["s21"]) + [2] * len(rule["s111"])
+        p = ([mp.mpf(rule["w0"])] if rule["w0"] is not None else []) + \
+            [mp.mpf(v) for o in rule["s21"] for v in o] + [mp.mpf(v) for o in rule["s111"] for v in o]
+        free = [c for c in range(len(p)) if c not in rule["fixed"]]
+        assert len(free) == len(idx), (deg, len(free), len(idx))
+
+        def orbit(c, k):
+            if k == 0:
+                t = mp.mpf(1) / 3
+                return (t, t, t), [], 1, p[c], 1
+            if k == 1:
+                a = p[c]
+                return (a, a, 1 - 2 * a), [(1, 1, -2)], 3, p[c + 1], 2
+            a, b = p[c], p[c + 1]
+            return (a, b, 1 - a - b), [(1, 0, -1), (0, 1, -1)], 6, p[c + 2], 3
+
+        def system():
+            R = [-v for v in exact]
+            J = [[mp.mpf(0)] * len(p) for _ in idx]
+            c = 0
+            for k in kinds:
+                lam, dirs, mult, w, n = orbit(c, k)
+                e2 = lam[0] * lam[1] + lam[0] * lam[2] + lam[1] * lam[2]
+                e3 = lam[0] * lam[1] * lam[2]
+                de2 = (lam[1] + lam[2], lam[0] + lam[2], lam[0] + lam[1])
+                de3 = (lam[1] * lam[2], lam[0] * lam[2], lam[0] * lam[1])
+                g2 = [sum(de2[q] * d[q] for q in range(3)) for d in dirs]
+                g3 = [sum(de3[q] * d[q] for q in range(3)) for d in dirs]
+                for r, (i, j) in enumerate(idx):
+                    v = e2 ** i * e3 ** j
+                    R[r] += mult * w * v
+                    di = i * e2 ** (i - 1) * e3 ** j if i else 0
+                    dj = j * e2 ** i * e3 ** (j - 1) if j else 0
+                    for s_, _ in enumerate(dirs):
+                        J[r][c + s_] += mult * w * (di * g2[s_] + dj * g3[s_])
+                    J[r][c + n - 1] += mult * v
+                c += n
+            return R, J
+
+        for _ in range(40):
+            R, J = system()
+            dx = mp.lu_solve(mp.matrix([[J[r][c] for c in free] for r in range(len(idx))]), mp.matrix(R))
+            for s_, c in enumerate(free):
+                p[c] -= dx[s_]
+            if max(abs(v) for v in dx) < mp.mpf(10) ** -70:
+                break
+        R, _ = system()
+        assert max(abs(v) for v in R) < mp.mpf(10) ** -70, deg
+        pts = []
+        c = 0
+        for k in kinds:
+            lam, _, _, w, n = orbit(c, k)
+            if k == 0:
+                pts.append((lam[1], lam[2], w))
+            elif k == 1:
+                a = lam[0]
+                pts += [(a, 1 - 2 * a, w), (1 - 2 * a, a, w), (a, a, w)]
+            else:
+                a, b, cc = lam
+                for l1, l2, l3 in ((a, b, cc), (a, cc, b), (b, a, cc), (b, cc, a), (cc, a, b), (cc, b, a)):
+                    pts.append((l2, l3, w))
+            c += n
+        assert all(w > 0 and x > 0 and y > 0 and 1 - x - y > 0 for x, y, w in pts), deg
+        return pts
+
+
+def radial5():
+    """Interpolatory radial rule of the self-interaction on the 5 Gauss-Legendre
+    nodes r_i of [0, 1]: weights a_i, b_i with sum_i a_i p(r_i) = int_0^1 r p(r) dr
+    and sum_i b_i p(r_i) = int_0^1 r log(r) p(r) dr for every p of degree <= 4
+    (moments 1 / (k + 2) and -1 / (k + 2)^2).  Along a ray the P_4 moments of
+    Section 3.4 need no more: the integrand is r log(r r0) times a polynomial of
+    degree <= 4 in r, for which this rule and the GGQ rule of order 8 are both
+    exact."""
+    r, _ = gl01(5)
+    V = mp.matrix([[ri ** k for ri in r] for k in range(5)])
+    a = mp.lu_solve(V, mp.matrix([mp.mpf(1) / (k + 2) for k in range(5)]))
+    b = mp.lu_solve(V, mp.matrix([-mp.mpf(1) / (k + 2) ** 2 for k in range(5)]))
+    return r, [a[i] for i in range(5)], [b[i] for i in range(5)]
 
 
 def ggq8():
@@ -396,19 +519,36 @@ def main():
         arr(f"VP_{name.upper()}_W", [p[2] for p in pts])
         out.append(f"static const double VP_{name.upper()}_WHAT = {cdbl(what(pts, deg))};")
         out.append(f"static const int VP_{name.upper()}_DEGREE = {deg};")
+    sym = _sym_defs()
+    for deg in sorted(sym):
+        pts = solve_sym_e23(deg, sym[deg])
+        arr(f"VP_SYM{deg}_X", [q[0] for q in pts])
+        arr(f"VP_SYM{deg}_Y", [q[1] for q in pts])
+        arr(f"VP_SYM{deg}_W", [q[2] for q in pts])
+        out.append(f"static const double VP_SYM{deg}_WHAT = {cdbl(what(pts, deg))};")
+    out.append("struct VpSymRule { int degree, n; const double *x, *y, *w; double what; };")
+    out.append(f"static const VpSymRule VP_SYM_RULES[{len(sym)}] = {{")
+    for deg in sorted(sym):
+        n = (1 if sym[deg]["w0"] is not None else 0) + 3 * len(sym[deg]["s21"]) + 6 * len(sym[deg]["s111"])
+        out.append(f"  {{{deg}, {n}, VP_SYM{deg}_X, VP_SYM{deg}_Y, VP_SYM{deg}_W, VP_SYM{deg}_WHAT}},")
+    out.append("};")
     Hinv = leg15_gram_inverse()
     arr("VP_LEG15_HINV", [Hinv[i, j] for i in range(Hinv.rows) for j in range(Hinv.cols)])
     Hinv = mon15_gram_inverse()
     arr("VP_MON15_HINV", [Hinv[i, j] for i in range(Hinv.rows) for j in range(Hinv.cols)])
-    pts = duffy(7)
-    arr("VP_NEAR49_X", [p[0] for p in pts])
-    arr("VP_NEAR49_Y", [p[1] for p in pts])
-    arr("VP_NEAR49_W", [p[2] for p in pts])
-    out.append(f"static const double VP_NEAR49_WHAT = {cdbl(what(pts, 12))};")
-    out.append("static const int VP_NEAR49_DEGREE = 12;")
+    pts = solve_sym_e23(12, sym[12])        # the near rule: the symmetric rule of degree 12
+    arr("VP_NEAR33_X", [p[0] for p in pts])
+    arr("VP_NEAR33_Y", [p[1] for p in pts])
+    arr("VP_NEAR33_W", [p[2] for p in pts])
+    out.append(f"static const double VP_NEAR33_WHAT = {cdbl(what(pts, 12))};")
+    out.append("static const int VP_NEAR33_DEGREE = 12;")
     r, w = ggq8()
     arr("VP_GGQ8_R", r)
     arr("VP_GGQ8_W", w)
+    r, a, b = radial5()
+    arr("VP_RAD5_R", r)
+    arr("VP_RAD5_A", a)
+    arr("VP_RAD5_B", b)
     t, w = gl01(16)
     arr("VP_GL16_X", t)
     arr("VP_GL16_W", w)

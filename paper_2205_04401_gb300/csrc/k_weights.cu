@@ -341,15 +341,10 @@ __device__ __forceinline__ void far_subtract_store(const WeightsArgs& a, const W
     if (a.C2) a.C2[p * a.nq + k] = make_float2(s.h, s.l);
 }
 
-// mu (float-float accumulators) -> C_k = sum_i Q_ki mu_i - [k != own] W_k G(x, y_k)
-__device__ __forceinline__ void finish_pair_f2(const WeightsArgs& a, const WeightsF2& b, int64_t p, int T, int t,
-                                               int own, const float* mh, const float* ml, int lane,
-                                               const float4* ftab, const LogSmem& lt, double ln2) {
-    f2 v[16];
-#pragma unroll
-    for (int q = 0; q < VP_NB; q++) v[q] = f2_fast(mh[q], ml[q]);
-    v[15] = {0.f, 0.f};
-    const f2 mine = reduce_scatter16_f2(v, lane);
+// mu_i on lanes 2i and 2i + 1 -> C_k = sum_i Q_ki mu_i - [k != own] W_k G(x, y_k)
+__device__ __forceinline__ void finish_pair_mine(const WeightsArgs& a, const WeightsF2& b, int64_t p, int T, int t,
+                                                 int own, f2 mine, int lane, const float4* ftab, const LogSmem& lt,
+                                                 double ln2) {
     for (int k0 = 0; k0 < a.nq; k0 += 32) {   // node k0 + lane of every group of 32
         const int k = k0 + lane;
         const float2* Qk = a.Q2 + (k < a.nq ? k : 0) * VP_NB;
@@ -362,6 +357,17 @@ __device__ __forceinline__ void finish_pair_f2(const WeightsArgs& a, const Weigh
         }
         if (k < a.nq) far_subtract_store(a, b, p, T, t, own, k, f2_fast(ah, al), ftab, lt, ln2);
     }
+}
+
+// mu (float-float accumulators of every lane) -> the warp totals -> C_k
+__device__ __forceinline__ void finish_pair_f2(const WeightsArgs& a, const WeightsF2& b, int64_t p, int T, int t,
+                                               int own, const float* mh, const float* ml, int lane,
+                                               const float4* ftab, const LogSmem& lt, double ln2) {
+    f2 v[16];
+#pragma unroll
+    for (int q = 0; q < VP_NB; q++) v[q] = f2_fast(mh[q], ml[q]);
+    v[15] = {0.f, 0.f};
+    finish_pair_mine(a, b, p, T, t, own, reduce_scatter16_f2(v, lane), lane, ftab, lt, ln2);
 }
 
 // Stop test of a sub-triangle S of T (vertices v) whose FP32 filters were
@@ -530,7 +536,7 @@ __global__ void __launch_bounds__(256) k_near_root_split(WeightsArgs a, WeightsF
 // fixed reference points z_j, so the moments and the moment-to-weight map
 // fold into one constant matrix of the far rule, C_k = sum_j B_jk g_j with
 // g_j = log|y_j - x|^2 w_j J_T / 4pi (B = QM M(z)^T, tabulated per rule).
-// A warp takes RPW pairs at once, so that its lanes stay busy: the RPW x 49
+// A warp takes RPW pairs at once, so that its lanes stay busy: the RPW x 33
 // values g_j are spread over the lanes into shared memory, then the RPW x nq
 // dot products (one (pair, node) per lane) and the far-rule subtraction.
 // Each (pair, node) result is computed by the same operations in the same
@@ -562,54 +568,56 @@ __global__ void __launch_bounds__(WARPS * 32, VP_ROOT_MINB) k_weights_near_root(
     }
     load_logtab(a.tab, lt);              // ends with __syncthreads
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int64_t w0 = ((int64_t)blockIdx.x * WARPS + wl) * RPW;
-    if (w0 >= n) return;
-    const int np = (int)min((int64_t)RPW, n - w0);
     const double ln2 = a.tab->ln2;
     RootPair* rp = rp_all[wl];
-    if (lane < np) {
-        RootPair r;
-        r.p = idx[w0 + lane];
-        r.T = a.ptri[r.p];
-        r.t = a.ptgt[r.p];
-        r.own = own_index(a, r.t, r.T);
-        r.g = near_pair_f2(b, r.T, r.t);
-        rp[lane] = r;
-    }
-    __syncwarp();
-    for (int e = lane; e < np * VP_NNEAR; e += 32) {
-        const int q = e / VP_NNEAR, j = e - q * VP_NNEAR;
-        const NearPairF2 g = rp[q].g;
-        const float4 Z = nz_s[j];
-        const f2 zx = {Z.x, Z.y}, zy = {Z.z, Z.w};
-        const f2 dx = f2_add(g.ax, f2_add(f2_mul(zx, g.ex), f2_mul(zy, g.fx)));   // y_j - x
-        const f2 dy = f2_add(g.ay, f2_add(f2_mul(zx, g.ey), f2_mul(zy, g.fy)));
-        const f2 r2 = f2_add(f2_sqr(dx), f2_sqr(dy));
-        f2 lg;
-        if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);
-        else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
-        const float2 W = nw_s[j];
-        const f2 gj = f2_mul(lg, f2_mul({W.x, W.y}, g.wj));
-        g_all[wl][q][j] = make_float2(gj.h, gj.l);
-    }
-    __syncwarp();
-    for (int sl = lane; sl < np * a.nq; sl += 32) {
-        const int q = sl / a.nq, k = sl - q * a.nq;
-        const float2* gs = g_all[wl][q];
-        const float2* Bk = a.B2 + k;
-        float ah = 0.f, al = 0.f;
-#pragma unroll 7
-        for (int j = 0; j < VP_NNEAR; j++) {
-            const float2 gj = gs[j], B = Bk[(int64_t)j * a.nq];
-            f2_acc(ah, al, {B.x, B.y}, {gj.x, gj.y});
-            if ((j & 7) == 7) {
-                const f2 r = f2_fast(ah, al);
-                ah = r.h;
-                al = r.l;
-            }
+    // persistent: each warp takes the groups of RPW pairs at w0, w0 + RPW (warps in the grid), ...
+    for (int64_t w0 = ((int64_t)blockIdx.x * WARPS + wl) * RPW; w0 < n; w0 += (int64_t)gridDim.x * WARPS * RPW) {
+        const int np = (int)min((int64_t)RPW, n - w0);
+        __syncwarp();
+        if (lane < np) {
+            RootPair r;
+            r.p = idx[w0 + lane];
+            r.T = a.ptri[r.p];
+            r.t = a.ptgt[r.p];
+            r.own = own_index(a, r.t, r.T);
+            r.g = near_pair_f2(b, r.T, r.t);
+            rp[lane] = r;
         }
-        const RootPair& r = rp[q];
-        far_subtract_store(a, b, r.p, r.T, r.t, r.own, k, f2_fast(ah, al), ftab, lt, ln2);
+        __syncwarp();
+        for (int e = lane; e < np * VP_NNEAR; e += 32) {
+            const int q = e / VP_NNEAR, j = e - q * VP_NNEAR;
+            const NearPairF2 g = rp[q].g;
+            const float4 Z = nz_s[j];
+            const f2 zx = {Z.x, Z.y}, zy = {Z.z, Z.w};
+            const f2 dx = f2_add(g.ax, f2_add(f2_mul(zx, g.ex), f2_mul(zy, g.fx)));   // y_j - x
+            const f2 dy = f2_add(g.ay, f2_add(f2_mul(zx, g.ey), f2_mul(zy, g.fy)));
+            const f2 r2 = f2_add(f2_sqr(dx), f2_sqr(dy));
+            f2 lg;
+            if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);
+            else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
+            const float2 W = nw_s[j];
+            const f2 gj = f2_mul(lg, f2_mul({W.x, W.y}, g.wj));
+            g_all[wl][q][j] = make_float2(gj.h, gj.l);
+        }
+        __syncwarp();
+        for (int sl = lane; sl < np * a.nq; sl += 32) {
+            const int q = sl / a.nq, k = sl - q * a.nq;
+            const float2* gs = g_all[wl][q];
+            const float2* Bk = a.B2 + k;
+            float ah = 0.f, al = 0.f;
+#pragma unroll 11
+            for (int j = 0; j < VP_NNEAR; j++) {
+                const float2 gj = gs[j], B = Bk[(int64_t)j * a.nq];
+                f2_acc(ah, al, {B.x, B.y}, {gj.x, gj.y});
+                if ((j & 7) == 7) {
+                    const f2 r = f2_fast(ah, al);
+                    ah = r.h;
+                    al = r.l;
+                }
+            }
+            const RootPair& r = rp[q];
+            far_subtract_store(a, b, r.p, r.T, r.t, r.own, k, f2_fast(ah, al), ftab, lt, ln2);
+        }
     }
 }
 
@@ -623,7 +631,35 @@ struct LeafRec {
     int32_t L;
     int32_t flip;    // 1: the inverted child (m12, m20, m01), sh = -2^-L
 };
-constexpr int DSTK = 128;   // per-thread stack: 3 per level of depth + 4
+// Per-thread stack of the depth-first subdivision: 3 entries per level of
+// depth + 4 (depth cap 30), 12 bytes each.  Every sub-triangle of the 4-way
+// midpoint split is a right triangle of the reference simplex with legs of
+// one unit at its scale 2^-L, upright, (x, y), (x + 1, y), (x, y + 1), or
+// inverted, (x, y), (x - 1, y), (x, y - 1), so its first vertex, level and
+// orientation determine it.
+constexpr int DSTK = 96;
+struct StackRec {
+    int32_t x, y;    // first vertex, numerators at scale 2^-L
+    int32_t lf;      // 2 L + (1: inverted)
+};
+
+__device__ __forceinline__ SubTri stack_subtri(StackRec r) {
+    const int32_t sg = (r.lf & 1) ? -1 : 1;
+    SubTri S;
+    S.v[0] = r.x; S.v[1] = r.y; S.v[2] = r.x + sg; S.v[3] = r.y; S.v[4] = r.x; S.v[5] = r.y + sg;
+    S.L = r.lf >> 1;
+    return S;
+}
+
+// The four children of r in push_children's order: (v0, m01, m20),
+// (m01, v1, m12), (m20, m12, v2) keep the orientation, (m12, m20, m01) flips it.
+__device__ __forceinline__ void push_children_rec(StackRec r, StackRec* stk, int base) {
+    const int32_t sg = (r.lf & 1) ? -1 : 1, lf = r.lf + 2;
+    stk[base + 0] = {2 * r.x, 2 * r.y, lf};
+    stk[base + 1] = {2 * r.x + sg, 2 * r.y, lf};
+    stk[base + 2] = {2 * r.x, 2 * r.y + sg, lf};
+    stk[base + 3] = {2 * r.x + sg, 2 * r.y + sg, lf ^ 1};
+}
 
 __global__ void __launch_bounds__(128) k_near_deep_leaves(WeightsArgs a, WeightsF2 b, const int32_t* __restrict__ idx,
                                                           int64_t n, int pass, int32_t* __restrict__ cnt,
@@ -636,10 +672,8 @@ __global__ void __launch_bounds__(128) k_near_deep_leaves(WeightsArgs a, Weights
     const double R_root = b.Rn[T];
     const float Rf_root = (float)R_root;
     const NearPairF2 g = near_pair_f2(b, T, t);
-    SubTri stk[DSTK];
-    SubTri r;
-    r.v[0] = 0; r.v[1] = 0; r.v[2] = 1; r.v[3] = 0; r.v[4] = 0; r.v[5] = 1; r.L = 0;
-    push_children(r, stk, 0);
+    StackRec stk[DSTK];
+    push_children_rec({0, 0, 0}, stk, 0);
     int sp = 4, capped = 0, visited = 1;
     int64_t nleaf = 0;
     bool overflow = false;
@@ -649,7 +683,8 @@ __global__ void __launch_bounds__(128) k_near_deep_leaves(WeightsArgs a, Weights
             overflow = true;
             break;
         }
-        const SubTri S = stk[--sp];
+        const StackRec R = stk[--sp];
+        const SubTri S = stack_subtri(R);
         float scale;
         f2 d0x, d0y, a0x, a0y;
         bool stop = subtri_stop_f2(a, g, S, T, t, Nn, R_root, Rf_root, scale, d0x, d0y, a0x, a0y);
@@ -672,7 +707,7 @@ __global__ void __launch_bounds__(128) k_near_deep_leaves(WeightsArgs a, Weights
                 overflow = true;
                 break;
             }
-            push_children(S, stk, sp);
+            push_children_rec(R, stk, sp);
             sp += 4;
         }
     }
@@ -686,7 +721,7 @@ __global__ void __launch_bounds__(128) k_near_deep_leaves(WeightsArgs a, Weights
 }
 
 #ifndef VP_DEEP_MINB
-#define VP_DEEP_MINB 6
+#define VP_DEEP_MINB 5
 #endif
 __global__ void __launch_bounds__(WARPS * 32, VP_DEEP_MINB) k_weights_near_deep(WeightsArgs a, WeightsF2 b,
                                                                                 const int32_t* __restrict__ idx,
@@ -708,56 +743,79 @@ __global__ void __launch_bounds__(WARPS * 32, VP_DEEP_MINB) k_weights_near_deep(
     }
     load_logtab(a.tab, lt);              // ends with __syncthreads
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int64_t w = (int64_t)blockIdx.x * WARPS + wl;
-    if (w >= n) return;
     const double ln2 = a.tab->ln2;
     LeafF2* leaves = leaf_all[wl];
     float4* exy = exy_all[wl];
-    const int64_t p = idx[w];
-    const int T = a.ptri[p], t = a.ptgt[p];
-    const int own = own_index(a, t, T);
-    const NearPairF2 g = near_pair_f2(b, T, t);
-    near_exy(g, nz_s, exy, lane);
-    float mh[VP_NB], ml[VP_NB];
+    // persistent: each warp takes pairs w, w + (warps in the grid), ...
+    for (int64_t w = (int64_t)blockIdx.x * WARPS + wl; w < n; w += (int64_t)gridDim.x * WARPS) {
+        __syncwarp();
+        const int64_t p = idx[w];
+        const int T = a.ptri[p], t = a.ptgt[p];
+        const int own = own_index(a, t, T);
+        const NearPairF2 g = near_pair_f2(b, T, t);
+        near_exy(g, nz_s, exy, lane);
+        float mh[VP_NB], ml[VP_NB];
 #pragma unroll
-    for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
-    const int64_t l0 = off[w], l1 = off[w + 1];
-    for (int64_t c0 = l0; c0 < l1; c0 += 32) {
-        const int nl = (int)min((int64_t)32, l1 - c0);
-        __syncwarp();
-        if (lane < nl) {
-            // the leaf data exactly as the traversal forms it (subtri_stop_f2)
-            const LeafRec lr = recs[c0 + lane];
-            const float scale = __int_as_float((127 - lr.L) << 23);
-            const f2 xi = dyadic_f2(lr.x, scale), eta = dyadic_f2(lr.y, scale);
-            const f2 d0x = rel_coord(g.ax, xi, eta, g.ex, g.fx), d0y = rel_coord(g.ay, xi, eta, g.ey, g.fy);
-            const f2 u0 = f2_axpb(xi, 3.0f, -1.0f), v0 = f2_axpb(eta, 3.0f, -1.0f);
-            const f2 wj = f2_scale(g.wj, __fmul_rn(scale, scale));
-            LeafF2 lf;
-            lf.d0xh = d0x.h; lf.d0xl = d0x.l; lf.d0yh = d0y.h; lf.d0yl = d0y.l;
-            lf.u0h = u0.h; lf.u0l = u0.l; lf.v0h = v0.h; lf.v0l = v0.l;
-            lf.sh = lr.flip ? -scale : scale;
-            lf.wjh = wj.h; lf.wjl = wj.l; lf.pad = 0.f;
-            leaves[lane] = lf;
+        for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
+        const int64_t l0 = off[w], l1 = off[w + 1];
+        for (int64_t c0 = l0; c0 < l1; c0 += 32) {
+            const int nl = (int)min((int64_t)32, l1 - c0);
+            __syncwarp();
+            if (lane < nl) {
+                // the leaf data exactly as the traversal forms it (subtri_stop_f2)
+                const LeafRec lr = recs[c0 + lane];
+                const float scale = __int_as_float((127 - lr.L) << 23);
+                const f2 xi = dyadic_f2(lr.x, scale), eta = dyadic_f2(lr.y, scale);
+                const f2 d0x = rel_coord(g.ax, xi, eta, g.ex, g.fx), d0y = rel_coord(g.ay, xi, eta, g.ey, g.fy);
+                const f2 u0 = f2_axpb(xi, 3.0f, -1.0f), v0 = f2_axpb(eta, 3.0f, -1.0f);
+                const f2 wj = f2_scale(g.wj, __fmul_rn(scale, scale));
+                LeafF2 lf;
+                lf.d0xh = d0x.h; lf.d0xl = d0x.l; lf.d0yh = d0y.h; lf.d0yl = d0y.l;
+                lf.u0h = u0.h; lf.u0l = u0.l; lf.v0h = v0.h; lf.v0l = v0.l;
+                lf.sh = lr.flip ? -scale : scale;
+                lf.wjh = wj.h; lf.wjl = wj.l; lf.pad = 0.f;
+                leaves[lane] = lf;
+            }
+            __syncwarp();
+            const int combos = nl * VP_NNEAR;
+            for (int i = lane; i < combos; i += 32) {
+                const int li = i / VP_NNEAR, j = i - li * VP_NNEAR;
+                near_leaf_node(leaves[li], exy[j], nz3_s[j], nw_s[j], ftab, lt, ln2, mh, ml);
+            }
         }
-        __syncwarp();
-        const int combos = nl * VP_NNEAR;
-        for (int i = lane; i < combos; i += 32) {
-            const int li = i / VP_NNEAR, j = i - li * VP_NNEAR;
-            near_leaf_node(leaves[li], exy[j], nz3_s[j], nw_s[j], ftab, lt, ln2, mh, ml);
-        }
+        finish_pair_f2(a, b, p, T, t, own, mh, ml, lane, ftab, lt, ln2);
     }
-    finish_pair_f2(a, b, p, T, t, own, mh, ml, lane, ftab, lt, ln2);
 }
 
 // ---------------------------------------------------- self, float-float
-// Section 3.4 with the per-edge geometry that fixes the panels (side
-// lengths, the foot of the perpendicular, the distance to the side, the
-// dyadic panel counts) in FP64 exactly as in the FP64 kernel, and everything
-// per panel and per point in float-float.  Lanes: Gauss-Legendre node
-// lane >> 1 of every panel, GGQ nodes 4 (lane & 1) .. +3.
-__global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(WeightsArgs a, WeightsF2 b, const int32_t* __restrict__ idx,
-                                                              int64_t n) {
+// Section 3.4: the fan of the target over each side of T, panels dyadic
+// towards the foot of the perpendicular, a Gauss-Legendre rule in arc length
+// per panel and a radial rule along each ray.  The per-edge geometry that
+// fixes the panels (side lengths, the foot of the perpendicular, the
+// distance to the side, the dyadic panel counts) is FP64 exactly as in the
+// FP64 kernel; everything per panel in float-float.
+//
+// Along the ray from the target x to the boundary point gamma(s) at distance
+// r0, the point at fraction r has (u, v) = (u0, v0) + r (al, be), so each
+// monomial u^a v^b of the P_4 moments is a polynomial of degree <= 4 in r and
+// the radial integrand is r log(r r0) times it.  The interpolatory rule on
+// the 5 Gauss-Legendre nodes of [0, 1] with the weights of int r p and
+// int r log(r) p (vp_tables.h) is exact for these, as the paper's
+// generalized Gaussian rule of order 8 is: the moments are the same up to
+// rounding, with one logarithm per ray and 5 points instead of 8.
+// Lanes: Gauss-Legendre node lane & 15 of panel 2 i + (lane >> 4).
+__device__ __forceinline__ f2 self_bound(int k, int Nd, int side, f2 L2, f2 st2, f2 len2) {
+    if (k == 0) return side == 0 ? f2{0.f, 0.f} : L2;           // the side's end
+    if (k == Nd + 1) return st2;                                  // the foot
+    const f2 om = k <= 24 ? f2{__fsub_rn(1.f, __int_as_float((127 - k) << 23)), 0.f}   // 1 - 2^-k, exact
+                          : f2{1.f, -__int_as_float((127 - min(k, 126)) << 23)};
+    const f2 frac = f2_mul(len2, om);
+    return side == 0 ? frac : f2_add(L2, f2_neg(frac));
+}
+
+__global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(WeightsArgs a, WeightsF2 b,
+                                                                              const int32_t* __restrict__ idx,
+                                                                              int64_t n) {
     __shared__ float4 ftab[LOG_N];
     __shared__ LogSmem lt;
     load_logtab(a.tab, lt);
@@ -776,29 +834,16 @@ __global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(We
     const double xx = a.txy[2 * t], xy = a.txy[2 * t + 1];
     const double qx0 = xx - Ax, qy0 = xy - Ay;
     const f2 xi0 = f2_from_d((qx0 * fy - qy0 * fx) * invJ), eta0 = f2_from_d((ex * qy0 - ey * qx0) * invJ);
-    const f2 u0 = f2_axpb(xi0, 3.0f, -1.0f), v0 = f2_axpb(eta0, 3.0f, -1.0f);   // the target's (u, v)
     const int own = own_index(a, t, T);
     // float-float triangle relative to the target
     const float4 TA = b.tA[T], TE = b.te[T], TF = b.tf[T], X = b.x2[t];
     const f2 ax = f2_add({TA.x, TA.y}, {-X.x, -X.y}), ay = f2_add({TA.z, TA.w}, {-X.z, -X.w});
     const f2 e2x = {TE.x, TE.y}, e2y = {TE.z, TE.w}, f2x = {TF.x, TF.y}, f2y = {TF.z, TF.w};
-    const int gl = lane >> 1, jb = (lane & 1) * 4;
+    const int gl = lane & 15, half = lane >> 4;
     const float2 LX = a.tab->lx2[gl], LW = a.tab->lw2[gl];
     const f2 lx = {LX.x, LX.y}, lw = {LW.x, LW.y};
-    f2 gr[4], glr[4], gwl[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const float2 r = a.tab->gr2[jb + q], lr = a.tab->glr2[jb + q], gw = a.tab->gwl2[jb + q];
-        gr[q] = {r.x, r.y};
-        glr[q] = {lr.x, lr.y};
-        gwl[q] = {gw.x, gw.y};
-    }
-    float mh[VP_NB], ml[VP_NB];
-#pragma unroll
-    for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
-    // The three sides' FP64 geometry (it fixes the dyadic panels exactly as
-    // the FP64 scheme does), side e on lane e: the FP64 pipe is charged per
-    // warp instruction, so one instruction serves all three sides.
+    // The three sides' FP64 geometry, side e on lane e (the FP64 pipe is
+    // charged per warp instruction: one instruction serves all three sides).
     double gL = 0.0, gh = 0.0;
     f2 ginvL = {0.f, 0.f}, gst = {0.f, 0.f};
     int gnd0 = -1, gnd1 = -1;            // -1: no panels on that half of the side
@@ -823,13 +868,36 @@ __global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(We
             gst = f2_from_d(st);
         }
     }
-    int panels = 0;
+    const f2 gL2 = f2_from_d(gL), gh2 = f2_from_d(gh);
+    // panels of the six (side, half) segments, in the order side 0 half 0, ...
+    int cnt[6], total = 0;
+#pragma unroll
     for (int e = 0; e < 3; e++) {
-        const double L = __shfl_sync(0xffffffffu, gL, e), h = __shfl_sync(0xffffffffu, gh, e);
-        const int nd0 = __shfl_sync(0xffffffffu, gnd0, e), nd1 = __shfl_sync(0xffffffffu, gnd1, e);
+        cnt[2 * e] = __shfl_sync(0xffffffffu, gnd0, e) + 1;
+        cnt[2 * e + 1] = __shfl_sync(0xffffffffu, gnd1, e) + 1;
+        total += cnt[2 * e] + cnt[2 * e + 1];
+    }
+    const f2 u0 = f2_axpb(xi0, 3.0f, -1.0f), v0 = f2_axpb(eta0, 3.0f, -1.0f);   // the target's (u, v)
+    float mh[VP_NB], ml[VP_NB];
+#pragma unroll
+    for (int q = 0; q < VP_NB; q++) mh[q] = ml[q] = 0.f;
+    for (int pb = 0; pb < total; pb += 2) {
+        const int pi = pb + half;
+        const bool active = pi < total;
+        int i = active ? pi : total - 1, seg = 0, Nd = cnt[0] - 1;
+#pragma unroll
+        for (int k = 0; k < 5; k++)            // the segment of panel i (static indices: registers)
+            if (seg == k && i >= cnt[k]) {
+                i -= cnt[k];
+                seg = k + 1;
+                Nd = cnt[k + 1] - 1;
+            }
+        const int e = seg >> 1, side = seg & 1;
+        const f2 L2 = {__shfl_sync(0xffffffffu, gL2.h, e), __shfl_sync(0xffffffffu, gL2.l, e)};
+        const f2 h2 = {__shfl_sync(0xffffffffu, gh2.h, e), __shfl_sync(0xffffffffu, gh2.l, e)};
         const f2 invL = {__shfl_sync(0xffffffffu, ginvL.h, e), __shfl_sync(0xffffffffu, ginvL.l, e)};
         const f2 st2 = {__shfl_sync(0xffffffffu, gst.h, e), __shfl_sync(0xffffffffu, gst.l, e)};
-        if (L == 0.0 || h == 0.0) continue;
+        if (!active) continue;
         // the side in float-float: P - x, Q - P, and in reference coordinates
         const f2 pxr = e == 0 ? ax : f2_add(ax, e == 1 ? e2x : f2x);
         const f2 pyr = e == 0 ? ay : f2_add(ay, e == 1 ? e2y : f2y);
@@ -839,51 +907,32 @@ __global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(We
         const float dref_x = e == 0 ? 1.f : (e == 1 ? -1.f : 0.f);                   // Q - P there
         const float dref_y = e == 0 ? 0.f : (e == 1 ? 1.f : -1.f);
         const f2 xiP = f2_add_f(f2_neg(xi0), pref_x), etaP = f2_add_f(f2_neg(eta0), pref_y);   // P - x, reference
-        const f2 h2 = f2_from_d(h), L2 = f2_from_d(L);
-        for (int side = 0; side < 2; side++) {
-            const int Nd = side == 0 ? nd0 : nd1;
-            if (Nd < 0) continue;
-            const f2 len2 = side == 0 ? st2 : f2_add(L2, f2_neg(st2));
-            // panel boundaries: b_0 = end, b_i = end -/+ (1 - 2^-i) len, b_{Nd+1} = st
-            f2 b0 = side == 0 ? f2{0.f, 0.f} : L2;
-            for (int i = 0; i <= Nd; i++) {
-                f2 b1;
-                if (i == Nd) {
-                    b1 = st2;
-                } else {
-                    const int k = i + 1;                                      // 1 - 2^-k, exact as a pair
-                    const f2 om = k <= 24 ? f2{__fsub_rn(1.f, __int_as_float((127 - k) << 23)), 0.f}
-                                          : f2{1.f, -__int_as_float((127 - min(k, 126)) << 23)};
-                    const f2 frac = f2_mul(len2, om);
-                    b1 = side == 0 ? frac : f2_add(L2, f2_neg(frac));
-                }
-                panels++;
-                const f2 D = f2_add(b1, f2_neg(b0));
-                const f2 s = f2_add(b0, f2_mul(D, lx));
-                f2 wd = f2_mul(D, lw);
-                if (wd.h < 0.f) wd = f2_neg(wd);
-                const f2 ws = f2_mul(wd, h2);
-                const f2 sl = f2_mul(s, invL);
-                const f2 rx = f2_add(pxr, f2_mul(sl, sdx)), ry = f2_add(pyr, f2_mul(sl, sdy));
-                const f2 r2 = f2_add(f2_sqr(rx), f2_sqr(ry));
-                f2 lg;
-                if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);
-                else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
-                const f2 lr0 = f2_scale(lg, 0.5f);                            // log r0
-                const f2 xig = f2_add(xiP, f2_scale(sl, dref_x)), etag = f2_add(etaP, f2_scale(sl, dref_y));
-                const f2 al = f2_mulf(xig, 3.0f), be = f2_mulf(etag, 3.0f);   // (u, v) = (u0, v0) + r (al, be)
+        const f2 len2 = side == 0 ? st2 : f2_add(L2, f2_neg(st2));
+        const f2 b0 = self_bound(i, Nd, side, L2, st2, len2), b1 = self_bound(i + 1, Nd, side, L2, st2, len2);
+        const f2 D = f2_add(b1, f2_neg(b0));
+        const f2 s = f2_add(b0, f2_mul(D, lx));
+        f2 wd = f2_mul(D, lw);
+        if (wd.h < 0.f) wd = f2_neg(wd);
+        const f2 ws = f2_mul(wd, h2);
+        const f2 sl = f2_mul(s, invL);
+        const f2 rx = f2_add(pxr, f2_mul(sl, sdx)), ry = f2_add(pyr, f2_mul(sl, sdy));
+        const f2 r2 = f2_add(f2_sqr(rx), f2_sqr(ry));
+        f2 lg;
+        if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);
+        else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
+        const f2 lr0 = f2_scale(lg, 0.5f);                                // log r0
+        const f2 al = f2_mulf(f2_add(xiP, f2_scale(sl, dref_x)), 3.0f);   // (u, v) = (u0, v0) + r (al, be)
+        const f2 be = f2_mulf(f2_add(etaP, f2_scale(sl, dref_y)), 3.0f);
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const f2 g = f2_mul(f2_add(lr0, glr[q]), f2_mul(ws, gwl[q]));
-                    f2_mon15_acc_uv(mh, ml, g, f2_add(f2_mul(gr[q], al), u0), f2_add(f2_mul(gr[q], be), v0));
-                }
-                b0 = b1;
-            }
+        for (int q = 0; q < VP_NRAD; q++) {
+            const float2 R = a.tab->rr2[q], A = a.tab->ra2[q], B = a.tab->rb2[q];
+            const f2 g = f2_mul(ws, f2_add(f2_mul(lr0, {A.x, A.y}), {B.x, B.y}));
+            f2_mon15_acc_uv(mh, ml, g, f2_add(f2_mul({R.x, R.y}, al), u0), f2_add(f2_mul({R.x, R.y}, be), v0));
         }
     }
     finish_pair_f2(a, b, p, T, t, own, mh, ml, lane, ftab, lt, ln2);
     if (lane == 0) {
-        a.pstat[p] = panels;
+        a.pstat[p] = total;
         a.pcap[p] = 0;
     }
 }
@@ -959,6 +1008,19 @@ static WeightsF2 weights_f2_prepare(const WeightsArgs& a, cudaStream_t s, char*&
 
 static __global__ void k_set_flag(int32_t* flag, int32_t bits) { atomicOr(flag, bits); }
 
+// Resident blocks per SM of the persistent weight kernels (weights_module_prepare).
+static struct {
+    int deep = 1, root = 1;
+} g_occ;
+
+// Blocks of a persistent launch over n units, per_block units a block: no
+// more than fill the GPU once.
+static unsigned persistent_grid(const vp_ctx* ctx, int64_t n, int per_block, int occ) {
+    const int64_t need = (n + per_block - 1) / per_block;
+    const int64_t full = (int64_t)std::max(ctx->sm_count, 1) * std::max(occ, 1);
+    return (unsigned)std::max<int64_t>(1, std::min(need, full));
+}
+
 // The deep near pairs: leaf counts, their scan, the leaf records, the
 // evaluation (k_near_deep_leaves, k_weights_near_deep).
 static void near_deep(const WeightsArgs& a, const WeightsF2& b, const int32_t* deep_idx, int64_t n_deep, cudaStream_t s,
@@ -981,8 +1043,8 @@ static void near_deep(const WeightsArgs& a, const WeightsF2& b, const int32_t* d
         cudaStreamSynchronize(s) == cudaSuccess &&
         cudaMalloc(&recs, std::max<int64_t>(total, 1) * sizeof(LeafRec)) == cudaSuccess) {
         k_near_deep_leaves<<<gt, 128, 0, s>>>(a, b, deep_idx, n_deep, 1, cnt, off, recs);
-        k_weights_near_deep<<<(unsigned)((n_deep + WARPS - 1) / WARPS), WARPS * 32, 0, s>>>(a, b, deep_idx, n_deep, off,
-                                                                                         recs);
+        k_weights_near_deep<<<persistent_grid(ctx, n_deep, WARPS, g_occ.deep), WARPS * 32, 0, s>>>(a, b, deep_idx,
+                                                                                                   n_deep, off, recs);
     } else {
         k_set_flag<<<1, 1, 0, s>>>(a.flag, VP_DEV_ERR_ALLOC);
     }
@@ -1022,11 +1084,18 @@ void launch_weights(const WeightsArgs& a, const int32_t* self_idx, int64_t n_sel
         cudaStreamSynchronize(s);
         const int64_t n_root = (int64_t)h_cnt[0], n_deep = (int64_t)h_cnt[1];
         if (n_root > 0)
-            k_weights_near_root<<<(unsigned)((n_root + WARPS * RPW - 1) / (WARPS * RPW)), WARPS * 32, 0, s>>>(
+            k_weights_near_root<<<persistent_grid(ctx, n_root, WARPS * RPW, g_occ.root), WARPS * 32, 0, s>>>(
                 a, b, root_idx, n_root);
         if (n_deep > 0) near_deep(a, b, deep_idx, n_deep, s, ctx);
     });
 }
 
 // Loads this unit's log table on the current device (vp_create).
-cudaError_t weights_module_prepare() { return ensure_logtab(); }
+cudaError_t weights_module_prepare() {
+    cudaError_t e = ensure_logtab();
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ.deep, k_weights_near_deep, WARPS * 32, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ.root, k_weights_near_root, WARPS * 32, 0);
+    return e;
+}

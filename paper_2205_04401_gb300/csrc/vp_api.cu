@@ -79,20 +79,20 @@ void fill_tables(VpTables& t) {
         }
     }
     for (int j = 0; j < VP_NNEAR; j++) {
-        t.nx[j] = VP_NEAR49_X[j];
-        t.ny[j] = VP_NEAR49_Y[j];
-        t.nw[j] = VP_NEAR49_W[j];
+        t.nx[j] = VP_NEAR33_X[j];
+        t.ny[j] = VP_NEAR33_Y[j];
+        t.nw[j] = VP_NEAR33_W[j];
     }
     auto split = [](double d) {
         const float h = (float)d;
         return make_float2(h, (float)(d - (double)h));
     };
     for (int j = 0; j < VP_NNEAR; j++) {
-        const float2 x = split(VP_NEAR49_X[j]), y = split(VP_NEAR49_Y[j]);
+        const float2 x = split(VP_NEAR33_X[j]), y = split(VP_NEAR33_Y[j]);
         t.nz2[j] = make_float4(x.x, x.y, y.x, y.y);
-        const float2 x3 = split(3.0 * VP_NEAR49_X[j]), y3 = split(3.0 * VP_NEAR49_Y[j]);
+        const float2 x3 = split(3.0 * VP_NEAR33_X[j]), y3 = split(3.0 * VP_NEAR33_Y[j]);
         t.nz3[j] = make_float4(x3.x, x3.y, y3.x, y3.y);
-        t.nw2[j] = split(VP_NEAR49_W[j]);
+        t.nw2[j] = split(VP_NEAR33_W[j]);
     }
     for (int r = 0; r < 2; r++)
         for (int k = 0; k < nq[r]; k++)
@@ -107,8 +107,13 @@ void fill_tables(VpTables& t) {
         t.glr2[j] = split(std::log(VP_GGQ8_R[j]));
         t.gwl2[j] = split(VP_GGQ8_W[j] * VP_INV_TWO_PI);
     }
-    t.near_what = VP_NEAR49_WHAT;
-    t.near_degree = VP_NEAR49_DEGREE;
+    for (int j = 0; j < VP_NRAD; j++) {
+        t.rr2[j] = split(VP_RAD5_R[j]);
+        t.ra2[j] = split(VP_RAD5_A[j] * VP_INV_TWO_PI);
+        t.rb2[j] = split(VP_RAD5_B[j] * VP_INV_TWO_PI);
+    }
+    t.near_what = VP_NEAR33_WHAT;
+    t.near_degree = VP_NEAR33_DEGREE;
     for (int j = 0; j < VP_NGGQ; j++) {
         t.gr[j] = VP_GGQ8_R[j];
         t.gw[j] = VP_GGQ8_W[j];
@@ -1443,7 +1448,7 @@ int vp_rule_table(int32_t which, double* x, double* y, double* w, double* what, 
     switch (which) {
         case 16: X = VP_FAR16_X; Y = VP_FAR16_Y; Wt = VP_FAR16_W; wh = VP_FAR16_WHAT; len = 16; break;
         case 19: X = VP_FAR19_X; Y = VP_FAR19_Y; Wt = VP_FAR19_W; wh = VP_FAR19_WHAT; len = 19; break;
-        case 49: X = VP_NEAR49_X; Y = VP_NEAR49_Y; Wt = VP_NEAR49_W; wh = VP_NEAR49_WHAT; len = 49; break;
+        case 33: X = VP_NEAR33_X; Y = VP_NEAR33_Y; Wt = VP_NEAR33_W; wh = VP_NEAR33_WHAT; len = 33; break;
         case 8: X = VP_GGQ8_R; Wt = VP_GGQ8_W; len = 8; break;
         case 116: X = VP_GL16_X; Wt = VP_GL16_W; len = 16; break;
         default: return VP_ERR_INVALID_ARG;

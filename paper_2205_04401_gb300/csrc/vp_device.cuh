@@ -6,9 +6,10 @@
 
 #define VP_NB 15            // dim P_4
 #define VP_MAXQ 19          // largest far rule
-#define VP_NNEAR 49         // near rule length
+#define VP_NNEAR 33         // near rule length
 #define VP_NGGQ 8
 #define VP_NGL 16
+#define VP_NRAD 5           // radial rule of the float-float self weights
 #define VP_INV_TWO_PI 0.15915494309189533576888376337251
 #define VP_INV_FOUR_PI 0.079577471545947667884441881686257
 
@@ -40,6 +41,7 @@ struct VpTables {
     float2 B2[2][VP_NNEAR * VP_MAXQ];
     float2 lx2[VP_NGL], lw2[VP_NGL];    // Gauss-Legendre nodes and weights on [0, 1]
     float2 gr2[VP_NGGQ], glr2[VP_NGGQ], gwl2[VP_NGGQ];   // GGQ nodes, their logs, weights / 2pi
+    float2 rr2[VP_NRAD], ra2[VP_NRAD], rb2[VP_NRAD];     // radial nodes, weights / 2pi of r p and r log(r) p
 };
 
 // Tensor-Legendre basis of P_4 used to accumulate moments on the device:

@@ -1,8 +1,9 @@
 // Far rules (Section 3.2) on the host: the two built-in S3-symmetric rules of
-// degree 8 and 9, and generated conical-product rules of any total degree
-// n in [VP_RULE_CONICAL_MIN, VP_RULE_CONICAL_MAX] for the order sweep of
-// Section 4.2 (raising the far order N_f offloads near-field work to the far
-// sum).  A conical-product rule maps the Gauss-Legendre rule of
+// degree 8 and 9, the tabulated S3-symmetric rules of degree 12-50
+// (VP_RULE_SYM(n), vp_tables.h) and generated conical-product rules of any
+// total degree n in [VP_RULE_CONICAL_MIN, VP_RULE_CONICAL_MAX], for the order
+// sweep of Section 4.2 (raising the far order N_f offloads near-field work to
+// the far sum).  A conical-product rule maps the Gauss-Legendre rule of
 // m = floor((n + 3)/2) points on [0, 1]^2 to the simplex by
 // (u, v) -> (u, (1 - u) v) with Jacobian (1 - u):
 //   node k = i m + j:  x = u_i,  y = (1 - u_i) u_j,  w = a_i a_j (1 - u_i),
@@ -176,7 +177,7 @@ void projection_q(const Rule& r, std::vector<double>& Q, std::vector<double>& QM
 void root_leaf_map(const double* QM, int nq, float2* B2) {
     for (int j = 0; j < VP_NNEAR; j++) {
         long double M[VP_NB];
-        mon15_ld(VP_NEAR49_X[j], VP_NEAR49_Y[j], M);
+        mon15_ld(VP_NEAR33_X[j], VP_NEAR33_Y[j], M);
         for (int k = 0; k < nq; k++) {
             long double b = 0.0L;
             for (int i = 0; i < VP_NB; i++) b += (long double)QM[(size_t)k * VP_NB + i] * M[i];
@@ -193,12 +194,38 @@ bool conical_code(int32_t rule) {
     return rule >= VP_RULE_CONICAL(VP_RULE_CONICAL_MIN) && rule <= VP_RULE_CONICAL(VP_RULE_CONICAL_MAX);
 }
 
+// The tabulated S3-symmetric rule of VP_RULE_SYM(n), or null.
+const VpSymRule* sym_entry(int32_t rule) {
+    for (const VpSymRule& r : VP_SYM_RULES)
+        if (rule == VP_RULE_SYM(r.degree)) return &r;
+    return nullptr;
+}
+
+Rule sym_rule(const VpSymRule& t) {
+    Rule r;
+    r.degree = t.degree;
+    r.x.assign(t.x, t.x + t.n);
+    r.y.assign(t.y, t.y + t.n);
+    r.w.assign(t.w, t.w + t.n);
+    r.what = t.what;
+    return r;
+}
+
+// A generated (conical) or tabulated (symmetric) far rule.
+Rule host_rule(int32_t rule) {
+    if (const VpSymRule* t = sym_entry(rule)) return sym_rule(*t);
+    return conical_rule(rule - VP_RULE_CONICAL(0));
+}
+
 }  // namespace
 
-bool far_rule_valid(int32_t rule) { return rule == VP_RULE_16_D8 || rule == VP_RULE_19_D9 || conical_code(rule); }
+bool far_rule_valid(int32_t rule) {
+    return rule == VP_RULE_16_D8 || rule == VP_RULE_19_D9 || conical_code(rule) || sym_entry(rule);
+}
 
 int far_rule_nq(int32_t rule) {
     if (rule == VP_RULE_16_D8 || rule == VP_RULE_19_D9) return rule;
+    if (const VpSymRule* t = sym_entry(rule)) return t->n;
     if (!conical_code(rule)) return 0;
     const int m = (rule - VP_RULE_CONICAL(0) + 3) / 2;
     return m * m;
@@ -224,14 +251,14 @@ int far_rule_get(vp_ctx* ctx, int32_t rule, FarRule* out) {
         *out = r;
         return VP_OK;
     }
-    if (!conical_code(rule)) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "unknown far rule");
+    if (!conical_code(rule) && !sym_entry(rule)) return vp_set_error(ctx, VP_ERR_INVALID_ARG, "unknown far rule");
     std::lock_guard<std::mutex> lk(ctx->rule_mu);
     for (const FarRule& r : ctx->gen_rules)
         if (r.code == rule) {
             *out = r;
             return VP_OK;
         }
-    const Rule g = conical_rule(rule - VP_RULE_CONICAL(0));
+    const Rule g = host_rule(rule);
     const int nq = (int)g.w.size();
     std::vector<double> Q, QM;
     projection_q(g, Q, QM);
@@ -291,7 +318,7 @@ extern "C" int vp_far_rule(int32_t rule, double* x, double* y, double* w, double
         g.what = r16 ? VP_FAR16_WHAT : VP_FAR19_WHAT;
         g.degree = r16 ? VP_FAR16_DEGREE : VP_FAR19_DEGREE;
     } else {
-        g = conical_rule(rule - VP_RULE_CONICAL(0));
+        g = host_rule(rule);
     }
     const int32_t len = (int32_t)g.w.size();
     if (n) *n = len;

@@ -26,9 +26,19 @@ VP_RULE_CONICAL_MIN = 8
 VP_RULE_CONICAL_MAX = 50
 
 
+VP_RULE_SYM_DEGREES = (12, 20, 25, 30, 40)
+
+
 def VP_RULE_CONICAL(n: int) -> int:
     """Rule code of the conical-product Gauss far rule of total degree n (vp.h)."""
     return 1000 + int(n)
+
+
+def VP_RULE_SYM(n: int) -> int:
+    """Rule code of the tabulated S3-symmetric far rule of degree n (vp.h)."""
+    return 2000 + int(n)
+
+
 VP_FP64 = 0
 VP_MIXED = 1
 VP_MIXED_TC = 2
@@ -710,7 +720,8 @@ def pinned_empty(shape):
 
 
 def far_rule(rule: int):
-    """(x, y, w, what, degree) of a far rule: VP_RULE_16_D8, VP_RULE_19_D9 or VP_RULE_CONICAL(n)."""
+    """(x, y, w, what, degree) of a far rule: VP_RULE_16_D8, VP_RULE_19_D9, VP_RULE_CONICAL(n) or
+    VP_RULE_SYM(n)."""
     lib = load()
     n = C.c_int32()
     what = C.c_double()

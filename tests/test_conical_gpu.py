@@ -1,10 +1,12 @@
-"""GPU parity with the conical-product far rules of the far-order sweep
+"""GPU parity with the higher-order far rules of the far-order sweep
 (Section 4.2: raising the far order N_f offloads near-field work to the far
-sum), through the C ABI against the FP64 oracle.
+sum), through the C ABI against the FP64 oracle: the conical-product rules
+and the S3-symmetric ones (about half the nodes).
 
-The rules are generated independently on both sides (host long double in the
-library, 60-digit arithmetic in the oracle) and agree to one unit in the last
-place, so node coordinates are compared to a few units in the last place;
+The rules are generated independently on both sides (conical: host long
+double in the library, 60-digit arithmetic in the oracle, equal to one unit
+in the last place; symmetric: two Newton solvers in 90 digits, equal bit for
+bit), so node coordinates are compared to a few units in the last place;
 everything else keeps the bars of the built-in rules: lists bit-exact,
 weights within 1e-12 max|C| + 1e-13 |J_T| (1e-15 |J_T| with FP64 node
 quadratures), FP64 potential 1e-12, mixed and FMM potentials 1e-10.  Rules
@@ -81,17 +83,25 @@ def check_weights(Cg, Co, J, ptri, jtol):
 
 
 # 256-triangle disk, extra targets (interior, near vertices and edges, outside)
-@pytest.fixture(scope="module", params=[12, 30])
+def far_rule(vp, tables, family, deg):
+    """(oracle rule, library rule code) of a sweep rule."""
+    if family == "sym":
+        return f"sym{deg}", vp.VP_RULE_SYM(deg)
+    return gen_rules.conical_rule(deg), vp.VP_RULE_CONICAL(deg)
+
+
+@pytest.fixture(scope="module", params=[("conical", 12), ("conical", 30), ("sym", 20), ("sym", 40)],
+                ids=lambda p: f"{p[0]}{p[1]}")
 def disk_extra(request, vp, ctx, tables):
-    deg = request.param
+    family, deg = request.param
     mesh, dens = inputs.config1()
     extra = np.concatenate([inputs.random_interior_points(mesh, 300, 11),
                             mesh.vxy[::7] + 1e-9, [[1.01, 0.02], [0.0, -1.2]]])
-    o = Oracle(gen_rules.conical_rule(deg), tables=tables, far_cn=CN_TABLE[deg])
+    orule, rule = far_rule(vp, tables, family, deg)
+    o = Oracle(orule, tables=tables, far_cn=CN_TABLE[deg])
     s = o.setup(mesh.vxy, mesh.tri, node_targets=False, extra=extra)
     f = np.stack([d(s["yxy"]) for d in dens])
     u_or, info = o.potential(s, f)
-    rule = vp.VP_RULE_CONICAL(deg)
     g = run(vp, ctx, mesh, rule, CN_TABLE[deg], f, extra=extra, node_targets=False)
     g64 = run(vp, ctx, mesh, rule, CN_TABLE[deg], f, extra=extra, node_targets=False, fp64_weights=True,
               precisions=(0,))
@@ -125,25 +135,28 @@ def test_conical_potentials(disk_extra):
     assert rel_err(g["u3"], u_or).max() <= 1e-10
 
 
-# 18-triangle disk, node targets, the degree-50 rule (676 nodes per triangle):
-# own-node skipping in the far sum and the subtraction, the symmetric far sum
-# and 22 node groups per pair in the moment-to-weight step
-@pytest.fixture(scope="module")
-def tiny_nodes(vp, ctx, tables):
+# 18-triangle disk, node targets, the conical rule of degree 50 (676 nodes per
+# triangle) and the symmetric one of degree 40 (295): own-node skipping in the
+# far sum and the subtraction, the symmetric far sum and 22 / 10 node groups
+# per pair in the moment-to-weight step
+@pytest.fixture(scope="module", params=[("conical", 50), ("sym", 40)], ids=lambda p: f"{p[0]}{p[1]}")
+def tiny_nodes(request, vp, ctx, tables):
     mesh = inputs.disk_mesh(n_b=10, n_i=5)
-    o = Oracle(gen_rules.conical_rule(50), tables=tables, far_cn=CN_TABLE[50])
+    family, deg = request.param
+    orule, rule = far_rule(vp, tables, family, deg)
+    o = Oracle(orule, tables=tables, far_cn=CN_TABLE[deg])
     s = o.setup(mesh.vxy, mesh.tri)
     y = s["yxy"]
     f = np.stack([1.0 + 0.0 * y[:, 0], np.exp(-4.0 * ((y[:, 0] - 0.2) ** 2 + (y[:, 1] + 0.1) ** 2))])
     u_or, info = o.potential(s, f)
-    g = run(vp, ctx, mesh, vp.VP_RULE_CONICAL(50), CN_TABLE[50], f)
-    one = run(vp, ctx, mesh, vp.VP_RULE_CONICAL(50), CN_TABLE[50], f[1:])   # d = 1: symmetric far sum
-    return s, u_or, info, g, one
+    g = run(vp, ctx, mesh, rule, CN_TABLE[deg], f)
+    one = run(vp, ctx, mesh, rule, CN_TABLE[deg], f[1:])   # d = 1: symmetric far sum
+    return family, s, u_or, info, g, one
 
 
-def test_conical50_node_targets(tiny_nodes):
-    s, u_or, info, g, one = tiny_nodes
-    assert s["N"] == 18 * 676
+def test_high_order_node_targets(tiny_nodes):
+    family, s, u_or, info, g, one = tiny_nodes
+    assert s["N"] == 18 * (676 if family == "conical" else 295)
     check_nodes(g, s)
     check_lists(g, s, info)
     check_weights(g["C"], info["C"], s["J"], info["ptri"], 1e-13)
@@ -165,18 +178,18 @@ def test_conical_refused_where_unsupported(vp, ctx):
 
 @pytest.mark.parametrize("prec", [1, 3])
 def test_conical_rules_in_a_batch(vp, ctx, prec):
-    """Meshes on different far rules (a conical rule of degree 20 among the
-    built-in ones) in one graph-captured batch, direct (run-time node count
+    """Meshes on different far rules (a conical rule of degree 20 and a
+    symmetric one of degree 30 beside a built-in one) in one graph-captured batch, direct (run-time node count
     in the batched apply) and with the FMM: each item equals its single
     evaluation (FMM: bit for bit; direct: to 1e-12, the FP64 parity bar: the
     batched far sum is one-sided where the single evaluation is symmetric, so
     its FP64 partial sums are added in another order)."""
     meshes = [(inputs.disk_uniform_mesh(300, 11, 2), vp.VP_RULE_CONICAL(20)),
-              (inputs.lshape_mesh(400, 12, 2), 19), (inputs.disk_mesh(n_b=10, n_i=5), vp.VP_RULE_CONICAL(30))]
+              (inputs.lshape_mesh(400, 12, 2), 19), (inputs.disk_mesh(n_b=10, n_i=5), vp.VP_RULE_SYM(30))]
     items, refs, keep = [], [], []
     for k, (mesh, rule) in enumerate(meshes):
         m = vp.mesh_upload(ctx, mesh.vxy, mesh.tri, rule)
-        nf = vp.nearfield_build(ctx, m, node_targets=True, c_far=CN_TABLE.get(rule - 1000, 1.0) if rule > 1000 else 1.0)
+        nf = vp.nearfield_build(ctx, m, node_targets=True, c_far=CN_TABLE.get(rule % 1000, 1.0) if rule > 1000 else 1.0)
         y, _ = vp.mesh_nodes(m)
         yn = y.cpu().numpy()
         f = torch.from_numpy(np.stack([np.cos(2 * yn[:, 0] + k) * yn[:, 1] + 1.0])).cuda()

@@ -25,7 +25,7 @@ def max_moment_error(x, y, w, degree):
     return err
 
 
-@pytest.mark.parametrize("name,n,degree", [("far16", 16, 8), ("far19", 19, 9), ("near49", 49, 12)])
+@pytest.mark.parametrize("name,n,degree", [("far16", 16, 8), ("far19", 19, 9), ("near33", 33, 12)])
 def test_triangle_rule_exact(tables, name, n, degree):
     r = tables[name]
     x, y, w = r["x"], r["y"], r["w"]
@@ -38,7 +38,7 @@ def test_triangle_rule_exact(tables, name, n, degree):
     assert max_moment_error(x, y, w, degree + 1) > 1e-10
 
 
-@pytest.mark.parametrize("name", ["far16", "far19"])
+@pytest.mark.parametrize("name", ["far16", "far19", "near33"] + [f"sym{d}" for d in (12, 20, 25, 30, 40)])
 def test_far_rule_symmetric(tables, name):
     r = tables[name]
     pts = np.c_[1 - r["x"] - r["y"], r["x"], r["y"]]
@@ -72,7 +72,7 @@ def test_ggq8(tables):
 def test_what(tables):
     """w of Eq. rho0: largest weight among the ceil((N+1)/2) nodes closest to
     an edge, max over edges (reading of the '~n/2 nodes' passage)."""
-    for name in ["far16", "far19", "near49"]:
+    for name in ["far16", "far19", "near33"]:
         r = tables[name]
         k = (r["degree"] + 2) // 2
         dists = [r["y"], r["x"], (1 - r["x"] - r["y"]) / np.sqrt(2)]
@@ -89,7 +89,7 @@ def test_oracle_basis_orthonormal(tables):
     8 products, integrated exactly by the degree-12 rule) and spans P_4."""
     from oracle.oracle import Oracle
     o = Oracle("far19", tables=tables)
-    nr = tables["near49"]
+    nr = tables["near33"]
     K = o.basis(nr["x"], nr["y"])
     Gm = (K * nr["w"][:, None]).T @ K
     assert np.abs(Gm - np.eye(15)).max() < 1e-13
@@ -156,3 +156,66 @@ def test_conical_projection_exact():
     x, y, w = (np.array(r[k]) for k in "xyw")
     K = o.basis(x, y)
     assert np.abs((K * w[:, None]).T @ K - np.eye(15)).max() < 1e-13
+
+
+# S3-symmetric far rules of Section 4.2's orders, with the node counts of the
+# orbit structures (the paper's Xiao-Gimbutas rules: 32 at degree 12, 290 at
+# 40, 444 at 50; the conical rules of the same degrees have 49 ... 676).
+SYM = {12: 33, 20: 81, 25: 124, 30: 175, 40: 295}
+
+
+def exact_moment_error(x, y, w, degree):
+    """max over x^i y^j, i + j <= degree, of |sum w x^i y^j - i! j! / (i+j+2)!|
+    relative to the moment, the sum taken exactly from the stored doubles."""
+    X = [Fraction(v) for v in x]
+    Y = [Fraction(v) for v in y]
+    W = [Fraction(v) for v in w]
+    err = 0.0
+    px = [[Fraction(1)] * len(X)]
+    for _ in range(degree):
+        px.append([a * b for a, b in zip(px[-1], X)])
+    py = [[Fraction(1)] * len(Y)]
+    for _ in range(degree):
+        py.append([a * b for a, b in zip(py[-1], Y)])
+    for n in range(degree + 1):
+        for i in range(n + 1):
+            j = n - i
+            q = sum(wk * a * b for wk, a, b in zip(W, px[i], py[j]))
+            ex = simplex_moment(i, j)
+            err = max(err, float(abs(q - ex) / ex))
+    return err
+
+
+@pytest.mark.parametrize("degree", sorted(SYM))
+def test_symmetric_rule_exact(tables, degree):
+    """The S3-symmetric far rule of each sweep degree: every monomial of degree
+    <= n integrated to rounding (the sum of the stored doubles in exact
+    arithmetic against i! j! / (i + j + 2)!), positive weights, nodes strictly
+    inside, the stated node count, and not exact one degree higher."""
+    r = tables[f"sym{degree}"]
+    x, y, w = r["x"], r["y"], r["w"]
+    assert len(w) == SYM[degree] and r["degree"] == degree
+    assert np.all(w > 0) and np.all(x > 0) and np.all(y > 0) and np.all(x + y < 1)
+    # positive terms: the rounding of the stored nodes moves each moment by a
+    # few units of 1e-16 relative, whatever its size
+    assert exact_moment_error(x, y, w, degree) < 1e-13
+    assert max_moment_error(x, y, w, degree + 1) > 1e-17
+
+
+def test_near_rule_is_sym12(tables):
+    """The near rule (order 12, Section 5.1) is the degree-12 symmetric rule."""
+    a, b = tables["near33"], tables["sym12"]
+    for k in "xyw":
+        assert np.array_equal(a[k], b[k])
+    assert a["what"] == b["what"]
+
+
+@pytest.mark.parametrize("degree", sorted(SYM))
+def test_symmetric_what(tables, degree):
+    """w-hat (Eq. rho0) of a symmetric rule is one of its weights: the largest
+    among the (n + 2) // 2 nodes nearest the edge y = 0 (all three edges give
+    the same by symmetry), found here by sorting the distances directly."""
+    r = tables[f"sym{degree}"]
+    k = (degree + 2) // 2
+    order = np.lexsort((np.arange(len(r["y"])), r["y"]))[:k]
+    assert r["what"] == r["w"][order].max()
