@@ -29,7 +29,7 @@
 #include "vp_f2.cuh"
 
 #ifndef VP_AS_WARPS
-#define VP_AS_WARPS 16
+#define VP_AS_WARPS 18
 #endif
 #ifndef VP_AS_STAGES
 #define VP_AS_STAGES 2
