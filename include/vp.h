@@ -74,11 +74,11 @@ typedef enum vp_rule { VP_RULE_16_D8 = 16, VP_RULE_19_D9 = 19 } vp_rule;
 #define VP_RULE_CONICAL(n) (1000 + (n))
 #define VP_RULE_CONICAL_MIN 8
 #define VP_RULE_CONICAL_MAX 50
-/* VP_RULE_SYM(n), n in {12, 20, 25, 30, 40}: S3-symmetric rules of degree n
- * with positive weights and all nodes inside the simplex, about half the
- * nodes of the conical rule of the same degree (33, 81, 124, 175 and 295
- * nodes; the Xiao-Gimbutas rules the paper takes have 32 at degree 12 and
- * 290 at 40).  Each is the root of its S3-invariant moment
+/* VP_RULE_SYM(n), n in {12, 20, 25, 30, 40, 50}: S3-symmetric rules of
+ * degree n with positive weights and all nodes inside the simplex, about
+ * two-thirds of the nodes of the conical rule of the same degree (33, 81,
+ * 124, 175, 295 and 453 nodes; the Xiao-Gimbutas rules the paper takes have
+ * 32 at degree 12, 290 at 40 and 444 at 50).  Each is the root of its S3-invariant moment
  * equations next to an orbit structure found by orbit elimination (a
  * symmetrised product rule reduced one orbit at a time, the equations
  * restored by Gauss-Newton after each step), computed in 90-digit

@@ -268,10 +268,10 @@ def symmetric_far_rule(degree):
             step = mp.lu_solve(mp.matrix([[J[k][c] for c in free] for k in range(len(pairs))]), mp.matrix(R))
             for s, c in enumerate(free):
                 p[c] -= step[s]
-            if max(abs(v) for v in step) < mp.mpf(10) ** -70:
+            if max(abs(v) for v in step) < mp.mpf(10) ** -60:   # far below double precision
                 break
         R, _ = _sym_system(p, spec, pairs, exact)
-        assert max(abs(v) for v in R) < mp.mpf(10) ** -70
+        assert max(abs(v) for v in R) < mp.mpf(10) ** -60
         n21, n111 = len(spec["s21"]), len(spec["s111"])
         X, Y, W = [], [], []
         c = 0

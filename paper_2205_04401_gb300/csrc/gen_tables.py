@@ -255,10 +255,10 @@ def solve_sym_e23(deg, rule):
             dx = mp.lu_solve(mp.matrix([[J[r][c] for c in free] for r in range(len(idx))]), mp.matrix(R))
             for s_, c in enumerate(free):
                 p[c] -= dx[s_]
-            if max(abs(v) for v in dx) < mp.mpf(10) ** -70:
+            if max(abs(v) for v in dx) < mp.mpf(10) ** -60:   # far below double precision
                 break
         R, _ = system()
-        assert max(abs(v) for v in R) < mp.mpf(10) ** -70, deg
+        assert max(abs(v) for v in R) < mp.mpf(10) ** -60, deg
         pts = []
         c = 0
         for k in kinds:

@@ -116,8 +116,19 @@ __device__ __forceinline__ void accumulate(double* m, double g, double x, double
     for (int c = 1; c < VP_NB; c++) m[c] = fma(g, L[c], m[c]);
 }
 
-// N = min{n >= 0 : 2^-n len < dist}
+// N = min{n >= 0 : 2^-n len < dist}.  Scaling by 2^-n is exact, so for
+// positive normal len = m1 2^e1 and dist = m2 2^e2 (1 <= m < 2) the test
+// compares exponents, then mantissas: N = e1 - e2 + [m1 >= m2], at least 0.
+// Integer work on the bit patterns instead of an FP64 loop (GB300's FP64 pipe
+// is narrow); other operands take the loop.
 __device__ __forceinline__ int dyadic_count(double len, double dist) {
+    const long long bl = __double_as_longlong(len), bd = __double_as_longlong(dist);
+    const int el = (int)((bl >> 52) & 0x7ff), ed = (int)((bd >> 52) & 0x7ff);
+    if (bl > 0 && bd > 0 && el != 0 && ed != 0 && el != 0x7ff && ed != 0x7ff) {
+        const long long mask = (1LL << 52) - 1;
+        const int n = el - ed + ((bl & mask) >= (bd & mask) ? 1 : 0);
+        return n > 0 ? n : 0;
+    }
     int n = 0;
     while (ldexp(len, -n) >= dist && n < 1100) n++;
     return n;

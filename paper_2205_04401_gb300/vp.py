@@ -26,7 +26,7 @@ VP_RULE_CONICAL_MIN = 8
 VP_RULE_CONICAL_MAX = 50
 
 
-VP_RULE_SYM_DEGREES = (12, 20, 25, 30, 40)
+VP_RULE_SYM_DEGREES = (12, 20, 25, 30, 40, 50)
 
 
 def VP_RULE_CONICAL(n: int) -> int:

@@ -135,11 +135,11 @@ def test_conical_potentials(disk_extra):
     assert rel_err(g["u3"], u_or).max() <= 1e-10
 
 
-# 18-triangle disk, node targets, the conical rule of degree 50 (676 nodes per
-# triangle) and the symmetric one of degree 40 (295): own-node skipping in the
-# far sum and the subtraction, the symmetric far sum and 22 / 10 node groups
-# per pair in the moment-to-weight step
-@pytest.fixture(scope="module", params=[("conical", 50), ("sym", 40)], ids=lambda p: f"{p[0]}{p[1]}")
+# 18-triangle disk, node targets, the degree-50 rules (676 / 453 nodes per
+# triangle): own-node skipping in the far sum and the subtraction, the
+# symmetric far sum and 22 / 15 node groups per pair in the moment-to-weight
+# step
+@pytest.fixture(scope="module", params=[("conical", 50), ("sym", 50)], ids=lambda p: f"{p[0]}{p[1]}")
 def tiny_nodes(request, vp, ctx, tables):
     mesh = inputs.disk_mesh(n_b=10, n_i=5)
     family, deg = request.param
@@ -156,7 +156,7 @@ def tiny_nodes(request, vp, ctx, tables):
 
 def test_high_order_node_targets(tiny_nodes):
     family, s, u_or, info, g, one = tiny_nodes
-    assert s["N"] == 18 * (676 if family == "conical" else 295)
+    assert s["N"] == 18 * (676 if family == "conical" else 453)
     check_nodes(g, s)
     check_lists(g, s, info)
     check_weights(g["C"], info["C"], s["J"], info["ptri"], 1e-13)

@@ -38,7 +38,7 @@ def test_triangle_rule_exact(tables, name, n, degree):
     assert max_moment_error(x, y, w, degree + 1) > 1e-10
 
 
-@pytest.mark.parametrize("name", ["far16", "far19", "near33"] + [f"sym{d}" for d in (12, 20, 25, 30, 40)])
+@pytest.mark.parametrize("name", ["far16", "far19", "near33"] + [f"sym{d}" for d in (12, 20, 25, 30, 40, 50)])
 def test_far_rule_symmetric(tables, name):
     r = tables[name]
     pts = np.c_[1 - r["x"] - r["y"], r["x"], r["y"]]
@@ -161,7 +161,7 @@ def test_conical_projection_exact():
 # S3-symmetric far rules of Section 4.2's orders, with the node counts of the
 # orbit structures (the paper's Xiao-Gimbutas rules: 32 at degree 12, 290 at
 # 40, 444 at 50; the conical rules of the same degrees have 49 ... 676).
-SYM = {12: 33, 20: 81, 25: 124, 30: 175, 40: 295}
+SYM = {12: 33, 20: 81, 25: 124, 30: 175, 40: 295, 50: 453}
 
 
 def exact_moment_error(x, y, w, degree):
