@@ -1139,9 +1139,11 @@ def main():
     # correction weights: the paper's work counters per second (no roofline
     # fraction: their float-float instruction mix has no algorithmic count)
     n_near = len(vp.rule_table(33)[2])           # the near rule's length
+    n_rad = 8 if args.fp64_weights else 5        # radial points: GGQ-8 (FP64 kernel), 5-point rule (float-float)
     for k, cnt, what in (("weights_near", stats["near_leaves"] * n_near,
                           f"near-rule node evaluations (leaves x {n_near})"),
-                         ("weights_self", stats["self_panels"] * 16 * 8, "self panel points (panels x 16 x 8)")):
+                         ("weights_self", stats["self_panels"] * 16 * n_rad,
+                          f"self panel points (panels x 16 arc-length x {n_rad} radial)")):
         n_l, ms_l = prof.get(k, (0, 0.0))
         if n_l and ms_l > 0:
             rooflines[k] = {"bound": "alu", "units_per_s": round(cnt * args.steps / (ms_l / 1e3), 1),
