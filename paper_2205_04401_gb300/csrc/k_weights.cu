@@ -923,8 +923,8 @@ __global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(We
         const f2 lr0 = f2_scale(lg, 0.5f);                                // log r0
         const f2 al = f2_mulf(f2_add(xiP, f2_scale(sl, dref_x)), 3.0f);   // (u, v) = (u0, v0) + r (al, be)
         const f2 be = f2_mulf(f2_add(etaP, f2_scale(sl, dref_y)), 3.0f);
-#pragma unroll
-        for (int q = 0; q < VP_NRAD; q++) {
+#pragma unroll 1
+        for (int q = 0; q < VP_NRAD; q++) {   // not unrolled: the body stays in the instruction cache
             const float2 R = a.tab->rr2[q], A = a.tab->ra2[q], B = a.tab->rb2[q];
             const f2 g = f2_mul(ws, f2_add(f2_mul(lr0, {A.x, A.y}), {B.x, B.y}));
             f2_mon15_acc_uv(mh, ml, g, f2_add(f2_mul({R.x, R.y}, al), u0), f2_add(f2_mul({R.x, R.y}, be), v0));
