@@ -13,6 +13,11 @@ transposed map, a missing fan) fails at least one of them:
 * Bernstein-ellipse predicate against the complex-variable definition
   (Section 2.4) and against the true far-rule error map (Section 5.1).
 * dyadic panel counts of Section 3.4 on hand-checked cases.
+* the far sum against the same terms summed in 40-digit arithmetic.
+* the correction weights' scaling: C(2x) = 4 C(x) with eps scaled by 4
+  (the kernel's added constant must cancel between the near integral and
+  the far-rule subtraction).
+* Delta u = f by the 5-point stencil at interior points.
 """
 import math
 
@@ -336,3 +341,81 @@ def test_tiny_mesh_gaussian_brute_force(tables):
         for i, ti in enumerate(idx):
             ref[i] += X.fan_poly(s["txy"][ti], A, B, C, q) / (2 * math.pi)
     assert np.abs(u[0] - ref).max() < 1e-11
+
+
+def test_far_sum_matches_extended_precision(disk_setup, o16):
+    """The far sum (step 2 of the oracle: all nodes as charges, the target's
+    own node skipped) against the same sum of the same terms in 40-digit
+    arithmetic, on node targets (own node skipped) and on one point off the
+    nodes: within a few units of the last place of sum |term|."""
+    import mpmath as mp
+    s = disk_setup
+    rng = np.random.default_rng(7)
+    y, W = s["yxy"], s["W"]
+    f = np.cos(3 * y[:, 0]) * np.exp(y[:, 1]) + 0.5
+    idx = rng.choice(s["N"], 6, replace=False)
+    txy = np.vstack([y[idx], [[0.123456789, -0.2718281828]]])
+    tnode = np.concatenate([idx, [-1]]).astype(np.int64)
+    got = o16.far(y, W, f[None, :], txy, tnode)[0]
+    with mp.workdps(40):
+        for t in range(len(txy)):
+            tot, mag = mp.mpf(0), mp.mpf(0)
+            for j in range(s["N"]):
+                if j == tnode[t]:
+                    continue
+                dx = mp.mpf(txy[t, 0]) - mp.mpf(y[j, 0])
+                dy = mp.mpf(txy[t, 1]) - mp.mpf(y[j, 1])
+                term = mp.mpf(W[j]) * mp.mpf(f[j]) * mp.log(dx * dx + dy * dy) / (4 * mp.pi)
+                tot += term
+                mag += abs(term)
+            assert abs(got[t] - tot) <= 1e-15 * mag, (t, float(got[t] - tot), float(mag))
+
+
+def test_weights_scale_with_the_area(cfg1, tables):
+    """Scaling the geometry by lambda = 2 (exact in binary) with eps scaled by
+    lambda^2 keeps every tree and list (R of Eq. rho0 and the ellipse shapes
+    are unchanged) and adds the constant log(lambda)/2pi to the kernel; since
+    the projection reproduces constants (|J_T| int phi_k = W_k), the near
+    integral and the far-rule subtraction gain the same lambda^2 W_k log
+    lambda / 2pi, so C(lambda x) = lambda^2 C(x).  A normalisation of one side
+    different from the other's, or a projection that loses constants, breaks
+    the cancellation."""
+    mesh, _ = cfg1
+    extra = np.array([[0.11, 0.07], [0.93, 0.2], [-0.4, 0.52], [0.0, -0.999]])
+    res = []
+    for lam in (1.0, 2.0):
+        o = Oracle("far16", tables=tables, eps=1e-12 * lam * lam)
+        s = o.setup(mesh.vxy * lam, mesh.tri, node_targets=False, extra=extra * lam)
+        u, info = o.potential(s, np.ones((1, s["N"])))
+        res.append(info)
+        if lam == 1.0:
+            a_J = s["J"]
+    a, b = res
+    assert np.array_equal(a["row"], b["row"]) and np.array_equal(a["ptri"], b["ptri"])
+    assert np.array_equal(a["stats"], b["stats"])
+    # C is a difference of terms of size ~|J_T| log; per pair, its rounding is
+    # a few 1e-16 |J_T| whatever the size of C itself
+    scale = np.abs(a["C"]).max(axis=1, keepdims=True)
+    Jp = 4.0 * np.abs(a_J)[a["ptri"]][:, None]
+    assert np.abs(b["C"] - 4.0 * a["C"]).max() < 1e-12 * 4.0 * scale.max()
+    assert (np.abs(b["C"] - 4.0 * a["C"]) <= 1e-12 * 4.0 * scale + 1e-15 * Jp).all()
+
+
+def test_laplacian_of_the_potential_is_the_density(tables):
+    """Delta u = f (the potential of the 1/2pi log kernel) by the 5-point
+    stencil at interior points of a 256-triangle disk, f a smooth Gaussian
+    bump: truncation O(h^2) and the potential's own error amplified by
+    1/h^2 both stay far below the 1e-3 bar at h = 2e-3."""
+    from paper_2205_04401_gb300 import inputs
+    mesh, _ = inputs.config1()
+    o = Oracle("far19", tables=tables)
+    h = 2e-3
+    centres = np.array([[0.1, 0.05], [-0.3, 0.2], [0.25, -0.35]])
+    offs = np.array([[0, 0], [h, 0], [-h, 0], [0, h], [0, -h]])
+    pts = (centres[:, None, :] + offs[None, :, :]).reshape(-1, 2)
+    s = o.setup(mesh.vxy, mesh.tri, node_targets=False, extra=pts)
+    fun = lambda p: np.exp(-((p[..., 0] - 0.05) ** 2 + (p[..., 1] + 0.1) ** 2) / 0.3)
+    u, _ = o.potential(s, fun(s["yxy"])[None, :])
+    u = u[0].reshape(len(centres), 5)
+    lap = (u[:, 1] + u[:, 2] + u[:, 3] + u[:, 4] - 4 * u[:, 0]) / (h * h)
+    assert np.abs(lap - fun(centres)).max() < 1e-3 * np.abs(fun(centres)).max()
