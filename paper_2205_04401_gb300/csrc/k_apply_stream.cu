@@ -5,22 +5,23 @@
 //
 // The weights are pair-major (pairs in target order, nq float-float weights
 // per pair), so a run of pairs is a run of bytes.  Work is cut into tiles of
-// AS_TILE pairs (32 by default: 4,864 bytes of weights for nq = 19).  Each warp of a persistent
+// 32 pairs (4,864 bytes of weights for nq = 19).  Each warp of a persistent
 // grid owns a ring of VP_AS_STAGES tiles in shared memory that one lane
 // refills with cp.async.bulk (three copies per tile: weights, triangles,
 // targets, all completing on the stage's mbarrier), so that the warp computes
-// one tile while the next ones stream in.  A tile is processed in two
-// passes over shared memory: entry-parallel (consecutive lanes take
-// consecutive weights, so their density gathers, float-float values of 8
-// bytes from the L2-resident density, are coalesced) forming the float-float
-// products in place, then pair-parallel (lane l sums the nq products of pair
-// p0 + l), followed by a float-float segmented sum over the lanes by target
-// (the pairs of a target are adjacent).  The FP64 pipe, slow on this part,
-// only converts the segment sums.  A target whose whole row lies in the tile is updated directly;
-// the first and last segment of a tile whose rows cross the tile boundary go
-// to two per-tile slots, and a second kernel adds those, in tile order, to
-// the targets whose rows cross tiles.  The order of every sum is fixed, so
-// the result does not depend on timing.
+// one tile while the next ones stream in.  Lane l takes pair p0 + l: its
+// weights from the tile, its triangle's density values from the L2-resident
+// float-float density, padded to fd2_stride(nq) pairs per triangle so that
+// they come in 16-byte loads (half the gather instructions of 8-byte ones),
+// the products split exactly into four float-float partial sums; then a
+// float-float segmented sum over the lanes by target (the pairs of a target
+// are adjacent).  The FP64 pipe, slow on this part, only converts the segment
+// sums.  A target whose whole row lies in the tile (read off the targets of
+// the pairs just before and after the tile) gets its one update as an atomic
+// add; the first and last segment of a tile whose rows cross the tile
+// boundary go to two per-tile slots, and a second kernel adds those, in tile
+// order, to the targets whose rows cross tiles.  The order of every sum is
+// fixed, so the result does not depend on timing.
 #include <algorithm>
 #include <climits>
 
@@ -29,21 +30,17 @@
 #include "vp_f2.cuh"
 
 #ifndef VP_AS_WARPS
-#define VP_AS_WARPS 18
+#define VP_AS_WARPS 22
 #endif
 #ifndef VP_AS_STAGES
 #define VP_AS_STAGES 2
-#endif
-#ifndef VP_AS_TILE
-#define VP_AS_TILE 32
 #endif
 
 namespace {
 
 constexpr int AS_WARPS = VP_AS_WARPS;
 constexpr int AS_STAGES = VP_AS_STAGES;
-constexpr int AS_TILE = VP_AS_TILE;   // pairs per tile: 32 (one per lane) or 16 (two lanes per pair)
-static_assert(AS_TILE == 32 || AS_TILE == 16, "tile of 16 or 32 pairs");
+constexpr int AS_TILE = 32;   // pairs per tile, one per lane
 
 template <int NQ>
 struct __align__(16) AsStage {
@@ -59,7 +56,7 @@ constexpr size_t as_smem_bytes() {
 
 template <int NQ>
 __global__ void __launch_bounds__(AS_WARPS * 32, 1)
-    k_apply_stream(const int64_t* __restrict__ row, const int32_t* __restrict__ ptri, const int32_t* __restrict__ ptgt,
+    k_apply_stream(const int32_t* __restrict__ ptri, const int32_t* __restrict__ ptgt,
                    const float2* __restrict__ C2, const float2* __restrict__ fd2, int64_t P, double* __restrict__ u,
                    double* __restrict__ slots, int32_t* flag) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -101,48 +98,40 @@ __global__ void __launch_bounds__(AS_WARPS * 32, 1)
         }
         const int64_t p0 = tile * AS_TILE;
         const int n = (int)min((int64_t)AS_TILE, P - p0);
-        // pair-parallel: with 32-pair tiles lane l takes pair p0 + l (with
-        // 16-pair tiles the two half-warps take the first and the second half
-        // of its nodes).  Its weights come from the tile in shared memory,
-        // its density values straight from the L2-resident float-float
-        // density (the nq values of one triangle are contiguous, so a lane's
-        // successive gathers fall in the same few sectors); each product is
-        // split exactly and added into one of four float-float partial sums
-        // (hi by two-sum, lo collecting the errors) in a fixed order.
-        const int pl = lane & (AS_TILE - 1);
+        // pair-parallel: lane l takes pair p0 + l.  Its weights come from the
+        // tile in shared memory, its density values straight from the
+        // L2-resident float-float density (one triangle's values contiguous);
+        // each product is split exactly and added into one of four
+        // float-float partial sums (hi by two-sum, lo collecting the errors)
+        // in a fixed order.
+        const int pl = lane;
         int t = INT_MAX;   // padding lanes form their own segment
-        int64_t r0 = 0, r1 = 0;
-        double u0 = 0.0;
+        // the targets of the pairs just before and just after the tile (-1
+        // past either end): whether a row crosses the tile's edges
+        int nb = -1;
+        if (lane == 0 && p0 > 0) nb = __ldg(ptgt + p0 - 1);
+        if (lane == 1 && p0 + n < P) nb = __ldg(ptgt + p0 + n);
         f2 ps = {0.f, 0.f};
         if (pl < n) {
             t = st[s].tgt[pl];
-            constexpr int HQ = AS_TILE == 32 ? NQ : (NQ + 1) / 2;
-            const int q0 = AS_TILE == 32 ? 0 : (lane >> 4) * HQ;
-            const float2* fp = fd2 + (int64_t)st[s].tri[pl] * NQ + q0;
-            float2 fv[HQ];
+            // the triangle's values, fd2_stride(NQ) pairs from a 16-byte boundary: 16-byte loads
+            const float4* fp = reinterpret_cast<const float4*>(fd2 + (int64_t)st[s].tri[pl] * fd2_stride(NQ));
+            float2 fv[NQ + 1];
 #pragma unroll
-            for (int q = 0; q < HQ; q++) fv[q] = (q0 + q < NQ) ? __ldg(fp + q) : make_float2(0.f, 0.f);
-            if (lane == pl) {
-                r0 = row[t];
-                r1 = row[t + 1];
-                u0 = u[t];
+            for (int q = 0; q < (NQ + 1) / 2; q++) {
+                const float4 v4 = __ldg(fp + q);
+                fv[2 * q] = make_float2(v4.x, v4.y);
+                fv[2 * q + 1] = make_float2(v4.z, v4.w);
             }
-            const float2* c = st[s].C + pl * NQ + q0;
+            const float2* c = st[s].C + pl * NQ;
             float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int q = 0; q < HQ; q++) {
-                if (q0 + q < NQ) {
-                    const float2 cv = c[q];
-                    f2_acc(ah[q & 3], al[q & 3], f2{cv.x, cv.y}, f2{fv[q].x, fv[q].y});
-                }
+            for (int q = 0; q < NQ; q++) {
+                const float2 cv = c[q];
+                f2_acc(ah[q & 3], al[q & 3], f2{cv.x, cv.y}, f2{fv[q].x, fv[q].y});
             }
             ps = f2_add(f2_add(f2_fast(ah[0], al[0]), f2_fast(ah[1], al[1])),
                         f2_add(f2_fast(ah[2], al[2]), f2_fast(ah[3], al[3])));
-        }
-        if (AS_TILE == 16) {
-            // both halves: (first half) + (second half), the same on both
-            const float oh = __shfl_xor_sync(0xffffffffu, ps.h, 16), ol = __shfl_xor_sync(0xffffffffu, ps.l, 16);
-            ps = lane < 16 ? f2_add(ps, {oh, ol}) : f2_add({oh, ol}, ps);
         }
         // segmented inclusive sum over the pairs (targets are non-decreasing)
 #pragma unroll
@@ -154,10 +143,12 @@ __global__ void __launch_bounds__(AS_WARPS * 32, 1)
         }
         const int t_next = __shfl_down_sync(0xffffffffu, t, 1, AS_TILE);
         const int t_lane0 = __shfl_sync(0xffffffffu, t, 0);
+        const int t_before = __shfl_sync(0xffffffffu, nb, 0), t_after = __shfl_sync(0xffffffffu, nb, 1);
         if (lane == pl && lane < n && (lane == n - 1 || t_next != t)) {   // the last pair of a segment
             const double sum = (double)ps.h + (double)ps.l;
-            if (r0 >= p0 && r1 <= p0 + AS_TILE) {
-                u[t] = u0 + sum;                              // the whole row is in this tile
+            const bool starts_here = !(t == t_lane0 && t_before == t), ends_here = !(lane == n - 1 && t_after == t);
+            if (starts_here && ends_here) {
+                atomicAdd(u + t, sum);                        // the whole row is in this tile: its only update
             } else {
                 if (t == t_lane0) slots[2 * tile] = sum;      // segment at the start of the tile
                 if (lane == n - 1) slots[2 * tile + 1] = sum; // segment at the end of the tile
@@ -212,14 +203,29 @@ void apply_stream(const int64_t* row, const int32_t* ptri, const int32_t* ptgt, 
     const int64_t ntiles = (P + AS_TILE - 1) / AS_TILE;
     // one CTA per SM (persistent), fewer when there are fewer tiles than warps
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(sm_count, (ntiles + AS_WARPS - 1) / AS_WARPS));
-    k_apply_stream<NQ><<<grid, AS_WARPS * 32, smem, s>>>(row, ptri, ptgt, C2, fd2, P, u, slots, flag);
+    k_apply_stream<NQ><<<grid, AS_WARPS * 32, smem, s>>>(ptri, ptgt, C2, fd2, P, u, slots, flag);
     k_apply_stream_fix<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(row, M, slots, u);
 }
 
 }  // namespace
 
+// the padded float-float density: at most N (nq + 1) / nq <= N 17/16 pairs
+// for nq >= 16
+static size_t fd2_region_bytes(int64_t N) {
+    return ((size_t)(N + N / 16 + 2) * sizeof(float2) + 255) & ~(size_t)255;
+}
+
 size_t apply_stream_ws_bytes(int64_t N, int64_t P) {
-    return (((size_t)N * sizeof(float2) + 255) & ~(size_t)255) + (size_t)((P + AS_TILE - 1) / AS_TILE) * 2 * sizeof(double);
+    return fd2_region_bytes(N) + (size_t)((P + AS_TILE - 1) / AS_TILE) * 2 * sizeof(double);
+}
+
+// f (node values, FP64) -> the padded triangle-major float-float density
+__global__ void k_to_fd2(const double* __restrict__ f, int64_t N, int nq, float2* __restrict__ fd2) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const double v = f[j];
+    const float h = __double2float_rn(v);
+    fd2[(j / nq) * fd2_stride(nq) + j % nq] = make_float2(h, __double2float_rn(v - (double)h));
 }
 
 void launch_apply_stream(const int64_t* row, const int32_t* ptri, const int32_t* ptgt, const float2* C2, int nq,
@@ -228,8 +234,8 @@ void launch_apply_stream(const int64_t* row, const int32_t* ptri, const int32_t*
     if (P <= 0 || M <= 0) return;
     // the density as float-float pairs, then the slots
     float2* fd2 = (float2*)ws;
-    double* slots = (double*)((char*)ws + (((size_t)N * sizeof(float2) + 255) & ~(size_t)255));
-    if (!f2_ready) launch_to_f2(f, N, fd2, s);
+    double* slots = (double*)((char*)ws + fd2_region_bytes(N));
+    if (!f2_ready) k_to_fd2<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(f, N, nq, fd2);
     if (nq == 19) apply_stream<19>(row, ptri, ptgt, C2, fd2, P, M, u, slots, flag, sm_count, s);
     else apply_stream<16>(row, ptri, ptgt, C2, fd2, P, M, u, slots, flag, sm_count, s);
 }

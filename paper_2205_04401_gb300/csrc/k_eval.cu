@@ -382,7 +382,7 @@ void launch_far_fp64(const double* y, const double* W, int64_t N, const double* 
 
 void launch_far_ff(const FFCoords& src, const double* W, int64_t N, const double* f, int d, const FFCoords& tgt,
                    const int32_t* tnode, int64_t M, double* partial, float* qbuf, int splits, cudaStream_t s,
-                   float2* f2out) {
+                   float2* f2out, int nq) {
     ensure_logtab();
     dim3 grid((unsigned)((M + FF_THREADS * FF_TPT - 1) / (FF_THREADS * FF_TPT)), (unsigned)splits);
     const unsigned pb = (unsigned)((N + 255) / 256);
@@ -402,7 +402,7 @@ void launch_far_ff(const FFCoords& src, const double* W, int64_t N, const double
                 k_far_ff<2><<<grid, FF_THREADS, 0, s>>>(src.hi, src.lo, qbuf, N, tgt.hi, tgt.lo, tnode, M, d, d0, partial, splits);
                 break;
             default:
-                k_prep_q_ff<1><<<pb, 256, 0, s>>>(W, f, N, d, d0, qbuf, d == 1 ? f2out : nullptr);
+                k_prep_q_ff<1><<<pb, 256, 0, s>>>(W, f, N, d, d0, qbuf, d == 1 ? f2out : nullptr, nq);
                 k_far_ff<1><<<grid, FF_THREADS, 0, s>>>(src.hi, src.lo, qbuf, N, tgt.hi, tgt.lo, tnode, M, d, d0, partial, splits);
                 break;
         }

@@ -374,7 +374,7 @@ void launch_far_sym(const vp_ctx* ctx, const vp_nf* nf, const double* W, const d
     double* xpart = (double*)w;
     const float* shi = nf->src_ff.hi;
     const float* slo = nf->src_ff.lo;
-    k_prep_q_ff<1><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(W, f, N, 1, 0, q, f2out);
+    k_prep_q_ff<1><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(W, f, N, 1, 0, q, f2out, nf->mesh->nq);
     for (size_t b = 0; b < p->bands.size(); b++) {
         const SymBand& bd = p->bands[b];
         if (bd.u1 > bd.u0)

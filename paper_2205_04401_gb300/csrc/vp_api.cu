@@ -960,7 +960,7 @@ int eval_impl(vp_ctx* ctx, const vp_nf* nf, const double* f_dev, int32_t d, doub
     else
         PROF(ctx, ST_FAR_FF, s,
              launch_far_ff(nf->src_ff, mesh->d_W, N, f_dev, d, nf->tgt_ff, nf->d_tnode, M, partial, qbuf, splits, s,
-                           f2out));
+                           f2out, mesh->nq));
     if (splits > 1) PROF(ctx, ST_REDUCE, s, launch_reduce_splits(partial, splits, (int64_t)d * M, u_dev, s));
     if (precision == VP_MIXED_TC) {
         int rc = VP_OK;

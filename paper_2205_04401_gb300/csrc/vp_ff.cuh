@@ -311,16 +311,17 @@ __device__ __forceinline__ void ff_far_block(FFSmem<D>& sm, const float* __restr
 
 // q_j = W_j f_j as two floats per density: layout [N][2*D] (hi..., lo...);
 // with f2out (one density) also f_j itself as a float-float pair, the form
-// the streamed correction apply gathers.
+// the streamed correction apply gathers (triangle-major, fd2_stride(nq) pairs
+// per triangle).
 template <int D>
 __global__ void k_prep_q_ff(const double* __restrict__ W, const double* __restrict__ f, int64_t N, int d, int d0,
-                            float* __restrict__ q, float2* __restrict__ f2out = nullptr) {
+                            float* __restrict__ q, float2* __restrict__ f2out = nullptr, int nq = 1) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     if (D == 1 && f2out) {
         const double v = f[(int64_t)d0 * N + j];
         const float h = __double2float_rn(v);
-        f2out[j] = make_float2(h, __double2float_rn(v - (double)h));
+        f2out[(j / nq) * fd2_stride(nq) + j % nq] = make_float2(h, __double2float_rn(v - (double)h));
     }
 #pragma unroll
     for (int k = 0; k < D; k++) {

@@ -306,7 +306,7 @@ void launch_far_fp64(const double* y, const double* W, int64_t N, const double* 
 // pairs for the streamed correction apply (fused into the charge preparation)
 void launch_far_ff(const FFCoords& src, const double* W, int64_t N, const double* f, int d, const FFCoords& tgt,
                    const int32_t* tnode, int64_t M, double* partial, float* qbuf, int splits, cudaStream_t s,
-                   float2* f2out = nullptr);
+                   float2* f2out = nullptr, int nq = 1);
 void launch_reduce_splits(const double* partial, int splits, int64_t count, double* out, cudaStream_t s);
 // Densities from which the correction is applied with densities across lanes
 // (needs a node-major copy of f: apply_ws_bytes); fewer, or fT == nullptr,
@@ -345,6 +345,10 @@ void launch_apply_f2(const int64_t* row, const int32_t* ptri, const float2* C2, 
 // streamed float-float apply of one density (k_apply_stream.cu), workspace of
 // apply_stream_ws_bytes(N, P); ptri, ptgt and C2 carry 16 bytes of padding
 size_t apply_stream_ws_bytes(int64_t N, int64_t P);
+// The float-float density the streamed apply gathers is triangle-major with
+// fd2_stride(nq) pairs per triangle (a multiple of 16 bytes, so that a lane
+// reads a triangle's values with 16-byte loads); the padding entry is unused.
+constexpr int fd2_stride(int nq) { return (nq + 1) & ~1; }
 // f2_ready: the workspace already holds the float-float density (written by
 // the far sum's charge preparation), else it is converted first
 void launch_apply_stream(const int64_t* row, const int32_t* ptri, const int32_t* ptgt, const float2* C2, int nq,
