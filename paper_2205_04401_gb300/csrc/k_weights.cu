@@ -466,7 +466,7 @@ __device__ __forceinline__ void near_leaf_node(const LeafF2& lf, float4 E, float
     f2 lg;
     if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);              // log |y - x|^2
     else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));        // far below any mesh scale
-    const f2 g = f2_mul(lg, f2_mul({W.x, W.y}, {lf.wjh, lf.wjl}));
+    const f2 g = f2_mul_u(lg, f2_mul_u({W.x, W.y}, {lf.wjh, lf.wjl}));   // only multiplied and added on
     const f2 u = f2_add({lf.u0h, lf.u0l}, {__fmul_rn(Z.x, sh), __fmul_rn(Z.y, sh)});   // Z = 3 z_j
     const f2 v = f2_add({lf.v0h, lf.v0l}, {__fmul_rn(Z.z, sh), __fmul_rn(Z.w, sh)});
     f2_mon15_acc_uv(mh, ml, g, u, v);
@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(WARPS * 32, VP_ROOT_MINB) k_weights_near_root(
             if (r2.h > 1e-30f) ff_log(ftab, r2.h, r2.l, lg.h, lg.l);
             else lg = f2_from_d(vp_logd(f2_to_d(r2), lt.rc, lt.lc, ln2));
             const float2 W = nw_s[j];
-            const f2 gj = f2_mul(lg, f2_mul({W.x, W.y}, g.wj));
+            const f2 gj = f2_mul_u(lg, f2_mul_u({W.x, W.y}, g.wj));   // a factor of the products below
             g_all[wl][q][j] = make_float2(gj.h, gj.l);
         }
         __syncwarp();
@@ -926,8 +926,9 @@ __global__ void __launch_bounds__(WARPS * 32, VP_SELF_MINB) k_weights_self_f2(We
 #pragma unroll 1
         for (int q = 0; q < VP_NRAD; q++) {   // not unrolled: the body stays in the instruction cache
             const float2 R = a.tab->rr2[q], A = a.tab->ra2[q], B = a.tab->rb2[q];
-            const f2 g = f2_mul(ws, f2_add(f2_mul(lr0, {A.x, A.y}), {B.x, B.y}));
-            f2_mon15_acc_uv(mh, ml, g, f2_add(f2_mul({R.x, R.y}, al), u0), f2_add(f2_mul({R.x, R.y}, be), v0));
+            // products that are only added or multiplied on stay unnormalised
+            const f2 g = f2_mul_u(ws, f2_add(f2_mul_u(lr0, {A.x, A.y}), {B.x, B.y}));
+            f2_mon15_acc_uv(mh, ml, g, f2_add(f2_mul_u({R.x, R.y}, al), u0), f2_add(f2_mul_u({R.x, R.y}, be), v0));
         }
     }
     finish_pair_f2(a, b, p, T, t, own, mh, ml, lane, ftab, lt, ln2);
