@@ -82,8 +82,9 @@ constexpr float LN2_L18 = 1.4286068202862268e-06f;
 //     2^-19 = 7e-12 (1e-12 for |E| <= 8, r^2 above 2^-8);
 //   * log(1 + w) - w = -w^2/2 + w^3/3 (the dropped w^4/4 < 2^-42), and wl
 //     without its w wl part (< 2^-44);
-//   * corr / s with an approximate reciprocal (relative 2^-22 of 2^-23).
-// The result is renormalised (|lo| <= 2^-24 |hi|) for the products that follow.
+//   * corr / s with an approximate reciprocal (relative 2^-22 of 2^-23);
+//   * the result not renormalised (|lo| up to 2^-17 |hi|): the float-float
+//     products that follow keep 41 bits, 5e-13 of each term.
 // The accurate ff_log (error ~1e-13) stays with the correction weights.
 __device__ __forceinline__ void ff_log_far(const float4* __restrict__ tab, float s, float corr, float& hi,
                                            float& lo) {
@@ -108,12 +109,12 @@ __device__ __forceinline__ void ff_log_far(const float4* __restrict__ tab, float
     tail = __fadd_rn(tail, __fmaf_rn(fe, LN2_L18, t.z));
     tail = __fadd_rn(tail, p);
     tail = __fadd_rn(tail, __fadd_rn(e1, e2));
-    // renormalise: |tail| reaches 2^-17 |b| (the E LN2_L18 term), which would
-    // cost the far sum's float-float products and sums six bits; fast two-sum,
-    // exact unless |b| < |tail| (then both are below 1e-4 and the error is
-    // below 2^-24 1e-4)
-    hi = __fadd_rn(b, tail);
-    lo = __fsub_rn(tail, __fsub_rn(hi, b));
+    // left unnormalised: |tail| reaches 2^-17 |b| (the E LN2_L18 term), so
+    // the products that follow keep about 41 bits instead of 47 (q ll is
+    // rounded to 2^-24 of itself: 2^-41 of q log r^2, or 2^-24 1e-4 |q|
+    // where |b| < |tail| < 1e-4), within the per-pair budget
+    hi = b;
+    lo = tail;
 }
 
 // |x_t - y_s|^2 for the far sum: (a + al)^2 + (b + bl)^2 with a, b the exact

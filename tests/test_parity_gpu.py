@@ -206,9 +206,11 @@ def test_forty_densities_on_the_star_mesh(vp, ctx, tables, star):
         for k in (0, 17, 39):
             # alone, a mixed density takes the symmetric far sum, which groups
             # the float-float partial sums differently: rounding differences
-            # of order 2^-48 sum|q log r^2| / max|u|, far below the 1e-10 bar
+            # of order 2^-41 sum|q log r^2| / max|u| (the far logarithm's
+            # unnormalised tail leaves its products 41 bits), far below the
+            # 1e-10 bar
             alone = vp.potential_eval(ctx, g["nf"], fd[k:k + 1].contiguous(), precision=prec).cpu().numpy()
-            assert rel_err(u[k:k + 1], alone).max() <= (1e-13 if prec == 0 else 1e-12)
+            assert rel_err(u[k:k + 1], alone).max() <= (1e-13 if prec == 0 else 1e-11)
 
 
 @pytest.mark.parametrize("which", ["star", "lshape"])
