@@ -114,7 +114,12 @@ __global__ void __launch_bounds__(SYM_THREADS) k_far_sym(const float* __restrict
                         ff_dist2_far<false>(thx[r], thy[r], tlx[r], tly[r], sv, s, corr);   // distinct nodes
                         ff_log_far(sm.stab, s, corr, lh, ll);     // log |x_i - y_j|^2
                         ff_madd(qj.x, qj.y, lh, ll, sh[r], sl[r]);
-                        ff_madd(qh[r], ql[r], lh, ll, ch, cl);
+                        if (r == 0) {                              // the column sum starts at this product
+                            ch = __fmul_rn(qh[0], lh);
+                            cl = __fmaf_rn(qh[0], ll, __fmaf_rn(ql[0], lh, __fmaf_rn(qh[0], lh, -ch)));
+                        } else {
+                            ff_madd(qh[r], ql[r], lh, ll, ch, cl);
+                        }
                     }
                     const float2 c = col[jl];
                     float cs, ce;
