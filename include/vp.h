@@ -95,7 +95,9 @@ VP_API int vp_far_rule(int32_t rule, double* x, double* y, double* w, double* wh
 
 /* Arithmetic of vp_potential_eval.  VP_FP64: FP64 everywhere.  VP_MIXED: the
  * far sum in compensated FP32 (float-float coordinates and logarithm, FP64
- * per-tile reduction); correction weights and their application stay FP64.
+ * per-tile reduction); the stored correction weights applied with
+ * float-float products and FP64 sums (1 to 15 densities) or in FP64 (16 or
+ * more).
  * VP_MIXED_TC: the far sum of VP_MIXED; the corrections applied on the tensor
  * cores from an exact split of C and f into L balanced base-128 digits held
  * as bf16 (vp_nf_prepare_tc), accumulated exactly in FP32 and combined in
@@ -133,8 +135,11 @@ VP_API int vp_nf_params_default(vp_nf_params* out);
 /* vp_nf_params.flags: evaluate the node quadratures of the correction
  * weights in FP64.  By default they run in float-float arithmetic (pairs of
  * FP32 values with error-free transformations, ~2^-48 per operation), which
- * GB300 executes some 20x faster than FP64; the subdivision tree and every
- * geometric predicate are FP64 (bit-exact) either way. */
+ * GB300 executes some 20x faster than FP64, and the self interaction's
+ * radial sums take a 5-point rule that, like the 8-point generalized
+ * Gaussian rule of the FP64 path (Section 3.4), is exact for the P_4
+ * moments; the subdivision tree and every geometric predicate are FP64
+ * (bit-exact) either way. */
 #define VP_NF_FP64_WEIGHTS 1
 
 /* Counters of Section 5 (c, s_n, s_l) and sizes of a near-field build. */
