@@ -328,3 +328,32 @@ def test_depth_cap_trees_match_oracle(vp, ctx, tables, cfg1, cap):
     assert st["near_leaves"] == int(info["stats"][info["pkind"] == 0].sum())
     compare_weights(C, info["C"], s["J"], info["ptri"])
     assert rel_err(u, u_or).max() <= 1e-12
+
+
+@pytest.mark.parametrize("rule", [16, 19])
+def test_streamed_apply_rows_across_many_tiles(vp, ctx, tables, rule):
+    """The streamed apply of one density (mixed path) cuts the pairs into
+    tiles of 32; a target whose row spans several tiles takes the per-tile
+    slots and the fix-up kernel, a row inside one tile a single update.  At
+    eps = 1e-14 the targets inside the disk have rows of 100-250 pairs, the
+    ones outside rows of 0-50 (one has none): against the oracle with the
+    same eps (mixed bar) and against the GPU FP64 path (FP64 bar)."""
+    mesh, _ = inputs.config1()
+    extra = np.array([[0.013, 0.021], [1.08, 0.02], [-0.41, 0.33], [1.6, 0.0], [3.0, 0.1], [0.0, -1.15],
+                      [0.2, -0.6]])
+    o = Oracle("far16" if rule == 16 else "far19", tables=tables, eps=1e-14)
+    s = o.setup(mesh.vxy, mesh.tri, node_targets=False, extra=extra)
+    f = np.stack([np.exp(-((s["yxy"][:, 0] - 0.1) ** 2 + s["yxy"][:, 1] ** 2) / 0.2)])
+    u_or, info = o.potential(s, f)
+    rows = np.diff(info["row"])
+    assert rows.max() > 96 and rows.min() == 0
+    m = vp.mesh_upload(ctx, mesh.vxy, mesh.tri, rule)
+    nf = vp.nearfield_build(ctx, m, node_targets=False, txy=torch.from_numpy(extra).cuda(), eps=1e-14)
+    fd = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+    u1 = vp.potential_eval(ctx, nf, fd, precision=1).cpu().numpy()
+    u0 = vp.potential_eval(ctx, nf, fd, precision=0).cpu().numpy()
+    assert rel_err(u0, u_or).max() <= 1e-12
+    assert rel_err(u1, u_or).max() <= 1e-10
+    assert rel_err(u1, u0).max() <= 1e-12
+    nf.release()
+    m.release()
