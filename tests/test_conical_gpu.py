@@ -166,14 +166,21 @@ def test_high_order_node_targets(tiny_nodes):
     assert rel_err(one["u1"], u_or[1:]).max() <= 1e-10
 
 
-def test_conical_refused_where_unsupported(vp, ctx):
+@pytest.mark.parametrize("family", ["conical", "sym"])
+def test_higher_order_rules_refused_where_unsupported(vp, ctx, family):
+    """The tensor-core apply takes the built-in rules only; rule codes outside
+    the tabulated or generated ranges are refused at upload."""
     mesh = inputs.disk_mesh(n_b=10, n_i=5)
-    m = vp.mesh_upload(ctx, mesh.vxy, mesh.tri, vp.VP_RULE_CONICAL(12))
+    code = vp.VP_RULE_CONICAL(12) if family == "conical" else vp.VP_RULE_SYM(12)
+    m = vp.mesh_upload(ctx, mesh.vxy, mesh.tri, code)
     nf = vp.nearfield_build(ctx, m)
     with pytest.raises(vp.VPError):
         vp.nf_prepare_tc(nf)
+    bad = vp.VP_RULE_CONICAL(51) if family == "conical" else vp.VP_RULE_SYM(13)
     with pytest.raises(vp.VPError):
-        vp.mesh_upload(ctx, mesh.vxy, mesh.tri, vp.VP_RULE_CONICAL(51))
+        vp.mesh_upload(ctx, mesh.vxy, mesh.tri, bad)
+    nf.release()
+    m.release()
 
 
 @pytest.mark.parametrize("prec", [1, 3])
