@@ -531,7 +531,9 @@ VP_API void vp_interp_release(vp_interp* interp);
 
 /* The compiled quadrature tables, for inspection (host buffers of capacity
  * cap; *n receives the node count).  which: 16 / 19 (far rules), 33 (near
- * rule: the S3-symmetric rule of degree 12), 8 (radial generalized Gaussian rule: x = r, y unused), 116 (the
+ * rule: the S3-symmetric rule of degree 12), 8 (radial generalized Gaussian rule: x = r, y unused), 5 (the
+ * radial rule of the float-float self weights: x = r, w = weights of int_0^1 r p(r) dr, y = weights of
+ * int_0^1 r log(r) p(r) dr, both exact for deg p <= 4), 116 (the
  * arc-length Gauss-Legendre rule on [0,1]).  *what receives w of Eq. rho0
  * (0 for the 1-D rules). */
 VP_API int vp_rule_table(int32_t which, double* x, double* y, double* w, double* what, int32_t cap, int32_t* n);

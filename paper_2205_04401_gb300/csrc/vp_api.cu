@@ -1450,6 +1450,7 @@ int vp_rule_table(int32_t which, double* x, double* y, double* w, double* what, 
         case 19: X = VP_FAR19_X; Y = VP_FAR19_Y; Wt = VP_FAR19_W; wh = VP_FAR19_WHAT; len = 19; break;
         case 33: X = VP_NEAR33_X; Y = VP_NEAR33_Y; Wt = VP_NEAR33_W; wh = VP_NEAR33_WHAT; len = 33; break;
         case 8: X = VP_GGQ8_R; Wt = VP_GGQ8_W; len = 8; break;
+        case 5: X = VP_RAD5_R; Y = VP_RAD5_B; Wt = VP_RAD5_A; len = 5; break;
         case 116: X = VP_GL16_X; Wt = VP_GL16_W; len = 16; break;
         default: return VP_ERR_INVALID_ARG;
     }

@@ -736,7 +736,8 @@ def far_rule(rule: int):
 
 
 def rule_table(which: int):
-    """(x, y, w, what) of a compiled rule: 16, 19 (far), 49 (near), 8 (radial), 116 (arc-length)."""
+    """(x, y, w, what) of a compiled rule: 16, 19 (far), 33 (near), 8 (radial GGQ), 5 (radial rule of the
+    float-float self weights: w for int r p, y for int r log(r) p), 116 (arc-length)."""
     lib = load()
     cap = 64
     x, y, w = (np.zeros(cap) for _ in range(3))

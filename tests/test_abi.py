@@ -52,6 +52,27 @@ def test_tables_match_oracle_bitwise(tables, which, name):
     assert what == r["what"]
 
 
+def test_radial_rule_of_the_self_weights():
+    """The library's 5-point radial rule (float-float self weights) on the
+    Gauss-Legendre nodes of [0, 1]: sum_i w_i r_i^k = int_0^1 r r^k dr =
+    1/(k+2) and sum_i y_i r_i^k = int_0^1 r r^k log r dr = -1/(k+2)^2 for
+    k <= 4, the radial integrands of the P_4 moments (Section 3.4), checked
+    in exact rational arithmetic on the stored doubles; the log weights are
+    not exact at k = 5 (five nodes fix five moments)."""
+    from fractions import Fraction
+    from paper_2205_04401_gb300 import vp
+    r, y, w, _ = vp.rule_table(5)
+    assert len(r) == 5 and np.all((r > 0) & (r < 1)) and np.all(np.diff(r) > 0)
+    R, Wa, Wb = ([Fraction(v) for v in a] for a in (r, w, y))
+    for k in range(5):
+        sa = sum(a * x ** k for a, x in zip(Wa, R))
+        sb = sum(b * x ** k for b, x in zip(Wb, R))
+        assert abs(float(sa - Fraction(1, k + 2))) < 4e-16
+        assert abs(float(sb + Fraction(1, (k + 2) ** 2))) < 4e-16
+    sb5 = sum(b * x ** 5 for b, x in zip(Wb, R))
+    assert abs(float(sb5 + Fraction(1, 49))) > 1e-10
+
+
 def test_1d_tables_match_oracle_bitwise(tables):
     from paper_2205_04401_gb300 import vp
     x, _, w, _ = vp.rule_table(8)
