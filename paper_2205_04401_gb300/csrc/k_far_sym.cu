@@ -80,9 +80,12 @@ __global__ void __launch_bounds__(SYM_THREADS) k_far_sym(const float* __restrict
         qh[r] = active[r] ? q[2 * t] : 0.f;             // inactive targets carry no charge
         ql[r] = active[r] ? q[2 * t + 1] : 0.f;
     }
-    double acc[SYM_TPT];
+    // row sums in float-float across the unit, renormalised after every
+    // source tile (the FP64 pipe, 1/64 of the FP32 rate here, only converts
+    // the unit's result)
+    float sh[SYM_TPT], sl[SYM_TPT];
 #pragma unroll
-    for (int r = 0; r < SYM_TPT; r++) acc[r] = 0.0;
+    for (int r = 0; r < SYM_TPT; r++) sh[r] = sl[r] = 0.f;
     for (int64_t base = j0; base < j1; base += SYM_TJ) {
         const int nt = (int)min((int64_t)SYM_TJ, j1 - base);
         __syncthreads();
@@ -96,9 +99,6 @@ __global__ void __launch_bounds__(SYM_THREADS) k_far_sym(const float* __restrict
             for (int ww = 0; ww < SYM_THREADS / 32; ww++) sm.col[ww][i] = make_float2(0.f, 0.f);
         }
         __syncthreads();
-        float sh[SYM_TPT], sl[SYM_TPT];
-#pragma unroll
-        for (int r = 0; r < SYM_TPT; r++) sh[r] = sl[r] = 0.f;
         float2* col = sm.col[w];
         for (int sb = 0; sb < nt; sb += 32) {
 #pragma unroll 2
@@ -129,19 +129,30 @@ __global__ void __launch_bounds__(SYM_THREADS) k_far_sym(const float* __restrict
             }
         }
 #pragma unroll
-        for (int r = 0; r < SYM_TPT; r++) acc[r] += (double)sh[r] + (double)sl[r];
+        for (int r = 0; r < SYM_TPT; r++) {                        // |sl| back to half an ulp of sh
+            float h, e;
+            two_sum_s(sh[r], sl[r], h, e);
+            sh[r] = h;
+            sl[r] = e;
+        }
         __syncthreads();
-        // column sums of this tile: the four warps' accumulators, fixed order
+        // column sums of this tile: the four warps' accumulators added in
+        // float-float in a fixed order, then one conversion
         for (int i = threadIdx.x; i < nt; i += SYM_THREADS) {
-            double v = 0.0;
+            float2 c = sm.col[0][i];
 #pragma unroll
-            for (int ww = 0; ww < SYM_THREADS / 32; ww++) v += (double)sm.col[ww][i].x + (double)sm.col[ww][i].y;
-            colbuf[coff[I] - cb0 + (base + i - jstart)] = v;
+            for (int ww = 1; ww < SYM_THREADS / 32; ww++) {
+                const float2 d = sm.col[ww][i];
+                float h, e;
+                two_sum_s(c.x, d.x, h, e);
+                c = make_float2(h, __fadd_rn(c.y, __fadd_rn(e, d.y)));
+            }
+            colbuf[coff[I] - cb0 + (base + i - jstart)] = (double)c.x + (double)c.y;
         }
     }
 #pragma unroll
     for (int r = 0; r < SYM_TPT; r++)
-        if (active[r]) rowbuf[(u - u0) * SYM_TI + r * SYM_THREADS + threadIdx.x] = acc[r];
+        if (active[r]) rowbuf[(u - u0) * SYM_TI + r * SYM_THREADS + threadIdx.x] = (double)sh[r] + (double)sl[r];
 }
 
 // Pairs inside each tile, one-sided with the own node excluded: block I.
