@@ -306,9 +306,9 @@ static void band_maxima(const std::vector<SymBand>& bands, int64_t* mu, int64_t*
     }
 }
 
-// Source splits of the extra-target sum: about 16 blocks per SM (two waves at
-// eight resident blocks), so that few targets still fill the GPU and the last
-// wave is short (4 per SM left half the block slots empty).
+// Source splits of the extra-target sum: about 16 blocks per SM (more than two
+// waves of the resident blocks), so that few targets still fill the GPU and
+// the last wave is short (4 per SM left half the block slots empty).
 static int extra_splits(int64_t N, int64_t m, int sm_count) {
     if (m <= 0) return 0;
     const int64_t blocks = (m + SYM_TI - 1) / SYM_TI;
