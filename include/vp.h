@@ -94,8 +94,9 @@ VP_API int vp_far_rule(int32_t rule, double* x, double* y, double* w, double* wh
                        int32_t* n);
 
 /* Arithmetic of vp_potential_eval.  VP_FP64: FP64 everywhere.  VP_MIXED: the
- * far sum in compensated FP32 (float-float coordinates and logarithm, FP64
- * per-tile reduction); the stored correction weights applied with
+ * far sum in compensated FP32 (float-float coordinates and logarithm;
+ * float-float partial sums over at most 2,048 sources, reduced in FP64); the
+ * stored correction weights applied with
  * float-float products and FP64 sums (1 to 15 densities on the built-in far
  * rules) or in FP64 (16 or more densities, or a higher-order far rule).
  * VP_MIXED_TC: the far sum of VP_MIXED; the corrections applied on the tensor
