@@ -22,8 +22,10 @@
 // 32 rotation steps (lane l takes source (l + k) mod 32 at step k), so each
 // source's column sum is updated by one lane at a time in the warp's own
 // shared-memory accumulator; the four warps' accumulators are added at the
-// end of every 128-source tile.  The distance, logarithm and accumulation
-// arithmetic is that of the one-sided kernel (vp_ff.cuh).
+// end of every 128-source tile in float-float.  The distance, logarithm and
+// per-pair accumulation arithmetic is that of the one-sided kernel
+// (vp_ff.cuh); a row sum stays float-float over its unit's 2,048 sources and
+// is converted to FP64 once.
 #include <algorithm>
 #include <vector>
 
